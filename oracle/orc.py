@@ -1,0 +1,209 @@
+"""ctypes wrapper of the FP64 oracle (``orc.c``).  TEST INFRASTRUCTURE ONLY.
+
+Every function takes numpy arrays: complex arrays are converted to complex128 (exact
+for complex64 inputs), measured intensities stay float32 as the method receives them.
+The oracle is a plain CPU restatement of the paper's Eq. 1-3, 5-7 and Algorithm 1; see
+the header of ``orc.c`` for the readings it takes where the paper is silent.
+"""
+from __future__ import annotations
+
+import ctypes
+import hashlib
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+ORC_OK, ORC_ERR_ARG, ORC_ERR_BOUNDS, ORC_ERR_NOMEM, ORC_STALLED = 0, 1, 2, 3, 4
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "orc.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_lib = None
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [
+        ("gamma0", ctypes.c_double),
+        ("tau", ctypes.c_double),
+        ("t", ctypes.c_double),
+        ("max_halvings", ctypes.c_int),
+        ("eps", ctypes.c_double),
+    ]
+
+
+@dataclass
+class OrcOpts:
+    """Line-search and objective options; defaults follow Algorithm 1 (gamma0=1, tau=0.5, t=0)."""
+
+    gamma0: float = 1.0
+    tau: float = 0.5
+    t: float = 0.0
+    max_halvings: int = 60
+    eps: float = 1e-6
+
+
+def build(force: bool = False) -> str:
+    """Compile orc.c into _lib/liborc-<hash>.so with gcc (-O2, OpenMP); return its path."""
+    src = open(_SRC, "rb").read()
+    tag = hashlib.sha1(src).hexdigest()[:12]
+    os.makedirs(_LIBDIR, exist_ok=True)
+    out = os.path.join(_LIBDIR, f"liborc-{tag}.so")
+    if force or not os.path.exists(out):
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+    return out
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i = ctypes.c_int
+        d = ctypes.c_double
+        lib.orc_fft2.argtypes = [P, i, i]
+        lib.orc_Q.argtypes = [i, i, i, P, i, P, P, P]
+        lib.orc_QH.argtypes = [i, i, i, P, i, P, P, P]
+        lib.orc_forward.argtypes = [i, i, i, P, i, P, P, P, i]
+        lib.orc_adjoint.argtypes = [i, i, i, P, i, P, P, P, i]
+        lib.orc_objective.argtypes = [i, i, i, P, i, P, P, d, P, P, i]
+        lib.orc_gradient.argtypes = [i, i, i, P, i, P, P, d, P, P, P, i]
+        lib.orc_cg_solve.argtypes = [i, i, i, P, i, P, P, ctypes.POINTER(_Opts), P, i, P, P, P, P, P, i]
+        for f in ("orc_fft2", "orc_Q", "orc_QH", "orc_forward", "orc_adjoint", "orc_objective",
+                  "orc_gradient", "orc_cg_solve"):
+            getattr(lib, f).restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _c128(a):
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def _pos(pos):
+    return np.ascontiguousarray(pos, dtype=np.int32).reshape(-1, 2)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(st, what):
+    if st != ORC_OK:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def fft2(x, inverse=False):
+    """Unitary 2-D DFT of a P x P array (Eq. 1's F, or F^H when inverse)."""
+    x = _c128(x).copy()
+    _check(_get().orc_fft2(_ptr(x), x.shape[0], int(bool(inverse))), "fft2")
+    return x
+
+
+def Q(psi, probe, pos):
+    """Q psi: probe times the P x P patch at every scan position -> [K][P][P]."""
+    psi, probe, pos = _c128(psi), _c128(probe), _pos(pos)
+    H, W = psi.shape
+    P = probe.shape[0]
+    out = np.empty((pos.shape[0], P, P), np.complex128)
+    _check(_get().orc_Q(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(psi), _ptr(out)), "Q")
+    return out
+
+
+def QH(y, probe, pos, shape):
+    """Q^H y: conj(probe) times each patch, scatter-added into an H x W object."""
+    y, probe, pos = _c128(y), _c128(probe), _pos(pos)
+    H, W = shape
+    P = probe.shape[0]
+    out = np.empty((H, W), np.complex128)
+    _check(_get().orc_QH(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(y), _ptr(out)), "QH")
+    return out
+
+
+def forward(psi, probe, pos, nthreads=1):
+    """G psi = F Q psi (Eq. 1), unitary F -> [K][P][P] complex128."""
+    psi, probe, pos = _c128(psi), _c128(probe), _pos(pos)
+    H, W = psi.shape
+    P = probe.shape[0]
+    out = np.empty((pos.shape[0], P, P), np.complex128)
+    st = _get().orc_forward(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(psi), _ptr(out), nthreads)
+    _check(st, "forward")
+    return out
+
+
+def adjoint(y, probe, pos, shape, nthreads=1):
+    """G^H y = Q^H F^H y (the operator of Eq. 3) -> [H][W] complex128."""
+    y, probe, pos = _c128(y), _c128(probe), _pos(pos)
+    H, W = shape
+    P = probe.shape[0]
+    out = np.empty((H, W), np.complex128)
+    st = _get().orc_adjoint(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(y), _ptr(out), nthreads)
+    _check(st, "adjoint")
+    return out
+
+
+def objective(psi, probe, pos, d, eps=1e-6, nthreads=1):
+    """F_eps(psi) = sum |G psi|^2 - d log(|G psi|^2 + eps) (Eq. 2 with the eps guard)."""
+    psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
+    H, W = psi.shape
+    P = probe.shape[0]
+    F = ctypes.c_double(0.0)
+    st = _get().orc_objective(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, _ptr(psi),
+                              ctypes.byref(F), nthreads)
+    _check(st, "objective")
+    return F.value
+
+
+def gradient(psi, probe, pos, d, eps=1e-6, nthreads=1):
+    """(g, F): g = G^H(G psi - d G psi / (|G psi|^2 + eps)) (Eq. 3), F as in objective()."""
+    psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
+    H, W = psi.shape
+    P = probe.shape[0]
+    g = np.empty((H, W), np.complex128)
+    F = ctypes.c_double(0.0)
+    st = _get().orc_gradient(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, _ptr(psi),
+                             _ptr(g), ctypes.byref(F), nthreads)
+    _check(st, "gradient")
+    return g, F.value
+
+
+def cg_solve(psi0, probe, pos, d, niter, opts: OrcOpts | None = None, nthreads=1):
+    """Run niter ML-CG iterations (Eq. 5-7, Algorithm 1 on one device).
+
+    Returns a dict with psi, F (F_hist[0..iters_done]), gamma, halvings, alpha,
+    iters_done and status (ORC_OK or ORC_STALLED).
+    """
+    opts = opts or OrcOpts()
+    psi = _c128(psi0).copy()
+    probe, pos, d = _c128(probe), _pos(pos), _f32(d)
+    H, W = psi.shape
+    P = probe.shape[0]
+    o = _Opts(opts.gamma0, opts.tau, opts.t, opts.max_halvings, opts.eps)
+    F = np.full(niter + 1, np.nan)
+    gam = np.full(max(niter, 1), np.nan)
+    halv = np.zeros(max(niter, 1), np.int32)
+    alpha = np.full(max(niter, 1), np.nan)
+    done = ctypes.c_int(0)
+    st = _get().orc_cg_solve(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), ctypes.byref(o),
+                             _ptr(psi), niter, _ptr(F), _ptr(gam), _ptr(halv), _ptr(alpha),
+                             ctypes.byref(done), nthreads)
+    if st not in (ORC_OK, ORC_STALLED):
+        _check(st, "cg_solve")
+    n = done.value
+    return {
+        "psi": psi,
+        "F": F[: n + 1],
+        "gamma": gam[:n],
+        "halvings": halv[: min(niter, n + (st == ORC_STALLED))],
+        "alpha": alpha[: min(niter, n + (st == ORC_STALLED))],
+        "iters_done": n,
+        "status": st,
+    }

@@ -1,0 +1,188 @@
+/*
+ * pty.h -- C ABI of the GB300 (sm_103a) maximum-likelihood conjugate-gradient
+ * ptychography library (libpty).
+ *
+ * The method is the object reconstruction of Yu et al., "Scalable and accurate multi-GPU
+ * based image reconstruction of large-scale ptychography data" (arXiv 2106.07575),
+ * section "Inverse problem for ptychography", run on one GPU:
+ *   Eq. 1  forward model   |G psi|^2 = |F Q psi|^2 = d
+ *          Q: probe p times the P x P patch of the object psi at every scan position
+ *          F: 2-D far-field Fourier transform of each exit wave
+ *   Eq. 2  ML objective    F(psi) = sum_j |G psi|_j^2 - 2 d_j log|G psi|_j
+ *   Eq. 3  gradient        grad F = G^H (G psi - d / (G psi)^*),  G^H = Q^H F^H
+ *   Eq. 5  CG update       psi_{m+1} = psi_m + gamma_m eta_m
+ *   Eq. 6  Dai-Yuan        eta_m = -g_m + ||g_m||^2 / <eta_{m-1}, g_m - g_{m-1}> eta_{m-1}
+ *   Eq. 7  line search     shrink gamma until F(psi + gamma eta) <= F(psi) + gamma t
+ *   Algorithm 1            GRAD -> DIR -> LS -> Update per iteration, gamma^(0) = 1, tau = 0.5
+ *
+ * Conventions (the paper leaves these open; the library fixes them):
+ *  - psi is the object transmission, [H][W] complex; positions are integer top-left
+ *    corners (row, col) of the P x P patch, 0 <= row <= H-P, 0 <= col <= W-P.
+ *  - F is the unitary 2-D DFT (scale 1/P per 2-D transform, kernel exp(-2 pi i k.n / P),
+ *    no fftshift), so F^H = F^{-1}.  Detector arrays are in natural DFT order.
+ *  - The objective is F_eps = sum |u|^2 - d log(|u|^2 + eps) (0 log(.) := 0 when d = 0),
+ *    whose Wirtinger gradient is G^H(u - d u / (|u|^2 + eps)), u = G psi; Eq. 3 is used
+ *    literally (derivative with respect to psi^*, no factor 2).
+ *  - <a,b> in Eq. 6 is Re sum conj(a) b.  A denominator <= 0 or not finite restarts the
+ *    direction with eta = -g.
+ *  - Line search: gamma = gamma0; repeat { gamma *= tau; trial } until Eq. 7 holds, at
+ *    most max_halvings trials; the first trial is gamma0 * tau.
+ *
+ * Data types.  Complex arrays are interleaved single precision (re, im) pairs, i.e.
+ * `float` pointers to 2*N floats, layout-compatible with CUDA float2 / C float complex.
+ * Scalars that are reductions (objective, step length, Dai-Yuan coefficient) are double.
+ *
+ * Memory.  Every array argument may be a host pointer or a device pointer of the device
+ * the context was created on; the library detects which (unified addressing) and copies
+ * host arrays through its own staging buffers.  Arguments are read or written only during
+ * the call.  `data` is the exception: a device pointer is BORROWED (it must stay valid and
+ * unchanged until pty_destroy and is never written); a host pointer is copied once.
+ *
+ * Streams and threads.  All device work of a context runs on the stream given at
+ * creation (a cudaStream_t passed as void*; NULL = the legacy default stream).  Every
+ * call returns after that work completed.  A context must not be used from two host
+ * threads at once; distinct contexts are independent.
+ *
+ * Errors.  Every call returns a pty_status.  No call aborts or throws; after an error
+ * pty_last_error() gives a one-line description.  A context stays usable after
+ * PTY_ERR_ARG / PTY_ERR_BOUNDS / PTY_STALLED; after PTY_ERR_CUDA it should be destroyed.
+ */
+#ifndef PTY_H_
+#define PTY_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PTY_API __attribute__((visibility("default")))
+#else
+#define PTY_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PTY_OK = 0,
+    PTY_ERR_ARG = 1,         /* bad size, null pointer, unsupported P, bad option */
+    PTY_ERR_BOUNDS = 2,      /* a scan position puts the patch outside the object */
+    PTY_ERR_NOMEM = 3,       /* device or host allocation failed */
+    PTY_ERR_CUDA = 4,        /* a CUDA runtime call failed (message in pty_last_error) */
+    PTY_ERR_NONFINITE = 5,   /* measured data holds NaN, Inf or negative values */
+    PTY_STALLED = 6,         /* line search found no step within max_halvings trials */
+    PTY_ERR_TIMEOUT = 7,     /* a bounded device-side wait gave up */
+    PTY_ERR_UNSUPPORTED = 8  /* option or size not supported by this build */
+} pty_status;
+
+/* Solver options; pty_default_opts fills Algorithm 1's values. */
+typedef struct {
+    double gamma0;       /* initial step length of every line search (1.0) */
+    double tau;          /* shrink factor per trial, 0 < tau < 1 (0.5) */
+    double t;            /* Eq. 7 termination constant (0.0) */
+    int32_t max_halvings;/* trials per line search before PTY_STALLED (60) */
+    double eps;          /* guard of log and division in the objective, >= 0 (1e-6) */
+    int32_t ls_window;   /* line-search trials evaluated per pass over the data: 4, 8, 16
+                            or 32 (16); the accepted step does not depend on it */
+    int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times) */
+} pty_opts;
+
+typedef struct pty_ctx pty_ctx;
+
+/* Per-iteration record of pty_cg_solve.  Each array pointer is host memory or NULL.
+ *   F[niter+1]      F(psi_m) for m = 0..iters_done (the last entry is F of the final psi)
+ *   gamma[niter]    accepted step length gamma_m
+ *   halvings[niter] line-search trials used in iteration m
+ *   alpha[niter]    Dai-Yuan coefficient of Eq. 6 (0 for the first iteration or a restart)
+ * iters_done counts the iterations whose step was accepted. */
+typedef struct {
+    double *F;
+    double *gamma;
+    int32_t *halvings;
+    double *alpha;
+    int32_t iters_done;
+} pty_cg_report;
+
+/* Fill *o with the defaults listed in pty_opts. */
+PTY_API void pty_default_opts(pty_opts *o);
+
+/*
+ * Create a context for one reconstruction problem (the inputs of Algorithm 1).
+ *   out    receives the context; *out is NULL on failure.
+ *   H, W   object height and width, P <= H, P <= W.
+ *   P      probe / detector size; 64 or 128.
+ *   probe  [P][P] complex, copied.
+ *   K      number of scan positions, >= 1.
+ *   pos    [K][2] int32 (row, col) top-left corners, copied.
+ *   data   [K][P][P] float32 measured intensities, natural DFT order, finite and >= 0;
+ *          borrowed if a device pointer, copied if a host pointer.
+ *   opts   options, or NULL for the defaults.
+ *   stream cudaStream_t (as void*) on which all work of the context runs.
+ * The current CUDA device at the call is the context's device.
+ * Errors: PTY_ERR_ARG, PTY_ERR_BOUNDS, PTY_ERR_NONFINITE, PTY_ERR_NOMEM, PTY_ERR_CUDA.
+ */
+PTY_API int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *probe, int32_t K,
+               const int32_t *pos, const float *data, const pty_opts *opts, void *stream);
+
+/* Release every resource of the context (NULL is ignored). */
+PTY_API void pty_destroy(pty_ctx *ctx);
+
+/* Description of the last error on this context (or of the last failed pty_create when
+ * ctx is NULL).  The string lives until the next call on the same context. */
+PTY_API const char *pty_last_error(const pty_ctx *ctx);
+
+/*
+ * Forward model, Eq. 1: out[k] = F(p * patch_k(psi)), unitary F, for every position k
+ * in the caller's order.  psi [H][W] complex, out [K][P][P] complex.
+ */
+PTY_API int pty_forward(pty_ctx *ctx, const float *psi, float *out);
+
+/*
+ * Adjoint of the forward model, the G^H of Eq. 3: x = sum_k shift_k(conj(p) * F^H y_k).
+ * y [K][P][P] complex (natural DFT order), x [H][W] complex.  The scatter-add of
+ * overlapping patches is summed in a fixed order: results are bitwise reproducible.
+ */
+PTY_API int pty_adjoint(pty_ctx *ctx, const float *y, float *x);
+
+/*
+ * Objective and gradient, Eq. 2 and 3, at psi.  grad [H][W] complex (may be NULL to get
+ * only the objective); F receives the objective (may be NULL).  Bitwise reproducible.
+ */
+PTY_API int pty_gradient(pty_ctx *ctx, const float *psi, float *grad, double *F);
+
+/*
+ * niter iterations of ML-CG (Eq. 5-7, Algorithm 1 on one GPU) updating psi_inout
+ * ([H][W] complex) in place.  The conjugate-gradient state (previous gradient and
+ * direction) persists in the context, so consecutive calls continue one solve; the
+ * first call after pty_create or pty_cg_reset starts with eta_0 = -g_0.
+ * rep may be NULL.  Returns PTY_OK, or PTY_STALLED when an iteration found no step
+ * (psi then holds the last accepted iterate and rep->iters_done says how many were
+ * accepted).  The iteration runs without host synchronisation between its stages.
+ */
+PTY_API int pty_cg_solve(pty_ctx *ctx, float *psi_inout, int32_t niter, pty_cg_report *rep);
+
+/* Forget the conjugate-gradient state: the next pty_cg_solve starts with eta = -g. */
+PTY_API int pty_cg_reset(pty_ctx *ctx);
+
+/*
+ * Checkpoint of the conjugate-gradient state (previous gradient and direction, the
+ * iteration count and the last step): pty_cg_state_size bytes of host memory.
+ * pty_cg_state_load restores it into a context of the same problem sizes; a solve
+ * resumed from a checkpoint reproduces the uninterrupted solve bit for bit.
+ */
+PTY_API size_t pty_cg_state_size(const pty_ctx *ctx);
+PTY_API int pty_cg_state_save(pty_ctx *ctx, void *host_buf);
+PTY_API int pty_cg_state_load(pty_ctx *ctx, const void *host_buf);
+
+/*
+ * Per-stage GPU time accumulated since the last reset (needs opts.flags bit 0):
+ * ms[0] GRAD pattern pass, ms[1] scatter-add + direction reductions, ms[2] LS pattern
+ * passes, ms[3] small reductions and update; launches[i] the matching kernel counts.
+ * Either pointer may be NULL.  reset != 0 clears the counters after reading.
+ */
+PTY_API int pty_stage_times(pty_ctx *ctx, double ms[4], int64_t launches[4], int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTY_H_ */

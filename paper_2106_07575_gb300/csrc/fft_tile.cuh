@@ -1,0 +1,235 @@
+// fft_tile.cuh -- batched 2-D DFT of one P x P complex tile held in shared memory.
+//
+// This is the F of Eq. 1 (and F^H of Eq. 3) in the paper: the far-field transform of one
+// exit wave.  Each 1-D transform of length P = R1 * R2 (R1 = 16, R2 = P/16) is split
+// Cooley-Tukey style into two in-place passes over the tile:
+//   stride pass: radix-16 DFT over the elements n2 + R2*n1 (n1 = 0..15), then the
+//                twiddle W_P^{n2 k1}, written back to the same slots;
+//   block pass : radix-R2 DFT over the contiguous block n2 + R2*k1 (n2 = 0..R2-1),
+//                written back to the same slots.
+// Forward (stride, block) leaves frequency k1 + R1*k2 in slot k2 + R2*k1 ("permuted"
+// order); the inverse runs (block, stride) with conjugate twiddles applied before the
+// radix-16 step and takes the permuted order back to natural order.  Both passes are in
+// place, so a thread keeps one small line segment in registers at a time and only a
+// barrier separates passes.  The tile row stride is P + 1 float2: with lines mapped to
+// consecutive threads (rows for row passes, columns for column passes) every warp access
+// is free of shared-memory bank conflicts.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace pty {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cconjmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+
+// cos(2 pi m / 16), m in [0, 16): the 16th roots of unity (exact decimal expansions of
+// cos(pi/8), sin(pi/8) and sqrt(2)/2 rounded to float).
+__host__ __device__ constexpr float cos16(int m)
+{
+    return m == 0    ? 1.0f
+           : m == 1  ? 0.923879532511286756f
+           : m == 2  ? 0.707106781186547524f
+           : m == 3  ? 0.382683432365089772f
+           : m == 4  ? 0.0f
+           : m == 5  ? -0.382683432365089772f
+           : m == 6  ? -0.707106781186547524f
+           : m == 7  ? -0.923879532511286756f
+           : m == 8  ? -1.0f
+           : m == 9  ? -0.923879532511286756f
+           : m == 10 ? -0.707106781186547524f
+           : m == 11 ? -0.382683432365089772f
+           : m == 12 ? 0.0f
+           : m == 13 ? 0.382683432365089772f
+           : m == 14 ? 0.707106781186547524f
+                     : 0.923879532511286756f;
+}
+
+// a * exp(SIGN * 2 pi i m / 16) for m known at compile time after unrolling.
+template <int SIGN>
+__device__ __forceinline__ float2 rot16(float2 a, int m)
+{
+    m &= 15;
+    if (m == 0) return a;
+    if (m == 4) return SIGN < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+    if (m == 8) return make_float2(-a.x, -a.y);
+    if (m == 12) return SIGN < 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+    const float c = cos16(m), s = (SIGN < 0 ? -1.0f : 1.0f) * cos16((m + 12) & 15);
+    return make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.x, s, a.y * c));
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft2(float2 &a, float2 &b)
+{
+    float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+// X[k] = sum_n x[n] exp(SIGN 2 pi i n k / 4)
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2 &x0, float2 &x1, float2 &x2, float2 &x3)
+{
+    float2 a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = csub(x1, x3);
+    float2 dw = SIGN < 0 ? make_float2(d.y, -d.x) : make_float2(-d.y, d.x);  // d * (SIGN i)
+    x0 = cadd(a, c);
+    x2 = csub(a, c);
+    x1 = cadd(b, dw);
+    x3 = csub(b, dw);
+}
+
+// In-register DFT of N in {4, 8, 16} points, natural order in and out.
+template <int N, int SIGN>
+__device__ __forceinline__ void dft_reg(float2 (&x)[N])
+{
+    if constexpr (N == 4) {
+        dft4<SIGN>(x[0], x[1], x[2], x[3]);
+    } else if constexpr (N == 8) {
+        // n = n2 + 4 n1 (n1 < 2): radix-2 over n1, twiddle W8^{n2 k1}, radix-4 over n2
+#pragma unroll
+        for (int n2 = 0; n2 < 4; n2++) dft2<SIGN>(x[n2], x[n2 + 4]);
+#pragma unroll
+        for (int n2 = 1; n2 < 4; n2++) x[n2 + 4] = rot16<SIGN>(x[n2 + 4], 2 * n2);
+        dft4<SIGN>(x[0], x[1], x[2], x[3]);
+        dft4<SIGN>(x[4], x[5], x[6], x[7]);
+        // slot k2 + 4 k1 holds X[k1 + 2 k2]
+        float2 y[8];
+#pragma unroll
+        for (int k1 = 0; k1 < 2; k1++)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; k2++) y[k1 + 2 * k2] = x[k2 + 4 * k1];
+#pragma unroll
+        for (int i = 0; i < 8; i++) x[i] = y[i];
+    } else if constexpr (N == 16) {
+        // n = n2 + 4 n1: radix-4 over n1, twiddle W16^{n2 k1}, radix-4 over n2
+#pragma unroll
+        for (int n2 = 0; n2 < 4; n2++) dft4<SIGN>(x[n2], x[n2 + 4], x[n2 + 8], x[n2 + 12]);
+#pragma unroll
+        for (int k1 = 1; k1 < 4; k1++)
+#pragma unroll
+            for (int n2 = 1; n2 < 4; n2++) x[n2 + 4 * k1] = rot16<SIGN>(x[n2 + 4 * k1], n2 * k1);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++) dft4<SIGN>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+        float2 y[16];
+#pragma unroll
+        for (int k1 = 0; k1 < 4; k1++)
+#pragma unroll
+            for (int k2 = 0; k2 < 4; k2++) y[k1 + 4 * k2] = x[k2 + 4 * k1];
+#pragma unroll
+        for (int i = 0; i < 16; i++) x[i] = y[i];
+    }
+}
+
+template <int P>
+struct Tile {
+    static constexpr int R1 = 16;
+    static constexpr int R2 = P / 16;
+    static constexpr int LD = P + 1;  // row stride in float2
+    static constexpr int ELEMS = P * LD;
+    // natural frequency held by slot q after a forward transform
+    static __device__ __forceinline__ int nat(int q) { return q / R2 + R1 * (q % R2); }
+    // slot holding natural frequency k
+    static __device__ __forceinline__ int slot(int k) { return k / R1 + R2 * (k % R1); }
+};
+
+// Address of element e of line `line`: rows are contiguous, columns stride LD.
+template <int P, bool ROWS>
+__device__ __forceinline__ int taddr(int line, int e)
+{
+    return ROWS ? line * Tile<P>::LD + e : e * Tile<P>::LD + line;
+}
+
+// Forward stride pass: radix-16 over n1, then twiddle W_P^{n2 k1} (tw = exp(-2 pi i m/P)).
+template <int P, int NT, bool ROWS>
+__device__ __forceinline__ void pass_stride_fwd(float2 *tile, const float2 *tw)
+{
+    constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2;
+    for (int t = threadIdx.x; t < P * R2; t += NT) {
+        const int line = t % P, n2 = t / P;
+        float2 x[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; n1++) x[n1] = tile[taddr<P, ROWS>(line, n2 + R2 * n1)];
+        dft_reg<R1, -1>(x);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmul(x[k1], tw[(n2 * k1) & (P - 1)]);
+#pragma unroll
+        for (int k1 = 0; k1 < R1; k1++) tile[taddr<P, ROWS>(line, n2 + R2 * k1)] = x[k1];
+    }
+}
+
+// Inverse stride pass: conjugate twiddle W_P^{-n2 k1}, then inverse radix-16.
+template <int P, int NT, bool ROWS>
+__device__ __forceinline__ void pass_stride_inv(float2 *tile, const float2 *tw)
+{
+    constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2;
+    for (int t = threadIdx.x; t < P * R2; t += NT) {
+        const int line = t % P, n2 = t / P;
+        float2 x[R1];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; k1++) x[k1] = tile[taddr<P, ROWS>(line, n2 + R2 * k1)];
+#pragma unroll
+        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmulc(x[k1], tw[(n2 * k1) & (P - 1)]);
+        dft_reg<R1, +1>(x);
+#pragma unroll
+        for (int n1 = 0; n1 < R1; n1++) tile[taddr<P, ROWS>(line, n2 + R2 * n1)] = x[n1];
+    }
+}
+
+// Block pass (either direction): radix-R2 over the contiguous block of R2 slots.
+template <int P, int NT, bool ROWS, int SIGN>
+__device__ __forceinline__ void pass_block(float2 *tile)
+{
+    constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2;
+    for (int t = threadIdx.x; t < P * R1; t += NT) {
+        const int line = t % P, k1 = t / P;
+        float2 x[R2];
+#pragma unroll
+        for (int j = 0; j < R2; j++) x[j] = tile[taddr<P, ROWS>(line, j + R2 * k1)];
+        dft_reg<R2, SIGN>(x);
+#pragma unroll
+        for (int j = 0; j < R2; j++) tile[taddr<P, ROWS>(line, j + R2 * k1)] = x[j];
+    }
+}
+
+// Unnormalised forward 2-D DFT: natural order in, permuted order out.  Caller syncs before.
+template <int P, int NT>
+__device__ __forceinline__ void fft2_fwd(float2 *tile, const float2 *tw)
+{
+    pass_stride_fwd<P, NT, true>(tile, tw);
+    __syncthreads();
+    pass_block<P, NT, true, -1>(tile);
+    __syncthreads();
+    pass_stride_fwd<P, NT, false>(tile, tw);
+    __syncthreads();
+    pass_block<P, NT, false, -1>(tile);
+    __syncthreads();
+}
+
+// Unnormalised inverse 2-D DFT: permuted order in, natural order out.  Caller syncs before.
+template <int P, int NT>
+__device__ __forceinline__ void fft2_inv(float2 *tile, const float2 *tw)
+{
+    pass_block<P, NT, false, +1>(tile);
+    __syncthreads();
+    pass_stride_inv<P, NT, false>(tile, tw);
+    __syncthreads();
+    pass_block<P, NT, true, +1>(tile);
+    __syncthreads();
+    pass_stride_inv<P, NT, true>(tile, tw);
+    __syncthreads();
+}
+
+}  // namespace pty

@@ -1,0 +1,297 @@
+// object_kernels.cu -- object-sized steps of ML-CG and the small scalar kernels.
+//
+//   k_scatter     Q^H of Eq. 3: the patch-sized results of all positions are summed into
+//                 the object.  One thread block owns one object tile and walks the
+//                 position-sorted list of patterns that overlap it (built once on the
+//                 host), accumulating in registers in that fixed order: no atomics, and
+//                 bitwise reproducible.  Optionally fuses the two reductions of the
+//                 Dai-Yuan coefficient (Eq. 6): ||g||^2 and Re <eta_prev, g - g_prev>.
+//   k_dy_finalize DIR stage scalars (Eq. 6, with the restart rule) and F(psi_m) (Eq. 2).
+//   k_ls_decide   LS stage decision (Eq. 7): the first candidate of the window that does
+//                 not increase the objective, else open the next window or stall.
+//   k_update      Update stage (Eq. 5): psi += gamma eta, keeping eta and g for Eq. 6.
+// All sums of partials run in FP64 in a fixed order.
+#include <cmath>
+
+#include "pty_internal.h"
+#include "reduce.cuh"
+
+namespace pty {
+
+namespace {
+constexpr int kScTY = 32, kScTX = 64, kScNT = 256, kScNJ = kScTY * kScTX / kScNT;
+constexpr int kSumNT = 256;
+}  // namespace
+
+template <int P>
+__global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan plan, const float2 *__restrict__ w,
+                                                   float2 *__restrict__ out, int dy, const float2 *__restrict__ ep,
+                                                   const float2 *__restrict__ gp, double *__restrict__ part,
+                                                   const DevState *__restrict__ st)
+{
+    if (st && st->stalled) return;
+    __shared__ double red[(kScNT / 32) * 2];
+    __shared__ double tot[2];
+    const int b = blockIdx.x;
+    const int ty = b / plan.ntile_x, tx = b % plan.ntile_x;
+    const int x = tx * kScTX + (threadIdx.x % kScTX);
+    const int y0 = ty * kScTY + threadIdx.x / kScTX;
+    float2 acc[kScNJ];
+#pragma unroll
+    for (int j = 0; j < kScNJ; j++) acc[j] = make_float2(0.f, 0.f);
+    const int q0 = plan.tile_start[b], q1 = plan.tile_start[b + 1];
+    for (int q = q0; q < q1; q++) {
+        const int i = __ldg(plan.tile_list + q);
+        const int2 rc = __ldg(a.pos + i);
+        const int dx = x - rc.y;
+        if (dx < 0 || dx >= P) continue;
+        const float2 *wi = w + (size_t)i * P * P + dx;
+#pragma unroll
+        for (int j = 0; j < kScNJ; j++) {
+            const int yy = y0 + (kScNT / kScTX) * j - rc.x;
+            if (yy >= 0 && yy < P) {
+                const float2 v = __ldg(wi + yy * P);
+                acc[j].x += v.x;
+                acc[j].y += v.y;
+            }
+        }
+    }
+    float gg = 0.f, den = 0.f;
+    if (x < a.W) {
+#pragma unroll
+        for (int j = 0; j < kScNJ; j++) {
+            const int y = y0 + (kScNT / kScTX) * j;
+            if (y < a.H) {
+                const size_t o = (size_t)y * a.W + x;
+                out[o] = acc[j];
+                if (dy) {
+                    const float2 e = __ldg(ep + o), g0 = __ldg(gp + o);
+                    gg = fmaf(acc[j].x, acc[j].x, fmaf(acc[j].y, acc[j].y, gg));
+                    den = fmaf(e.x, acc[j].x - g0.x, fmaf(e.y, acc[j].y - g0.y, den));
+                }
+            }
+        }
+    }
+    if (dy) {
+        double v[2] = {(double)gg, (double)den};
+        block_sum<kScNT, 2>(v, red, tot);
+        if (threadIdx.x < 2) part[2 * b + threadIdx.x] = tot[threadIdx.x];
+    }
+}
+
+// Each thread sums a fixed strided subset, then the block combines: fixed order.
+__device__ __forceinline__ double strided_sum(const double *v, int n, int stride, int off)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += kSumNT) s += v[(size_t)i * stride + off];
+    return s;
+}
+
+__global__ void __launch_bounds__(kSumNT) k_sum(const double *__restrict__ v, int n, double *__restrict__ out)
+{
+    __shared__ double red[kSumNT / 32];
+    __shared__ double tot[1];
+    double x[1] = {strided_sum(v, n, 1, 0)};
+    block_sum<kSumNT, 1>(x, red, tot);
+    if (threadIdx.x == 0) *out = tot[0];
+}
+
+__device__ __forceinline__ void open_window(DevState *st, double gamma0, double tau, int L)
+{
+    // candidates gamma0 tau^(k0 + l + 1), l < L
+    double g = gamma0;
+    for (int k = 0; k < st->k0; k++) g *= tau;
+    for (int l = 0; l < L; l++) {
+        g *= tau;
+        st->cand[l] = g;
+    }
+}
+
+__global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict__ fpart, int K,
+                                                        const double *__restrict__ part, int nparts, DevState *st,
+                                                        DevHist h, LsArgs ls)
+{
+    if (st->stalled) return;
+    __shared__ double red[(kSumNT / 32) * 3];
+    __shared__ double tot[3];
+    double v[3] = {strided_sum(fpart, K, 1, 0), strided_sum(part, nparts, 2, 0), strided_sum(part, nparts, 2, 1)};
+    block_sum<kSumNT, 3>(v, red, tot);
+    if (threadIdx.x == 0) {
+        const double Fm = tot[0], gg = tot[1], den = tot[2];
+        double alpha = 0.0;
+        if (den > 0.0 && isfinite(den) && isfinite(gg)) {
+            alpha = gg / den;
+        } else if (st->total > 0) {
+            st->restarts += 1;
+        }
+        st->alpha = alpha;
+        st->Fm = Fm;
+        st->k0 = 0;
+        st->decided = 0;
+        open_window(st, ls.gamma0, ls.tau, ls.L);
+        const int m = st->m;
+        if (m < h.cap) {
+            h.F[m] = Fm;
+            h.alpha[m] = alpha;
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__ part, int K, DevState *st,
+                                                      DevHist h, LsArgs ls)
+{
+    if (st->stalled || st->decided) return;
+    __shared__ double red[(kSumNT / 32) * (L + 2)];
+    __shared__ double tot[L + 2];
+    double v[L + 2];
+#pragma unroll
+    for (int j = 0; j < L + 2; j++) v[j] = 0.0;
+    for (int i = threadIdx.x; i < K; i += kSumNT) {
+#pragma unroll
+        for (int j = 0; j < L + 2; j++) v[j] += part[(size_t)i * (L + 2) + j];
+    }
+    block_sum<kSumNT, L + 2>(v, red, tot);
+    if (threadIdx.x == 0) {
+        const int m = st->m, k0 = st->k0;
+        for (int l = 0; l < L && k0 + l + 1 <= ls.max_halvings; l++) {
+            const double gam = st->cand[l];
+            // F(psi + gam eta) - F(psi): quadratic part of the d = 0 pixels plus the rest
+            const double dF = gam * (2.0 * tot[0] + gam * tot[1]) + tot[2 + l];
+            if (dF <= gam * ls.t) {
+                st->gamma = gam;
+                st->Fnext = st->Fm + dF;
+                st->decided = 1;
+                if (m < h.cap) {
+                    h.gamma[m] = gam;
+                    h.halvings[m] = k0 + l + 1;
+                    h.F[m + 1] = st->Fm + dF;
+                }
+                return;
+            }
+        }
+        const int k1 = k0 + L;
+        if (k1 >= ls.max_halvings) {
+            st->stalled = 1;
+            if (m < h.cap) {
+                h.gamma[m] = st->cand[ls.max_halvings - 1 - k0];
+                h.halvings[m] = ls.max_halvings;
+                h.F[m + 1] = st->Fm;
+            }
+        } else {
+            st->k0 = k1;
+            open_window(st, ls.gamma0, ls.tau, L);
+        }
+    }
+}
+
+__global__ void k_update(int n, float2 *__restrict__ psi, const float2 *__restrict__ g, float2 *__restrict__ ep,
+                         float2 *__restrict__ gp, DevState *st)
+{
+    if (st->stalled || !st->decided) return;
+    const float gam = (float)st->gamma, alpha = (float)st->alpha;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 gv = g[i], ev = ep[i];
+        const float2 eta = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
+        float2 p = psi[i];
+        p.x = fmaf(gam, eta.x, p.x);
+        p.y = fmaf(gam, eta.y, p.y);
+        psi[i] = p;
+        ep[i] = eta;
+        gp[i] = gv;
+    }
+}
+
+__global__ void k_update_counters(DevState *st)
+{
+    if (st->stalled || !st->decided) return;
+    st->m += 1;
+    st->total += 1;
+    st->last_gamma = st->gamma;
+}
+
+__global__ void k_check_data(const float *__restrict__ d, size_t n, int *flag)
+{
+    int bad = 0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = d[i];
+        bad |= !(v >= 0.0f) || isinf(v);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
+__global__ void k_begin_solve(DevState *st)
+{
+    st->m = 0;
+    st->stalled = 0;
+    st->decided = 0;
+}
+
+// ------------------------------------------------------------------------------------
+cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *w, float2 *out,
+                           int dy, const float2 *eta_prev, const float2 *g_prev, double *part, const DevState *st,
+                           cudaStream_t s)
+{
+    const int nb = plan.ntile_x * plan.ntile_y;
+    switch (P) {
+    case 64: k_scatter<64><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st); break;
+    case 128: k_scatter<128><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st); break;
+    case 256: k_scatter<256><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s)
+{
+    k_sum<<<1, kSumNT, 0, s>>>(v, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dy_finalize(const double *fpart, int K, const double *part, int nparts, DevState *st, DevHist h,
+                               const LsArgs &ls, cudaStream_t s)
+{
+    k_dy_finalize<<<1, kSumNT, 0, s>>>(fpart, K, part, nparts, st, h, ls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_decide(const double *part, int K, const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
+{
+    switch (ls.L) {
+    case 4: k_ls_decide<4><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
+    case 8: k_ls_decide<8><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
+    case 16: k_ls_decide<16><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
+    case 32: k_ls_decide<32><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(int n, float2 *psi, const float2 *g, float2 *eta_prev, float2 *g_prev, DevState *st,
+                          cudaStream_t s)
+{
+    int nb = (n + 255) / 256;
+    if (nb > 152 * 8) nb = 152 * 8;
+    k_update<<<nb, 256, 0, s>>>(n, psi, g, eta_prev, g_prev, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_update_counters<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t s)
+{
+    size_t nb = (n + 255) / 256;
+    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb < 1) nb = 1;
+    k_check_data<<<(unsigned)nb, 256, 0, s>>>(d, n, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_begin_solve(DevState *st, cudaStream_t s)
+{
+    k_begin_solve<<<1, 1, 0, s>>>(st);
+    return cudaGetLastError();
+}
+
+}  // namespace pty

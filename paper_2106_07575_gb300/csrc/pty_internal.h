@@ -1,0 +1,101 @@
+// pty_internal.h -- declarations shared by the translation units of libpty (not part of
+// the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace pty {
+
+// Solver state that lives in device memory so that one CG iteration runs without host
+// synchronisation: the line-search decision, the Dai-Yuan coefficient and the stall flag
+// are produced and consumed by kernels.
+struct DevState {
+    int m;         // iterations accepted in the current pty_cg_solve call
+    int k0;        // line-search trials already rejected in the current iteration
+    int decided;   // the current iteration's step has been chosen
+    int stalled;   // no step within max_halvings: the solve is over
+    int total;     // iterations accepted since the last reset (checkpointed)
+    int restarts;  // Dai-Yuan restarts (denominator <= 0 or not finite)
+    int pad[2];
+    double alpha;  // Dai-Yuan coefficient of the current iteration (Eq. 6)
+    double gamma;  // accepted step of the current iteration
+    double Fm;     // F(psi_m)
+    double Fnext;  // F(psi_m + gamma eta_m) of the accepted trial
+    double last_gamma;
+    double cand[32];  // candidate steps gamma0 tau^(k0+l+1) of the open line-search window
+};
+
+// Per-call history arrays (device), indexed by DevState::m.
+struct DevHist {
+    double *F;      // [cap + 1]
+    double *gamma;  // [cap]
+    int *halvings;  // [cap]
+    double *alpha;  // [cap]
+    int cap;
+};
+
+// Everything a per-pattern kernel needs about the problem.
+struct PatternArgs {
+    int H, W, K;
+    const float2 *probe;   // [P][P], scaled by 1/P (the unitary normalisation)
+    const float2 *tw;      // [P] exp(-2 pi i m / P)
+    const int2 *pos;       // [K] (row, col), position-sorted order
+    const int *perm;       // [K] caller index of sorted pattern i
+    const float *data;     // [K][P][P], caller order, natural DFT order
+    float eps;
+};
+
+// Line-search window description (device scalars come from DevState).
+struct LsArgs {
+    double gamma0, tau, t;
+    int max_halvings;
+    int L;  // candidates per pass
+};
+
+// ---- pattern kernels (pattern_kernels.cu) ----
+// out[perm[i]] = F(p * patch_i(psi))   (unitary)
+cudaError_t launch_forward(int P, const PatternArgs &a, const float2 *psi, float2 *out, cudaStream_t s);
+// w[i] = conj(p) * F^H y[perm[i]]
+cudaError_t launch_adjoint_fft(int P, const PatternArgs &a, const float2 *y, float2 *w, cudaStream_t s);
+// GRAD pattern pass: w[i] = conj(p) * F^H r_i with r the likelihood residual of
+// u = F(p * patch_i(psi)); fpart[i] = sum_j f_j of pattern i.  Exits early when st->stalled.
+cudaError_t launch_grad(int P, const PatternArgs &a, const float2 *psi, float2 *w, double *fpart,
+                        const DevState *st, cudaStream_t s);
+// LS pattern pass over the candidates gamma0 tau^(k0+l+1), l < L, with
+// eta = -g + alpha eta_prev; part[i][0..1] = (sum b, sum c) over d = 0 pixels,
+// part[i][2+l] = sum over d > 0 pixels of the objective change at candidate l.
+// Exits early when st->decided or st->stalled.
+cudaError_t launch_ls(int P, const PatternArgs &a, const LsArgs &ls, const float2 *psi, const float2 *g,
+                      const float2 *eta_prev, double *part, const DevState *st, cudaStream_t s);
+bool pattern_supported(int P);
+int ls_window_supported(int L);  // 1 if L is an instantiated window size
+
+// ---- object kernels (object_kernels.cu) ----
+struct ScatterPlan {
+    int TY, TX;       // object tile
+    int ntile_y, ntile_x;
+    const int *tile_start;  // [ntiles + 1] CSR offsets
+    const int *tile_list;   // sorted pattern indices overlapping each tile, ascending
+};
+// out[y][x] = sum over patterns i covering (y, x), in ascending i, of w[i][y-r_i][x-c_i].
+// With dy != 0 also part[b] = (sum |out|^2, sum Re conj(eta_prev) (out - g_prev)) per tile b.
+cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *w,
+                           float2 *out, int dy, const float2 *eta_prev, const float2 *g_prev,
+                           double *part, const DevState *st, cudaStream_t s);
+// Fixed-order sum of n doubles into *out (one block).
+cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
+// DIR stage scalars: F_m = sum fpart; alpha from the tile partials (restart rule);
+// resets the line-search window; writes the history of iteration m.
+cudaError_t launch_dy_finalize(const double *fpart, int K, const double *part, int nparts, DevState *st,
+                               DevHist h, const LsArgs &ls, cudaStream_t s);
+// LS decision over one window of candidates.
+cudaError_t launch_ls_decide(const double *part, int K, const LsArgs &ls, DevState *st, DevHist h,
+                             cudaStream_t s);
+// Update stage: psi += gamma eta, eta_prev <- eta = -g + alpha eta_prev, g_prev <- g.
+cudaError_t launch_update(int n, float2 *psi, const float2 *g, float2 *eta_prev, float2 *g_prev,
+                          DevState *st, cudaStream_t s);
+// flag |= 1 if any of the n floats is NaN, Inf or negative.
+cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t s);
+cudaError_t launch_begin_solve(DevState *st, cudaStream_t s);
+
+}  // namespace pty

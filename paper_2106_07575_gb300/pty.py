@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libpty (include/pty.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts Python arguments
+(torch tensors on the GPU or the CPU, or numpy arrays) into the raw pointers and sizes
+of the C ABI, and turns status codes into exceptions.  There is no fallback: if the
+library cannot be built or loaded, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+PTY_OK, PTY_ERR_ARG, PTY_ERR_BOUNDS, PTY_ERR_NOMEM, PTY_ERR_CUDA = 0, 1, 2, 3, 4
+PTY_ERR_NONFINITE, PTY_STALLED, PTY_ERR_TIMEOUT, PTY_ERR_UNSUPPORTED = 5, 6, 7, 8
+STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_NOMEM", 4: "PTY_ERR_CUDA",
+                5: "PTY_ERR_NONFINITE", 6: "PTY_STALLED", 7: "PTY_ERR_TIMEOUT", 8: "PTY_ERR_UNSUPPORTED"}
+
+EXPORTED = ["pty_default_opts", "pty_create", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
+            "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
+            "pty_cg_state_load", "pty_stage_times"]
+
+
+class PtyError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class pty_opts(ctypes.Structure):
+    _fields_ = [("gamma0", ctypes.c_double), ("tau", ctypes.c_double), ("t", ctypes.c_double),
+                ("max_halvings", ctypes.c_int32), ("eps", ctypes.c_double), ("ls_window", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class pty_cg_report(ctypes.Structure):
+    _fields_ = [("F", ctypes.POINTER(ctypes.c_double)), ("gamma", ctypes.POINTER(ctypes.c_double)),
+                ("halvings", ctypes.POINTER(ctypes.c_int32)), ("alpha", ctypes.POINTER(ctypes.c_double)),
+                ("iters_done", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(build_if_missing: bool = True):
+    """Load libpty (building it first if needed) and declare the C signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpty not built ({path}); run paper_2106_07575_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+    lib.pty_default_opts.argtypes = [ctypes.POINTER(pty_opts)]
+    lib.pty_default_opts.restype = None
+    lib.pty_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, vp, i32, vp, vp, ctypes.POINTER(pty_opts), vp]
+    lib.pty_destroy.argtypes = [vp]
+    lib.pty_destroy.restype = None
+    lib.pty_last_error.argtypes = [vp]
+    lib.pty_last_error.restype = ctypes.c_char_p
+    lib.pty_forward.argtypes = [vp, vp, vp]
+    lib.pty_adjoint.argtypes = [vp, vp, vp]
+    lib.pty_gradient.argtypes = [vp, vp, vp, ctypes.POINTER(dbl)]
+    lib.pty_cg_solve.argtypes = [vp, vp, i32, ctypes.POINTER(pty_cg_report)]
+    lib.pty_cg_reset.argtypes = [vp]
+    lib.pty_cg_state_size.argtypes = [vp]
+    lib.pty_cg_state_size.restype = ctypes.c_size_t
+    lib.pty_cg_state_save.argtypes = [vp, vp]
+    lib.pty_cg_state_load.argtypes = [vp, vp]
+    lib.pty_stage_times.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    for f in ("pty_create", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
+              "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a, dtype_ok):
+    """Raw pointer of a contiguous torch tensor or numpy array (no copy)."""
+    if a is None:
+        return None
+    try:
+        import torch
+
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if str(a.dtype).replace("torch.", "") not in dtype_ok:
+                raise TypeError(f"dtype {a.dtype} not in {dtype_ok}")
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if a.dtype.name not in dtype_ok:
+            raise TypeError(f"dtype {a.dtype} not in {dtype_ok}")
+        return ctypes.c_void_p(a.ctypes.data)
+    raise TypeError(f"unsupported argument type {type(a)}")
+
+
+_C = ("complex64",)
+_F = ("float32",)
+_I = ("int32",)
+
+
+def default_opts() -> pty_opts:
+    o = pty_opts()
+    load().pty_default_opts(ctypes.byref(o))
+    return o
+
+
+def _check(lib, ctx, st, allow=()):
+    if st != PTY_OK and st not in allow:
+        msg = lib.pty_last_error(ctx)
+        raise PtyError(st, msg.decode() if msg else "")
+    return st
+
+
+def pty_create(H, W, P, probe, K, pos, data, opts: pty_opts | None = None, stream=None):
+    lib = load()
+    ctx = ctypes.c_void_p()
+    st = lib.pty_create(ctypes.byref(ctx), H, W, P, _ptr(probe, _C), K, _ptr(pos, _I), _ptr(data, _F),
+                        ctypes.byref(opts) if opts is not None else None,
+                        ctypes.c_void_p(stream) if stream else None)
+    _check(lib, None, st)
+    return ctx
+
+
+def pty_destroy(ctx):
+    load().pty_destroy(ctx)
+
+
+def pty_forward(ctx, psi, out):
+    lib = load()
+    return _check(lib, ctx, lib.pty_forward(ctx, _ptr(psi, _C), _ptr(out, _C)))
+
+
+def pty_adjoint(ctx, y, x):
+    lib = load()
+    return _check(lib, ctx, lib.pty_adjoint(ctx, _ptr(y, _C), _ptr(x, _C)))
+
+
+def pty_gradient(ctx, psi, grad):
+    lib = load()
+    F = ctypes.c_double(0.0)
+    _check(lib, ctx, lib.pty_gradient(ctx, _ptr(psi, _C), _ptr(grad, _C), ctypes.byref(F)))
+    return F.value
+
+
+def pty_cg_solve(ctx, psi, niter, report=True):
+    """Run niter iterations in place; returns (status, dict) with F, gamma, halvings, alpha, iters_done."""
+    lib = load()
+    rep = None
+    arrays = {}
+    if report:
+        arrays = {"F": np.full(niter + 1, np.nan), "gamma": np.full(max(niter, 1), np.nan),
+                  "halvings": np.zeros(max(niter, 1), np.int32), "alpha": np.full(max(niter, 1), np.nan)}
+        rep = pty_cg_report(arrays["F"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            arrays["gamma"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                            arrays["halvings"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                            arrays["alpha"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+    st = lib.pty_cg_solve(ctx, _ptr(psi, _C), niter, ctypes.byref(rep) if rep is not None else None)
+    _check(lib, ctx, st, allow=(PTY_STALLED,))
+    out = {}
+    if report:
+        n = rep.iters_done
+        k = min(niter, n + (st == PTY_STALLED))
+        out = {"F": arrays["F"][: n + 1], "gamma": arrays["gamma"][:k], "halvings": arrays["halvings"][:k],
+               "alpha": arrays["alpha"][:k], "iters_done": n}
+    return st, out
+
+
+def pty_cg_reset(ctx):
+    lib = load()
+    return _check(lib, ctx, lib.pty_cg_reset(ctx))
+
+
+def pty_cg_state_save(ctx) -> bytes:
+    lib = load()
+    n = lib.pty_cg_state_size(ctx)
+    buf = ctypes.create_string_buffer(n)
+    _check(lib, ctx, lib.pty_cg_state_save(ctx, buf))
+    return buf.raw
+
+
+def pty_cg_state_load(ctx, blob: bytes):
+    lib = load()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    return _check(lib, ctx, lib.pty_cg_state_load(ctx, buf))
+
+
+def pty_stage_times(ctx, reset=False):
+    lib = load()
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int64 * 4)()
+    _check(lib, ctx, lib.pty_stage_times(ctx, ms, n, int(bool(reset))))
+    return list(ms), list(n)
+
+
+@dataclass
+class Problem:
+    H: int
+    W: int
+    P: int
+    K: int
+
+
+class Context:
+    """Owning wrapper: one libpty context per reconstruction problem."""
+
+    def __init__(self, probe, pos, data, H, W, opts: pty_opts | None = None, stream=None):
+        P = probe.shape[0]
+        K = pos.shape[0]
+        self.shape = (H, W)
+        self.P, self.K = P, K
+        self._keep = (probe, pos, data)  # borrowed device data must outlive the context
+        self.ctx = pty_create(H, W, P, probe, K, pos, data, opts, stream)
+
+    def close(self):
+        if self.ctx:
+            pty_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, psi, out):
+        return pty_forward(self.ctx, psi, out)
+
+    def adjoint(self, y, x):
+        return pty_adjoint(self.ctx, y, x)
+
+    def gradient(self, psi, grad):
+        return pty_gradient(self.ctx, psi, grad)
+
+    def cg_solve(self, psi, niter, report=True):
+        return pty_cg_solve(self.ctx, psi, niter, report)
+
+    def cg_reset(self):
+        return pty_cg_reset(self.ctx)
+
+    def state_save(self):
+        return pty_cg_state_save(self.ctx)
+
+    def state_load(self, blob):
+        return pty_cg_state_load(self.ctx, blob)
+
+    def stage_times(self, reset=False):
+        return pty_stage_times(self.ctx, reset)

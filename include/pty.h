@@ -81,7 +81,9 @@ typedef struct {
     double tau;          /* shrink factor per trial, 0 < tau < 1 (0.5) */
     double t;            /* Eq. 7 termination constant (0.0) */
     int32_t max_halvings;/* trials per line search before PTY_STALLED (60) */
-    double eps;          /* guard of log and division in the objective, >= 0 (1e-6) */
+    double eps;          /* guard of log and division in the objective, in counts, >= 0
+                            (0.1: with a smaller guard the gradient at dark detector pixels
+                            holding counts is too ill-conditioned for single precision) */
     int32_t ls_window;   /* line-search trials evaluated per pass over the data: 4, 8, 16
                             or 32 (16); the accepted step does not depend on it */
     int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times) */

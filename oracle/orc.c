@@ -25,6 +25,7 @@
  *  - Eq. 2 is 2 log|u| = log|u|^2; the implemented objective is
  *    F_eps = sum |u|^2 - d log(|u|^2 + eps) with 0*log(.) := 0 when d = 0, whose exact
  *    Wirtinger gradient is u - d u / (|u|^2 + eps) (Eq. 3 with d/u^* = d u/|u|^2).
+ *    The guard eps (in counts, default 0.1) is an input of every function here.
  *  - Eq. 3 is used literally (derivative w.r.t. psi^*, no factor 2).
  *  - <a,b> in Eq. 6 is taken as Re sum conj(a) b; a denominator that is <= 0 or not
  *    finite restarts the direction with eta = -g.

@@ -41,7 +41,7 @@ class OrcOpts:
     tau: float = 0.5
     t: float = 0.0
     max_halvings: int = 60
-    eps: float = 1e-6
+    eps: float = 0.1
 
 
 def build(force: bool = False) -> str:
@@ -150,7 +150,7 @@ def adjoint(y, probe, pos, shape, nthreads=1):
     return out
 
 
-def objective(psi, probe, pos, d, eps=1e-6, nthreads=1):
+def objective(psi, probe, pos, d, eps=0.1, nthreads=1):
     """F_eps(psi) = sum |G psi|^2 - d log(|G psi|^2 + eps) (Eq. 2 with the eps guard)."""
     psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
     H, W = psi.shape
@@ -162,7 +162,7 @@ def objective(psi, probe, pos, d, eps=1e-6, nthreads=1):
     return F.value
 
 
-def gradient(psi, probe, pos, d, eps=1e-6, nthreads=1):
+def gradient(psi, probe, pos, d, eps=0.1, nthreads=1):
     """(g, F): g = G^H(G psi - d G psi / (|G psi|^2 + eps)) (Eq. 3), F as in objective()."""
     psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
     H, W = psi.shape

@@ -263,7 +263,7 @@ void pty_default_opts(pty_opts *o)
     o->tau = 0.5;
     o->t = 0.0;
     o->max_halvings = 60;
-    o->eps = 1e-6;
+    o->eps = 0.1;
     o->ls_window = 16;
     o->flags = 0;
 }

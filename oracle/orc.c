@@ -439,8 +439,8 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
     int T = nthreads_eff(nthreads);
     long n = (long)H * W;
     cplx *psi = (cplx *)psi_io;
-    cplx *g = (cplx *)malloc(sizeof(cplx) * n), *g_prev = (cplx *)malloc(sizeof(cplx) * n);
-    cplx *eta = (cplx *)malloc(sizeof(cplx) * n), *trial = (cplx *)malloc(sizeof(cplx) * n);
+    cplx *g = (cplx *)calloc((size_t)n, sizeof(cplx)), *g_prev = (cplx *)calloc((size_t)n, sizeof(cplx));
+    cplx *eta = (cplx *)calloc((size_t)n, sizeof(cplx)), *trial = (cplx *)calloc((size_t)n, sizeof(cplx));
     cplx *tw = make_twiddles(P);
     if (!g || !g_prev || !eta || !trial || !tw) {
         st = ORC_ERR_NOMEM;
@@ -466,7 +466,11 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
             }
             if (den > 0.0 && isfinite(den) && isfinite(num)) alpha = num / den;
         }
-        for (long i = 0; i < n; i++) eta[i] = -g[i] + alpha * eta[i];
+        if (m == 0 || alpha == 0.0) {
+            for (long i = 0; i < n; i++) eta[i] = -g[i]; /* eta_0 = -grad F(psi_0); restart */
+        } else {
+            for (long i = 0; i < n; i++) eta[i] = -g[i] + alpha * eta[i];
+        }
         if (alpha_out) alpha_out[m] = alpha;
         /* LS stage: gamma^(0) = gamma0; do { gamma *= tau; F(psi+gamma eta) } while Eq. 7 fails */
         double gam = opts->gamma0, Ft = 0.0;

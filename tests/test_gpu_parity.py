@@ -240,12 +240,12 @@ def test_edge_positions_duplicates_and_ragged_object(orc):
 
 def test_single_position(orc):
     rng = np.random.default_rng(9)
-    psi_true = synth.ellipse_phantom(128, 128, rng)
-    pos = np.array([[32, 32]], np.int32)
+    psi_true = synth.ellipse_phantom(192, 160, rng)
+    pos = np.array([[32, 17]], np.int32)
     probe, d = synth.simulate_counts(psi_true, synth.gaussian_probe(128), pos, 1e5, rng)
     p = synth.Problem("one", psi_true, probe, pos, d, 2)
     ctx = make_ctx(p)
-    g = torch.empty((128, 128), dtype=torch.complex64, device="cuda")
+    g = torch.empty((192, 160), dtype=torch.complex64, device="cuda")
     F = ctx.gradient(dev(p.psi0()), g)
     gw, Fw = orc.gradient(p.psi0(), probe, pos, d)
     assert rel(g.cpu().numpy(), gw) <= GRAD_TOL

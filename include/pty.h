@@ -35,8 +35,8 @@
  * Memory.  Every array argument may be a host pointer or a device pointer of the device
  * the context was created on; the library detects which (unified addressing) and copies
  * host arrays through its own staging buffers.  Arguments are read or written only during
- * the call.  `data` is the exception: a device pointer is BORROWED (it must stay valid and
- * unchanged until pty_destroy and is never written); a host pointer is copied once.
+ * the call; `data` is read during pty_create only (the library keeps a compact copy of
+ * the detector pixels that hold counts).
  *
  * Streams and threads.  All device work of a context runs on the stream given at
  * creation (a cudaStream_t passed as void*; NULL = the legacy default stream).  Every
@@ -117,7 +117,7 @@ PTY_API void pty_default_opts(pty_opts *o);
  *   K      number of scan positions, >= 1.
  *   pos    [K][2] int32 (row, col) top-left corners, copied.
  *   data   [K][P][P] float32 measured intensities, natural DFT order, finite and >= 0;
- *          borrowed if a device pointer, copied if a host pointer.
+ *          read during the call only.
  *   opts   options, or NULL for the defaults.
  *   stream cudaStream_t (as void*) on which all work of the context runs.
  * The current CUDA device at the call is the context's device.

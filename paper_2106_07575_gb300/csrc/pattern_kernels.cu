@@ -7,13 +7,14 @@
 //   k_grad         GRAD stage: gather x probe -> F -> likelihood residual (Eq. 3) and the
 //                  objective terms (Eq. 2) -> F^H -> x conj(p); one patch-sized result
 //                  per pattern, summed into the object by the scatter kernel
-//   k_ls           LS stage: u = G psi and v = G eta for one pattern, then the change of
-//                  the objective F(psi + gamma eta) - F(psi) (Eq. 2, 7) for a window of
-//                  candidate steps gamma, using G(psi + gamma eta) = u + gamma v
+//   k_ls           LS stage: v = G eta for one pattern, then the change of the objective
+//                  F(psi + gamma eta) - F(psi) (Eq. 2, 7) for a window of candidate steps
+//                  gamma, using G(psi + gamma eta) = u + gamma v with u kept by k_grad
+//   k_nz_*         create time: the compact list of detector pixels with counts
 //
 // The forward DFT leaves the spectrum in the permuted slot order of fft_tile.cuh; the
-// elementwise steps read the measured data at the matching natural index, and the
-// inverse DFT returns to natural order, so no separate reordering pass exists.
+// measured data are stored in that order, and the inverse DFT returns to natural order,
+// so no separate reordering pass exists.
 #include "fft_tile.cuh"
 #include "pty_internal.h"
 #include "reduce.cuh"
@@ -25,13 +26,13 @@ struct Cfg;
 template <>
 struct Cfg<64> {
     static constexpr int NT_A = 256;  // GRAD pass threads
-    static constexpr int NT_B = 256;  // LS pass threads (holds u in registers: P*P/NT_B complex)
-    static constexpr int NT_F = 256;  // forward / adjoint
+    static constexpr int NT_B = 256;  // LS pass threads
+    static constexpr int NT_F = 256;  // forward / adjoint / data compaction
 };
 template <>
 struct Cfg<128> {
     static constexpr int NT_A = 512;
-    static constexpr int NT_B = 256;
+    static constexpr int NT_B = 512;
     static constexpr int NT_F = 512;
 };
 
@@ -55,21 +56,6 @@ __device__ __forceinline__ void gather_patch(float2 *tile, const float2 *__restr
     for (int e = threadIdx.x; e < P * P; e += NT) {
         const int y = e / P, x = e % P;
         tile[y * Tile<P>::LD + x] = cmul(__ldg(probe + e), __ldg(src + (size_t)(r + y) * W + (c + x)));
-    }
-}
-
-// Same with the Dai-Yuan direction eta = -g + alpha eta_prev formed on the fly (Eq. 6).
-template <int P, int NT>
-__device__ __forceinline__ void gather_direction(float2 *tile, const float2 *__restrict__ probe,
-                                                 const float2 *__restrict__ g, const float2 *__restrict__ ep,
-                                                 float alpha, int W, int r, int c)
-{
-    for (int e = threadIdx.x; e < P * P; e += NT) {
-        const int y = e / P, x = e % P;
-        const size_t o = (size_t)(r + y) * W + (c + x);
-        const float2 gv = __ldg(g + o), ev = __ldg(ep + o);
-        const float2 eta = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
-        tile[y * Tile<P>::LD + x] = cmul(__ldg(probe + e), eta);
     }
 }
 
@@ -115,7 +101,19 @@ __global__ void __launch_bounds__(NT) k_adjoint_fft(PatternArgs a, const float2 
     }
 }
 
+// Kahan-compensated single-precision accumulation (per thread; the block sum is FP64).
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
+{
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
 // GRAD pattern pass (Eq. 2 and 3 for one pattern).
+//   f = sum_j |u_j|^2 - sum_{entries} d log(|u|^2 + eps)
+//   r = u, except r = u (1 - d / (|u|^2 + eps)) at the entries
+//   w = conj(p) F^H r;  u at the entries is kept for the line search of this iteration.
 template <int P, int NT>
 __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__restrict__ psi,
                                              float2 *__restrict__ w, double *__restrict__ fpart,
@@ -128,31 +126,32 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
     float2 *tile = sm, *tw = sm + Tile<P>::ELEMS;
     const int i = blockIdx.x;
     const int2 rc = a.pos[i];
-    const float *d = a.data + (size_t)a.perm[i] * P * P;
     load_twiddles<P, NT>(tw, a.tw);
     gather_patch<P, NT>(tile, a.probe, psi, a.W, rc.x, rc.y);
     __syncthreads();
     fft2_fwd<P, NT>(tile, tw);
-    // u - d u / (|u|^2 + eps) and |u|^2 - d log(|u|^2 + eps), slot by slot
     float f = 0.0f;
     for (int e = threadIdx.x; e < P * P; e += NT) {
-        const int qy = e / P, qx = e % P;
-        const float dv = __ldg(d + Tile<P>::nat(qy) * P + Tile<P>::nat(qx));
-        float2 u = tile[qy * Tile<P>::LD + qx];
-        const float au = fmaf(u.x, u.x, u.y * u.y);
-        if (dv > 0.0f) {
-            const float den = au + a.eps;
-            f += au - dv * logf(den);
-            const float s = 1.0f - dv / den;
-            u.x *= s;
-            u.y *= s;
-            tile[qy * Tile<P>::LD + qx] = u;
-        } else {
-            f += au;
-        }
+        const float2 u = tile[(e / P) * Tile<P>::LD + (e % P)];
+        f = fmaf(u.x, u.x, fmaf(u.y, u.y, f));
+    }
+    __syncthreads();
+    const long long e0 = a.nz_off[i], e1 = a.nz_off[i + 1];
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+        const int s = a.nz_slot[e];
+        const float dv = a.nz_d[e];
+        float2 *pu = tile + (s / P) * Tile<P>::LD + (s % P);
+        float2 u = *pu;
+        a.nz_u[e] = u;
+        const float den = fmaf(u.x, u.x, u.y * u.y) + a.eps;
+        f -= dv * logf(den);
+        const float sc = 1.0f - dv / den;
+        u.x *= sc;
+        u.y *= sc;
+        *pu = u;
     }
     double v[1] = {(double)f};
-    block_sum<NT, 1>(v, red, tot);
+    block_sum<NT, 1>(v, red, tot);  // its barriers also order the residual writes before F^H
     if (threadIdx.x == 0) fpart[i] = tot[0];
     fft2_inv<P, NT>(tile, tw);
     float2 *wi = w + (size_t)i * P * P;
@@ -162,74 +161,135 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
     }
 }
 
-// LS pattern pass for a window of L candidate steps.
+// LS pattern pass for a window of L candidate steps gamma_l (Eq. 7 with Eq. 2):
+//   F(psi + gamma eta) - F(psi) = sum_j q_j - sum_{entries} d log1p(q / (|u|^2 + eps)),
+//   q_j = |u_j + gamma v_j|^2 - |u_j|^2 = gamma (2 Re conj(u_j) v_j + gamma |v_j|^2),
+// with u = G psi (kept by the GRAD pass at the entries) and v = G eta (one forward DFT).
+// Over all pixels, sum conj(u) v and sum |v|^2 equal P^2 sum conj(x) y and P^2 sum |y|^2
+// of the real-space exit waves x = p psi / P, y = p eta / P (Parseval); the d = 0 part is
+// that total minus the entries' part.
 template <int P, int NT, int L>
 __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restrict__ psi,
                                            const float2 *__restrict__ g, const float2 *__restrict__ ep,
                                            double *__restrict__ part, const DevState *__restrict__ st)
 {
     if (st->stalled || st->decided) return;
-    constexpr int NS = P * P / NT;  // slots per thread
     extern __shared__ __align__(16) float2 sm[];
     __shared__ double red[(NT / 32) * (L + 2)];
     __shared__ double tot[L + 2];
     float2 *tile = sm, *tw = sm + Tile<P>::ELEMS;
     const int i = blockIdx.x;
     const int2 rc = a.pos[i];
-    const float *d = a.data + (size_t)a.perm[i] * P * P;
     const float alpha = (float)st->alpha;
     float gam[L];
 #pragma unroll
     for (int l = 0; l < L; l++) gam[l] = (float)st->cand[l];
-
     load_twiddles<P, NT>(tw, a.tw);
-    gather_patch<P, NT>(tile, a.probe, psi, a.W, rc.x, rc.y);
-    __syncthreads();
-    fft2_fwd<P, NT>(tile, tw);
-    float2 u[NS];
-#pragma unroll
-    for (int j = 0; j < NS; j++) {
-        const int e = threadIdx.x + NT * j, qy = e / P, qx = e % P;
-        u[j] = tile[qy * Tile<P>::LD + qx];
+
+    // y = p eta / P into the tile, with the real-space sums of Parseval's identity
+    float sb = 0.f, sbc = 0.f, scc = 0.f, sccc = 0.f;
+    for (int e = threadIdx.x; e < P * P; e += NT) {
+        const int y = e / P, x = e % P;
+        const size_t o = (size_t)(rc.x + y) * a.W + (rc.y + x);
+        const float2 gv = __ldg(g + o), ev = __ldg(ep + o), pv = __ldg(a.probe + e);
+        const float2 eta = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
+        const float2 yv = cmul(pv, eta), xv = cmul(pv, __ldg(psi + o));
+        tile[y * Tile<P>::LD + x] = yv;
+        kahan_add(sb, sbc, fmaf(xv.x, yv.x, xv.y * yv.y));
+        kahan_add(scc, sccc, fmaf(yv.x, yv.x, yv.y * yv.y));
     }
     __syncthreads();
-    gather_direction<P, NT>(tile, a.probe, g, ep, alpha, a.W, rc.x, rc.y);
-    __syncthreads();
     fft2_fwd<P, NT>(tile, tw);
 
-    float b0 = 0.0f, c0 = 0.0f, acc[L];
+    float bp = 0.0f, cp = 0.0f, acc[L];
 #pragma unroll
     for (int l = 0; l < L; l++) acc[l] = 0.0f;
-#pragma unroll
-    for (int j = 0; j < NS; j++) {
-        const int e = threadIdx.x + NT * j, qy = e / P, qx = e % P;
-        const float2 v = tile[qy * Tile<P>::LD + qx];
-        const float dv = __ldg(d + Tile<P>::nat(qy) * P + Tile<P>::nat(qx));
-        const float au = fmaf(u[j].x, u[j].x, u[j].y * u[j].y);
-        const float bu = fmaf(u[j].x, v.x, u[j].y * v.y);  // Re conj(u) v
+    const long long e0 = a.nz_off[i], e1 = a.nz_off[i + 1];
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+        const int s = a.nz_slot[e];
+        const float dv = a.nz_d[e];
+        const float2 u = a.nz_u[e];
+        const float2 v = tile[(s / P) * Tile<P>::LD + (s % P)];
+        const float au = fmaf(u.x, u.x, u.y * u.y);
+        const float bu = fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
         const float cu = fmaf(v.x, v.x, v.y * v.y);
-        if (dv > 0.0f) {
-            // |u + gamma v|^2 - |u|^2 = q; objective change q - d log1p(q / (|u|^2 + eps))
-            const float inv = 1.0f / (au + a.eps);
-            const float tmin = -au * inv;
+        bp += bu;
+        cp += cu;
+        const float inv = 1.0f / (au + a.eps);
+        const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
 #pragma unroll
-            for (int l = 0; l < L; l++) {
-                const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
-                const float t = fmaxf(q * inv, tmin);
-                acc[l] += q - dv * log1pf(t);
-            }
-        } else {
-            b0 += bu;
-            c0 += cu;
+        for (int l = 0; l < L; l++) {
+            const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
+            const float t = fmaxf(q * inv, tmin);
+            acc[l] += q - dv * log1pf(t);
         }
     }
+    constexpr double PP = (double)P * (double)P;
     double vals[L + 2];
-    vals[0] = b0;
-    vals[1] = c0;
+    vals[0] = PP * ((double)sb - (double)sbc) - (double)bp;
+    vals[1] = PP * ((double)scc - (double)sccc) - (double)cp;
 #pragma unroll
     for (int l = 0; l < L; l++) vals[2 + l] = acc[l];
     block_sum<NT, L + 2>(vals, red, tot);
     if (threadIdx.x < L + 2) part[(size_t)i * (L + 2) + threadIdx.x] = tot[threadIdx.x];
+}
+
+// Natural-order index of tile slot s.
+template <int P>
+__device__ __forceinline__ int slot_to_natural(int s)
+{
+    return Tile<P>::nat(s / P) * P + Tile<P>::nat(s % P);
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) k_nz_count(const float *__restrict__ d, const int *__restrict__ perm,
+                                                 int *__restrict__ cnt)
+{
+    __shared__ int red[NT / 32];
+    const float *dk = d + (size_t)perm[blockIdx.x] * P * P;
+    int c = 0;
+    for (int s = threadIdx.x; s < P * P; s += NT) c += dk[slot_to_natural<P>(s)] > 0.0f;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < NT / 32; w++) t += red[w];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// Ordered compaction: entries of sorted pattern i in ascending slot order.
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) k_nz_fill(const float *__restrict__ d, const int *__restrict__ perm,
+                                                const long long *__restrict__ off, unsigned short *__restrict__ slot,
+                                                float *__restrict__ dval)
+{
+    __shared__ int wsum[NT / 32];
+    const float *dk = d + (size_t)perm[blockIdx.x] * P * P;
+    const long long base = off[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long running = 0;
+    for (int s0 = 0; s0 < P * P; s0 += NT) {
+        const int s = s0 + threadIdx.x;
+        const float v = dk[slot_to_natural<P>(s)];
+        const bool flag = v > 0.0f;
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int woff = 0, total = 0;
+        for (int w2 = 0; w2 < NT / 32; w2++) {
+            woff += (w2 < warp) ? wsum[w2] : 0;
+            total += wsum[w2];
+        }
+        if (flag) {
+            const long long p = base + running + woff + __popc(m & ((1u << lane) - 1u));
+            slot[p] = (unsigned short)s;
+            dval[p] = v;
+        }
+        running += total;
+        __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -297,6 +357,40 @@ static cudaError_t ls_p(const PatternArgs &a, int L, const float2 *psi, const fl
     case 8: return ls_pl<P, 8>(a, psi, g, ep, part, st, s);
     case 16: return ls_pl<P, 16>(a, psi, g, ep, part, st, s);
     case 32: return ls_pl<P, 32>(a, psi, g, ep, part, st, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int P>
+static cudaError_t nz_count_p(const float *d, const int *perm, int K, int *cnt, cudaStream_t s)
+{
+    k_nz_count<P, Cfg<P>::NT_F><<<K, Cfg<P>::NT_F, 0, s>>>(d, perm, cnt);
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t nz_fill_p(const float *d, const int *perm, int K, const long long *off, unsigned short *slot,
+                             float *dval, cudaStream_t s)
+{
+    k_nz_fill<P, Cfg<P>::NT_F><<<K, Cfg<P>::NT_F, 0, s>>>(d, perm, off, slot, dval);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nz_count(int P, const float *d, const int *perm, int K, int *cnt, cudaStream_t s)
+{
+    switch (P) {
+    case 64: return nz_count_p<64>(d, perm, K, cnt, s);
+    case 128: return nz_count_p<128>(d, perm, K, cnt, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_nz_fill(int P, const float *d, const int *perm, int K, const long long *off,
+                           unsigned short *slot, float *dval, cudaStream_t s)
+{
+    switch (P) {
+    case 64: return nz_fill_p<64>(d, perm, K, off, slot, dval, s);
+    case 128: return nz_fill_p<128>(d, perm, K, off, slot, dval, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -39,8 +39,11 @@ struct pty_ctx {
     float2 *tw = nullptr;     // [P]
     int2 *pos = nullptr;      // [K] sorted
     int *perm = nullptr;      // [K]
-    const float *data = nullptr;
-    float *data_owned = nullptr;
+    long long *nz_off = nullptr;      // [K+1]
+    unsigned short *nz_slot = nullptr;  // [E]
+    float *nz_d = nullptr;            // [E]
+    float2 *nz_u = nullptr;           // [E]
+    long long n_entries = 0;
     int *tile_start = nullptr, *tile_list = nullptr;
     int ntile_y = 0, ntile_x = 0;
 
@@ -111,7 +114,8 @@ cudaError_t dalloc(T **p, size_t n)
 
 void free_all(pty_ctx *c)
 {
-    void *ptrs[] = {c->probe,   c->tw,       c->pos,       c->perm,   c->data_owned, c->tile_start, c->tile_list,
+    void *ptrs[] = {c->probe,   c->tw,       c->pos,       c->perm,   c->nz_off,  c->nz_slot, c->nz_d, c->nz_u,
+                    c->tile_start, c->tile_list,
                     c->w,       c->fpart,    c->part_sc,   c->part_ls, c->g,         c->g_prev,     c->eta_prev,
                     c->st,      c->dscalar,  c->hist.F,    c->hist.gamma, c->hist.halvings, c->hist.alpha,
                     c->stage_obj, c->stage_obj2, c->stage_pat};
@@ -130,7 +134,10 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.tw = c->tw;
     a.pos = c->pos;
     a.perm = c->perm;
-    a.data = c->data;
+    a.nz_off = c->nz_off;
+    a.nz_slot = c->nz_slot;
+    a.nz_d = c->nz_d;
+    a.nz_u = c->nz_u;
     a.eps = (float)c->opts.eps;
     return a;
 }
@@ -420,21 +427,55 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     CKC(cudaMemsetAsync(c->eta_prev, 0, sizeof(float2) * HW, c->stream));
     CKC(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
 
-    // measured data: borrowed device pointer, or an owned copy of a host array
-    if (is_device_ptr(data)) {
-        c->data = data;
-    } else {
-        CKC(dalloc(&c->data_owned, (size_t)K * PP));
-        CKC(cudaMemcpyAsync(c->data_owned, data, sizeof(float) * K * PP, cudaMemcpyHostToDevice, c->stream));
-        c->data = c->data_owned;
+    // measured data: read here only (a host array goes through a temporary device copy)
+    // and kept as the compact list of pixels with counts, in tile slot order
+    const float *dd = data;
+    float *dtmp = nullptr;
+    if (!is_device_ptr(data)) {
+        CKC(dalloc(&dtmp, (size_t)K * PP));
+        CKC(cudaMemcpyAsync(dtmp, data, sizeof(float) * K * PP, cudaMemcpyHostToDevice, c->stream));
+        dd = dtmp;
     }
+    auto free_tmp = [&]() {
+        if (dtmp) cudaFree(dtmp);
+        dtmp = nullptr;
+    };
     int *flag = (int *)c->dscalar;
-    CKC(cudaMemsetAsync(flag, 0, sizeof(int), c->stream));
-    CKC(pty::launch_check_data(c->data, (size_t)K * PP, flag, c->stream));
+    int *dcnt = nullptr;
+    std::vector<int> hcnt(K);
     int hflag = 0;
-    CKC(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CKC(cudaStreamSynchronize(c->stream));
-    if (hflag) return bail(fail(c, PTY_ERR_NONFINITE, "measured data holds NaN, Inf or negative values"));
+    cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
+    if (ce == cudaSuccess) ce = pty::launch_check_data(dd, (size_t)K * PP, flag, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = dalloc(&dcnt, (size_t)K);
+    if (ce == cudaSuccess) ce = pty::launch_nz_count(P, dd, c->perm, K, dcnt, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int) * K, cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (dcnt) cudaFree(dcnt);
+    if (ce != cudaSuccess) {
+        free_tmp();
+        return bail(fail(c, PTY_ERR_CUDA, "data check: %s", cudaGetErrorString(ce)));
+    }
+    if (hflag) {
+        free_tmp();
+        return bail(fail(c, PTY_ERR_NONFINITE, "measured data holds NaN, Inf or negative values"));
+    }
+    std::vector<long long> hoff(K + 1, 0);
+    for (int i = 0; i < K; i++) hoff[i + 1] = hoff[i] + hcnt[i];
+    c->n_entries = hoff[K];
+    const size_t E = (size_t)std::max<long long>(c->n_entries, 1);
+    ce = dalloc(&c->nz_off, (size_t)K + 1);
+    if (ce == cudaSuccess) ce = dalloc(&c->nz_slot, E);
+    if (ce == cudaSuccess) ce = dalloc(&c->nz_d, E);
+    if (ce == cudaSuccess) ce = dalloc(&c->nz_u, E);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (K + 1), cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess) ce = pty::launch_nz_fill(P, dd, c->perm, K, c->nz_off, c->nz_slot, c->nz_d, c->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    free_tmp();
+    if (ce != cudaSuccess)
+        return bail(fail(c, ce == cudaErrorMemoryAllocation ? PTY_ERR_NOMEM : PTY_ERR_CUDA, "data compaction: %s",
+                         cudaGetErrorString(ce)));
     (void)st;
 #undef CKC
     *out = c;

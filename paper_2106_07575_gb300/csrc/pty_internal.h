@@ -34,14 +34,21 @@ struct DevHist {
     int cap;
 };
 
-// Everything a per-pattern kernel needs about the problem.
+// Everything a per-pattern kernel needs about the problem.  The measured intensities are
+// held as a compact list of the detector pixels with counts ("entries"), per pattern in
+// ascending slot order (the permuted order the forward DFT leaves the spectrum in): pixels
+// with d = 0 enter the objective, the gradient and the line search only through |u|^2,
+// u and sums that Parseval's identity turns into real-space sums.
 struct PatternArgs {
     int H, W, K;
-    const float2 *probe;   // [P][P], scaled by 1/P (the unitary normalisation)
-    const float2 *tw;      // [P] exp(-2 pi i m / P)
-    const int2 *pos;       // [K] (row, col), position-sorted order
-    const int *perm;       // [K] caller index of sorted pattern i
-    const float *data;     // [K][P][P], caller order, natural DFT order
+    const float2 *probe;        // [P][P], scaled by 1/P (the unitary normalisation)
+    const float2 *tw;           // [P] exp(-2 pi i m / P)
+    const int2 *pos;            // [K] (row, col), position-sorted order
+    const int *perm;            // [K] caller index of sorted pattern i
+    const long long *nz_off;    // [K + 1] first entry of sorted pattern i
+    const unsigned short *nz_slot;  // [E] tile slot of each entry
+    const float *nz_d;          // [E] measured counts (> 0) of each entry
+    float2 *nz_u;               // [E] u = G psi_m at each entry (GRAD pass -> LS pass)
     float eps;
 };
 
@@ -62,11 +69,16 @@ cudaError_t launch_adjoint_fft(int P, const PatternArgs &a, const float2 *y, flo
 cudaError_t launch_grad(int P, const PatternArgs &a, const float2 *psi, float2 *w, double *fpart,
                         const DevState *st, cudaStream_t s);
 // LS pattern pass over the candidates gamma0 tau^(k0+l+1), l < L, with
-// eta = -g + alpha eta_prev; part[i][0..1] = (sum b, sum c) over d = 0 pixels,
-// part[i][2+l] = sum over d > 0 pixels of the objective change at candidate l.
+// eta = -g + alpha eta_prev and v = G eta: part[i][0..1] = (sum Re conj(u) v, sum |v|^2)
+// over the d = 0 pixels, part[i][2+l] = sum over the entries of the objective change at
+// candidate l.  u at the entries comes from the GRAD pass of the same iteration.
 // Exits early when st->decided or st->stalled.
 cudaError_t launch_ls(int P, const PatternArgs &a, const LsArgs &ls, const float2 *psi, const float2 *g,
                       const float2 *eta_prev, double *part, const DevState *st, cudaStream_t s);
+// Entries of the measured data: counts per sorted pattern, then the compact list.
+cudaError_t launch_nz_count(int P, const float *d, const int *perm, int K, int *cnt, cudaStream_t s);
+cudaError_t launch_nz_fill(int P, const float *d, const int *perm, int K, const long long *off,
+                           unsigned short *slot, float *dval, cudaStream_t s);
 bool pattern_supported(int P);
 int ls_window_supported(int L);  // 1 if L is an instantiated window size
 

@@ -1,0 +1,28 @@
+/*
+ * pty_selftest.h -- device self-tests of libpty's building blocks, for the test suite.
+ *
+ * These entry points run one device function of the library on caller data so that tests
+ * can compare it with a higher-precision reference.  They are not part of the
+ * reconstruction method of the paper.
+ */
+#ifndef PTY_SELFTEST_H_
+#define PTY_SELFTEST_H_
+
+#include "pty.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * out[i] = log(1 + t[i]) as computed by the line-search kernels (single precision,
+ * within 5 ulp of the exact value for -1 < t < 1e7).  t and out: n floats each, host or
+ * device memory (copied as needed); runs on the current device and synchronises.
+ * Returns PTY_OK, PTY_ERR_ARG (n < 0 or a NULL pointer with n > 0) or PTY_ERR_CUDA.
+ */
+PTY_API int pty_selftest_log1p(const float *t, float *out, int32_t n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTY_SELFTEST_H_ */

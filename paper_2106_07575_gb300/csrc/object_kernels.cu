@@ -142,16 +142,18 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
                                                       DevHist h, LsArgs ls)
 {
     if (st->stalled || st->decided) return;
-    __shared__ double red[(kSumNT / 32) * (L + 2)];
     __shared__ double tot[L + 2];
-    double v[L + 2];
-#pragma unroll
-    for (int j = 0; j < L + 2; j++) v[j] = 0.0;
-    for (int i = threadIdx.x; i < K; i += kSumNT) {
-#pragma unroll
-        for (int j = 0; j < L + 2; j++) v[j] += part[(size_t)i * (L + 2) + j];
+    // part is [L+2][K]: warp w sums the values j = w, w + 8, ... over K patterns, each
+    // lane a fixed strided subset, then a butterfly across the warp (fixed order).
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = warp; j < L + 2; j += kSumNT / 32) {
+        const double *pj = part + (size_t)j * K;
+        double s = 0.0;
+        for (int i = lane; i < K; i += 32) s += pj[i];
+        s = warp_sum(s);
+        if (lane == 0) tot[j] = s;
     }
-    block_sum<kSumNT, L + 2>(v, red, tot);
+    __syncthreads();
     if (threadIdx.x == 0) {
         const int m = st->m, k0 = st->k0;
         for (int l = 0; l < L && k0 + l + 1 <= ls.max_halvings; l++) {

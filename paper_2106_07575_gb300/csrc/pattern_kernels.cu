@@ -16,6 +16,7 @@
 // measured data are stored in that order, and the inverse DFT returns to natural order,
 // so no separate reordering pass exists.
 #include "fft_tile.cuh"
+#include "mathx.cuh"
 #include "pty_internal.h"
 #include "reduce.cuh"
 
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restri
         for (int l = 0; l < L; l++) {
             const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
             const float t = fmaxf(q * inv, tmin);
-            acc[l] += q - dv * log1pf(t);
+            acc[l] += q - dv * log1p_fast(t);
         }
     }
     constexpr double PP = (double)P * (double)P;
@@ -231,7 +232,18 @@ __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restri
 #pragma unroll
     for (int l = 0; l < L; l++) vals[2 + l] = acc[l];
     block_sum<NT, L + 2>(vals, red, tot);
-    if (threadIdx.x < L + 2) part[(size_t)i * (L + 2) + threadIdx.x] = tot[threadIdx.x];
+    if (threadIdx.x < L + 2) part[(size_t)threadIdx.x * a.K + i] = tot[threadIdx.x];  // [L+2][K]
+}
+
+__global__ void k_selftest_log1p(const float *__restrict__ t, float *__restrict__ out, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = log1p_fast(t[i]);
+}
+
+cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_t s)
+{
+    k_selftest_log1p<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, s>>>(t, out, n);
+    return cudaGetLastError();
 }
 
 // Natural-order index of tile slot s.

@@ -333,7 +333,6 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     c->K = K;
     c->opts = o;
 
-    int st = PTY_OK;
     auto bail = [&](int code) {
         g_create_err = c->err;
         free_all(c);
@@ -476,7 +475,6 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     if (ce != cudaSuccess)
         return bail(fail(c, ce == cudaErrorMemoryAllocation ? PTY_ERR_NOMEM : PTY_ERR_CUDA, "data compaction: %s",
                          cudaGetErrorString(ce)));
-    (void)st;
 #undef CKC
     *out = c;
     return PTY_OK;
@@ -676,3 +674,25 @@ int pty_stage_times(pty_ctx *c, double ms[4], int64_t launches[4], int reset)
 }
 
 }  // extern "C"
+
+#include "pty_selftest.h"
+
+extern "C" int pty_selftest_log1p(const float *t, float *out, int32_t n)
+{
+    pty_ctx *c = nullptr;
+    if (n < 0 || (n > 0 && (!t || !out))) return fail(nullptr, PTY_ERR_ARG, "bad arguments");
+    if (n == 0) return PTY_OK;
+    float *dt = nullptr, *dout = nullptr;
+    const bool dev_t = is_device_ptr(t), dev_o = is_device_ptr(out);
+    cudaError_t e = cudaSuccess;
+    if (!dev_t) e = cudaMalloc(&dt, sizeof(float) * n);
+    if (e == cudaSuccess && !dev_o) e = cudaMalloc(&dout, sizeof(float) * n);
+    if (e == cudaSuccess && !dev_t) e = cudaMemcpy(dt, t, sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = pty::launch_selftest_log1p(dev_t ? t : dt, dev_o ? out : dout, n, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && !dev_o) e = cudaMemcpy(out, dout, sizeof(float) * n, cudaMemcpyDeviceToHost);
+    if (dt) cudaFree(dt);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(c, PTY_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));
+    return PTY_OK;
+}

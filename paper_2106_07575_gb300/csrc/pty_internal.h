@@ -69,9 +69,9 @@ cudaError_t launch_adjoint_fft(int P, const PatternArgs &a, const float2 *y, flo
 cudaError_t launch_grad(int P, const PatternArgs &a, const float2 *psi, float2 *w, double *fpart,
                         const DevState *st, cudaStream_t s);
 // LS pattern pass over the candidates gamma0 tau^(k0+l+1), l < L, with
-// eta = -g + alpha eta_prev and v = G eta: part[i][0..1] = (sum Re conj(u) v, sum |v|^2)
-// over the d = 0 pixels, part[i][2+l] = sum over the entries of the objective change at
-// candidate l.  u at the entries comes from the GRAD pass of the same iteration.
+// eta = -g + alpha eta_prev and v = G eta: part[0][i], part[1][i] = (sum Re conj(u) v,
+// sum |v|^2) over the d = 0 pixels of pattern i, part[2+l][i] = sum over the entries of the
+// objective change at candidate l (layout [L+2][K]).  u at the entries comes from the GRAD pass of the same iteration.
 // Exits early when st->decided or st->stalled.
 cudaError_t launch_ls(int P, const PatternArgs &a, const LsArgs &ls, const float2 *psi, const float2 *g,
                       const float2 *eta_prev, double *part, const DevState *st, cudaStream_t s);
@@ -80,6 +80,8 @@ cudaError_t launch_nz_count(int P, const float *d, const int *perm, int K, int *
 cudaError_t launch_nz_fill(int P, const float *d, const int *perm, int K, const long long *off,
                            unsigned short *slot, float *dval, cudaStream_t s);
 bool pattern_supported(int P);
+// out[i] = log1p_fast(t[i]) (device self-test of the line-search logarithm)
+cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_t s);
 int ls_window_supported(int L);  // 1 if L is an instantiated window size
 
 // ---- object kernels (object_kernels.cu) ----

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_
 
 EXPORTED = ["pty_default_opts", "pty_create", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
             "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
-            "pty_cg_state_load", "pty_stage_times"]
+            "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p"]
 
 
 class PtyError(RuntimeError):
@@ -77,8 +77,9 @@ def load(build_if_missing: bool = True):
     lib.pty_cg_state_save.argtypes = [vp, vp]
     lib.pty_cg_state_load.argtypes = [vp, vp]
     lib.pty_stage_times.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
+    lib.pty_selftest_log1p.argtypes = [vp, vp, i32]
     for f in ("pty_create", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
-              "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times"):
+              "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -205,6 +206,11 @@ def pty_stage_times(ctx, reset=False):
     n = (ctypes.c_int64 * 4)()
     _check(lib, ctx, lib.pty_stage_times(ctx, ms, n, int(bool(reset))))
     return list(ms), list(n)
+
+
+def pty_selftest_log1p(t, out):
+    lib = load()
+    return _check(lib, None, lib.pty_selftest_log1p(_ptr(t, _F), _ptr(out, _F), int(t.numel() if hasattr(t, "numel") else t.size)))
 
 
 @dataclass

@@ -10,7 +10,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "pty.h")).read()
+    import glob
+
+    src = "".join(open(f).read() for f in glob.glob(os.path.join(ROOT, "include", "*.h")))
     return sorted(set(re.findall(r"PTY_API\s+[\w\s\*]*?\b(pty_\w+)\s*\(", src)))
 
 

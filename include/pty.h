@@ -184,6 +184,31 @@ PTY_API int pty_cg_state_load(pty_ctx *ctx, const void *host_buf);
  */
 PTY_API int pty_stage_times(pty_ctx *ctx, double ms[4], int64_t launches[4], int reset);
 
+/*
+ * Objective and gradient (as pty_gradient) without a context and without allocating any
+ * memory.  The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory -- code running inside another framework's fixed memory budget,
+ * a plug-in that must not grow the process's device footprint, or a path that must not
+ * take the implicit device synchronisation of cudaMalloc/cudaFree.
+ *   H, W, P, K   as in pty_create; P is 64 or 128; K <= 16384 and K*P*P <= 4194304.
+ *   probe, pos, data, psi   device pointers, layouts as in pty_create / pty_gradient
+ *                (data is the dense [K][P][P] array; positions in any order).
+ *   eps          the objective's guard (pty_opts.eps).
+ *   grad         device [H][W] complex output; F: device double output or NULL.
+ *   stream       cudaStream_t (as void*) the work runs on; the call synchronises it.
+ * The only scratch is a fixed 32.2 MiB device array inside the library, held on every
+ * device where the library's code is loaded until the process exits.  Every call shares
+ * it, so calls that overlap on the GPU race; calls ordered on one stream are safe.  The
+ * first call on a device looks up the array's address with that device current: make it
+ * before any stream capture.
+ * Returns PTY_OK; PTY_ERR_ARG for a size beyond the limits, a NULL or host pointer;
+ * PTY_ERR_BOUNDS if a position puts the patch outside the object (nothing is written);
+ * PTY_ERR_CUDA if a CUDA call failed.
+ */
+PTY_API int pty_gradient_noalloc(int32_t H, int32_t W, int32_t P, const float *probe, int32_t K,
+                                 const int32_t *pos, const float *data, double eps, const float *psi,
+                                 float *grad, double *F, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_
 
 EXPORTED = ["pty_default_opts", "pty_create", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
             "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
-            "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p"]
+            "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_gradient_noalloc"]
 
 
 class PtyError(RuntimeError):
@@ -78,8 +78,10 @@ def load(build_if_missing: bool = True):
     lib.pty_cg_state_load.argtypes = [vp, vp]
     lib.pty_stage_times.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.pty_selftest_log1p.argtypes = [vp, vp, i32]
+    lib.pty_gradient_noalloc.argtypes = [i32, i32, i32, vp, i32, vp, vp, dbl, vp, vp, vp, vp]
     for f in ("pty_create", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
-              "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p"):
+              "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p",
+              "pty_gradient_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -211,6 +213,17 @@ def pty_stage_times(ctx, reset=False):
 def pty_selftest_log1p(t, out):
     lib = load()
     return _check(lib, None, lib.pty_selftest_log1p(_ptr(t, _F), _ptr(out, _F), int(t.numel() if hasattr(t, "numel") else t.size)))
+
+
+def pty_gradient_noalloc(H, W, P, probe, K, pos, data, eps, psi, grad, F=None, stream=None):
+    """Objective and gradient without a context or any allocation; every array on the device.
+
+    Returns the raw status (PTY_OK, PTY_ERR_ARG, PTY_ERR_BOUNDS, PTY_ERR_CUDA).
+    """
+    lib = load()
+    return lib.pty_gradient_noalloc(H, W, P, _ptr(probe, _C), K, _ptr(pos, _I), _ptr(data, _F), float(eps),
+                                    _ptr(psi, _C), _ptr(grad, _C), _ptr(F, ("float64",)),
+                                    ctypes.c_void_p(stream) if stream else None)
 
 
 @dataclass

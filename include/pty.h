@@ -87,6 +87,8 @@ typedef struct {
     int32_t ls_window;   /* line-search trials evaluated per pass over the data: 4, 8, 16
                             or 32 (16); the accepted step does not depend on it */
     int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times) */
+    int32_t tile_config; /* pattern-kernel configuration: -1 = the library's choice for P,
+                            0.. = an index into pty_tile_configs' table for P */
 } pty_opts;
 
 typedef struct pty_ctx pty_ctx;
@@ -112,7 +114,7 @@ PTY_API void pty_default_opts(pty_opts *o);
  * Create a context for one reconstruction problem (the inputs of Algorithm 1).
  *   out    receives the context; *out is NULL on failure.
  *   H, W   object height and width, P <= H, P <= W.
- *   P      probe / detector size; 64 or 128.
+ *   P      probe / detector size; 64, 128 or 256.
  *   probe  [P][P] complex, copied.
  *   K      number of scan positions, >= 1.
  *   pos    [K][2] int32 (row, col) top-left corners, copied.

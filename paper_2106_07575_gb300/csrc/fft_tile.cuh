@@ -1,8 +1,9 @@
-// fft_tile.cuh -- batched 2-D DFT of one P x P complex tile held in shared memory.
+// fft_tile.cuh -- 2-D DFT of one P x P complex exit wave held in shared memory, by one CTA
+// or by a thread-block cluster of CS = P / R CTAs.
 //
 // This is the F of Eq. 1 (and F^H of Eq. 3) in the paper: the far-field transform of one
 // exit wave.  Each 1-D transform of length P = R1 * R2 (R1 = 16, R2 = P/16) is split
-// Cooley-Tukey style into two in-place passes over the tile:
+// Cooley-Tukey style into two in-place passes over the lines of a buffer:
 //   stride pass: radix-16 DFT over the elements n2 + R2*n1 (n1 = 0..15), then the
 //                twiddle W_P^{n2 k1}, written back to the same slots;
 //   block pass : radix-R2 DFT over the contiguous block n2 + R2*k1 (n2 = 0..R2-1),
@@ -10,11 +11,17 @@
 // Forward (stride, block) leaves frequency k1 + R1*k2 in slot k2 + R2*k1 ("permuted"
 // order); the inverse runs (block, stride) with conjugate twiddles applied before the
 // radix-16 step and takes the permuted order back to natural order.  Both passes are in
-// place, so a thread keeps one small line segment in registers at a time and only a
-// barrier separates passes.  The tile row stride is P + 1 float2: with lines mapped to
-// consecutive threads (rows for row passes, columns for column passes) every warp access
-// is free of shared-memory bank conflicts.
+// place: a thread keeps one line segment in registers at a time and a barrier separates
+// passes.
+//
+// Layout.  CTA c of a cluster owns the R rows [cR, cR+R) during the row passes ("row
+// slab", row stride P+1) and the R columns [cR, cR+R) during the column passes ("column
+// slab", row stride R+1).  The change of slab is an all-to-all through distributed shared
+// memory (exchange_*).  With R = P the two layouts coincide and no exchange happens.
+// Lines are mapped to consecutive threads in both layouts, which keeps every warp access
+// free of shared-memory bank conflicts.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 namespace pty {
@@ -133,11 +140,12 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[N])
     }
 }
 
+// Slot order of one transform of length P.
 template <int P>
 struct Tile {
     static constexpr int R1 = 16;
     static constexpr int R2 = P / 16;
-    static constexpr int LD = P + 1;  // row stride in float2
+    static constexpr int LD = P + 1;  // row stride of the single-CTA tile (R = P)
     static constexpr int ELEMS = P * LD;
     // natural frequency held by slot q after a forward transform
     static __device__ __forceinline__ int nat(int q) { return q / R2 + R1 * (q % R2); }
@@ -145,91 +153,176 @@ struct Tile {
     static __device__ __forceinline__ int slot(int k) { return k / R1 + R2 * (k % R1); }
 };
 
-// Address of element e of line `line`: rows are contiguous, columns stride LD.
-template <int P, bool ROWS>
-__device__ __forceinline__ int taddr(int line, int e)
-{
-    return ROWS ? line * Tile<P>::LD + e : e * Tile<P>::LD + line;
-}
+// Geometry of the slab decomposition: CS = P / R CTAs per pattern.
+template <int P, int R>
+struct Slab {
+    static_assert(P % R == 0, "R must divide P");
+    static constexpr int CS = P / R;
+    static constexpr int LDA = P + 1;  // row slab: R rows x P columns
+    static constexpr int LDB = R + 1;  // column slab: P rows x R columns
+    static constexpr int ELEMS = (R * LDA > P * LDB) ? R * LDA : P * LDB;
+    static constexpr int PER_CTA = P * R;  // values owned by one CTA
+};
 
-// Forward stride pass: radix-16 over n1, then twiddle W_P^{n2 k1} (tw = exp(-2 pi i m/P)).
-template <int P, int NT, bool ROWS>
-__device__ __forceinline__ void pass_stride_fwd(float2 *tile, const float2 *tw)
+// Stride pass over NLINES lines of length P; element e of line l at buf[l * LS + e * ES].
+template <int P, int NT, int NLINES, int LS, int ES, int SIGN>
+__device__ __forceinline__ void pass_stride(float2 *buf, const float2 *tw)
 {
     constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2;
-    for (int t = threadIdx.x; t < P * R2; t += NT) {
-        const int line = t % P, n2 = t / P;
+    for (int t = threadIdx.x; t < NLINES * R2; t += NT) {
+        const int line = t % NLINES, n2 = t / NLINES;
+        float2 *b = buf + line * LS + n2 * ES;
         float2 x[R1];
 #pragma unroll
-        for (int n1 = 0; n1 < R1; n1++) x[n1] = tile[taddr<P, ROWS>(line, n2 + R2 * n1)];
-        dft_reg<R1, -1>(x);
+        for (int n1 = 0; n1 < R1; n1++) x[n1] = b[(R2 * n1) * ES];
+        if constexpr (SIGN < 0) {
+            dft_reg<R1, -1>(x);
 #pragma unroll
-        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmul(x[k1], tw[(n2 * k1) & (P - 1)]);
+            for (int k1 = 1; k1 < R1; k1++) x[k1] = cmul(x[k1], tw[(n2 * k1) & (P - 1)]);
+        } else {
 #pragma unroll
-        for (int k1 = 0; k1 < R1; k1++) tile[taddr<P, ROWS>(line, n2 + R2 * k1)] = x[k1];
+            for (int k1 = 1; k1 < R1; k1++) x[k1] = cmulc(x[k1], tw[(n2 * k1) & (P - 1)]);
+            dft_reg<R1, +1>(x);
+        }
+#pragma unroll
+        for (int n1 = 0; n1 < R1; n1++) b[(R2 * n1) * ES] = x[n1];
     }
 }
 
-// Inverse stride pass: conjugate twiddle W_P^{-n2 k1}, then inverse radix-16.
-template <int P, int NT, bool ROWS>
-__device__ __forceinline__ void pass_stride_inv(float2 *tile, const float2 *tw)
+// Block pass (either direction) over NLINES lines.
+template <int P, int NT, int NLINES, int LS, int ES, int SIGN>
+__device__ __forceinline__ void pass_block(float2 *buf)
 {
     constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2;
-    for (int t = threadIdx.x; t < P * R2; t += NT) {
-        const int line = t % P, n2 = t / P;
-        float2 x[R1];
-#pragma unroll
-        for (int k1 = 0; k1 < R1; k1++) x[k1] = tile[taddr<P, ROWS>(line, n2 + R2 * k1)];
-#pragma unroll
-        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmulc(x[k1], tw[(n2 * k1) & (P - 1)]);
-        dft_reg<R1, +1>(x);
-#pragma unroll
-        for (int n1 = 0; n1 < R1; n1++) tile[taddr<P, ROWS>(line, n2 + R2 * n1)] = x[n1];
-    }
-}
-
-// Block pass (either direction): radix-R2 over the contiguous block of R2 slots.
-template <int P, int NT, bool ROWS, int SIGN>
-__device__ __forceinline__ void pass_block(float2 *tile)
-{
-    constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2;
-    for (int t = threadIdx.x; t < P * R1; t += NT) {
-        const int line = t % P, k1 = t / P;
+    for (int t = threadIdx.x; t < NLINES * R1; t += NT) {
+        const int line = t % NLINES, k1 = t / NLINES;
+        float2 *b = buf + line * LS + (R2 * k1) * ES;
         float2 x[R2];
 #pragma unroll
-        for (int j = 0; j < R2; j++) x[j] = tile[taddr<P, ROWS>(line, j + R2 * k1)];
+        for (int j = 0; j < R2; j++) x[j] = b[j * ES];
         dft_reg<R2, SIGN>(x);
 #pragma unroll
-        for (int j = 0; j < R2; j++) tile[taddr<P, ROWS>(line, j + R2 * k1)] = x[j];
+        for (int j = 0; j < R2; j++) b[j * ES] = x[j];
     }
 }
 
-// Unnormalised forward 2-D DFT: natural order in, permuted order out.  Caller syncs before.
+// Row passes over the R rows of a row slab; caller syncs before; ends with a barrier.
+template <int P, int R, int NT, int SIGN>
+__device__ __forceinline__ void rows_fft(float2 *buf, const float2 *tw)
+{
+    constexpr int LDA = Slab<P, R>::LDA;
+    if constexpr (SIGN < 0) {
+        pass_stride<P, NT, R, LDA, 1, -1>(buf, tw);
+        __syncthreads();
+        pass_block<P, NT, R, LDA, 1, -1>(buf);
+    } else {
+        pass_block<P, NT, R, LDA, 1, +1>(buf);
+        __syncthreads();
+        pass_stride<P, NT, R, LDA, 1, +1>(buf, tw);
+    }
+    __syncthreads();
+}
+
+// Column passes over the R columns of a column slab; caller syncs before; ends with a barrier.
+template <int P, int R, int NT, int SIGN>
+__device__ __forceinline__ void cols_fft(float2 *buf, const float2 *tw)
+{
+    constexpr int LDB = Slab<P, R>::LDB;
+    if constexpr (SIGN < 0) {
+        pass_stride<P, NT, R, 1, LDB, -1>(buf, tw);
+        __syncthreads();
+        pass_block<P, NT, R, 1, LDB, -1>(buf);
+    } else {
+        pass_block<P, NT, R, 1, LDB, +1>(buf);
+        __syncthreads();
+        pass_stride<P, NT, R, 1, LDB, +1>(buf, tw);
+    }
+    __syncthreads();
+}
+
+// Row slab -> column slab across the cluster (all CTAs of the cluster call it).
+// Every value is read into registers, the cluster synchronises (all reads done, the
+// buffers are free), every value is stored into its owner's buffer, the cluster
+// synchronises again (all stores visible).
+template <int P, int R, int NT>
+__device__ __forceinline__ void exchange_to_cols(float2 *buf)
+{
+    if constexpr (P != R) {
+        namespace cg = cooperative_groups;
+        constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, N = P * R / NT;
+        cg::cluster_group cl = cg::this_cluster();
+        const int c = (int)cl.block_rank();
+        float2 v[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            const int j = threadIdx.x + NT * k, rl = j / P, qx = j % P;
+            v[k] = buf[rl * LDA + qx];
+        }
+        cl.sync();
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            const int j = threadIdx.x + NT * k, rl = j / P, qx = j % P;
+            float2 *dst = cl.map_shared_rank(buf, qx / R);
+            dst[(c * R + rl) * LDB + (qx % R)] = v[k];
+        }
+        cl.sync();
+    }
+}
+
+// Column slab -> row slab across the cluster.
+template <int P, int R, int NT>
+__device__ __forceinline__ void exchange_to_rows(float2 *buf)
+{
+    if constexpr (P != R) {
+        namespace cg = cooperative_groups;
+        constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, N = P * R / NT;
+        cg::cluster_group cl = cg::this_cluster();
+        const int c = (int)cl.block_rank();
+        float2 v[N];
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            const int j = threadIdx.x + NT * k, r = j / R, xl = j % R;
+            v[k] = buf[r * LDB + xl];
+        }
+        cl.sync();
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            const int j = threadIdx.x + NT * k, r = j / R, xl = j % R;
+            float2 *dst = cl.map_shared_rank(buf, r / R);
+            dst[(r % R) * LDA + (c * R + xl)] = v[k];
+        }
+        cl.sync();
+    }
+}
+
+// Unnormalised forward 2-D DFT: natural order in (row slab), permuted order out (column slab).
+template <int P, int R, int NT>
+__device__ __forceinline__ void fft2_fwd(float2 *buf, const float2 *tw)
+{
+    rows_fft<P, R, NT, -1>(buf, tw);
+    exchange_to_cols<P, R, NT>(buf);
+    cols_fft<P, R, NT, -1>(buf, tw);
+}
+
+// Unnormalised inverse 2-D DFT: permuted order in (column slab), natural order out (row slab).
+template <int P, int R, int NT>
+__device__ __forceinline__ void fft2_inv(float2 *buf, const float2 *tw)
+{
+    cols_fft<P, R, NT, +1>(buf, tw);
+    exchange_to_rows<P, R, NT>(buf);
+    rows_fft<P, R, NT, +1>(buf, tw);
+}
+
+// Single-CTA forms (R = P), kept for callers that hold the whole tile.
 template <int P, int NT>
 __device__ __forceinline__ void fft2_fwd(float2 *tile, const float2 *tw)
 {
-    pass_stride_fwd<P, NT, true>(tile, tw);
-    __syncthreads();
-    pass_block<P, NT, true, -1>(tile);
-    __syncthreads();
-    pass_stride_fwd<P, NT, false>(tile, tw);
-    __syncthreads();
-    pass_block<P, NT, false, -1>(tile);
-    __syncthreads();
+    fft2_fwd<P, P, NT>(tile, tw);
 }
-
-// Unnormalised inverse 2-D DFT: permuted order in, natural order out.  Caller syncs before.
 template <int P, int NT>
 __device__ __forceinline__ void fft2_inv(float2 *tile, const float2 *tw)
 {
-    pass_block<P, NT, false, +1>(tile);
-    __syncthreads();
-    pass_stride_inv<P, NT, false>(tile, tw);
-    __syncthreads();
-    pass_block<P, NT, true, +1>(tile);
-    __syncthreads();
-    pass_stride_inv<P, NT, true>(tile, tw);
-    __syncthreads();
+    fft2_inv<P, P, NT>(tile, tw);
 }
 
 }  // namespace pty

@@ -1,0 +1,396 @@
+// pattern_kernels.cuh -- the per-scan-position passes of ML-CG.  One pattern is owned by a
+// thread-block cluster of CS = P / R CTAs (CS = 1: a single CTA) that keeps the P x P exit
+// wave in shared memory and runs the 2-D DFTs of fft_tile.cuh on it.
+//
+//   k_forward      Eq. 1: u = F(p * patch(psi)) written out (pty_forward)
+//   k_adjoint_fft  the F^H and conj(p) factors of G^H (pty_adjoint)
+//   k_grad         GRAD stage: gather x probe -> F -> likelihood residual (Eq. 3) and the
+//                  objective terms (Eq. 2) -> F^H -> x conj(p); one patch-sized result
+//                  per pattern, summed into the object by the scatter kernel
+//   k_ls           LS stage: v = G eta for one pattern, then the change of the objective
+//                  F(psi + gamma eta) - F(psi) (Eq. 2, 7) for a window of candidate steps
+//                  gamma, using G(psi + gamma eta) = u + gamma v with u kept by k_grad
+//   k_nz_*         create time: the compact list of detector pixels with counts
+//
+// The forward DFT leaves the spectrum in the permuted slot order of fft_tile.cuh, in
+// column slabs; the measured data are stored in that order ("entries", one contiguous
+// range per CTA of a pattern), and the inverse DFT returns to natural order, so no
+// separate reordering pass exists.  Per-pattern sums are produced per CTA; the small
+// reduction kernels add the CS partials of a pattern like any others.
+#pragma once
+#include "fft_tile.cuh"
+#include "mathx.cuh"
+#include "pty_internal.h"
+#include "reduce.cuh"
+
+namespace pty {
+
+template <int P, int R>
+constexpr size_t slab_bytes()
+{
+    return sizeof(float2) * (size_t)(Slab<P, R>::ELEMS + P);
+}
+
+// Pattern and cluster rank of this CTA.
+template <int P, int R>
+__device__ __forceinline__ void who(int &i, int &c)
+{
+    i = blockIdx.x / Slab<P, R>::CS;
+    c = blockIdx.x % Slab<P, R>::CS;
+}
+
+template <int P, int NT>
+__device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restrict__ g_tw)
+{
+    for (int m = threadIdx.x; m < P; m += NT) tw[m] = g_tw[m];
+}
+
+// Row slab of Q psi: rows [cR, cR+R) of probe[y][x] * src[r0 + y][c0 + x]  (Eq. 1)
+template <int P, int R, int NT>
+__device__ __forceinline__ void gather_rows(float2 *buf, const float2 *__restrict__ probe,
+                                            const float2 *__restrict__ src, int W, int r0, int c0, int c)
+{
+    constexpr int LDA = Slab<P, R>::LDA;
+    for (int e = threadIdx.x; e < R * P; e += NT) {
+        const int rl = e / P, x = e % P, y = c * R + rl;
+        buf[rl * LDA + x] = cmul(__ldg(probe + y * P + x), __ldg(src + (size_t)(r0 + y) * W + (c0 + x)));
+    }
+}
+
+// Kahan-compensated single-precision accumulation (per thread; the block sum is FP64).
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
+{
+    const float y = x - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// Cluster-wide barrier so that no CTA touches a peer's shared memory before the peer runs.
+template <int P, int R>
+__device__ __forceinline__ void cluster_start()
+{
+    if constexpr (P != R) cooperative_groups::this_cluster().sync();
+}
+
+// ------------------------------------------------------------------------------------
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_forward(PatternArgs a, const float2 *__restrict__ psi,
+                                                float2 *__restrict__ out)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
+    int i, c;
+    who<P, R>(i, c);
+    const int2 rc = a.pos[i];
+    cluster_start<P, R>();
+    load_twiddles<P, NT>(tw, a.tw);
+    gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+    __syncthreads();
+    fft2_fwd<P, R, NT>(buf, tw);
+    float2 *o = out + (size_t)a.perm[i] * P * P;
+    for (int e = threadIdx.x; e < P * R; e += NT) {
+        const int r = e / R, xl = e % R;
+        o[Tile<P>::nat(r) * P + Tile<P>::nat(c * R + xl)] = buf[r * Slab<P, R>::LDB + xl];
+    }
+}
+
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_adjoint_fft(PatternArgs a, const float2 *__restrict__ y,
+                                                    float2 *__restrict__ w)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB;
+    float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
+    int i, c;
+    who<P, R>(i, c);
+    cluster_start<P, R>();
+    const float2 *yi = y + (size_t)a.perm[i] * P * P;
+    load_twiddles<P, NT>(tw, a.tw);
+    for (int e = threadIdx.x; e < P * R; e += NT) {
+        const int r = e / R, xl = e % R;
+        buf[r * LDB + xl] = __ldg(yi + Tile<P>::nat(r) * P + Tile<P>::nat(c * R + xl));
+    }
+    __syncthreads();
+    fft2_inv<P, R, NT>(buf, tw);
+    float2 *wi = w + (size_t)i * P * P;
+    for (int e = threadIdx.x; e < R * P; e += NT) {
+        const int rl = e / P, x = e % P, yy = c * R + rl;
+        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
+    }
+}
+
+// GRAD pattern pass (Eq. 2 and 3 for one pattern).
+//   f = sum_j |u_j|^2 - sum_{entries} d log(|u|^2 + eps)
+//   r = u, except r = u (1 - d / (|u|^2 + eps)) at the entries
+//   w = conj(p) F^H r;  u at the entries is kept for the line search of this iteration.
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__restrict__ psi,
+                                             float2 *__restrict__ w, double *__restrict__ fpart,
+                                             const DevState *__restrict__ st)
+{
+    if (st && st->stalled) return;
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
+    __shared__ double red[NT / 32];
+    __shared__ double tot[1];
+    float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
+    int i, c;
+    who<P, R>(i, c);
+    const int2 rc = a.pos[i];
+    cluster_start<P, R>();
+    load_twiddles<P, NT>(tw, a.tw);
+    gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+    __syncthreads();
+    fft2_fwd<P, R, NT>(buf, tw);
+    float f = 0.0f;
+    for (int e = threadIdx.x; e < P * R; e += NT) {
+        const float2 u = buf[(e / R) * LDB + (e % R)];
+        f = fmaf(u.x, u.x, fmaf(u.y, u.y, f));
+    }
+    __syncthreads();
+    const long long e0 = a.nz_off[i * CS + c], e1 = a.nz_off[i * CS + c + 1];
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+        const int s = a.nz_slot[e];
+        const float dv = a.nz_d[e];
+        float2 *pu = buf + (s / R) * LDB + (s % R);
+        float2 u = *pu;
+        a.nz_u[e] = u;
+        const float den = fmaf(u.x, u.x, u.y * u.y) + a.eps;
+        f -= dv * logf(den);
+        const float sc = 1.0f - dv / den;
+        u.x *= sc;
+        u.y *= sc;
+        *pu = u;
+    }
+    double v[1] = {(double)f};
+    block_sum<NT, 1>(v, red, tot);  // its barriers also order the residual writes before F^H
+    if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
+    fft2_inv<P, R, NT>(buf, tw);
+    float2 *wi = w + (size_t)i * P * P;
+    for (int e = threadIdx.x; e < R * P; e += NT) {
+        const int rl = e / P, x = e % P, yy = c * R + rl;
+        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
+    }
+}
+
+// LS pattern pass for a window of L candidate steps gamma_l (Eq. 7 with Eq. 2):
+//   F(psi + gamma eta) - F(psi) = sum_j q_j - sum_{entries} d log1p(q / (|u|^2 + eps)),
+//   q_j = |u_j + gamma v_j|^2 - |u_j|^2 = gamma (2 Re conj(u_j) v_j + gamma |v_j|^2),
+// with u = G psi (kept by the GRAD pass at the entries) and v = G eta (one forward DFT).
+// Over all pixels, sum conj(u) v and sum |v|^2 equal P^2 sum conj(x) y and P^2 sum |y|^2
+// of the real-space exit waves x = p psi / P, y = p eta / P (Parseval); the d = 0 part is
+// that total minus the entries' part.
+template <int P, int R, int NT, int L>
+__global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restrict__ psi,
+                                           const float2 *__restrict__ g, const float2 *__restrict__ ep,
+                                           double *__restrict__ part, const DevState *__restrict__ st)
+{
+    if (st->stalled || st->decided) return;
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
+    __shared__ double red[(NT / 32) * (L + 2)];
+    __shared__ double tot[L + 2];
+    float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
+    int i, c;
+    who<P, R>(i, c);
+    const int2 rc = a.pos[i];
+    const float alpha = (float)st->alpha;
+    float gam[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) gam[l] = (float)st->cand[l];
+    cluster_start<P, R>();
+    load_twiddles<P, NT>(tw, a.tw);
+
+    // y = p eta / P into the row slab, with the real-space sums of Parseval's identity
+    float sb = 0.f, sbc = 0.f, scc = 0.f, sccc = 0.f;
+    for (int e = threadIdx.x; e < R * P; e += NT) {
+        const int rl = e / P, x = e % P, y = c * R + rl;
+        const size_t o = (size_t)(rc.x + y) * a.W + (rc.y + x);
+        const float2 gv = __ldg(g + o), ev = __ldg(ep + o), pv = __ldg(a.probe + y * P + x);
+        const float2 eta = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
+        const float2 yv = cmul(pv, eta), xv = cmul(pv, __ldg(psi + o));
+        buf[rl * LDA + x] = yv;
+        kahan_add(sb, sbc, fmaf(xv.x, yv.x, xv.y * yv.y));
+        kahan_add(scc, sccc, fmaf(yv.x, yv.x, yv.y * yv.y));
+    }
+    __syncthreads();
+    fft2_fwd<P, R, NT>(buf, tw);
+
+    float bp = 0.0f, cp = 0.0f, acc[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) acc[l] = 0.0f;
+    const long long e0 = a.nz_off[i * CS + c], e1 = a.nz_off[i * CS + c + 1];
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+        const int s = a.nz_slot[e];
+        const float dv = a.nz_d[e];
+        const float2 u = a.nz_u[e];
+        const float2 v = buf[(s / R) * LDB + (s % R)];
+        const float au = fmaf(u.x, u.x, u.y * u.y);
+        const float bu = fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
+        const float cu = fmaf(v.x, v.x, v.y * v.y);
+        bp += bu;
+        cp += cu;
+        const float inv = 1.0f / (au + a.eps);
+        const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
+            const float t = fmaxf(q * inv, tmin);
+            acc[l] += q - dv * log1p_fast(t);
+        }
+    }
+    constexpr double PP = (double)P * (double)P;
+    double vals[L + 2];
+    vals[0] = PP * ((double)sb - (double)sbc) - (double)bp;
+    vals[1] = PP * ((double)scc - (double)sccc) - (double)cp;
+#pragma unroll
+    for (int l = 0; l < L; l++) vals[2 + l] = acc[l];
+    block_sum<NT, L + 2>(vals, red, tot);
+    const int KC = a.K * CS;
+    if (threadIdx.x < L + 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // [L+2][K*CS]
+}
+
+// Natural-order index of local slot s of CTA c (column slab, row-major over P x R).
+template <int P, int R>
+__device__ __forceinline__ int slot_to_natural(int s, int c)
+{
+    return Tile<P>::nat(s / R) * P + Tile<P>::nat(c * R + (s % R));
+}
+
+// Counts per (pattern, CTA) chunk.
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_nz_count(const float *__restrict__ d, const int *__restrict__ perm,
+                                                 int *__restrict__ cnt)
+{
+    __shared__ int red[NT / 32];
+    constexpr int CS = Slab<P, R>::CS;
+    const int i = blockIdx.x / CS, c = blockIdx.x % CS;
+    const float *dk = d + (size_t)perm[i] * P * P;
+    int n = 0;
+    for (int s = threadIdx.x; s < P * R; s += NT) n += dk[slot_to_natural<P, R>(s, c)] > 0.0f;
+    n = __reduce_add_sync(0xffffffffu, n);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w2 = 0; w2 < NT / 32; w2++) t += red[w2];
+        cnt[blockIdx.x] = t;
+    }
+}
+
+// Ordered compaction: entries of chunk (pattern i, CTA c) in ascending local slot order.
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_nz_fill(const float *__restrict__ d, const int *__restrict__ perm,
+                                                const long long *__restrict__ off, unsigned short *__restrict__ slot,
+                                                float *__restrict__ dval)
+{
+    __shared__ int wsum[NT / 32];
+    constexpr int CS = Slab<P, R>::CS;
+    const int i = blockIdx.x / CS, c = blockIdx.x % CS;
+    const float *dk = d + (size_t)perm[i] * P * P;
+    const long long base = off[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long running = 0;
+    for (int s0 = 0; s0 < P * R; s0 += NT) {
+        const int s = s0 + threadIdx.x;
+        const float v = dk[slot_to_natural<P, R>(s, c)];
+        const bool flag = v > 0.0f;
+        const unsigned m = __ballot_sync(0xffffffffu, flag);
+        if (lane == 0) wsum[warp] = __popc(m);
+        __syncthreads();
+        int woff = 0, total = 0;
+        for (int w2 = 0; w2 < NT / 32; w2++) {
+            woff += (w2 < warp) ? wsum[w2] : 0;
+            total += wsum[w2];
+        }
+        if (flag) {
+            const long long p = base + running + woff + __popc(m & ((1u << lane) - 1u));
+            slot[p] = (unsigned short)s;
+            dval[p] = v;
+        }
+        running += total;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Launch helpers: cluster launch when CS > 1.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pattern(void (*kern)(KArgs...), int nblocks, int nthreads, size_t smem, int cs, cudaStream_t s,
+                           Args... args)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3((unsigned)nthreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    if (cs > 1) {
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// All launchers of one (P, R, NT) configuration.
+template <int P, int R, int NT>
+struct PatternOps {
+    static constexpr int CS = Slab<P, R>::CS;
+    static cudaError_t forward(const PatternArgs &a, const float2 *psi, float2 *out, cudaStream_t s)
+    {
+        return launch_pattern(k_forward<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, psi, out);
+    }
+    static cudaError_t adjoint(const PatternArgs &a, const float2 *y, float2 *w, cudaStream_t s)
+    {
+        return launch_pattern(k_adjoint_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, y, w);
+    }
+    static cudaError_t grad(const PatternArgs &a, const float2 *psi, float2 *w, double *fpart, const DevState *st,
+                            cudaStream_t s)
+    {
+        return launch_pattern(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, psi, w, fpart, st);
+    }
+    template <int L>
+    static cudaError_t ls_l(const PatternArgs &a, const float2 *psi, const float2 *g, const float2 *ep, double *part,
+                            const DevState *st, cudaStream_t s)
+    {
+        return launch_pattern(k_ls<P, R, NT, L>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, psi, g, ep, part, st);
+    }
+    static cudaError_t ls(const PatternArgs &a, int L, const float2 *psi, const float2 *g, const float2 *ep,
+                          double *part, const DevState *st, cudaStream_t s)
+    {
+        switch (L) {
+        case 4: return ls_l<4>(a, psi, g, ep, part, st, s);
+        case 8: return ls_l<8>(a, psi, g, ep, part, st, s);
+        case 16: return ls_l<16>(a, psi, g, ep, part, st, s);
+        case 32: return ls_l<32>(a, psi, g, ep, part, st, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    static cudaError_t nz_count(const float *d, const int *perm, int K, int *cnt, cudaStream_t s)
+    {
+        k_nz_count<P, R, NT><<<K * CS, NT, 0, s>>>(d, perm, cnt);
+        return cudaGetLastError();
+    }
+    static cudaError_t nz_fill(const float *d, const int *perm, int K, const long long *off, unsigned short *slot,
+                               float *dval, cudaStream_t s)
+    {
+        k_nz_fill<P, R, NT><<<K * CS, NT, 0, s>>>(d, perm, off, slot, dval);
+        return cudaGetLastError();
+    }
+};
+
+template <int P, int R, int NT>
+constexpr PatternImpl make_impl()
+{
+    using O = PatternOps<P, R, NT>;
+    return PatternImpl{P, R, NT, &O::forward, &O::adjoint, &O::grad, &O::ls, &O::nz_count, &O::nz_fill};
+}
+
+}  // namespace pty

@@ -31,6 +31,8 @@ struct pty_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
     int H = 0, W = 0, P = 0, K = 0;
+    int CS = 1;                              // CTAs per pattern of the chosen configuration
+    const pty::PatternImpl *impl = nullptr;  // pattern-kernel configuration
     pty_opts opts{};
     std::string err;
 
@@ -39,7 +41,7 @@ struct pty_ctx {
     float2 *tw = nullptr;     // [P]
     int2 *pos = nullptr;      // [K] sorted
     int *perm = nullptr;      // [K]
-    long long *nz_off = nullptr;      // [K+1]
+    long long *nz_off = nullptr;      // [K * CS + 1]
     unsigned short *nz_slot = nullptr;  // [E]
     float *nz_d = nullptr;            // [E]
     float2 *nz_u = nullptr;           // [E]
@@ -49,9 +51,9 @@ struct pty_ctx {
 
     // CG state and scratch (device)
     float2 *w = nullptr;         // [K][P][P] per-pattern adjoint results
-    double *fpart = nullptr;     // [K]
+    double *fpart = nullptr;     // [K * CS]
     double *part_sc = nullptr;   // [ntiles][2]
-    double *part_ls = nullptr;   // [K][L+2]
+    double *part_ls = nullptr;   // [L+2][K * CS]
     float2 *g = nullptr, *g_prev = nullptr, *eta_prev = nullptr;  // [H][W]
     DevState *st = nullptr;
     double *dscalar = nullptr;
@@ -273,6 +275,7 @@ void pty_default_opts(pty_opts *o)
     o->eps = 0.1;
     o->ls_window = 16;
     o->flags = 0;
+    o->tile_config = -1;
 }
 
 const char *pty_last_error(const pty_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
@@ -296,7 +299,7 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     if (!out) return fail(nullptr, PTY_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (!probe || !pos || !data) return fail(nullptr, PTY_ERR_ARG, "probe, pos and data must be non-NULL");
-    if (!pty::pattern_supported(P)) return fail(nullptr, PTY_ERR_ARG, "P=%d not supported (64 or 128)", P);
+    if (!pty::pattern_supported(P)) return fail(nullptr, PTY_ERR_ARG, "P=%d not supported (64, 128 or 256)", P);
     if (H < P || W < P) return fail(nullptr, PTY_ERR_ARG, "object %dx%d smaller than probe %d", H, W, P);
     if (K < 1) return fail(nullptr, PTY_ERR_ARG, "K=%d < 1", K);
     if ((int64_t)H * W > (int64_t)1 << 31) return fail(nullptr, PTY_ERR_ARG, "object too large");
@@ -332,6 +335,18 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     c->P = P;
     c->K = K;
     c->opts = o;
+    {
+        const pty::PatternImpl *impls = nullptr;
+        const int n = pty::pattern_impls(P, &impls);
+        const int pick = (o.tile_config >= 0 && o.tile_config < n) ? o.tile_config : 0;
+        if (n == 0 || o.tile_config >= n) {
+            delete c;
+            return fail(nullptr, PTY_ERR_ARG, "tile_config %d not available for P=%d (%d configurations)",
+                        o.tile_config, P, n);
+        }
+        c->impl = &impls[pick];
+        c->CS = P / impls[pick].R;
+    }
 
     auto bail = [&](int code) {
         g_create_err = c->err;
@@ -407,9 +422,9 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     CKC(dalloc(&c->tile_start, (size_t)ntiles + 1));
     CKC(dalloc(&c->tile_list, std::max<size_t>(list.size(), 1)));
     CKC(dalloc(&c->w, (size_t)K * PP));
-    CKC(dalloc(&c->fpart, (size_t)K));
+    CKC(dalloc(&c->fpart, (size_t)K * c->CS));
     CKC(dalloc(&c->part_sc, (size_t)ntiles * 2));
-    CKC(dalloc(&c->part_ls, (size_t)K * (32 + 2)));
+    CKC(dalloc(&c->part_ls, (size_t)K * c->CS * (32 + 2)));
     CKC(dalloc(&c->g, HW));
     CKC(dalloc(&c->g_prev, HW));
     CKC(dalloc(&c->eta_prev, HW));
@@ -441,14 +456,15 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     };
     int *flag = (int *)c->dscalar;
     int *dcnt = nullptr;
-    std::vector<int> hcnt(K);
+    const int KC = K * c->CS;
+    std::vector<int> hcnt(KC);
     int hflag = 0;
     cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
     if (ce == cudaSuccess) ce = pty::launch_check_data(dd, (size_t)K * PP, flag, c->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-    if (ce == cudaSuccess) ce = dalloc(&dcnt, (size_t)K);
-    if (ce == cudaSuccess) ce = pty::launch_nz_count(P, dd, c->perm, K, dcnt, c->stream);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int) * K, cudaMemcpyDeviceToHost, c->stream);
+    if (ce == cudaSuccess) ce = dalloc(&dcnt, (size_t)KC);
+    if (ce == cudaSuccess) ce = c->impl->nz_count(dd, c->perm, K, dcnt, c->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int) * KC, cudaMemcpyDeviceToHost, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (dcnt) cudaFree(dcnt);
     if (ce != cudaSuccess) {
@@ -459,17 +475,17 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
         free_tmp();
         return bail(fail(c, PTY_ERR_NONFINITE, "measured data holds NaN, Inf or negative values"));
     }
-    std::vector<long long> hoff(K + 1, 0);
-    for (int i = 0; i < K; i++) hoff[i + 1] = hoff[i] + hcnt[i];
-    c->n_entries = hoff[K];
+    std::vector<long long> hoff(KC + 1, 0);
+    for (int i = 0; i < KC; i++) hoff[i + 1] = hoff[i] + hcnt[i];
+    c->n_entries = hoff[KC];
     const size_t E = (size_t)std::max<long long>(c->n_entries, 1);
-    ce = dalloc(&c->nz_off, (size_t)K + 1);
+    ce = dalloc(&c->nz_off, (size_t)KC + 1);
     if (ce == cudaSuccess) ce = dalloc(&c->nz_slot, E);
     if (ce == cudaSuccess) ce = dalloc(&c->nz_d, E);
     if (ce == cudaSuccess) ce = dalloc(&c->nz_u, E);
     if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (K + 1), cudaMemcpyHostToDevice, c->stream);
-    if (ce == cudaSuccess) ce = pty::launch_nz_fill(P, dd, c->perm, K, c->nz_off, c->nz_slot, c->nz_d, c->stream);
+        ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (KC + 1), cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess) ce = c->impl->nz_fill(dd, c->perm, K, c->nz_off, c->nz_slot, c->nz_d, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     free_tmp();
     if (ce != cudaSuccess)
@@ -491,7 +507,7 @@ int pty_forward(pty_ctx *c, const float *psi, float *out)
     const bool dev_out = is_device_ptr(out);
     if (!dev_out && (st = ensure_stage_pat(c))) return st;
     float2 *dout = dev_out ? (float2 *)out : c->stage_pat;
-    CK(pty::launch_forward(c->P, pattern_args(c), dpsi, dout, c->stream));
+    CK(c->impl->forward(pattern_args(c), dpsi, dout, c->stream));
     if (!dev_out)
         CK(cudaMemcpyAsync(out, dout, sizeof(float2) * (size_t)c->K * c->P * c->P, cudaMemcpyDeviceToHost,
                            c->stream));
@@ -514,7 +530,7 @@ int pty_adjoint(pty_ctx *c, const float *y, float *x)
     const bool dev_x = is_device_ptr(x);
     float2 *dx = dev_x ? (float2 *)x : c->stage_obj;
     pty::PatternArgs a = pattern_args(c);
-    CK(pty::launch_adjoint_fft(c->P, a, dy, c->w, c->stream));
+    CK(c->impl->adjoint(a, dy, c->w, c->stream));
     CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, dx, 0, nullptr, nullptr, nullptr, nullptr, c->stream));
     if (!dev_x) CK(cudaMemcpyAsync(x, dx, sizeof(float2) * (size_t)c->H * c->W, cudaMemcpyDeviceToHost, c->stream));
     return sync(c);
@@ -529,11 +545,11 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
     const float2 *dpsi;
     if ((st = obj_in(c, psi, c->stage_obj, &dpsi))) return st;
     pty::PatternArgs a = pattern_args(c);
-    CK(pty::launch_grad(c->P, a, dpsi, c->w, c->fpart, nullptr, c->stream));
+    CK(c->impl->grad(a, dpsi, c->w, c->fpart, nullptr, c->stream));
     const bool dev_g = grad && is_device_ptr(grad);
     float2 *dg = dev_g ? (float2 *)grad : c->stage_obj2;
     CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, dg, 0, nullptr, nullptr, nullptr, nullptr, c->stream));
-    CK(pty::launch_sum(c->fpart, c->K, c->dscalar, c->stream));
+    CK(pty::launch_sum(c->fpart, c->K * c->CS, c->dscalar, c->stream));
     if (grad && !dev_g)
         CK(cudaMemcpyAsync(grad, dg, sizeof(float2) * (size_t)c->H * c->W, cudaMemcpyDeviceToHost, c->stream));
     double hF = 0.0;
@@ -574,7 +590,7 @@ int pty_cg_solve(pty_ctx *c, float *psi_inout, int32_t niter, pty_cg_report *rep
     for (int it = 0; it < niter; it++) {
         {
             StageTimer t(c, 0);
-            CK(pty::launch_grad(c->P, a, psi, c->w, c->fpart, c->st, c->stream));
+            CK(c->impl->grad(a, psi, c->w, c->fpart, c->st, c->stream));
         }
         {
             StageTimer t(c, 1);
@@ -583,15 +599,15 @@ int pty_cg_solve(pty_ctx *c, float *psi_inout, int32_t niter, pty_cg_report *rep
         }
         {
             StageTimer t(c, 3);
-            CK(pty::launch_dy_finalize(c->fpart, c->K, c->part_sc, ntiles, c->st, c->hist, ls, c->stream));
+            CK(pty::launch_dy_finalize(c->fpart, c->K * c->CS, c->part_sc, ntiles, c->st, c->hist, ls, c->stream));
         }
         for (int wdx = 0; wdx < nwin; wdx++) {
             {
                 StageTimer t(c, 2);
-                CK(pty::launch_ls(c->P, a, ls, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
+                CK(c->impl->ls(a, ls.L, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
             }
             StageTimer t(c, 3);
-            CK(pty::launch_ls_decide(c->part_ls, c->K, ls, c->st, c->hist, c->stream));
+            CK(pty::launch_ls_decide(c->part_ls, c->K * c->CS, ls, c->st, c->hist, c->stream));
         }
         StageTimer t(c, 3);
         CK(pty::launch_update((int)HW, psi, c->g, c->eta_prev, c->g_prev, c->st, c->stream));

@@ -59,30 +59,36 @@ struct LsArgs {
     int L;  // candidates per pass
 };
 
-// ---- pattern kernels (pattern_kernels.cu) ----
-// out[perm[i]] = F(p * patch_i(psi))   (unitary)
-cudaError_t launch_forward(int P, const PatternArgs &a, const float2 *psi, float2 *out, cudaStream_t s);
-// w[i] = conj(p) * F^H y[perm[i]]
-cudaError_t launch_adjoint_fft(int P, const PatternArgs &a, const float2 *y, float2 *w, cudaStream_t s);
-// GRAD pattern pass: w[i] = conj(p) * F^H r_i with r the likelihood residual of
-// u = F(p * patch_i(psi)); fpart[i] = sum_j f_j of pattern i.  Exits early when st->stalled.
-cudaError_t launch_grad(int P, const PatternArgs &a, const float2 *psi, float2 *w, double *fpart,
-                        const DevState *st, cudaStream_t s);
-// LS pattern pass over the candidates gamma0 tau^(k0+l+1), l < L, with
-// eta = -g + alpha eta_prev and v = G eta: part[0][i], part[1][i] = (sum Re conj(u) v,
-// sum |v|^2) over the d = 0 pixels of pattern i, part[2+l][i] = sum over the entries of the
-// objective change at candidate l (layout [L+2][K]).  u at the entries comes from the GRAD pass of the same iteration.
-// Exits early when st->decided or st->stalled.
-cudaError_t launch_ls(int P, const PatternArgs &a, const LsArgs &ls, const float2 *psi, const float2 *g,
-                      const float2 *eta_prev, double *part, const DevState *st, cudaStream_t s);
-// Entries of the measured data: counts per sorted pattern, then the compact list.
-cudaError_t launch_nz_count(int P, const float *d, const int *perm, int K, int *cnt, cudaStream_t s);
-cudaError_t launch_nz_fill(int P, const float *d, const int *perm, int K, const long long *off,
-                           unsigned short *slot, float *dval, cudaStream_t s);
+// ---- pattern kernels (pattern_kernels.cuh, instantiated per P in pattern_p*.cu) ----
+// One configuration: patterns of P x P held by clusters of P / R CTAs of NT threads.
+// Per-pattern sums are written per CTA: fpart[K * CS], LS partials [L + 2][K * CS].
+struct PatternImpl {
+    int P, R, NT;
+    // out[perm[i]] = F(p * patch_i(psi))   (unitary)
+    cudaError_t (*forward)(const PatternArgs &, const float2 *psi, float2 *out, cudaStream_t);
+    // w[i] = conj(p) * F^H y[perm[i]]
+    cudaError_t (*adjoint)(const PatternArgs &, const float2 *y, float2 *w, cudaStream_t);
+    // GRAD pattern pass: w[i] = conj(p) F^H r_i, r the likelihood residual of u = G psi;
+    // fpart = objective terms; u kept at the entries.  Exits early when st->stalled.
+    cudaError_t (*grad)(const PatternArgs &, const float2 *psi, float2 *w, double *fpart, const DevState *st,
+                        cudaStream_t);
+    // LS pattern pass over the candidates gamma0 tau^(k0+l+1), l < L, with
+    // eta = -g + alpha eta_prev and v = G eta: part[0][.], part[1][.] = (sum Re conj(u) v,
+    // sum |v|^2) over the d = 0 pixels, part[2+l][.] = sum over the entries of the
+    // objective change at candidate l.  Exits early when st->decided or st->stalled.
+    cudaError_t (*ls)(const PatternArgs &, int L, const float2 *psi, const float2 *g, const float2 *eta_prev,
+                      double *part, const DevState *st, cudaStream_t);
+    // Entries of the measured data: counts per (pattern, CTA) chunk, then the compact list.
+    cudaError_t (*nz_count)(const float *d, const int *perm, int K, int *cnt, cudaStream_t);
+    cudaError_t (*nz_fill)(const float *d, const int *perm, int K, const long long *off, unsigned short *slot,
+                           float *dval, cudaStream_t);
+};
+// Configurations available for P (table of n entries; n = 0 if P is not supported).
+int pattern_impls(int P, const PatternImpl **out);
 bool pattern_supported(int P);
+int ls_window_supported(int L);  // 1 if L is an instantiated window size
 // out[i] = log1p_fast(t[i]) (device self-test of the line-search logarithm)
 cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_t s);
-int ls_window_supported(int L);  // 1 if L is an instantiated window size
 
 // ---- object kernels (object_kernels.cu) ----
 struct ScatterPlan {

@@ -300,3 +300,73 @@ def test_production_cg_two_iterations(orc, production):
     print("production objective rel err:", relF, "trials", list(rep["halvings"]), list(want["halvings"]))
     assert np.all(relF <= OBJ_TOL)
     assert list(rep["halvings"]) == list(want["halvings"])
+
+
+# ------------------------------------------------------------------------------- configurations
+def _cfg_opts(idx):
+    o = pty.default_opts()
+    o.tile_config = idx
+    return o
+
+
+@pytest.fixture(scope="module")
+def mid128():
+    """A 128^2-probe problem small enough for the oracle: 384^2 object, 10 x 10 raster."""
+    return synth.small_problem(H=384, W=352, P=128, n=10, step=22, jitter=2, peak=1e5, seed=21, niter=3,
+                               name="mid")
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2])
+def test_p128_configurations(orc, mid128, cfg):
+    """One CTA per pattern and clusters of 2 and 4 CTAs give oracle parity."""
+    p = mid128
+    ctx = make_ctx(p, _cfg_opts(cfg))
+    psi = random_object(p, 30)
+    out = torch.empty((p.K, p.P, p.P), dtype=torch.complex64, device="cuda")
+    ctx.forward(dev(psi), out)
+    e_f = rel(out.cpu().numpy(), orc.forward(psi, p.probe, p.pos, nthreads=0))
+    g = torch.empty((p.H, p.W), dtype=torch.complex64, device="cuda")
+    F = ctx.gradient(dev(psi), g)
+    gw, Fw = orc.gradient(psi, p.probe, p.pos, p.d, nthreads=0)
+    e_g = rel(g.cpu().numpy(), gw)
+    print(f"P=128 config {cfg}: forward {e_f:.2e}, gradient {e_g:.2e}, objective {abs(F - Fw) / abs(Fw):.2e}")
+    assert e_f <= FWD_TOL and e_g <= GRAD_TOL and abs(F - Fw) <= OBJ_TOL * abs(Fw)
+    st, rep = ctx.cg_solve(dev(p.psi0()), 3)
+    want = orc.cg_solve(p.psi0(), p.probe, p.pos, p.d, 3, nthreads=0)
+    assert list(rep["halvings"]) == list(want["halvings"])
+    assert np.all(np.abs(rep["F"] - want["F"]) <= OBJ_TOL * np.abs(want["F"]))
+
+
+@pytest.fixture(scope="module")
+def small256():
+    """256^2 probe: 640^2 object, 5 x 5 raster (step 80), peak 1e6."""
+    return synth.small_problem(H=640, W=640, P=256, n=5, step=80, jitter=2, peak=1e6, seed=22, niter=2,
+                               name="p256")
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_p256_parity(orc, small256, cfg):
+    """P = 256: the exit wave is shared by a cluster of 8 (or 4) CTAs."""
+    p = small256
+    ctx = make_ctx(p, _cfg_opts(cfg))
+    psi = random_object(p, 31)
+    out = torch.empty((p.K, p.P, p.P), dtype=torch.complex64, device="cuda")
+    ctx.forward(dev(psi), out)
+    e_f = rel(out.cpu().numpy(), orc.forward(psi, p.probe, p.pos, nthreads=0))
+    rng = np.random.default_rng(4)
+    y = (rng.standard_normal((p.K, p.P, p.P)) + 1j * rng.standard_normal((p.K, p.P, p.P))).astype(np.complex64)
+    x = torch.empty((p.H, p.W), dtype=torch.complex64, device="cuda")
+    ctx.adjoint(dev(y), x)
+    e_a = rel(x.cpu().numpy(), orc.adjoint(y, p.probe, p.pos, (p.H, p.W), nthreads=0))
+    g = torch.empty((p.H, p.W), dtype=torch.complex64, device="cuda")
+    F = ctx.gradient(dev(psi), g)
+    gw, Fw = orc.gradient(psi, p.probe, p.pos, p.d, nthreads=0)
+    e_g = rel(g.cpu().numpy(), gw)
+    print(f"P=256 config {cfg}: forward {e_f:.2e}, adjoint {e_a:.2e}, gradient {e_g:.2e}, "
+          f"objective {abs(F - Fw) / abs(Fw):.2e}")
+    assert e_f <= FWD_TOL and e_a <= GRAD_TOL and e_g <= GRAD_TOL and abs(F - Fw) <= OBJ_TOL * abs(Fw)
+    st, rep = ctx.cg_solve(dev(p.psi0()), 2)
+    want = orc.cg_solve(p.psi0(), p.probe, p.pos, p.d, 2, nthreads=0)
+    print("P=256 trials", list(rep["halvings"]), list(want["halvings"]))
+    assert list(rep["halvings"]) == list(want["halvings"])
+    assert np.all(np.abs(rep["F"] - want["F"]) <= OBJ_TOL * np.abs(want["F"]))

@@ -33,7 +33,24 @@ sys.path.insert(0, ROOT)
 
 METRIC = "diffraction patterns/s per CG iteration"
 UNIT = "patterns/s"
-WORKLOAD = "ml-cg 1024x1024 object, 128x128 probe, 3600 positions (60x60 raster, step 14, +-2), peak 1e5 counts"
+WORKLOADS = {
+    "production": "ml-cg 1024x1024 object, 128x128 probe, 3600 positions (60x60 raster, step 14, +-2), peak 1e5 counts",
+    "spiral": "ml-cg 2048x2048 object, 256x256 probe, 10000 positions (Fermat spiral, +-2), peak 1e6 counts",
+    "small": "ml-cg 256x256 object, 64x64 probe, 225 positions (15x15 raster, step 8, +-1), peak 1e4 counts",
+}
+WORKLOAD = WORKLOADS["production"]
+
+
+def make_problem(name):
+    from paper_2106_07575_gb300 import synth
+
+    if name == "spiral":
+        return synth.spiral_problem()
+    if name == "small":
+        return synth.small_problem()
+    return synth.production_problem()
+
+
 FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
@@ -48,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ls-window", type=int, default=None)
+    ap.add_argument("--tile-config", type=int, default=None)
+    ap.add_argument("--workload", choices=["production", "spiral", "small"], default="production")
     return ap.parse_args()
 
 
@@ -166,13 +185,16 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    p = synth.production_problem()
+    p = make_problem(args.workload)
+    workload = WORKLOADS[args.workload]
     stream = torch.cuda.current_stream()
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     opts = pty.default_opts()
     opts.flags = 1  # per-stage CUDA-event timing on the launching stream
     if args.ls_window:
         opts.ls_window = args.ls_window
+    if args.tile_config is not None:
+        opts.tile_config = args.tile_config
     probe_d, pos_d, d_d = dev(p.probe), dev(p.pos), dev(p.d)
     ctx = pty.Context(probe_d, pos_d, d_d, p.H, p.W, opts, stream=stream.cuda_stream)
     psi = dev(p.psi0())
@@ -230,7 +252,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "ls_window": L, "l2": "inputs larger than L2 (236 MB data)",
+        "config": {"workload": workload, "ls_window": L, "tile_config": opts.tile_config,
+                   "l2": f"inputs larger than L2 ({p.d.nbytes / 1e6:.0f} MB data)",
                    "parallelism": f"{world} independent replica(s)"},
         "status": pty.STATUS_NAMES[st], "roofline": roof, "clocks": clocks, "gpu_launches": launches,
         "stages_ms": {"grad": stage_ms[0], "scatter": stage_ms[1], "ls": stage_ms[2], "small": stage_ms[3]},
@@ -262,7 +285,7 @@ def main():
                       "d2h_bytes_per_step": int(psi_h.nbytes + 8 * 4 + 4),
                       "note": "pty_create from host arrays + one pty_cg_solve(niter=1) per step with host psi"}
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "production":
         out["cpu_baseline"] = cpu_baseline(p)
     if rank == 0:
         print(json.dumps(out), flush=True)

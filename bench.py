@@ -198,7 +198,7 @@ def main():
     probe_d, pos_d, d_d = dev(p.probe), dev(p.pos), dev(p.d)
     ctx = pty.Context(probe_d, pos_d, d_d, p.H, p.W, opts, stream=stream.cuda_stream)
     psi = dev(p.psi0())
-    ctx.cg_solve(psi, args.warmup)
+    _, warm_rep = ctx.cg_solve(psi, args.warmup)
     ctx.stage_times(reset=True)
 
     clk = Clocks(local)
@@ -224,27 +224,38 @@ def main():
 
     # roofline of the dominant pattern kernel (FP32 ALU bound: FFTs on CUDA cores)
     L = opts.ls_window
-    full_windows = int(sum(math.ceil(h / L) for h in rep["halvings"]))
+    first_h = warm_rep["halvings"][-1] if len(warm_rep["halvings"]) else 0
+    full_windows = 0
+    prev = first_h
+    for h in rep["halvings"]:
+        first = (min(32, max(4, prev + 2)) if prev > 0 else 16) if L == 0 else L
+        full_windows += 1 + (max(0, math.ceil((h - first) / (32 if L == 0 else L))) if h > first else 0)
+        prev = h
     P, K = p.P, p.K
+    # algorithmic flops: 5 N log2 N per 2-D DFT (N = P^2) plus the elementwise complex
+    # arithmetic; the line-search candidate evaluations (logarithms) are not counted
     grad_flops = K * (2 * fft2_flops(P) + 24 * P * P)
-    ls_flops = K * (2 * fft2_flops(P) + (18 + 6 * L) * P * P)
+    ls_flops = K * (fft2_flops(P) + 18 * P * P)
     grad_ms = stage_ms[0] / max(stage_n[0], 1)
-    ls_ms = stage_ms[2] / max(full_windows, 1)  # empty windows exit at once; charge time to full ones
+    ls_ms = stage_ms[2] / max(full_windows, 1)  # early-exit windows cost ~us; charge time to working ones
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    nnz = ctx.n_entries if hasattr(ctx, "n_entries") else None
     kernels = {
         "k_grad": {"ms": grad_ms, "tflops": grad_flops / (grad_ms * 1e-3) / 1e12, "share": stage_ms[0],
-                   "hbm_gbs": K * P * P * 12 / (grad_ms * 1e-3) / 1e9},
+                   "hbm_gbs": K * P * P * 8 / (grad_ms * 1e-3) / 1e9},
         "k_ls": {"ms": ls_ms, "tflops": ls_flops / (ls_ms * 1e-3) / 1e12, "share": stage_ms[2],
-                 "hbm_gbs": K * P * P * 4 / (ls_ms * 1e-3) / 1e9},
+                 "windows": full_windows},
     }
     dom = max(kernels, key=lambda k: kernels[k]["share"])
     roof = {"bound": "alu", "kernel": dom, "achieved": kernels[dom]["tflops"], "peak": peak_tflops,
             "unit": "TFLOP/s", "frac": kernels[dom]["tflops"] / peak_tflops, "traffic": None,
             "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-            "launch_ms": kernels[dom]["ms"], "hbm_gbs_algorithmic": kernels[dom]["hbm_gbs"],
+            "launch_ms": kernels[dom]["ms"],
             "other": {k: {kk: round(vv, 4) for kk, vv in v.items()} for k, v in kernels.items() if k != dom}}
 
-    nwin = (opts.max_halvings + L - 1) // L
+    Lcap = 32 if L == 0 else L
+    first_w = 4 if L == 0 else L
+    nwin = 1 + (max(0, opts.max_halvings - first_w) + Lcap - 1) // Lcap
     launches = args.steps * (5 + 2 * nwin) + 1
     value = world * K * steps_done / (ms * 1e-3)
 
@@ -252,7 +263,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload, "ls_window": L, "tile_config": opts.tile_config,
+        "config": {"workload": workload, "ls_window": L, "tile_config": opts.tile_config, "plan": ctx.plan(),
                    "l2": f"inputs larger than L2 ({p.d.nbytes / 1e6:.0f} MB data)",
                    "parallelism": f"{world} independent replica(s)"},
         "status": pty.STATUS_NAMES[st], "roofline": roof, "clocks": clocks, "gpu_launches": launches,

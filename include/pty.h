@@ -85,10 +85,16 @@ typedef struct {
                             (0.1: with a smaller guard the gradient at dark detector pixels
                             holding counts is too ill-conditioned for single precision) */
     int32_t ls_window;   /* line-search trials evaluated per pass over the data: 4, 8, 16
-                            or 32 (16); the accepted step does not depend on it */
+                            or 32, or 0 (default) for an adaptive first pass sized from the
+                            previous iteration's trial count, then passes of 32; the
+                            accepted step does not depend on it */
     int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times) */
-    int32_t tile_config; /* pattern-kernel configuration: -1 = the library's choice for P,
-                            0.. = an index into pty_tile_configs' table for P */
+    int32_t tile_config; /* pattern-kernel configuration: -1 (default) = autotune at
+                            pty_create (the GRAD and LS passes of every configuration for P are
+                            timed on the problem's own data; the choice is cached per problem
+                            shape for the process); 0.. = one fixed configuration for P
+                            (P=64: 0; P=128: 0 one CTA, 1 cluster of 2, 2 cluster of 4;
+                            P=256: 0 cluster of 8, 1 cluster of 4) */
 } pty_opts;
 
 typedef struct pty_ctx pty_ctx;
@@ -177,6 +183,13 @@ PTY_API int pty_cg_reset(pty_ctx *ctx);
 PTY_API size_t pty_cg_state_size(const pty_ctx *ctx);
 PTY_API int pty_cg_state_save(pty_ctx *ctx, void *host_buf);
 PTY_API int pty_cg_state_load(pty_ctx *ctx, const void *host_buf);
+
+/*
+ * The pattern-kernel plan of the context: plan[0], plan[1] = rows per CTA and threads per
+ * CTA of the GRAD pass; plan[2], plan[3] = the same for the LS pass (a pattern is shared by
+ * P / rows CTAs of one thread-block cluster).
+ */
+PTY_API int pty_get_plan(const pty_ctx *ctx, int32_t plan[4]);
 
 /*
  * Per-stage GPU time accumulated since the last reset (needs opts.flags bit 0):

@@ -96,12 +96,12 @@ __global__ void __launch_bounds__(kSumNT) k_sum(const double *__restrict__ v, in
     if (threadIdx.x == 0) *out = tot[0];
 }
 
-__device__ __forceinline__ void open_window(DevState *st, double gamma0, double tau, int L)
+__device__ __forceinline__ void open_window(DevState *st, double gamma0, double tau)
 {
-    // candidates gamma0 tau^(k0 + l + 1), l < L
+    // candidates gamma0 tau^(k0 + l + 1), l < Leff
     double g = gamma0;
     for (int k = 0; k < st->k0; k++) g *= tau;
-    for (int l = 0; l < L; l++) {
+    for (int l = 0; l < st->Leff; l++) {
         g *= tau;
         st->cand[l] = g;
     }
@@ -128,7 +128,14 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
         st->Fm = Fm;
         st->k0 = 0;
         st->decided = 0;
-        open_window(st, ls.gamma0, ls.tau, ls.L);
+        // first window: the previous iteration's trial count plus a margin (adaptive), or L
+        int Le = ls.L;
+        if (ls.adaptive) {
+            Le = st->last_halvings > 0 ? st->last_halvings + 2 : 16;
+            Le = Le < 4 ? 4 : (Le > ls.L ? ls.L : Le);
+        }
+        st->Leff = Le;
+        open_window(st, ls.gamma0, ls.tau);
         const int m = st->m;
         if (m < h.cap) {
             h.F[m] = Fm;
@@ -137,16 +144,18 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
     }
 }
 
+// part is [L+2][K] (L = the window capacity); the open window has st->Leff <= L candidates.
 template <int L>
 __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__ part, int K, DevState *st,
                                                       DevHist h, LsArgs ls)
 {
     if (st->stalled || st->decided) return;
     __shared__ double tot[L + 2];
-    // part is [L+2][K]: warp w sums the values j = w, w + 8, ... over K patterns, each
-    // lane a fixed strided subset, then a butterfly across the warp (fixed order).
+    // warp w sums the values j = w, w + 8, ... over K partials, each lane a fixed strided
+    // subset, then a butterfly across the warp (fixed order).
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = warp; j < L + 2; j += kSumNT / 32) {
+    const int Leff = st->Leff;
+    for (int j = warp; j < Leff + 2; j += kSumNT / 32) {
         const double *pj = part + (size_t)j * K;
         double s = 0.0;
         for (int i = lane; i < K; i += 32) s += pj[i];
@@ -156,7 +165,7 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
     __syncthreads();
     if (threadIdx.x == 0) {
         const int m = st->m, k0 = st->k0;
-        for (int l = 0; l < L && k0 + l + 1 <= ls.max_halvings; l++) {
+        for (int l = 0; l < Leff && k0 + l + 1 <= ls.max_halvings; l++) {
             const double gam = st->cand[l];
             // F(psi + gam eta) - F(psi): quadratic part of the d = 0 pixels plus the rest
             const double dF = gam * (2.0 * tot[0] + gam * tot[1]) + tot[2 + l];
@@ -164,6 +173,7 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
                 st->gamma = gam;
                 st->Fnext = st->Fm + dF;
                 st->decided = 1;
+                st->last_halvings = k0 + l + 1;
                 if (m < h.cap) {
                     h.gamma[m] = gam;
                     h.halvings[m] = k0 + l + 1;
@@ -172,7 +182,7 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
                 return;
             }
         }
-        const int k1 = k0 + L;
+        const int k1 = k0 + Leff;
         if (k1 >= ls.max_halvings) {
             st->stalled = 1;
             if (m < h.cap) {
@@ -182,7 +192,8 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
             }
         } else {
             st->k0 = k1;
-            open_window(st, ls.gamma0, ls.tau, L);
+            st->Leff = L;  // later windows use the full capacity
+            open_window(st, ls.gamma0, ls.tau);
         }
     }
 }

@@ -149,11 +149,12 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
         f = fmaf(u.x, u.x, fmaf(u.y, u.y, f));
     }
     __syncthreads();
-    const long long e0 = a.nz_off[i * CS + c], e1 = a.nz_off[i * CS + c + 1];
+    const int per = a.nzc / CS;  // entry chunks (of the finest column split) owned by this CTA
+    const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
     for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
-        const int s = a.nz_slot[e];
+        const int s = a.nz_slot[e];  // global slot qy * P + qx
         const float dv = a.nz_d[e];
-        float2 *pu = buf + (s / R) * LDB + (s % R);
+        float2 *pu = buf + (s / P) * LDB + (s % P - c * R);
         float2 u = *pu;
         a.nz_u[e] = u;
         const float den = fmaf(u.x, u.x, u.y * u.y) + a.eps;
@@ -174,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
     }
 }
 
-// LS pattern pass for a window of L candidate steps gamma_l (Eq. 7 with Eq. 2):
+// LS pattern pass for a window of st->Leff <= L candidate steps gamma_l (Eq. 7 with Eq. 2):
 //   F(psi + gamma eta) - F(psi) = sum_j q_j - sum_{entries} d log1p(q / (|u|^2 + eps)),
 //   q_j = |u_j + gamma v_j|^2 - |u_j|^2 = gamma (2 Re conj(u_j) v_j + gamma |v_j|^2),
 // with u = G psi (kept by the GRAD pass at the entries) and v = G eta (one forward DFT).
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restri
     who<P, R>(i, c);
     const int2 rc = a.pos[i];
     const float alpha = (float)st->alpha;
+    const int Leff = st->Leff;
     float gam[L];
 #pragma unroll
     for (int l = 0; l < L; l++) gam[l] = (float)st->cand[l];
@@ -220,12 +222,13 @@ __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restri
     float bp = 0.0f, cp = 0.0f, acc[L];
 #pragma unroll
     for (int l = 0; l < L; l++) acc[l] = 0.0f;
-    const long long e0 = a.nz_off[i * CS + c], e1 = a.nz_off[i * CS + c + 1];
+    const int per = a.nzc / CS;
+    const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
     for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
         const int s = a.nz_slot[e];
         const float dv = a.nz_d[e];
         const float2 u = a.nz_u[e];
-        const float2 v = buf[(s / R) * LDB + (s % R)];
+        const float2 v = buf[(s / P) * LDB + (s % P - c * R)];
         const float au = fmaf(u.x, u.x, u.y * u.y);
         const float bu = fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
         const float cu = fmaf(v.x, v.x, v.y * v.y);
@@ -235,9 +238,11 @@ __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restri
         const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
 #pragma unroll
         for (int l = 0; l < L; l++) {
-            const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
-            const float t = fmaxf(q * inv, tmin);
-            acc[l] += q - dv * log1p_fast(t);
+            if (l < Leff) {  // uniform over the block
+                const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
+                const float t = fmaxf(q * inv, tmin);
+                acc[l] += q - dv * log1p_fast(t);
+            }
         }
     }
     constexpr double PP = (double)P * (double)P;
@@ -251,7 +256,12 @@ __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restri
     if (threadIdx.x < L + 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // [L+2][K*CS]
 }
 
-// Natural-order index of local slot s of CTA c (column slab, row-major over P x R).
+// Global slot (qy * P + qx) and natural-order index of local slot s of column chunk c.
+template <int P, int R>
+__device__ __forceinline__ int chunk_slot(int s, int c)
+{
+    return (s / R) * P + c * R + (s % R);
+}
 template <int P, int R>
 __device__ __forceinline__ int slot_to_natural(int s, int c)
 {
@@ -279,7 +289,8 @@ __global__ void __launch_bounds__(NT) k_nz_count(const float *__restrict__ d, co
     }
 }
 
-// Ordered compaction: entries of chunk (pattern i, CTA c) in ascending local slot order.
+// Ordered compaction: entries of chunk (pattern i, column chunk c) in ascending local slot
+// order, stored as global slots so that any configuration with R >= this R can read them.
 template <int P, int R, int NT>
 __global__ void __launch_bounds__(NT) k_nz_fill(const float *__restrict__ d, const int *__restrict__ perm,
                                                 const long long *__restrict__ off, unsigned short *__restrict__ slot,
@@ -306,7 +317,7 @@ __global__ void __launch_bounds__(NT) k_nz_fill(const float *__restrict__ d, con
         }
         if (flag) {
             const long long p = base + running + woff + __popc(m & ((1u << lane) - 1u));
-            slot[p] = (unsigned short)s;
+            slot[p] = (unsigned short)chunk_slot<P, R>(s, c);
             dval[p] = v;
         }
         running += total;

@@ -13,6 +13,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -31,8 +34,10 @@ struct pty_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
     int H = 0, W = 0, P = 0, K = 0;
-    int CS = 1;                              // CTAs per pattern of the chosen configuration
-    const pty::PatternImpl *impl = nullptr;  // pattern-kernel configuration
+    const pty::PatternImpl *impl = nullptr;     // GRAD pass (and forward/adjoint) configuration
+    const pty::PatternImpl *impl_ls = nullptr;  // LS pass configuration
+    const pty::PatternImpl *impl_nz = nullptr;  // finest column split: the entry layout
+    int CS = 1, CSl = 1, nzc = 1, CSmax = 1;
     pty_opts opts{};
     std::string err;
 
@@ -137,6 +142,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.pos = c->pos;
     a.perm = c->perm;
     a.nz_off = c->nz_off;
+    a.nzc = c->nzc;
     a.nz_slot = c->nz_slot;
     a.nz_d = c->nz_d;
     a.nz_u = c->nz_u;
@@ -163,7 +169,8 @@ pty::LsArgs ls_args(const pty_ctx *c)
     l.tau = c->opts.tau;
     l.t = c->opts.t;
     l.max_halvings = c->opts.max_halvings;
-    l.L = c->opts.ls_window;
+    l.adaptive = c->opts.ls_window == 0;
+    l.L = l.adaptive ? 32 : c->opts.ls_window;
     return l;
 }
 
@@ -261,6 +268,95 @@ int sync(pty_ctx *c)
     return PTY_OK;
 }
 
+// The autotuner: time the GRAD and LS pattern passes of every configuration for P on the
+// context's own data (psi = 1, eta = 0, a 16-candidate window) and keep the fastest of
+// each.  The choice is cached per problem shape for the life of the process, so contexts of
+// the same problem use the same kernels (and give the same bits).
+struct PlanKey {
+    int P, H, W, K;
+    long long nnz;
+    bool operator<(const PlanKey &o) const
+    {
+        return std::tie(P, H, W, K, nnz) < std::tie(o.P, o.H, o.W, o.K, o.nnz);
+    }
+};
+std::mutex g_plan_mu;
+std::map<PlanKey, std::pair<int, int>> g_plan_cache;
+
+int autotune(pty_ctx *c)
+{
+    const pty::PatternImpl *impls = nullptr;
+    const int n = pty::pattern_impls(c->P, &impls);
+    const PlanKey key{c->P, c->H, c->W, c->K, c->n_entries};
+    int best_g = 0, best_l = 0;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_plan_mu);
+        auto it = g_plan_cache.find(key);
+        if (it != g_plan_cache.end()) {
+            best_g = it->second.first;
+            best_l = it->second.second;
+            cached = true;
+        }
+    }
+    if (!cached && n > 1) {
+        int st = ensure_stage(c);
+        if (st) return st;
+        const size_t HW = (size_t)c->H * c->W;
+        std::vector<float2> ones(HW, make_float2(1.f, 0.f));
+        CK(cudaMemcpyAsync(c->stage_obj, ones.data(), sizeof(float2) * HW, cudaMemcpyHostToDevice, c->stream));
+        DevState hs{};
+        hs.Leff = 16;
+        for (int l = 0; l < 16; l++) hs.cand[l] = std::ldexp(1.0, -(l + 1));
+        CK(cudaMemcpyAsync(c->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        pty::PatternArgs a = pattern_args(c);
+        pty::LsArgs ls = ls_args(c);
+        float tg = 1e30f, tl = 1e30f;
+        cudaError_t err = cudaSuccess;
+        for (int j = 0; j < n && err == cudaSuccess; j++) {
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
+                err = cudaEventRecord(e0, c->stream);
+                if (err == cudaSuccess) err = impls[j].grad(a, c->stage_obj, c->w, c->fpart, nullptr, c->stream);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (err == cudaSuccess && ms < tg) {
+                tg = ms;
+                best_g = j;
+            }
+            for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
+                err = cudaEventRecord(e0, c->stream);
+                if (err == cudaSuccess)
+                    err = impls[j].ls(a, ls.L, c->stage_obj, c->g, c->eta_prev, c->part_ls, c->st, c->stream);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+                if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+                if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (err == cudaSuccess && ms < tl) {
+                tl = ms;
+                best_l = j;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (err != cudaSuccess) return fail(c, PTY_ERR_CUDA, "autotune: %s", cudaGetErrorString(err));
+        CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        std::lock_guard<std::mutex> lock(g_plan_mu);
+        g_plan_cache[key] = {best_g, best_l};
+    }
+    c->impl = &impls[best_g];
+    c->impl_ls = &impls[best_l];
+    c->CS = c->P / c->impl->R;
+    c->CSl = c->P / c->impl_ls->R;
+    return PTY_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -273,7 +369,7 @@ void pty_default_opts(pty_opts *o)
     o->t = 0.0;
     o->max_halvings = 60;
     o->eps = 0.1;
-    o->ls_window = 16;
+    o->ls_window = 0;
     o->flags = 0;
     o->tile_config = -1;
 }
@@ -307,9 +403,9 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     pty_default_opts(&o);
     if (opts) o = *opts;
     if (!(o.tau > 0.0 && o.tau < 1.0) || !(o.gamma0 > 0.0) || o.max_halvings < 1 || o.max_halvings > 1000 ||
-        !(o.eps >= 0.0) || !std::isfinite(o.t) || !pty::ls_window_supported(o.ls_window))
+        !(o.eps >= 0.0) || !std::isfinite(o.t) || (o.ls_window != 0 && !pty::ls_window_supported(o.ls_window)))
         return fail(nullptr, PTY_ERR_ARG, "invalid options (tau in (0,1), gamma0 > 0, 1 <= max_halvings <= 1000, "
-                                          "eps >= 0, ls_window in {4,8,16,32})");
+                                          "eps >= 0, ls_window in {0,4,8,16,32})");
 
     // positions: host copy, bounds check, position sort
     std::vector<int32_t> hpos((size_t)2 * K);
@@ -338,14 +434,19 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     {
         const pty::PatternImpl *impls = nullptr;
         const int n = pty::pattern_impls(P, &impls);
-        const int pick = (o.tile_config >= 0 && o.tile_config < n) ? o.tile_config : 0;
         if (n == 0 || o.tile_config >= n) {
             delete c;
             return fail(nullptr, PTY_ERR_ARG, "tile_config %d not available for P=%d (%d configurations)",
                         o.tile_config, P, n);
         }
-        c->impl = &impls[pick];
-        c->CS = P / impls[pick].R;
+        const int pick = o.tile_config >= 0 ? o.tile_config : 0;
+        c->impl = c->impl_ls = &impls[pick];
+        c->impl_nz = &impls[0];
+        for (int j = 1; j < n; j++)
+            if (impls[j].R < c->impl_nz->R) c->impl_nz = &impls[j];
+        c->nzc = P / c->impl_nz->R;
+        c->CSmax = c->nzc;
+        c->CS = c->CSl = P / impls[pick].R;
     }
 
     auto bail = [&](int code) {
@@ -422,9 +523,9 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     CKC(dalloc(&c->tile_start, (size_t)ntiles + 1));
     CKC(dalloc(&c->tile_list, std::max<size_t>(list.size(), 1)));
     CKC(dalloc(&c->w, (size_t)K * PP));
-    CKC(dalloc(&c->fpart, (size_t)K * c->CS));
+    CKC(dalloc(&c->fpart, (size_t)K * c->CSmax));
     CKC(dalloc(&c->part_sc, (size_t)ntiles * 2));
-    CKC(dalloc(&c->part_ls, (size_t)K * c->CS * (32 + 2)));
+    CKC(dalloc(&c->part_ls, (size_t)K * c->CSmax * (32 + 2)));
     CKC(dalloc(&c->g, HW));
     CKC(dalloc(&c->g_prev, HW));
     CKC(dalloc(&c->eta_prev, HW));
@@ -456,14 +557,14 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     };
     int *flag = (int *)c->dscalar;
     int *dcnt = nullptr;
-    const int KC = K * c->CS;
+    const int KC = K * c->nzc;
     std::vector<int> hcnt(KC);
     int hflag = 0;
     cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
     if (ce == cudaSuccess) ce = pty::launch_check_data(dd, (size_t)K * PP, flag, c->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (ce == cudaSuccess) ce = dalloc(&dcnt, (size_t)KC);
-    if (ce == cudaSuccess) ce = c->impl->nz_count(dd, c->perm, K, dcnt, c->stream);
+    if (ce == cudaSuccess) ce = c->impl_nz->nz_count(dd, c->perm, K, dcnt, c->stream);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int) * KC, cudaMemcpyDeviceToHost, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     if (dcnt) cudaFree(dcnt);
@@ -485,13 +586,22 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     if (ce == cudaSuccess) ce = dalloc(&c->nz_u, E);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (KC + 1), cudaMemcpyHostToDevice, c->stream);
-    if (ce == cudaSuccess) ce = c->impl->nz_fill(dd, c->perm, K, c->nz_off, c->nz_slot, c->nz_d, c->stream);
+    if (ce == cudaSuccess) ce = c->impl_nz->nz_fill(dd, c->perm, K, c->nz_off, c->nz_slot, c->nz_d, c->stream);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
     free_tmp();
     if (ce != cudaSuccess)
         return bail(fail(c, ce == cudaErrorMemoryAllocation ? PTY_ERR_NOMEM : PTY_ERR_CUDA, "data compaction: %s",
                          cudaGetErrorString(ce)));
 #undef CKC
+    if (o.tile_config < 0) {
+        const int at = autotune(c);
+        if (at != PTY_OK) {
+            g_create_err = c->err;
+            free_all(c);
+            delete c;
+            return at;
+        }
+    }
     *out = c;
     return PTY_OK;
 }
@@ -584,7 +694,10 @@ int pty_cg_solve(pty_ctx *c, float *psi_inout, int32_t niter, pty_cg_report *rep
     const pty::PatternArgs a = pattern_args(c);
     const pty::ScatterPlan plan = scatter_plan(c);
     const pty::LsArgs ls = ls_args(c);
-    const int nwin = (c->opts.max_halvings + ls.L - 1) / ls.L;
+    // first window >= 4 candidates when adaptive (then full windows of L), else L each
+    const int first = ls.adaptive ? 4 : ls.L;
+    const int rest = std::max(0, c->opts.max_halvings - first);
+    const int nwin = 1 + (rest + ls.L - 1) / ls.L;
     const int ntiles = c->ntile_x * c->ntile_y;
     CK(pty::launch_begin_solve(c->st, c->stream));
     for (int it = 0; it < niter; it++) {
@@ -604,10 +717,10 @@ int pty_cg_solve(pty_ctx *c, float *psi_inout, int32_t niter, pty_cg_report *rep
         for (int wdx = 0; wdx < nwin; wdx++) {
             {
                 StageTimer t(c, 2);
-                CK(c->impl->ls(a, ls.L, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
+                CK(c->impl_ls->ls(a, ls.L, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
             }
             StageTimer t(c, 3);
-            CK(pty::launch_ls_decide(c->part_ls, c->K * c->CS, ls, c->st, c->hist, c->stream));
+            CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, ls, c->st, c->hist, c->stream));
         }
         StageTimer t(c, 3);
         CK(pty::launch_update((int)HW, psi, c->g, c->eta_prev, c->g_prev, c->st, c->stream));
@@ -672,6 +785,16 @@ int pty_cg_state_load(pty_ctx *c, const void *host_buf)
     CK(cudaMemcpyAsync(c->eta_prev, b + sizeof(float2) * HW, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
     return sync(c);
+}
+
+int pty_get_plan(const pty_ctx *c, int32_t plan[4])
+{
+    if (!c || !plan) return fail(nullptr, PTY_ERR_ARG, "ctx and plan must be non-NULL");
+    plan[0] = c->impl->R;
+    plan[1] = c->impl->NT;
+    plan[2] = c->impl_ls->R;
+    plan[3] = c->impl_ls->NT;
+    return PTY_OK;
 }
 
 int pty_stage_times(pty_ctx *c, double ms[4], int64_t launches[4], int reset)

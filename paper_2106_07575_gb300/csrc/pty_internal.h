@@ -16,7 +16,8 @@ struct DevState {
     int stalled;   // no step within max_halvings: the solve is over
     int total;     // iterations accepted since the last reset (checkpointed)
     int restarts;  // Dai-Yuan restarts (denominator <= 0 or not finite)
-    int pad[2];
+    int Leff;      // candidates in the open line-search window
+    int last_halvings;  // trials of the last accepted step (sizes the next first window)
     double alpha;  // Dai-Yuan coefficient of the current iteration (Eq. 6)
     double gamma;  // accepted step of the current iteration
     double Fm;     // F(psi_m)
@@ -45,8 +46,9 @@ struct PatternArgs {
     const float2 *tw;           // [P] exp(-2 pi i m / P)
     const int2 *pos;            // [K] (row, col), position-sorted order
     const int *perm;            // [K] caller index of sorted pattern i
-    const long long *nz_off;    // [K + 1] first entry of sorted pattern i
-    const unsigned short *nz_slot;  // [E] tile slot of each entry
+    const long long *nz_off;    // [K * nzc + 1] first entry of (sorted pattern i, column chunk c)
+    int nzc;                    // column chunks per pattern in the entry layout (P / R_min)
+    const unsigned short *nz_slot;  // [E] global slot qy * P + qx of each entry
     const float *nz_d;          // [E] measured counts (> 0) of each entry
     float2 *nz_u;               // [E] u = G psi_m at each entry (GRAD pass -> LS pass)
     float eps;
@@ -56,7 +58,8 @@ struct PatternArgs {
 struct LsArgs {
     double gamma0, tau, t;
     int max_halvings;
-    int L;  // candidates per pass
+    int L;         // candidates per pass (the kernel's capacity)
+    int adaptive;  // first window of an iteration sized from the previous trial count
 };
 
 // ---- pattern kernels (pattern_kernels.cuh, instantiated per P in pattern_p*.cu) ----

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_
 
 EXPORTED = ["pty_default_opts", "pty_create", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
             "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
-            "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_gradient_noalloc"]
+            "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_gradient_noalloc", "pty_get_plan"]
 
 
 class PtyError(RuntimeError):
@@ -79,9 +79,10 @@ def load(build_if_missing: bool = True):
     lib.pty_stage_times.argtypes = [vp, ctypes.POINTER(dbl), ctypes.POINTER(ctypes.c_int64), ctypes.c_int]
     lib.pty_selftest_log1p.argtypes = [vp, vp, i32]
     lib.pty_gradient_noalloc.argtypes = [i32, i32, i32, vp, i32, vp, vp, dbl, vp, vp, vp, vp]
+    lib.pty_get_plan.argtypes = [vp, ctypes.POINTER(i32)]
     for f in ("pty_create", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
               "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p",
-              "pty_gradient_noalloc"):
+              "pty_gradient_noalloc", "pty_get_plan"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -279,3 +280,10 @@ class Context:
 
     def stage_times(self, reset=False):
         return pty_stage_times(self.ctx, reset)
+
+    def plan(self):
+        """(rows, threads) per CTA of the GRAD pass and of the LS pass."""
+        lib = load()
+        out = (ctypes.c_int32 * 4)()
+        _check(lib, self.ctx, lib.pty_get_plan(self.ctx, out))
+        return {"grad": (out[0], out[1]), "ls": (out[2], out[3])}

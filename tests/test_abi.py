@@ -40,7 +40,7 @@ def test_default_options_match_algorithm_1():
 
     o = pty.default_opts()  # pure host function
     assert (o.gamma0, o.tau, o.t, o.max_halvings) == (1.0, 0.5, 0.0, 60)
-    assert o.ls_window in (4, 8, 16, 32)
+    assert o.ls_window in (0, 4, 8, 16, 32) and o.tile_config == -1
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu():

@@ -154,16 +154,17 @@ def test_cg_ten_iterations_small(orc, small):
 def test_cg_window_size_does_not_change_the_step(small):
     p = small
     reps = {}
-    for L in (4, 32):
+    for L in (4, 32, 0):
         o = pty.default_opts()
         o.ls_window = L
         ctx = make_ctx(p, o)
         psi = dev(p.psi0())
         st, rep = ctx.cg_solve(psi, 4)
         reps[L] = (rep, psi.cpu().numpy())
-    assert list(reps[4][0]["halvings"]) == list(reps[32][0]["halvings"])
-    np.testing.assert_array_equal(reps[4][0]["gamma"], reps[32][0]["gamma"])
-    assert np.array_equal(reps[4][1], reps[32][1])
+    for L in (32, 0):
+        assert list(reps[4][0]["halvings"]) == list(reps[L][0]["halvings"])
+        np.testing.assert_array_equal(reps[4][0]["gamma"], reps[L][0]["gamma"])
+        assert np.array_equal(reps[4][1], reps[L][1])
 
 
 def test_cg_deterministic_and_resumable(small):

@@ -256,7 +256,7 @@ def main():
     Lcap = 32 if L == 0 else L
     first_w = 4 if L == 0 else L
     nwin = 1 + (max(0, opts.max_halvings - first_w) + Lcap - 1) // Lcap
-    launches = args.steps * (5 + 2 * nwin) + 1
+    launches = args.steps * (5 + 2 * nwin + (1 if L == 0 else 0)) + 1
     value = world * K * steps_done / (ms * 1e-3)
 
     out = {

@@ -135,6 +135,7 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
             Le = Le < 4 ? 4 : (Le > ls.L ? ls.L : Le);
         }
         st->Leff = Le;
+        st->Lsel = ls.adaptive ? (Le <= 16 ? 16 : 32) : ls.L;
         open_window(st, ls.gamma0, ls.tau);
         const int m = st->m;
         if (m < h.cap) {
@@ -144,13 +145,12 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
     }
 }
 
-// part is [L+2][K] (L = the window capacity); the open window has st->Leff <= L candidates.
-template <int L>
+// part is [Leff+2][K] rows of K partials; the open window has st->Leff <= 32 candidates.
 __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__ part, int K, DevState *st,
                                                       DevHist h, LsArgs ls)
 {
     if (st->stalled || st->decided) return;
-    __shared__ double tot[L + 2];
+    __shared__ double tot[32 + 2];
     // warp w sums the values j = w, w + 8, ... over K partials, each lane a fixed strided
     // subset, then a butterfly across the warp (fixed order).
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
             }
         } else {
             st->k0 = k1;
-            st->Leff = L;  // later windows use the full capacity
+            st->Leff = ls.L;  // later windows use the full capacity
+            st->Lsel = ls.L;
             open_window(st, ls.gamma0, ls.tau);
         }
     }
@@ -270,13 +271,7 @@ cudaError_t launch_dy_finalize(const double *fpart, int K, const double *part, i
 
 cudaError_t launch_ls_decide(const double *part, int K, const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
 {
-    switch (ls.L) {
-    case 4: k_ls_decide<4><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
-    case 8: k_ls_decide<8><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
-    case 16: k_ls_decide<16><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
-    case 32: k_ls_decide<32><<<1, kSumNT, 0, s>>>(part, K, st, h, ls); break;
-    default: return cudaErrorInvalidValue;
-    }
+    k_ls_decide<<<1, kSumNT, 0, s>>>(part, K, st, h, ls);
     return cudaGetLastError();
 }
 

@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restri
                                            const float2 *__restrict__ g, const float2 *__restrict__ ep,
                                            double *__restrict__ part, const DevState *__restrict__ st)
 {
-    if (st->stalled || st->decided) return;
+    if (st->stalled || st->decided || st->Lsel != L) return;
     extern __shared__ __align__(16) float2 sm[];
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     __shared__ double red[(NT / 32) * (L + 2)];

@@ -170,7 +170,7 @@ pty::LsArgs ls_args(const pty_ctx *c)
     l.t = c->opts.t;
     l.max_halvings = c->opts.max_halvings;
     l.adaptive = c->opts.ls_window == 0;
-    l.L = l.adaptive ? 32 : c->opts.ls_window;
+    l.L = l.adaptive ? 32 : c->opts.ls_window;  // capacity of the later windows
     return l;
 }
 
@@ -307,6 +307,7 @@ int autotune(pty_ctx *c)
         CK(cudaMemcpyAsync(c->stage_obj, ones.data(), sizeof(float2) * HW, cudaMemcpyHostToDevice, c->stream));
         DevState hs{};
         hs.Leff = 16;
+        hs.Lsel = 16;
         for (int l = 0; l < 16; l++) hs.cand[l] = std::ldexp(1.0, -(l + 1));
         CK(cudaMemcpyAsync(c->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
         cudaEvent_t e0, e1;
@@ -332,7 +333,7 @@ int autotune(pty_ctx *c)
             for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
                 err = cudaEventRecord(e0, c->stream);
                 if (err == cudaSuccess)
-                    err = impls[j].ls(a, ls.L, c->stage_obj, c->g, c->eta_prev, c->part_ls, c->st, c->stream);
+                    err = impls[j].ls(a, 16, c->stage_obj, c->g, c->eta_prev, c->part_ls, c->st, c->stream);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
@@ -717,6 +718,10 @@ int pty_cg_solve(pty_ctx *c, float *psi_inout, int32_t niter, pty_cg_report *rep
         for (int wdx = 0; wdx < nwin; wdx++) {
             {
                 StageTimer t(c, 2);
+                // the first window of an adaptive search runs on the 16- or the 32-candidate
+                // kernel as the device chose; the other one returns at once
+                if (wdx == 0 && ls.adaptive)
+                    CK(c->impl_ls->ls(a, 16, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
                 CK(c->impl_ls->ls(a, ls.L, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
             }
             StageTimer t(c, 3);

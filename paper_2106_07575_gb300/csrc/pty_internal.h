@@ -18,6 +18,8 @@ struct DevState {
     int restarts;  // Dai-Yuan restarts (denominator <= 0 or not finite)
     int Leff;      // candidates in the open line-search window
     int last_halvings;  // trials of the last accepted step (sizes the next first window)
+    int Lsel;      // capacity of the LS kernel that runs the open window (16 or 32 when adaptive)
+    int pad2;
     double alpha;  // Dai-Yuan coefficient of the current iteration (Eq. 6)
     double gamma;  // accepted step of the current iteration
     double Fm;     // F(psi_m)

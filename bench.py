@@ -228,7 +228,7 @@ def main():
     full_windows = 0
     prev = first_h
     for h in rep["halvings"]:
-        first = (min(32, max(4, prev + 2)) if prev > 0 else 16) if L == 0 else L
+        first = (min(32, max(4, prev + 1)) if prev > 0 else 16) if L == 0 else L
         full_windows += 1 + (max(0, math.ceil((h - first) / (32 if L == 0 else L))) if h > first else 0)
         prev = h
     P, K = p.P, p.K

@@ -86,7 +86,7 @@ typedef struct {
                             holding counts is too ill-conditioned for single precision) */
     int32_t ls_window;   /* line-search trials evaluated per pass over the data: 4, 8, 16
                             or 32, or 0 (default) for an adaptive first pass sized from the
-                            previous iteration's trial count, then passes of 32; the
+                            previous iteration's trial count (plus one), then passes of 32; the
                             accepted step does not depend on it */
     int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times) */
     int32_t tile_config; /* pattern-kernel configuration: -1 (default) = autotune at

@@ -128,10 +128,10 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
         st->Fm = Fm;
         st->k0 = 0;
         st->decided = 0;
-        // first window: the previous iteration's trial count plus a margin (adaptive), or L
+        // first window: the previous iteration's trial count plus one (adaptive), or L
         int Le = ls.L;
         if (ls.adaptive) {
-            Le = st->last_halvings > 0 ? st->last_halvings + 2 : 16;
+            Le = st->last_halvings > 0 ? st->last_halvings + 1 : 16;
             Le = Le < 4 ? 4 : (Le > ls.L ? ls.L : Le);
         }
         st->Leff = Le;

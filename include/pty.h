@@ -38,9 +38,9 @@
  * the call; `data` is read during pty_create only (the library keeps a compact copy of
  * the detector pixels that hold counts).
  *
- * Streams and threads.  All device work of a context runs on the stream given at
- * creation (a cudaStream_t passed as void*; NULL = the legacy default stream).  Every
- * call returns after that work completed.  A context must not be used from two host
+ * Streams and threads.  Every call orders its device work after the work queued so far on
+ * the stream given at creation (a cudaStream_t passed as void*; NULL = the legacy default
+ * stream), runs it on the context's own stream, and returns after it completed.  A context must not be used from two host
  * threads at once; distinct contexts are independent.
  *
  * Errors.  Every call returns a pty_status.  No call aborts or throws; after an error
@@ -167,9 +167,39 @@ PTY_API int pty_gradient(pty_ctx *ctx, const float *psi, float *grad, double *F)
  * first call after pty_create or pty_cg_reset starts with eta_0 = -g_0.
  * rep may be NULL.  Returns PTY_OK, or PTY_STALLED when an iteration found no step
  * (psi then holds the last accepted iterate and rep->iters_done says how many were
- * accepted).  The iteration runs without host synchronisation between its stages.
+ * accepted).  The iteration runs without host synchronisation between its stages; it is
+ * captured once as a CUDA graph and replayed (unless opts.flags bit 0 asks for per-stage
+ * timing).  Needs a single-view context.
  */
 PTY_API int pty_cg_solve(pty_ctx *ctx, float *psi_inout, int32_t niter, pty_cg_report *rep);
+
+/*
+ * Batched form: n_views independent reconstructions (for instance the views of a
+ * tomographic series) of uneven object size and scan count, sharing one probe.  Every
+ * stage of an iteration is one launch over all views' patterns; the views' scalars (step,
+ * Dai-Yuan coefficient, objective, line-search window, stall) stay separate, so each view
+ * follows exactly the iteration it would follow alone.
+ *   H, W, K  [n_views] object sizes and scan counts.
+ *   pos      [sum K][2] positions, view after view, in each view's own coordinates.
+ *   data     [sum K][P][P] measured intensities, view after view.
+ *   probe, P, opts, stream as in pty_create.
+ * pty_forward, pty_adjoint, pty_gradient and pty_cg_solve need a single-view context;
+ * a batch is solved with pty_batch_cg_solve.
+ */
+PTY_API int pty_batch_create(pty_ctx **out, int32_t n_views, const int32_t *H, const int32_t *W,
+                             const int32_t *K, int32_t P, const float *probe, const int32_t *pos,
+                             const float *data, const pty_opts *opts, void *stream);
+
+/*
+ * niter iterations of every view of a batch.  psi: host array of n_views pointers, each
+ * to that view's [H_v][W_v] complex object (host or device memory), updated in place.
+ * reps: host array of n_views reports, or NULL.  Returns PTY_STALLED if any view stalled
+ * (that view keeps its last accepted iterate; the others complete their iterations).
+ */
+PTY_API int pty_batch_cg_solve(pty_ctx *ctx, float *const *psi, int32_t niter, pty_cg_report *reps);
+
+/* Number of views of a context (1 for pty_create). */
+PTY_API int32_t pty_num_views(const pty_ctx *ctx);
 
 /* Forget the conjugate-gradient state: the next pty_cg_solve starts with eta = -g. */
 PTY_API int pty_cg_reset(pty_ctx *ctx);

@@ -29,10 +29,10 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
                                                    const float2 *__restrict__ gp, double *__restrict__ part,
                                                    const DevState *__restrict__ st)
 {
-    if (st && st->stalled) return;
+    const int b = blockIdx.x;
+    if (st && st[plan.tile_view[b]].stalled) return;
     __shared__ double red[(kScNT / 32) * 2];
     __shared__ double tot[2];
-    const int b = blockIdx.x;
     const int ty = b / plan.ntile_x, tx = b % plan.ntile_x;
     const int x = tx * kScTX + (threadIdx.x % kScTX);
     const int y0 = ty * kScTY + threadIdx.x / kScTX;
@@ -107,15 +107,20 @@ __device__ __forceinline__ void open_window(DevState *st, double gamma0, double 
     }
 }
 
-__global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict__ fpart, int K,
-                                                        const double *__restrict__ part, int nparts, DevState *st,
+__global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict__ fpart, int cs,
+                                                        const double *__restrict__ part, ViewMap vm, DevState *sts,
                                                         DevHist h, LsArgs ls)
 {
+    const int v = blockIdx.x;
+    DevState *st = sts + v;
     if (st->stalled) return;
     __shared__ double red[(kSumNT / 32) * 3];
     __shared__ double tot[3];
-    double v[3] = {strided_sum(fpart, K, 1, 0), strided_sum(part, nparts, 2, 0), strided_sum(part, nparts, 2, 1)};
-    block_sum<kSumNT, 3>(v, red, tot);
+    const int f0 = vm.pat_off[v] * cs, f1 = vm.pat_off[v + 1] * cs;
+    const int t0 = vm.tile_off[v], t1 = vm.tile_off[v + 1];
+    double v3[3] = {strided_sum(fpart + f0, f1 - f0, 1, 0), strided_sum(part + 2 * (size_t)t0, t1 - t0, 2, 0),
+                    strided_sum(part + 2 * (size_t)t0, t1 - t0, 2, 1)};
+    block_sum<kSumNT, 3>(v3, red, tot);
     if (threadIdx.x == 0) {
         const double Fm = tot[0], gg = tot[1], den = tot[2];
         double alpha = 0.0;
@@ -139,32 +144,37 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
         open_window(st, ls.gamma0, ls.tau);
         const int m = st->m;
         if (m < h.cap) {
-            h.F[m] = Fm;
-            h.alpha[m] = alpha;
+            h.F[(size_t)v * (h.cap + 1) + m] = Fm;
+            h.alpha[(size_t)v * h.cap + m] = alpha;
         }
     }
 }
 
-// part is [Leff+2][K] rows of K partials; the open window has st->Leff <= 32 candidates.
-__global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__ part, int K, DevState *st,
-                                                      DevHist h, LsArgs ls)
+// Rows of partials have length kc; view v's entries are [pat_off[v] cs, pat_off[v+1] cs).
+// The open window of view v has st->Leff <= 32 candidates.
+__global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__ part, int kc, int cs, ViewMap vm,
+                                                      DevState *sts, DevHist h, LsArgs ls)
 {
+    const int v = blockIdx.x;
+    DevState *st = sts + v;
     if (st->stalled || st->decided) return;
     __shared__ double tot[32 + 2];
-    // warp w sums the values j = w, w + 8, ... over K partials, each lane a fixed strided
-    // subset, then a butterfly across the warp (fixed order).
+    // warp w sums the values j = w, w + 8, ... over the view's partials, each lane a fixed
+    // strided subset, then a butterfly across the warp (fixed order).
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Leff = st->Leff;
+    const int p0 = vm.pat_off[v] * cs, p1 = vm.pat_off[v + 1] * cs;
     for (int j = warp; j < Leff + 2; j += kSumNT / 32) {
-        const double *pj = part + (size_t)j * K;
+        const double *pj = part + (size_t)j * kc;
         double s = 0.0;
-        for (int i = lane; i < K; i += 32) s += pj[i];
+        for (int i = p0 + lane; i < p1; i += 32) s += pj[i];
         s = warp_sum(s);
         if (lane == 0) tot[j] = s;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         const int m = st->m, k0 = st->k0;
+        const size_t hf = (size_t)v * (h.cap + 1) + m, hi = (size_t)v * h.cap + m;
         for (int l = 0; l < Leff && k0 + l + 1 <= ls.max_halvings; l++) {
             const double gam = st->cand[l];
             // F(psi + gam eta) - F(psi): quadratic part of the d = 0 pixels plus the rest
@@ -175,9 +185,9 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
                 st->decided = 1;
                 st->last_halvings = k0 + l + 1;
                 if (m < h.cap) {
-                    h.gamma[m] = gam;
-                    h.halvings[m] = k0 + l + 1;
-                    h.F[m + 1] = st->Fm + dF;
+                    h.gamma[hi] = gam;
+                    h.halvings[hi] = k0 + l + 1;
+                    h.F[hf + 1] = st->Fm + dF;
                 }
                 return;
             }
@@ -186,9 +196,9 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
         if (k1 >= ls.max_halvings) {
             st->stalled = 1;
             if (m < h.cap) {
-                h.gamma[m] = st->cand[ls.max_halvings - 1 - k0];
-                h.halvings[m] = ls.max_halvings;
-                h.F[m + 1] = st->Fm;
+                h.gamma[hi] = st->cand[ls.max_halvings - 1 - k0];
+                h.halvings[hi] = ls.max_halvings;
+                h.F[hf + 1] = st->Fm;
             }
         } else {
             st->k0 = k1;
@@ -199,12 +209,14 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
     }
 }
 
-__global__ void k_update(int n, float2 *__restrict__ psi, const float2 *__restrict__ g, float2 *__restrict__ ep,
-                         float2 *__restrict__ gp, DevState *st)
+__global__ void k_update(int H, int W, ViewMap vm, float2 *__restrict__ psi, const float2 *__restrict__ g,
+                         float2 *__restrict__ ep, float2 *__restrict__ gp, const DevState *sts)
 {
-    if (st->stalled || !st->decided) return;
-    const float gam = (float)st->gamma, alpha = (float)st->alpha;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const size_t n = (size_t)H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const DevState *st = sts + vm.row_view[i / W];
+        if (st->stalled || !st->decided) continue;
+        const float gam = (float)st->gamma, alpha = (float)st->alpha;
         const float2 gv = g[i], ev = ep[i];
         const float2 eta = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
         float2 p = psi[i];
@@ -216,12 +228,15 @@ __global__ void k_update(int n, float2 *__restrict__ psi, const float2 *__restri
     }
 }
 
-__global__ void k_update_counters(DevState *st)
+__global__ void k_update_counters(DevState *sts, int V)
 {
-    if (st->stalled || !st->decided) return;
-    st->m += 1;
-    st->total += 1;
-    st->last_gamma = st->gamma;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        DevState *st = sts + v;
+        if (st->stalled || !st->decided) continue;
+        st->m += 1;
+        st->total += 1;
+        st->last_gamma = st->gamma;
+    }
 }
 
 __global__ void k_check_data(const float *__restrict__ d, size_t n, int *flag)
@@ -234,11 +249,13 @@ __global__ void k_check_data(const float *__restrict__ d, size_t n, int *flag)
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
-__global__ void k_begin_solve(DevState *st)
+__global__ void k_begin_solve(DevState *sts, int V)
 {
-    st->m = 0;
-    st->stalled = 0;
-    st->decided = 0;
+    for (int v = threadIdx.x; v < V; v += blockDim.x) {
+        sts[v].m = 0;
+        sts[v].stalled = 0;
+        sts[v].decided = 0;
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -262,28 +279,29 @@ cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_dy_finalize(const double *fpart, int K, const double *part, int nparts, DevState *st, DevHist h,
-                               const LsArgs &ls, cudaStream_t s)
+cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, const ViewMap &vm, DevState *st,
+                               DevHist h, const LsArgs &ls, cudaStream_t s)
 {
-    k_dy_finalize<<<1, kSumNT, 0, s>>>(fpart, K, part, nparts, st, h, ls);
+    k_dy_finalize<<<vm.V, kSumNT, 0, s>>>(fpart, cs, part, vm, st, h, ls);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_decide(const double *part, int K, const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
+cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const LsArgs &ls, DevState *st,
+                             DevHist h, cudaStream_t s)
 {
-    k_ls_decide<<<1, kSumNT, 0, s>>>(part, K, st, h, ls);
+    k_ls_decide<<<vm.V, kSumNT, 0, s>>>(part, kc, cs, vm, st, h, ls);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(int n, float2 *psi, const float2 *g, float2 *eta_prev, float2 *g_prev, DevState *st,
-                          cudaStream_t s)
+cudaError_t launch_update(int H, int W, const ViewMap &vm, float2 *psi, const float2 *g, float2 *eta_prev,
+                          float2 *g_prev, DevState *st, cudaStream_t s)
 {
-    int nb = (n + 255) / 256;
+    size_t nb = ((size_t)H * W + 255) / 256;
     if (nb > 152 * 8) nb = 152 * 8;
-    k_update<<<nb, 256, 0, s>>>(n, psi, g, eta_prev, g_prev, st);
+    k_update<<<(unsigned)nb, 256, 0, s>>>(H, W, vm, psi, g, eta_prev, g_prev, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_update_counters<<<1, 1, 0, s>>>(st);
+    k_update_counters<<<1, 32, 0, s>>>(st, vm.V);
     return cudaGetLastError();
 }
 
@@ -296,9 +314,9 @@ cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_begin_solve(DevState *st, cudaStream_t s)
+cudaError_t launch_begin_solve(DevState *st, int V, cudaStream_t s)
 {
-    k_begin_solve<<<1, 1, 0, s>>>(st);
+    k_begin_solve<<<1, 32, 0, s>>>(st, V);
     return cudaGetLastError();
 }
 

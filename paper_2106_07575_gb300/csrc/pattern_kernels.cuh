@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
                                              float2 *__restrict__ w, double *__restrict__ fpart,
                                              const DevState *__restrict__ st)
 {
-    if (st && st->stalled) return;
+    if (st && st[a.pat_view[blockIdx.x / Slab<P, R>::CS]].stalled) return;
     extern __shared__ __align__(16) float2 sm[];
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     __shared__ double red[NT / 32];
@@ -185,8 +185,9 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
 template <int P, int R, int NT, int L>
 __global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restrict__ psi,
                                            const float2 *__restrict__ g, const float2 *__restrict__ ep,
-                                           double *__restrict__ part, const DevState *__restrict__ st)
+                                           double *__restrict__ part, const DevState *__restrict__ sts)
 {
+    const DevState *st = sts + a.pat_view[blockIdx.x / Slab<P, R>::CS];  // uniform over the cluster
     if (st->stalled || st->decided || st->Lsel != L) return;
     extern __shared__ __align__(16) float2 sm[];
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;

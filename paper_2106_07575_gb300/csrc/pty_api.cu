@@ -1,27 +1,35 @@
 // pty_api.cu -- host side of libpty: the C ABI of include/pty.h.
 //
 // A context owns the device copies of the probe (pre-scaled by 1/P, the unitary DFT
-// normalisation), the twiddle table, the position-sorted scan positions, the object
-// tile -> pattern lists of the scatter-add, the conjugate-gradient state and scratch.
+// normalisation), the twiddle table, the position-sorted scan positions, the compact
+// measured data, the object tile -> pattern lists of the scatter-add, the conjugate-
+// gradient state and scratch, for one view or for a batch of independent views.  A batch
+// is packed into one "atlas" object: view v occupies rows [R0_v, R0_v + H_v) (R0_v a
+// multiple of the 32-row scatter tile) and columns [0, W_v) of an array of width max W_v,
+// so patterns, scatter tiles and rows of different views never mix and every stage runs
+// as one launch over all views.  Scalars of the method (alpha, gamma, F, the line-search
+// window, the stall flag) are per view.
+//
 // One CG iteration (Algorithm 1 of the paper, single GPU) is a fixed launch sequence:
 //   GRAD   k_grad (per pattern) -> k_scatter (per object tile, fused Eq. 6 reductions)
-//   DIR    k_dy_finalize (Dai-Yuan coefficient, objective F(psi_m))
-//   LS     windows of (k_ls per pattern -> k_ls_decide) until a step is accepted
+//   DIR    k_dy_finalize (per view: Dai-Yuan coefficient, objective F(psi_m))
+//   LS     windows of (k_ls per pattern -> k_ls_decide per view) until a step is accepted
 //   Update k_update
-// with every decision taken on the device, so the host only synchronises once per call.
+// with every decision taken on the device.  The sequence is captured once as a CUDA graph
+// and replayed per iteration; the host synchronises once per call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
-#include <map>
-#include <mutex>
-#include <tuple>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "pty.h"
@@ -32,8 +40,12 @@ using pty::DevState;
 
 struct pty_ctx {
     int dev = 0;
-    cudaStream_t stream = nullptr;
-    int H = 0, W = 0, P = 0, K = 0;
+    cudaStream_t user = nullptr;  // the caller's stream
+    cudaStream_t s = nullptr;     // the context's own stream (captured into graphs)
+    cudaEvent_t join = nullptr;
+    int V = 1, P = 0, K = 0;
+    int HA = 0, WA = 0;  // atlas rows and width
+    std::vector<int> Hv, Wv, Kv, R0, Koff;
     const pty::PatternImpl *impl = nullptr;     // GRAD pass (and forward/adjoint) configuration
     const pty::PatternImpl *impl_ls = nullptr;  // LS pass configuration
     const pty::PatternImpl *impl_nz = nullptr;  // finest column split: the entry layout
@@ -44,29 +56,35 @@ struct pty_ctx {
     // problem (device)
     float2 *probe = nullptr;  // [P][P] / P
     float2 *tw = nullptr;     // [P]
-    int2 *pos = nullptr;      // [K] sorted
-    int *perm = nullptr;      // [K]
-    long long *nz_off = nullptr;      // [K * CS + 1]
+    int2 *pos = nullptr;      // [K] sorted, atlas coordinates
+    int *perm = nullptr;      // [K] caller index of sorted pattern i
+    int *pat_view = nullptr;  // [K]
+    int *view_pat_off = nullptr, *view_tile_off = nullptr, *row_view = nullptr, *tile_view = nullptr;
+    long long *nz_off = nullptr;        // [K * nzc + 1]
     unsigned short *nz_slot = nullptr;  // [E]
-    float *nz_d = nullptr;            // [E]
-    float2 *nz_u = nullptr;           // [E]
+    float *nz_d = nullptr;              // [E]
+    float2 *nz_u = nullptr;             // [E]
     long long n_entries = 0;
     int *tile_start = nullptr, *tile_list = nullptr;
     int ntile_y = 0, ntile_x = 0;
 
     // CG state and scratch (device)
-    float2 *w = nullptr;         // [K][P][P] per-pattern adjoint results
-    double *fpart = nullptr;     // [K * CS]
-    double *part_sc = nullptr;   // [ntiles][2]
-    double *part_ls = nullptr;   // [L+2][K * CS]
-    float2 *g = nullptr, *g_prev = nullptr, *eta_prev = nullptr;  // [H][W]
-    DevState *st = nullptr;
+    float2 *w = nullptr;        // [K][P][P] per-pattern adjoint results
+    double *fpart = nullptr;    // [K * CS]
+    double *part_sc = nullptr;  // [ntiles][2]
+    double *part_ls = nullptr;  // [L+2][K * CS]
+    float2 *psi = nullptr, *g = nullptr, *g_prev = nullptr, *eta_prev = nullptr;  // atlas
+    DevState *st = nullptr;     // [V]
     double *dscalar = nullptr;
     DevHist hist{};
 
     // staging for host arguments (device)
     float2 *stage_obj = nullptr, *stage_obj2 = nullptr;
     float2 *stage_pat = nullptr;  // [K][P][P]
+
+    // one CG iteration as a CUDA graph
+    cudaGraphExec_t iter_exec = nullptr;
+    bool graph_failed = false;
 
     // stage timing
     std::vector<cudaEvent_t> ev_pool;
@@ -121,21 +139,25 @@ cudaError_t dalloc(T **p, size_t n)
 
 void free_all(pty_ctx *c)
 {
-    void *ptrs[] = {c->probe,   c->tw,       c->pos,       c->perm,   c->nz_off,  c->nz_slot, c->nz_d, c->nz_u,
-                    c->tile_start, c->tile_list,
-                    c->w,       c->fpart,    c->part_sc,   c->part_ls, c->g,         c->g_prev,     c->eta_prev,
-                    c->st,      c->dscalar,  c->hist.F,    c->hist.gamma, c->hist.halvings, c->hist.alpha,
-                    c->stage_obj, c->stage_obj2, c->stage_pat};
+    void *ptrs[] = {c->probe,      c->tw,         c->pos,        c->perm,      c->pat_view,     c->view_pat_off,
+                    c->view_tile_off, c->row_view, c->tile_view,  c->nz_off,    c->nz_slot,      c->nz_d,
+                    c->nz_u,       c->tile_start, c->tile_list,  c->w,         c->fpart,        c->part_sc,
+                    c->part_ls,    c->psi,        c->g,          c->g_prev,    c->eta_prev,     c->st,
+                    c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
+                    c->stage_obj2, c->stage_pat};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->iter_exec) cudaGraphExecDestroy(c->iter_exec);
+    if (c->join) cudaEventDestroy(c->join);
+    if (c->s) cudaStreamDestroy(c->s);
 }
 
 pty::PatternArgs pattern_args(const pty_ctx *c)
 {
     pty::PatternArgs a;
-    a.H = c->H;
-    a.W = c->W;
+    a.H = c->HA;
+    a.W = c->WA;
     a.K = c->K;
     a.probe = c->probe;
     a.tw = c->tw;
@@ -146,6 +168,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.nz_slot = c->nz_slot;
     a.nz_d = c->nz_d;
     a.nz_u = c->nz_u;
+    a.pat_view = c->pat_view;
     a.eps = (float)c->opts.eps;
     return a;
 }
@@ -159,7 +182,18 @@ pty::ScatterPlan scatter_plan(const pty_ctx *c)
     p.ntile_x = c->ntile_x;
     p.tile_start = c->tile_start;
     p.tile_list = c->tile_list;
+    p.tile_view = c->tile_view;
     return p;
+}
+
+pty::ViewMap view_map(const pty_ctx *c)
+{
+    pty::ViewMap m;
+    m.V = c->V;
+    m.pat_off = c->view_pat_off;
+    m.tile_off = c->view_tile_off;
+    m.row_view = c->row_view;
+    return m;
 }
 
 pty::LsArgs ls_args(const pty_ctx *c)
@@ -174,22 +208,19 @@ pty::LsArgs ls_args(const pty_ctx *c)
     return l;
 }
 
-// Device view of a caller array: the pointer itself, or a staging buffer filled from host.
-int obj_in(pty_ctx *c, const float *src, float2 *stage, const float2 **out)
+// Order the context's stream after the caller's (the caller may have just written inputs).
+int enter(pty_ctx *c)
 {
-    if (is_device_ptr(src)) {
-        *out = (const float2 *)src;
-        return PTY_OK;
-    }
-    CK(cudaMemcpyAsync(stage, src, sizeof(float2) * (size_t)c->H * c->W, cudaMemcpyHostToDevice, c->stream));
-    *out = stage;
+    CK(cudaEventRecord(c->join, c->user));
+    CK(cudaStreamWaitEvent(c->s, c->join, 0));
     return PTY_OK;
 }
 
 int ensure_stage(pty_ctx *c)
 {
-    if (!c->stage_obj) CK(dalloc(&c->stage_obj, (size_t)c->H * c->W));
-    if (!c->stage_obj2) CK(dalloc(&c->stage_obj2, (size_t)c->H * c->W));
+    const size_t n = (size_t)c->HA * c->WA;
+    if (!c->stage_obj) CK(dalloc(&c->stage_obj, n));
+    if (!c->stage_obj2) CK(dalloc(&c->stage_obj2, n));
     return PTY_OK;
 }
 
@@ -202,7 +233,7 @@ int ensure_stage_pat(pty_ctx *c)
 int ensure_hist(pty_ctx *c, int n)
 {
     if (c->hist.cap >= n && c->hist.F) return PTY_OK;
-    int cap = std::max(n, 64);
+    const int cap = std::max(n, 64);
     if (c->hist.F) {
         cudaFree(c->hist.F);
         cudaFree(c->hist.gamma);
@@ -210,11 +241,16 @@ int ensure_hist(pty_ctx *c, int n)
         cudaFree(c->hist.alpha);
         c->hist = DevHist{};
     }
-    CK(dalloc(&c->hist.F, (size_t)cap + 1));
-    CK(dalloc(&c->hist.gamma, (size_t)cap));
-    CK(dalloc(&c->hist.halvings, (size_t)cap));
-    CK(dalloc(&c->hist.alpha, (size_t)cap));
+    CK(dalloc(&c->hist.F, (size_t)c->V * (cap + 1)));
+    CK(dalloc(&c->hist.gamma, (size_t)c->V * cap));
+    CK(dalloc(&c->hist.halvings, (size_t)c->V * cap));
+    CK(dalloc(&c->hist.alpha, (size_t)c->V * cap));
     c->hist.cap = cap;
+    // the captured iteration refers to the history arrays: capture again
+    if (c->iter_exec) {
+        cudaGraphExecDestroy(c->iter_exec);
+        c->iter_exec = nullptr;
+    }
     return PTY_OK;
 }
 
@@ -227,21 +263,22 @@ size_t ev_mark(pty_ctx *c)
         c->ev_pool.push_back(e);
     }
     size_t i = c->ev_used++;
-    cudaEventRecord(c->ev_pool[i], c->stream);
+    cudaEventRecord(c->ev_pool[i], c->s);
     return i;
 }
 
 struct StageTimer {
     pty_ctx *c;
     int stage;
+    bool on;
     size_t a = (size_t)-1;
-    StageTimer(pty_ctx *c_, int s) : c(c_), stage(s)
+    StageTimer(pty_ctx *c_, int s, bool on_) : c(c_), stage(s), on(on_)
     {
-        if (c->opts.flags & 1) a = ev_mark(c);
+        if (on) a = ev_mark(c);
     }
     ~StageTimer()
     {
-        if ((c->opts.flags & 1) && a != (size_t)-1) {
+        if (on && a != (size_t)-1) {
             size_t b = ev_mark(c);
             if (b != (size_t)-1) c->ev_marks.push_back({stage, {a, b}});
         }
@@ -263,9 +300,88 @@ void collect_times(pty_ctx *c)
 
 int sync(pty_ctx *c)
 {
-    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaStreamSynchronize(c->s));
     collect_times(c);
     return PTY_OK;
+}
+
+// Copy the caller's objects (one per view, [H_v][W_v], host or device) into an atlas buffer.
+int views_in(pty_ctx *c, const float *const *psi, float2 *atlas)
+{
+    for (int v = 0; v < c->V; v++) {
+        const size_t pitch = sizeof(float2) * c->WA, width = sizeof(float2) * c->Wv[v];
+        CK(cudaMemcpy2DAsync(atlas + (size_t)c->R0[v] * c->WA, pitch, psi[v], width, width, c->Hv[v],
+                             cudaMemcpyDefault, c->s));
+    }
+    return PTY_OK;
+}
+
+int views_out(pty_ctx *c, float *const *psi, const float2 *atlas)
+{
+    for (int v = 0; v < c->V; v++) {
+        const size_t pitch = sizeof(float2) * c->WA, width = sizeof(float2) * c->Wv[v];
+        CK(cudaMemcpy2DAsync(psi[v], width, atlas + (size_t)c->R0[v] * c->WA, pitch, width, c->Hv[v],
+                             cudaMemcpyDefault, c->s));
+    }
+    return PTY_OK;
+}
+
+// The launches of one CG iteration on the context's stream (plain, timed or captured).
+int launch_iteration(pty_ctx *c, bool timed)
+{
+    const pty::PatternArgs a = pattern_args(c);
+    const pty::ScatterPlan plan = scatter_plan(c);
+    const pty::ViewMap vm = view_map(c);
+    const pty::LsArgs ls = ls_args(c);
+    // first window >= 4 candidates when adaptive (then full windows of L), else L each
+    const int first = ls.adaptive ? 4 : ls.L;
+    const int rest = std::max(0, c->opts.max_halvings - first);
+    const int nwin = 1 + (rest + ls.L - 1) / ls.L;
+    {
+        StageTimer t(c, 0, timed);
+        CK(c->impl->grad(a, c->psi, c->w, c->fpart, c->st, c->s));
+    }
+    {
+        StageTimer t(c, 1, timed);
+        CK(pty::launch_scatter(c->P, a, plan, c->w, c->g, 1, c->eta_prev, c->g_prev, c->part_sc, c->st, c->s));
+    }
+    {
+        StageTimer t(c, 3, timed);
+        CK(pty::launch_dy_finalize(c->fpart, c->CS, c->part_sc, vm, c->st, c->hist, ls, c->s));
+    }
+    for (int wdx = 0; wdx < nwin; wdx++) {
+        {
+            StageTimer t(c, 2, timed);
+            // the first window of an adaptive search runs on the 16- or the 32-candidate
+            // kernel as the device chose; the other one returns at once
+            if (wdx == 0 && ls.adaptive) CK(c->impl_ls->ls(a, 16, c->psi, c->g, c->eta_prev, c->part_ls, c->st, c->s));
+            CK(c->impl_ls->ls(a, ls.L, c->psi, c->g, c->eta_prev, c->part_ls, c->st, c->s));
+        }
+        StageTimer t(c, 3, timed);
+        CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, c->CSl, vm, ls, c->st, c->hist, c->s));
+    }
+    StageTimer t(c, 3, timed);
+    CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, c->s));
+    return PTY_OK;
+}
+
+// Capture one iteration into a graph (once per context and configuration).
+void build_graph(pty_ctx *c)
+{
+    if (c->iter_exec || c->graph_failed) return;
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        const int st = launch_iteration(c, false);
+        ok = cudaStreamEndCapture(c->s, &g) == cudaSuccess && st == PTY_OK;
+    }
+    if (ok) ok = cudaGraphInstantiate(&c->iter_exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        cudaGetLastError();
+        c->iter_exec = nullptr;
+        c->graph_failed = true;  // plain launches of the same kernels from now on
+    }
 }
 
 // The autotuner: time the GRAD and LS pattern passes of every configuration for P on the
@@ -273,11 +389,11 @@ int sync(pty_ctx *c)
 // each.  The choice is cached per problem shape for the life of the process, so contexts of
 // the same problem use the same kernels (and give the same bits).
 struct PlanKey {
-    int P, H, W, K;
+    int P, H, W, K, V;
     long long nnz;
     bool operator<(const PlanKey &o) const
     {
-        return std::tie(P, H, W, K, nnz) < std::tie(o.P, o.H, o.W, o.K, o.nnz);
+        return std::tie(P, H, W, K, V, nnz) < std::tie(o.P, o.H, o.W, o.K, o.V, o.nnz);
     }
 };
 std::mutex g_plan_mu;
@@ -287,7 +403,7 @@ int autotune(pty_ctx *c)
 {
     const pty::PatternImpl *impls = nullptr;
     const int n = pty::pattern_impls(c->P, &impls);
-    const PlanKey key{c->P, c->H, c->W, c->K, c->n_entries};
+    const PlanKey key{c->P, c->HA, c->WA, c->K, c->V, c->n_entries};
     int best_g = 0, best_l = 0;
     bool cached = false;
     {
@@ -300,29 +416,28 @@ int autotune(pty_ctx *c)
         }
     }
     if (!cached && n > 1) {
-        int st = ensure_stage(c);
-        if (st) return st;
-        const size_t HW = (size_t)c->H * c->W;
+        const size_t HW = (size_t)c->HA * c->WA;
         std::vector<float2> ones(HW, make_float2(1.f, 0.f));
-        CK(cudaMemcpyAsync(c->stage_obj, ones.data(), sizeof(float2) * HW, cudaMemcpyHostToDevice, c->stream));
-        DevState hs{};
-        hs.Leff = 16;
-        hs.Lsel = 16;
-        for (int l = 0; l < 16; l++) hs.cand[l] = std::ldexp(1.0, -(l + 1));
-        CK(cudaMemcpyAsync(c->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->psi, ones.data(), sizeof(float2) * HW, cudaMemcpyHostToDevice, c->s));
+        std::vector<DevState> hs(c->V);
+        for (auto &h : hs) {
+            h.Leff = 16;
+            h.Lsel = 16;
+            for (int l = 0; l < 16; l++) h.cand[l] = std::ldexp(1.0, -(l + 1));
+        }
+        CK(cudaMemcpyAsync(c->st, hs.data(), sizeof(DevState) * c->V, cudaMemcpyHostToDevice, c->s));
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        pty::PatternArgs a = pattern_args(c);
-        pty::LsArgs ls = ls_args(c);
+        const pty::PatternArgs a = pattern_args(c);
         float tg = 1e30f, tl = 1e30f;
         cudaError_t err = cudaSuccess;
         for (int j = 0; j < n && err == cudaSuccess; j++) {
             float ms = 0.f;
             for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
-                err = cudaEventRecord(e0, c->stream);
-                if (err == cudaSuccess) err = impls[j].grad(a, c->stage_obj, c->w, c->fpart, nullptr, c->stream);
-                if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+                err = cudaEventRecord(e0, c->s);
+                if (err == cudaSuccess) err = impls[j].grad(a, c->psi, c->w, c->fpart, nullptr, c->s);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, c->s);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
             }
@@ -331,10 +446,9 @@ int autotune(pty_ctx *c)
                 best_g = j;
             }
             for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
-                err = cudaEventRecord(e0, c->stream);
-                if (err == cudaSuccess)
-                    err = impls[j].ls(a, 16, c->stage_obj, c->g, c->eta_prev, c->part_ls, c->st, c->stream);
-                if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+                err = cudaEventRecord(e0, c->s);
+                if (err == cudaSuccess) err = impls[j].ls(a, 16, c->psi, c->g, c->eta_prev, c->part_ls, c->st, c->s);
+                if (err == cudaSuccess) err = cudaEventRecord(e1, c->s);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
             }
@@ -346,8 +460,8 @@ int autotune(pty_ctx *c)
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (err != cudaSuccess) return fail(c, PTY_ERR_CUDA, "autotune: %s", cudaGetErrorString(err));
-        CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
-        CK(cudaStreamSynchronize(c->stream));
+        CK(cudaMemsetAsync(c->st, 0, sizeof(DevState) * c->V, c->s));
+        CK(cudaStreamSynchronize(c->s));
         std::lock_guard<std::mutex> lock(g_plan_mu);
         g_plan_cache[key] = {best_g, best_l};
     }
@@ -358,48 +472,25 @@ int autotune(pty_ctx *c)
     return PTY_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-void pty_default_opts(pty_opts *o)
+int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws, const int32_t *Ks, int32_t P,
+                 const float *probe, const int32_t *pos, const float *data, const pty_opts *opts, void *stream)
 {
-    if (!o) return;
-    o->gamma0 = 1.0;
-    o->tau = 0.5;
-    o->t = 0.0;
-    o->max_halvings = 60;
-    o->eps = 0.1;
-    o->ls_window = 0;
-    o->flags = 0;
-    o->tile_config = -1;
-}
-
-const char *pty_last_error(const pty_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
-
-void pty_destroy(pty_ctx *ctx)
-{
-    if (!ctx) return;
-    int cur = 0;
-    cudaGetDevice(&cur);
-    cudaSetDevice(ctx->dev);
-    cudaStreamSynchronize(ctx->stream);
-    free_all(ctx);
-    cudaSetDevice(cur);
-    delete ctx;
-}
-
-int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *probe, int32_t K, const int32_t *pos,
-               const float *data, const pty_opts *opts, void *stream)
-{
-    pty_ctx *c = nullptr;
     if (!out) return fail(nullptr, PTY_ERR_ARG, "out is NULL");
     *out = nullptr;
+    if (V < 1 || !Hs || !Ws || !Ks) return fail(nullptr, PTY_ERR_ARG, "bad view description");
     if (!probe || !pos || !data) return fail(nullptr, PTY_ERR_ARG, "probe, pos and data must be non-NULL");
     if (!pty::pattern_supported(P)) return fail(nullptr, PTY_ERR_ARG, "P=%d not supported (64, 128 or 256)", P);
-    if (H < P || W < P) return fail(nullptr, PTY_ERR_ARG, "object %dx%d smaller than probe %d", H, W, P);
-    if (K < 1) return fail(nullptr, PTY_ERR_ARG, "K=%d < 1", K);
-    if ((int64_t)H * W > (int64_t)1 << 31) return fail(nullptr, PTY_ERR_ARG, "object too large");
+    long long K = 0, rows = 0;
+    int WA = 0;
+    for (int v = 0; v < V; v++) {
+        if (Hs[v] < P || Ws[v] < P)
+            return fail(nullptr, PTY_ERR_ARG, "view %d: object %dx%d smaller than probe %d", v, Hs[v], Ws[v], P);
+        if (Ks[v] < 1) return fail(nullptr, PTY_ERR_ARG, "view %d: K=%d < 1", v, Ks[v]);
+        K += Ks[v];
+        rows = (v + 1 < V) ? (rows + Hs[v] + 31) / 32 * 32 : rows + Hs[v];
+        WA = std::max(WA, (int)Ws[v]);
+    }
+    if (K > (1LL << 30) || rows * WA > (1LL << 31)) return fail(nullptr, PTY_ERR_ARG, "problem too large");
     pty_opts o;
     pty_default_opts(&o);
     if (opts) o = *opts;
@@ -408,7 +499,7 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
         return fail(nullptr, PTY_ERR_ARG, "invalid options (tau in (0,1), gamma0 > 0, 1 <= max_halvings <= 1000, "
                                           "eps >= 0, ls_window in {0,4,8,16,32})");
 
-    // positions: host copy, bounds check, position sort
+    // positions: host copy, bounds check per view, atlas coordinates, position sort
     std::vector<int32_t> hpos((size_t)2 * K);
     if (is_device_ptr(pos)) {
         if (cudaMemcpy(hpos.data(), pos, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -416,21 +507,36 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     } else {
         std::memcpy(hpos.data(), pos, sizeof(int32_t) * 2 * K);
     }
-    for (int k = 0; k < K; k++) {
-        int r = hpos[2 * k], cc = hpos[2 * k + 1];
-        if (r < 0 || cc < 0 || r > H - P || cc > W - P)
-            return fail(nullptr, PTY_ERR_BOUNDS, "position %d (%d,%d) puts the %dx%d patch outside %dx%d", k, r, cc, P,
-                        P, H, W);
+    std::vector<int> R0(V), Koff(V + 1, 0), view_of(K);
+    for (int v = 0, r = 0; v < V; v++) {
+        R0[v] = r;
+        r = (r + Hs[v] + 31) / 32 * 32;
+        Koff[v + 1] = Koff[v] + Ks[v];
     }
+    for (int v = 0; v < V; v++)
+        for (int k = Koff[v]; k < Koff[v + 1]; k++) {
+            const int r = hpos[2 * k], cc = hpos[2 * k + 1];
+            if (r < 0 || cc < 0 || r > Hs[v] - P || cc > Ws[v] - P)
+                return fail(nullptr, PTY_ERR_BOUNDS, "view %d position %d (%d,%d) puts the %dx%d patch outside %dx%d",
+                            v, k - Koff[v], r, cc, P, P, Hs[v], Ws[v]);
+            hpos[2 * k] = r + R0[v];
+            view_of[k] = v;
+        }
 
-    c = new (std::nothrow) pty_ctx;
+    pty_ctx *c = new (std::nothrow) pty_ctx;
     if (!c) return fail(nullptr, PTY_ERR_NOMEM, "host allocation failed");
     cudaGetDevice(&c->dev);
-    c->stream = (cudaStream_t)stream;
-    c->H = H;
-    c->W = W;
+    c->user = (cudaStream_t)stream;
+    c->V = V;
     c->P = P;
-    c->K = K;
+    c->K = (int)K;
+    c->HA = (int)rows;
+    c->WA = WA;
+    c->Hv.assign(Hs, Hs + V);
+    c->Wv.assign(Ws, Ws + V);
+    c->Kv.assign(Ks, Ks + V);
+    c->R0 = R0;
+    c->Koff = Koff;
     c->opts = o;
     {
         const pty::PatternImpl *impls = nullptr;
@@ -463,6 +569,9 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
             return bail(fail(c, e_ == cudaErrorMemoryAllocation ? PTY_ERR_NOMEM : PTY_ERR_CUDA, "%s: %s", #call, \
                              cudaGetErrorString(e_)));                                                     \
     } while (0)
+    CKC(cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+    CKC(cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming));
+    if (enter(c) != PTY_OK) return bail(PTY_ERR_CUDA);
 
     std::vector<int> perm(K);
     std::iota(perm.begin(), perm.end(), 0);
@@ -470,12 +579,17 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
         return hpos[2 * a] != hpos[2 * b] ? hpos[2 * a] < hpos[2 * b] : hpos[2 * a + 1] < hpos[2 * b + 1];
     });
     std::vector<int2> spos(K);
-    for (int i = 0; i < K; i++) spos[i] = make_int2(hpos[2 * perm[i]], hpos[2 * perm[i] + 1]);
+    std::vector<int> pview(K), vpoff(V + 1, 0);
+    for (int i = 0; i < K; i++) {
+        spos[i] = make_int2(hpos[2 * perm[i]], hpos[2 * perm[i] + 1]);
+        pview[i] = view_of[perm[i]];
+    }
+    for (int v = 0; v < V; v++) vpoff[v + 1] = vpoff[v] + Ks[v];  // views are contiguous after the sort
 
     // scatter plan: object tiles of 32 x 64, each with the ascending list of overlapping patterns
     const int TY = 32, TX = 64;
-    c->ntile_y = (H + TY - 1) / TY;
-    c->ntile_x = (W + TX - 1) / TX;
+    c->ntile_y = (c->HA + TY - 1) / TY;
+    c->ntile_x = (c->WA + TX - 1) / TX;
     const int ntiles = c->ntile_y * c->ntile_x;
     std::vector<int> cnt(ntiles + 1, 0);
     for (int i = 0; i < K; i++) {
@@ -493,6 +607,12 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
         for (int ty = ty0; ty <= ty1; ty++)
             for (int tx = tx0; tx <= tx1; tx++) list[fillp[ty * c->ntile_x + tx]++] = i;
     }
+    std::vector<int> rview(c->HA, V - 1), tview(ntiles), vtoff(V + 1, 0);
+    for (int v = 0; v < V; v++)
+        for (int y = R0[v]; y < std::min(c->HA, v + 1 < V ? R0[v + 1] : c->HA); y++) rview[y] = v;
+    for (int b = 0; b < ntiles; b++) tview[b] = rview[(b / c->ntile_x) * TY];
+    for (int v = 0; v < V; v++) vtoff[v] = (R0[v] / TY) * c->ntile_x;
+    vtoff[V] = ntiles;
 
     // probe / P and twiddles exp(-2 pi i m / P), from double precision
     std::vector<float2> hprobe((size_t)P * P), htw(P);
@@ -516,32 +636,44 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
         }
     }
 
-    const size_t PP = (size_t)P * P, HW = (size_t)H * W;
+    const size_t PP = (size_t)P * P, HW = (size_t)c->HA * c->WA;
     CKC(dalloc(&c->probe, PP));
     CKC(dalloc(&c->tw, (size_t)P));
     CKC(dalloc(&c->pos, (size_t)K));
     CKC(dalloc(&c->perm, (size_t)K));
+    CKC(dalloc(&c->pat_view, (size_t)K));
+    CKC(dalloc(&c->view_pat_off, (size_t)V + 1));
+    CKC(dalloc(&c->view_tile_off, (size_t)V + 1));
+    CKC(dalloc(&c->row_view, (size_t)c->HA));
+    CKC(dalloc(&c->tile_view, (size_t)ntiles));
     CKC(dalloc(&c->tile_start, (size_t)ntiles + 1));
     CKC(dalloc(&c->tile_list, std::max<size_t>(list.size(), 1)));
     CKC(dalloc(&c->w, (size_t)K * PP));
     CKC(dalloc(&c->fpart, (size_t)K * c->CSmax));
     CKC(dalloc(&c->part_sc, (size_t)ntiles * 2));
     CKC(dalloc(&c->part_ls, (size_t)K * c->CSmax * (32 + 2)));
+    CKC(dalloc(&c->psi, HW));
     CKC(dalloc(&c->g, HW));
     CKC(dalloc(&c->g_prev, HW));
     CKC(dalloc(&c->eta_prev, HW));
-    CKC(dalloc(&c->st, (size_t)1));
+    CKC(dalloc(&c->st, (size_t)V));
     CKC(dalloc(&c->dscalar, (size_t)4));
-    CKC(cudaMemcpyAsync(c->probe, hprobe.data(), sizeof(float2) * PP, cudaMemcpyHostToDevice, c->stream));
-    CKC(cudaMemcpyAsync(c->tw, htw.data(), sizeof(float2) * P, cudaMemcpyHostToDevice, c->stream));
-    CKC(cudaMemcpyAsync(c->pos, spos.data(), sizeof(int2) * K, cudaMemcpyHostToDevice, c->stream));
-    CKC(cudaMemcpyAsync(c->perm, perm.data(), sizeof(int) * K, cudaMemcpyHostToDevice, c->stream));
-    CKC(cudaMemcpyAsync(c->tile_start, cnt.data(), sizeof(int) * (ntiles + 1), cudaMemcpyHostToDevice, c->stream));
+    CKC(cudaMemcpyAsync(c->probe, hprobe.data(), sizeof(float2) * PP, cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->tw, htw.data(), sizeof(float2) * P, cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->pos, spos.data(), sizeof(int2) * K, cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->perm, perm.data(), sizeof(int) * K, cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->pat_view, pview.data(), sizeof(int) * K, cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->view_pat_off, vpoff.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->view_tile_off, vtoff.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->row_view, rview.data(), sizeof(int) * c->HA, cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->tile_view, tview.data(), sizeof(int) * ntiles, cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemcpyAsync(c->tile_start, cnt.data(), sizeof(int) * (ntiles + 1), cudaMemcpyHostToDevice, c->s));
     if (!list.empty())
-        CKC(cudaMemcpyAsync(c->tile_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->stream));
-    CKC(cudaMemsetAsync(c->g_prev, 0, sizeof(float2) * HW, c->stream));
-    CKC(cudaMemsetAsync(c->eta_prev, 0, sizeof(float2) * HW, c->stream));
-    CKC(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+        CKC(cudaMemcpyAsync(c->tile_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->s));
+    CKC(cudaMemsetAsync(c->g_prev, 0, sizeof(float2) * HW, c->s));
+    CKC(cudaMemsetAsync(c->eta_prev, 0, sizeof(float2) * HW, c->s));
+    CKC(cudaMemsetAsync(c->psi, 0, sizeof(float2) * HW, c->s));
+    CKC(cudaMemsetAsync(c->st, 0, sizeof(DevState) * V, c->s));
 
     // measured data: read here only (a host array goes through a temporary device copy)
     // and kept as the compact list of pixels with counts, in tile slot order
@@ -549,7 +681,7 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     float *dtmp = nullptr;
     if (!is_device_ptr(data)) {
         CKC(dalloc(&dtmp, (size_t)K * PP));
-        CKC(cudaMemcpyAsync(dtmp, data, sizeof(float) * K * PP, cudaMemcpyHostToDevice, c->stream));
+        CKC(cudaMemcpyAsync(dtmp, data, sizeof(float) * K * PP, cudaMemcpyHostToDevice, c->s));
         dd = dtmp;
     }
     auto free_tmp = [&]() {
@@ -558,16 +690,16 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     };
     int *flag = (int *)c->dscalar;
     int *dcnt = nullptr;
-    const int KC = K * c->nzc;
+    const int KC = (int)K * c->nzc;
     std::vector<int> hcnt(KC);
     int hflag = 0;
-    cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), c->stream);
-    if (ce == cudaSuccess) ce = pty::launch_check_data(dd, (size_t)K * PP, flag, c->stream);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t ce = cudaMemsetAsync(flag, 0, sizeof(int), c->s);
+    if (ce == cudaSuccess) ce = pty::launch_check_data(dd, (size_t)K * PP, flag, c->s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, c->s);
     if (ce == cudaSuccess) ce = dalloc(&dcnt, (size_t)KC);
-    if (ce == cudaSuccess) ce = c->impl_nz->nz_count(dd, c->perm, K, dcnt, c->stream);
-    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int) * KC, cudaMemcpyDeviceToHost, c->stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+    if (ce == cudaSuccess) ce = c->impl_nz->nz_count(dd, c->perm, (int)K, dcnt, c->s);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hcnt.data(), dcnt, sizeof(int) * KC, cudaMemcpyDeviceToHost, c->s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s);
     if (dcnt) cudaFree(dcnt);
     if (ce != cudaSuccess) {
         free_tmp();
@@ -586,9 +718,9 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
     if (ce == cudaSuccess) ce = dalloc(&c->nz_d, E);
     if (ce == cudaSuccess) ce = dalloc(&c->nz_u, E);
     if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (KC + 1), cudaMemcpyHostToDevice, c->stream);
-    if (ce == cudaSuccess) ce = c->impl_nz->nz_fill(dd, c->perm, K, c->nz_off, c->nz_slot, c->nz_d, c->stream);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+        ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (KC + 1), cudaMemcpyHostToDevice, c->s);
+    if (ce == cudaSuccess) ce = c->impl_nz->nz_fill(dd, c->perm, (int)K, c->nz_off, c->nz_slot, c->nz_d, c->s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s);
     free_tmp();
     if (ce != cudaSuccess)
         return bail(fail(c, ce == cudaErrorMemoryAllocation ? PTY_ERR_NOMEM : PTY_ERR_CUDA, "data compaction: %s",
@@ -596,32 +728,129 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
 #undef CKC
     if (o.tile_config < 0) {
         const int at = autotune(c);
-        if (at != PTY_OK) {
-            g_create_err = c->err;
-            free_all(c);
-            delete c;
-            return at;
-        }
+        if (at != PTY_OK) return bail(at);
     }
     *out = c;
     return PTY_OK;
+}
+
+// Fill a host report per view from the device history.
+int read_reports(pty_ctx *c, int niter, pty_cg_report *rep, const std::vector<DevState> &hs)
+{
+    if (!rep) return PTY_OK;
+    if (niter <= 0) {
+        for (int v = 0; v < c->V; v++) rep[v].iters_done = hs[v].m;
+        return PTY_OK;
+    }
+    const int cap = c->hist.cap;
+    std::vector<double> hF((size_t)c->V * (cap + 1)), hg((size_t)c->V * cap), ha((size_t)c->V * cap);
+    std::vector<int> hh((size_t)c->V * cap);
+    CK(cudaMemcpyAsync(hF.data(), c->hist.F, sizeof(double) * hF.size(), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(hg.data(), c->hist.gamma, sizeof(double) * hg.size(), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(ha.data(), c->hist.alpha, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(hh.data(), c->hist.halvings, sizeof(int) * hh.size(), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaStreamSynchronize(c->s));
+    for (int v = 0; v < c->V; v++) {
+        const int done = hs[v].m;
+        rep[v].iters_done = done;
+        const int nrec = std::min(niter, done + (hs[v].stalled ? 1 : 0));
+        if (rep[v].F)
+            for (int i = 0; i <= std::min(done, niter); i++) rep[v].F[i] = hF[(size_t)v * (cap + 1) + i];
+        for (int i = 0; i < nrec; i++) {
+            if (rep[v].gamma) rep[v].gamma[i] = hg[(size_t)v * cap + i];
+            if (rep[v].alpha) rep[v].alpha[i] = ha[(size_t)v * cap + i];
+            if (rep[v].halvings) rep[v].halvings[i] = hh[(size_t)v * cap + i];
+        }
+    }
+    return PTY_OK;
+}
+
+int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
+{
+    int st;
+    if ((st = enter(c))) return st;
+    if ((st = ensure_hist(c, niter))) return st;
+    if ((st = views_in(c, (const float *const *)psi, c->psi))) return st;
+    CK(pty::launch_begin_solve(c->st, c->V, c->s));
+    const bool timed = (c->opts.flags & 1) != 0;
+    if (!timed && niter > 0) build_graph(c);
+    for (int it = 0; it < niter; it++) {
+        if (!timed && c->iter_exec) {
+            CK(cudaGraphLaunch(c->iter_exec, c->s));
+        } else if ((st = launch_iteration(c, timed))) {
+            return st;
+        }
+    }
+    std::vector<DevState> hs(c->V);
+    CK(cudaMemcpyAsync(hs.data(), c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
+    if ((st = views_out(c, psi, c->psi))) return st;
+    if ((st = sync(c))) return st;
+    if ((st = read_reports(c, niter, rep, hs))) return st;
+    for (int v = 0; v < c->V; v++)
+        if (hs[v].stalled)
+            return fail(c, PTY_STALLED, "view %d: line search found no step within %d trials at iteration %d", v,
+                        c->opts.max_halvings, hs[v].m);
+    return PTY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pty_default_opts(pty_opts *o)
+{
+    if (!o) return;
+    o->gamma0 = 1.0;
+    o->tau = 0.5;
+    o->t = 0.0;
+    o->max_halvings = 60;
+    o->eps = 0.1;
+    o->ls_window = 0;
+    o->flags = 0;
+    o->tile_config = -1;
+}
+
+const char *pty_last_error(const pty_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+void pty_destroy(pty_ctx *ctx)
+{
+    if (!ctx) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(ctx->dev);
+    if (ctx->s) cudaStreamSynchronize(ctx->s);
+    free_all(ctx);
+    cudaSetDevice(cur);
+    delete ctx;
+}
+
+int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *probe, int32_t K, const int32_t *pos,
+               const float *data, const pty_opts *opts, void *stream)
+{
+    return create_views(out, 1, &H, &W, &K, P, probe, pos, data, opts, stream);
+}
+
+int pty_batch_create(pty_ctx **out, int32_t n_views, const int32_t *H, const int32_t *W, const int32_t *K,
+                     int32_t P, const float *probe, const int32_t *pos, const float *data, const pty_opts *opts,
+                     void *stream)
+{
+    return create_views(out, n_views, H, W, K, P, probe, pos, data, opts, stream);
 }
 
 int pty_forward(pty_ctx *c, const float *psi, float *out)
 {
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
     if (!psi || !out) return fail(c, PTY_ERR_ARG, "psi and out must be non-NULL");
-    int st = ensure_stage(c);
-    if (st) return st;
-    const float2 *dpsi;
-    if ((st = obj_in(c, psi, c->stage_obj, &dpsi))) return st;
+    if (c->V != 1) return fail(c, PTY_ERR_UNSUPPORTED, "pty_forward works on single-view contexts");
+    int st;
+    if ((st = enter(c)) || (st = ensure_stage(c))) return st;
+    if ((st = views_in(c, &psi, c->stage_obj))) return st;
     const bool dev_out = is_device_ptr(out);
     if (!dev_out && (st = ensure_stage_pat(c))) return st;
     float2 *dout = dev_out ? (float2 *)out : c->stage_pat;
-    CK(c->impl->forward(pattern_args(c), dpsi, dout, c->stream));
+    CK(c->impl->forward(pattern_args(c), c->stage_obj, dout, c->s));
     if (!dev_out)
-        CK(cudaMemcpyAsync(out, dout, sizeof(float2) * (size_t)c->K * c->P * c->P, cudaMemcpyDeviceToHost,
-                           c->stream));
+        CK(cudaMemcpyAsync(out, dout, sizeof(float2) * (size_t)c->K * c->P * c->P, cudaMemcpyDeviceToHost, c->s));
     return sync(c);
 }
 
@@ -629,21 +858,22 @@ int pty_adjoint(pty_ctx *c, const float *y, float *x)
 {
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
     if (!y || !x) return fail(c, PTY_ERR_ARG, "y and x must be non-NULL");
-    int st = ensure_stage(c);
-    if (st) return st;
+    if (c->V != 1) return fail(c, PTY_ERR_UNSUPPORTED, "pty_adjoint works on single-view contexts");
+    int st;
+    if ((st = enter(c)) || (st = ensure_stage(c))) return st;
     const size_t n = (size_t)c->K * c->P * c->P;
     const float2 *dy = (const float2 *)y;
     if (!is_device_ptr(y)) {
         if ((st = ensure_stage_pat(c))) return st;
-        CK(cudaMemcpyAsync(c->stage_pat, y, sizeof(float2) * n, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->stage_pat, y, sizeof(float2) * n, cudaMemcpyHostToDevice, c->s));
         dy = c->stage_pat;
     }
-    const bool dev_x = is_device_ptr(x);
-    float2 *dx = dev_x ? (float2 *)x : c->stage_obj;
     pty::PatternArgs a = pattern_args(c);
-    CK(c->impl->adjoint(a, dy, c->w, c->stream));
-    CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, dx, 0, nullptr, nullptr, nullptr, nullptr, c->stream));
-    if (!dev_x) CK(cudaMemcpyAsync(x, dx, sizeof(float2) * (size_t)c->H * c->W, cudaMemcpyDeviceToHost, c->stream));
+    CK(c->impl->adjoint(a, dy, c->w, c->s));
+    CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, c->stage_obj, 0, nullptr, nullptr, nullptr, nullptr,
+                           c->s));
+    float *xo[1] = {x};
+    if ((st = views_out(c, xo, c->stage_obj))) return st;
     return sync(c);
 }
 
@@ -651,20 +881,21 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
 {
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
     if (!psi) return fail(c, PTY_ERR_ARG, "psi must be non-NULL");
-    int st = ensure_stage(c);
-    if (st) return st;
-    const float2 *dpsi;
-    if ((st = obj_in(c, psi, c->stage_obj, &dpsi))) return st;
+    if (c->V != 1) return fail(c, PTY_ERR_UNSUPPORTED, "pty_gradient works on single-view contexts");
+    int st;
+    if ((st = enter(c)) || (st = ensure_stage(c))) return st;
+    if ((st = views_in(c, &psi, c->stage_obj))) return st;
     pty::PatternArgs a = pattern_args(c);
-    CK(c->impl->grad(a, dpsi, c->w, c->fpart, nullptr, c->stream));
-    const bool dev_g = grad && is_device_ptr(grad);
-    float2 *dg = dev_g ? (float2 *)grad : c->stage_obj2;
-    CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, dg, 0, nullptr, nullptr, nullptr, nullptr, c->stream));
-    CK(pty::launch_sum(c->fpart, c->K * c->CS, c->dscalar, c->stream));
-    if (grad && !dev_g)
-        CK(cudaMemcpyAsync(grad, dg, sizeof(float2) * (size_t)c->H * c->W, cudaMemcpyDeviceToHost, c->stream));
+    CK(c->impl->grad(a, c->stage_obj, c->w, c->fpart, nullptr, c->s));
+    CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, c->stage_obj2, 0, nullptr, nullptr, nullptr, nullptr,
+                           c->s));
+    CK(pty::launch_sum(c->fpart, c->K * c->CS, c->dscalar, c->s));
+    if (grad) {
+        float *go[1] = {grad};
+        if ((st = views_out(c, go, c->stage_obj2))) return st;
+    }
     double hF = 0.0;
-    CK(cudaMemcpyAsync(&hF, c->dscalar, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&hF, c->dscalar, sizeof(double), cudaMemcpyDeviceToHost, c->s));
     if ((st = sync(c))) return st;
     if (F) *F = hF;
     return PTY_OK;
@@ -673,10 +904,12 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
 int pty_cg_reset(pty_ctx *c)
 {
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
-    const size_t HW = (size_t)c->H * c->W;
-    CK(cudaMemsetAsync(c->g_prev, 0, sizeof(float2) * HW, c->stream));
-    CK(cudaMemsetAsync(c->eta_prev, 0, sizeof(float2) * HW, c->stream));
-    CK(cudaMemsetAsync(c->st, 0, sizeof(DevState), c->stream));
+    int st;
+    if ((st = enter(c))) return st;
+    const size_t HW = (size_t)c->HA * c->WA;
+    CK(cudaMemsetAsync(c->g_prev, 0, sizeof(float2) * HW, c->s));
+    CK(cudaMemsetAsync(c->eta_prev, 0, sizeof(float2) * HW, c->s));
+    CK(cudaMemsetAsync(c->st, 0, sizeof(DevState) * c->V, c->s));
     return sync(c);
 }
 
@@ -684,111 +917,58 @@ int pty_cg_solve(pty_ctx *c, float *psi_inout, int32_t niter, pty_cg_report *rep
 {
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
     if (!psi_inout || niter < 0) return fail(c, PTY_ERR_ARG, "psi must be non-NULL and niter >= 0");
-    int st = ensure_stage(c);
-    if (st) return st;
-    if ((st = ensure_hist(c, niter))) return st;
-    const size_t HW = (size_t)c->H * c->W;
-    const bool dev_psi = is_device_ptr(psi_inout);
-    float2 *psi = dev_psi ? (float2 *)psi_inout : c->stage_obj;
-    if (!dev_psi) CK(cudaMemcpyAsync(psi, psi_inout, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->stream));
-
-    const pty::PatternArgs a = pattern_args(c);
-    const pty::ScatterPlan plan = scatter_plan(c);
-    const pty::LsArgs ls = ls_args(c);
-    // first window >= 4 candidates when adaptive (then full windows of L), else L each
-    const int first = ls.adaptive ? 4 : ls.L;
-    const int rest = std::max(0, c->opts.max_halvings - first);
-    const int nwin = 1 + (rest + ls.L - 1) / ls.L;
-    const int ntiles = c->ntile_x * c->ntile_y;
-    CK(pty::launch_begin_solve(c->st, c->stream));
-    for (int it = 0; it < niter; it++) {
-        {
-            StageTimer t(c, 0);
-            CK(c->impl->grad(a, psi, c->w, c->fpart, c->st, c->stream));
-        }
-        {
-            StageTimer t(c, 1);
-            CK(pty::launch_scatter(c->P, a, plan, c->w, c->g, 1, c->eta_prev, c->g_prev, c->part_sc, c->st,
-                                   c->stream));
-        }
-        {
-            StageTimer t(c, 3);
-            CK(pty::launch_dy_finalize(c->fpart, c->K * c->CS, c->part_sc, ntiles, c->st, c->hist, ls, c->stream));
-        }
-        for (int wdx = 0; wdx < nwin; wdx++) {
-            {
-                StageTimer t(c, 2);
-                // the first window of an adaptive search runs on the 16- or the 32-candidate
-                // kernel as the device chose; the other one returns at once
-                if (wdx == 0 && ls.adaptive)
-                    CK(c->impl_ls->ls(a, 16, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
-                CK(c->impl_ls->ls(a, ls.L, psi, c->g, c->eta_prev, c->part_ls, c->st, c->stream));
-            }
-            StageTimer t(c, 3);
-            CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, ls, c->st, c->hist, c->stream));
-        }
-        StageTimer t(c, 3);
-        CK(pty::launch_update((int)HW, psi, c->g, c->eta_prev, c->g_prev, c->st, c->stream));
-    }
-    DevState hs;
-    CK(cudaMemcpyAsync(&hs, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
-    if (!dev_psi) CK(cudaMemcpyAsync(psi_inout, psi, sizeof(float2) * HW, cudaMemcpyDeviceToHost, c->stream));
-    std::vector<double> hF(niter + 1), hg(std::max(niter, 1)), ha(std::max(niter, 1));
-    std::vector<int> hh(std::max(niter, 1));
-    if (rep && niter > 0) {
-        CK(cudaMemcpyAsync(hF.data(), c->hist.F, sizeof(double) * (niter + 1), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(hg.data(), c->hist.gamma, sizeof(double) * niter, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(ha.data(), c->hist.alpha, sizeof(double) * niter, cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaMemcpyAsync(hh.data(), c->hist.halvings, sizeof(int) * niter, cudaMemcpyDeviceToHost, c->stream));
-    }
-    if ((st = sync(c))) return st;
-    if (rep) {
-        const int done = hs.m;
-        rep->iters_done = done;
-        const int nrec = std::min(niter, done + (hs.stalled ? 1 : 0));
-        if (rep->F)
-            for (int i = 0; i <= std::min(done, niter); i++) rep->F[i] = hF[i];
-        for (int i = 0; i < nrec; i++) {
-            if (rep->gamma) rep->gamma[i] = hg[i];
-            if (rep->alpha) rep->alpha[i] = ha[i];
-            if (rep->halvings) rep->halvings[i] = hh[i];
-        }
-    }
-    if (hs.stalled) return fail(c, PTY_STALLED, "line search found no step within %d trials at iteration %d",
-                                c->opts.max_halvings, hs.m);
-    return PTY_OK;
+    if (c->V != 1) return fail(c, PTY_ERR_UNSUPPORTED, "use pty_batch_cg_solve for a batch of views");
+    float *p[1] = {psi_inout};
+    return solve(c, p, niter, rep);
 }
+
+int pty_batch_cg_solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *reps)
+{
+    if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
+    if (!psi || niter < 0) return fail(c, PTY_ERR_ARG, "psi must be non-NULL and niter >= 0");
+    for (int v = 0; v < c->V; v++)
+        if (!psi[v]) return fail(c, PTY_ERR_ARG, "psi[%d] is NULL", v);
+    return solve(c, psi, niter, reps);
+}
+
+int32_t pty_num_views(const pty_ctx *c) { return c ? c->V : 0; }
 
 size_t pty_cg_state_size(const pty_ctx *c)
 {
     if (!c) return 0;
-    return 2 * sizeof(float2) * (size_t)c->H * c->W + sizeof(DevState);
+    return 2 * sizeof(float2) * (size_t)c->HA * c->WA + sizeof(DevState) * c->V;
 }
 
 int pty_cg_state_save(pty_ctx *c, void *host_buf)
 {
     if (!c || !host_buf) return fail(c, PTY_ERR_ARG, "ctx and buffer must be non-NULL");
-    const size_t HW = (size_t)c->H * c->W;
+    int st;
+    if ((st = enter(c))) return st;
+    const size_t HW = (size_t)c->HA * c->WA;
     char *b = (char *)host_buf;
-    CK(cudaMemcpyAsync(b, c->g_prev, sizeof(float2) * HW, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(b + sizeof(float2) * HW, c->eta_prev, sizeof(float2) * HW, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(b + 2 * sizeof(float2) * HW, c->st, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(b, c->g_prev, sizeof(float2) * HW, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(b + sizeof(float2) * HW, c->eta_prev, sizeof(float2) * HW, cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(b + 2 * sizeof(float2) * HW, c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
     return sync(c);
 }
 
 int pty_cg_state_load(pty_ctx *c, const void *host_buf)
 {
     if (!c || !host_buf) return fail(c, PTY_ERR_ARG, "ctx and buffer must be non-NULL");
-    const size_t HW = (size_t)c->H * c->W;
+    int st;
+    if ((st = enter(c))) return st;
+    const size_t HW = (size_t)c->HA * c->WA;
     const char *b = (const char *)host_buf;
-    DevState hs;
-    std::memcpy(&hs, b + 2 * sizeof(float2) * HW, sizeof(DevState));
-    hs.m = 0;
-    hs.decided = 0;
-    hs.stalled = 0;
-    CK(cudaMemcpyAsync(c->g_prev, b, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->eta_prev, b + sizeof(float2) * HW, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->st, &hs, sizeof(DevState), cudaMemcpyHostToDevice, c->stream));
+    std::vector<DevState> hs(c->V);
+    std::memcpy(hs.data(), b + 2 * sizeof(float2) * HW, sizeof(DevState) * c->V);
+    for (auto &h : hs) {
+        h.m = 0;
+        h.decided = 0;
+        h.stalled = 0;
+    }
+    CK(cudaMemcpyAsync(c->g_prev, b, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->eta_prev, b + sizeof(float2) * HW, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->s));
+    CK(cudaMemcpyAsync(c->st, hs.data(), sizeof(DevState) * c->V, cudaMemcpyHostToDevice, c->s));
     return sync(c);
 }
 

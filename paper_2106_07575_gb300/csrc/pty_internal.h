@@ -28,12 +28,13 @@ struct DevState {
     double cand[32];  // candidate steps gamma0 tau^(k0+l+1) of the open line-search window
 };
 
-// Per-call history arrays (device), indexed by DevState::m.
+// Per-call history arrays (device), one block of `cap` iterations per view, indexed by
+// DevState::m: F[v * (cap + 1) + m], gamma / halvings / alpha [v * cap + m].
 struct DevHist {
-    double *F;      // [cap + 1]
-    double *gamma;  // [cap]
-    int *halvings;  // [cap]
-    double *alpha;  // [cap]
+    double *F;
+    double *gamma;
+    int *halvings;
+    double *alpha;
     int cap;
 };
 
@@ -53,6 +54,7 @@ struct PatternArgs {
     const unsigned short *nz_slot;  // [E] global slot qy * P + qx of each entry
     const float *nz_d;          // [E] measured counts (> 0) of each entry
     float2 *nz_u;               // [E] u = G psi_m at each entry (GRAD pass -> LS pass)
+    const int *pat_view;        // [K] view of sorted pattern i (all 0 for one view)
     float eps;
 };
 
@@ -101,6 +103,15 @@ struct ScatterPlan {
     int ntile_y, ntile_x;
     const int *tile_start;  // [ntiles + 1] CSR offsets
     const int *tile_list;   // sorted pattern indices overlapping each tile, ascending
+    const int *tile_view;   // [ntiles] view of each tile (views start on tile rows)
+};
+
+// Per-view ranges of the batched layout (device arrays).
+struct ViewMap {
+    int V;
+    const int *pat_off;   // [V + 1] sorted pattern range of each view
+    const int *tile_off;  // [V + 1] scatter-tile range of each view
+    const int *row_view;  // [H] view of each object row
 };
 // out[y][x] = sum over patterns i covering (y, x), in ascending i, of w[i][y-r_i][x-c_i].
 // With dy != 0 also part[b] = (sum |out|^2, sum Re conj(eta_prev) (out - g_prev)) per tile b.
@@ -109,18 +120,21 @@ cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan,
                            double *part, const DevState *st, cudaStream_t s);
 // Fixed-order sum of n doubles into *out (one block).
 cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
-// DIR stage scalars: F_m = sum fpart; alpha from the tile partials (restart rule);
-// resets the line-search window; writes the history of iteration m.
-cudaError_t launch_dy_finalize(const double *fpart, int K, const double *part, int nparts, DevState *st,
+// DIR stage scalars per view (one block each): F_m = sum of the view's fpart (CS per
+// pattern); alpha from the view's tile partials (restart rule); opens the first line-search
+// window; writes the history of iteration m.
+cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, const ViewMap &vm, DevState *st,
                                DevHist h, const LsArgs &ls, cudaStream_t s);
-// LS decision over one window of candidates.
-cudaError_t launch_ls_decide(const double *part, int K, const LsArgs &ls, DevState *st, DevHist h,
-                             cudaStream_t s);
-// Update stage: psi += gamma eta, eta_prev <- eta = -g + alpha eta_prev, g_prev <- g.
-cudaError_t launch_update(int n, float2 *psi, const float2 *g, float2 *eta_prev, float2 *g_prev,
-                          DevState *st, cudaStream_t s);
+// LS stage decision per view over the open window; part rows have length kc (K * CS), the
+// view's partials are [pat_off[v] * cs, pat_off[v + 1] * cs).
+cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const LsArgs &ls, DevState *st,
+                             DevHist h, cudaStream_t s);
+// Update stage for every object pixel (W columns per row): psi += gamma eta,
+// eta_prev <- eta = -g + alpha eta_prev, g_prev <- g, with the scalars of the row's view.
+cudaError_t launch_update(int H, int W, const ViewMap &vm, float2 *psi, const float2 *g, float2 *eta_prev,
+                          float2 *g_prev, DevState *st, cudaStream_t s);
 // flag |= 1 if any of the n floats is NaN, Inf or negative.
 cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t s);
-cudaError_t launch_begin_solve(DevState *st, cudaStream_t s);
+cudaError_t launch_begin_solve(DevState *st, int V, cudaStream_t s);
 
 }  // namespace pty

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_
 
 EXPORTED = ["pty_default_opts", "pty_create", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
             "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
-            "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_gradient_noalloc", "pty_get_plan"]
+            "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_gradient_noalloc", "pty_get_plan",
+            "pty_batch_create", "pty_batch_cg_solve", "pty_num_views"]
 
 
 class PtyError(RuntimeError):
@@ -80,9 +81,14 @@ def load(build_if_missing: bool = True):
     lib.pty_selftest_log1p.argtypes = [vp, vp, i32]
     lib.pty_gradient_noalloc.argtypes = [i32, i32, i32, vp, i32, vp, vp, dbl, vp, vp, vp, vp]
     lib.pty_get_plan.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.pty_batch_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(pty_opts),
+                                     vp]
+    lib.pty_batch_cg_solve.argtypes = [vp, ctypes.POINTER(vp), i32, ctypes.POINTER(pty_cg_report)]
+    lib.pty_num_views.argtypes = [vp]
+    lib.pty_num_views.restype = i32
     for f in ("pty_create", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
               "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p",
-              "pty_gradient_noalloc", "pty_get_plan"):
+              "pty_gradient_noalloc", "pty_get_plan", "pty_batch_create", "pty_batch_cg_solve"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -225,6 +231,91 @@ def pty_gradient_noalloc(H, W, P, probe, K, pos, data, eps, psi, grad, F=None, s
     return lib.pty_gradient_noalloc(H, W, P, _ptr(probe, _C), K, _ptr(pos, _I), _ptr(data, _F), float(eps),
                                     _ptr(psi, _C), _ptr(grad, _C), _ptr(F, ("float64",)),
                                     ctypes.c_void_p(stream) if stream else None)
+
+
+def _reports(niter, n):
+    arrays, reps = [], (pty_cg_report * n)()
+    for v in range(n):
+        a = {"F": np.full(niter + 1, np.nan), "gamma": np.full(max(niter, 1), np.nan),
+             "halvings": np.zeros(max(niter, 1), np.int32), "alpha": np.full(max(niter, 1), np.nan)}
+        arrays.append(a)
+        reps[v] = pty_cg_report(a["F"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                a["gamma"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                a["halvings"].ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                a["alpha"].ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 0)
+    return arrays, reps
+
+
+def pty_batch_create(Hs, Ws, Ks, P, probe, pos, data, opts: pty_opts | None = None, stream=None):
+    lib = load()
+    n = len(Hs)
+    h = np.ascontiguousarray(Hs, np.int32)
+    w = np.ascontiguousarray(Ws, np.int32)
+    k = np.ascontiguousarray(Ks, np.int32)
+    ctx = ctypes.c_void_p()
+    st = lib.pty_batch_create(ctypes.byref(ctx), n, _ptr(h, _I), _ptr(w, _I), _ptr(k, _I), P, _ptr(probe, _C),
+                              _ptr(pos, _I), _ptr(data, _F), ctypes.byref(opts) if opts is not None else None,
+                              ctypes.c_void_p(stream) if stream else None)
+    _check(lib, None, st)
+    return ctx
+
+
+def pty_batch_cg_solve(ctx, psis, niter):
+    """psis: list of per-view objects (torch or numpy complex64), updated in place."""
+    lib = load()
+    n = len(psis)
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(p, _C).value for p in psis])
+    arrays, reps = _reports(niter, n)
+    st = lib.pty_batch_cg_solve(ctx, ptrs, niter, reps)
+    _check(lib, ctx, st, allow=(PTY_STALLED,))
+    out = []
+    for v in range(n):
+        d = reps[v].iters_done
+        a = arrays[v]
+        stalled = st == PTY_STALLED and d < niter and a["halvings"][d] > 0
+        k = min(niter, d + (1 if stalled else 0))
+        out.append({"F": a["F"][: d + 1], "gamma": a["gamma"][:k], "halvings": a["halvings"][:k],
+                    "alpha": a["alpha"][:k], "iters_done": d})
+    return st, out
+
+
+class BatchContext:
+    """Owning wrapper of a batch of views reconstructed together."""
+
+    def __init__(self, probe, views, opts: pty_opts | None = None, stream=None):
+        """views: list of (H, W, pos [K][2] int32, data [K][P][P] float32) on one device or the host."""
+        import torch
+
+        self.P = probe.shape[0]
+        Hs = [v[0] for v in views]
+        Ws = [v[1] for v in views]
+        Ks = [v[2].shape[0] for v in views]
+        pos = torch.cat([torch.as_tensor(v[2]) for v in views]).contiguous()
+        data = torch.cat([torch.as_tensor(v[3]) for v in views]).contiguous()
+        if data.is_cuda is False and probe.is_cuda:
+            pos, data = pos.cuda(), data.cuda()
+        self._keep = (probe, pos, data)
+        self.ctx = pty_batch_create(Hs, Ws, Ks, self.P, probe, pos, data, opts, stream)
+
+    def close(self):
+        if self.ctx:
+            pty_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def cg_solve(self, psis, niter):
+        return pty_batch_cg_solve(self.ctx, psis, niter)
+
+    def plan(self):
+        lib = load()
+        out = (ctypes.c_int32 * 4)()
+        _check(lib, self.ctx, lib.pty_get_plan(self.ctx, out))
+        return {"grad": (out[0], out[1]), "ls": (out[2], out[3])}
 
 
 @dataclass

@@ -207,17 +207,64 @@ def spiral_problem(seed=2, noise=True, K=10000, H=2048, P=256, c=8.94, peak=1e6)
                    {"seed": seed, "peak": peak})
 
 
-def view_sizes(n_views=64, seed=3):
-    """Object sizes of the multi-view workload: uniform over {512, 640, ..., 2048}."""
+def view_sizes(n_views=64, seed=3, lo=512, hi=2048, step=128):
+    """Object sizes of a multi-view series: uniform over {lo, lo + step, ..., hi}."""
     rng = np.random.default_rng(seed)
-    return [int(v) for v in rng.choice(np.arange(512, 2049, 128), size=n_views)]
+    return [int(v) for v in rng.choice(np.arange(lo, hi + 1, step), size=n_views)]
 
 
-def view_problem(v: int, N: int, P=128, step=16, jitter=2, peak=1e5):
-    """One tomographic view: N^2 ellipse phantom, raster filling the view at 16 px step."""
-    rng = np.random.default_rng(3 + v)
-    k = (N - 132) // step + 1
-    psi = ellipse_phantom(N, N, rng)
-    pos = raster_positions(N, N, P, k, step, jitter, rng)
-    probe, d = simulate_counts(psi, gaussian_probe(P), pos, peak, rng, True)
-    return Problem(f"view {v}: {N}x{N}, {k * k} positions", psi, probe, pos, d, 32, {"view": v})
+def measure(psi: np.ndarray, probe: np.ndarray, pos: np.ndarray, rng: np.random.Generator, noise: bool = True):
+    """Counts for an already scaled probe: Poisson(|orthonormal FFT2(probe * patch_k)|^2)."""
+    lam = _farfield_intensity(psi, probe, pos)
+    return (rng.poisson(lam) if noise else lam).astype(np.float32)
+
+
+def _measure_torch(psi, probe, pos, seed, batch=512):
+    """Same detector model on the GPU (torch.fft in float64, torch.poisson), for large series."""
+    import torch
+
+    dev = torch.device("cuda")
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    P = probe.shape[0]
+    K = pos.shape[0]
+    out = torch.empty((K, P, P), dtype=torch.float32, device=dev)
+    ps = torch.from_numpy(psi.astype(np.complex128)).to(dev)
+    pr = torch.from_numpy(probe.astype(np.complex128)).to(dev)
+    iy = torch.arange(P, device=dev)
+    pt = torch.from_numpy(pos.astype(np.int64)).to(dev)
+    for k0 in range(0, K, batch):
+        k1 = min(K, k0 + batch)
+        rows = pt[k0:k1, 0][:, None, None] + iy[None, :, None]
+        cols = pt[k0:k1, 1][:, None, None] + iy[None, None, :]
+        f = torch.fft.fft2(pr[None] * ps[rows, cols], norm="ortho")
+        lam = f.real**2 + f.imag**2
+        out[k0:k1] = torch.poisson(lam, generator=g).to(torch.float32)
+    return out
+
+
+def view_batch(n_views=64, seed=3, sizes=None, P=128, step=16, jitter=2, peak=1e5, backend="numpy"):
+    """A series of views sharing one probe (scaled so view 0's brightest pixel has `peak`).
+
+    View v: N_v x N_v ellipse phantom (seed seed + v), raster filling the view at `step`
+    (k = (N - P - 4) // step + 1 per side), +-jitter.  Returns (probe, views) with
+    views = [(psi_true, pos, d)]; d is a numpy array, or a CUDA tensor with backend="torch".
+    """
+    if sizes is None:
+        sizes = view_sizes(n_views, seed)
+    views = []
+    probe = None
+    for v, N in enumerate(sizes):
+        rng = np.random.default_rng(seed + v)
+        k = (N - P - 4) // step + 1
+        psi = ellipse_phantom(N, N, rng)
+        pos = raster_positions(N, N, P, k, step, jitter, rng)
+        if probe is None:
+            I0 = _farfield_intensity(psi, gaussian_probe(P), pos[: min(len(pos), 64)])
+            probe = (np.sqrt(peak / I0.max()) * gaussian_probe(P).astype(np.complex128)).astype(np.complex64)
+        if backend == "torch":
+            d = _measure_torch(psi, probe, pos, seed * 1000 + v)
+        else:
+            d = measure(psi, probe, pos, rng)
+        views.append((psi, pos, d))
+    return probe, views

@@ -82,6 +82,11 @@ struct pty_ctx {
     float2 *stage_obj = nullptr, *stage_obj2 = nullptr;
     float2 *stage_pat = nullptr;  // [K][P][P]
 
+    // tensor-core DFT form (opts.dft != 0)
+    uint8_t *tc_img_fwd = nullptr, *tc_img_inv = nullptr;
+    int *tc_err = nullptr;
+    float2 *tc_x = nullptr, *tc_t = nullptr;  // [K][P][P] work buffers
+
     // one CG iteration as a CUDA graph
     cudaGraphExec_t iter_exec = nullptr;
     bool graph_failed = false;
@@ -144,7 +149,7 @@ void free_all(pty_ctx *c)
                     c->nz_u,       c->tile_start, c->tile_list,  c->w,         c->fpart,        c->part_sc,
                     c->part_ls,    c->psi,        c->g,          c->g_prev,    c->eta_prev,     c->st,
                     c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
-                    c->stage_obj2, c->stage_pat};
+                    c->stage_obj2, c->stage_pat, c->tc_img_fwd, c->tc_img_inv, c->tc_err, c->tc_x, c->tc_t};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -495,9 +500,12 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     pty_default_opts(&o);
     if (opts) o = *opts;
     if (!(o.tau > 0.0 && o.tau < 1.0) || !(o.gamma0 > 0.0) || o.max_halvings < 1 || o.max_halvings > 1000 ||
-        !(o.eps >= 0.0) || !std::isfinite(o.t) || (o.ls_window != 0 && !pty::ls_window_supported(o.ls_window)))
+        !(o.eps >= 0.0) || !std::isfinite(o.t) || (o.ls_window != 0 && !pty::ls_window_supported(o.ls_window)) ||
+        o.dft < 0 || o.dft > 2)
         return fail(nullptr, PTY_ERR_ARG, "invalid options (tau in (0,1), gamma0 > 0, 1 <= max_halvings <= 1000, "
-                                          "eps >= 0, ls_window in {0,4,8,16,32})");
+                                          "eps >= 0, ls_window in {0,4,8,16,32}, dft in {0,1,2})");
+    if (o.dft != 0 && !pty::tc_dft_supported(P))
+        return fail(nullptr, PTY_ERR_UNSUPPORTED, "the tensor-core DFT supports P = 64 and 128");
 
     // positions: host copy, bounds check per view, atlas coordinates, position sort
     std::vector<int32_t> hpos((size_t)2 * K);
@@ -725,6 +733,20 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     if (ce != cudaSuccess)
         return bail(fail(c, ce == cudaErrorMemoryAllocation ? PTY_ERR_NOMEM : PTY_ERR_CUDA, "data compaction: %s",
                          cudaGetErrorString(ce)));
+    if (o.dft != 0) {
+        std::vector<uint8_t> img;
+        const bool bf16 = o.dft == 1;
+        CKC(pty::tc_dft_images(P, bf16, -1, img));
+        CKC(dalloc(&c->tc_img_fwd, img.size()));
+        CKC(cudaMemcpy(c->tc_img_fwd, img.data(), img.size(), cudaMemcpyHostToDevice));
+        CKC(pty::tc_dft_images(P, bf16, +1, img));
+        CKC(dalloc(&c->tc_img_inv, img.size()));
+        CKC(cudaMemcpy(c->tc_img_inv, img.data(), img.size(), cudaMemcpyHostToDevice));
+        CKC(dalloc(&c->tc_err, (size_t)1));
+        CKC(cudaMemset(c->tc_err, 0, sizeof(int)));
+        CKC(dalloc(&c->tc_x, (size_t)K * PP));
+        CKC(dalloc(&c->tc_t, (size_t)K * PP));
+    }
 #undef CKC
     if (o.tile_config < 0) {
         const int at = autotune(c);
@@ -808,6 +830,7 @@ void pty_default_opts(pty_opts *o)
     o->ls_window = 0;
     o->flags = 0;
     o->tile_config = -1;
+    o->dft = 0;
 }
 
 const char *pty_last_error(const pty_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
@@ -848,7 +871,19 @@ int pty_forward(pty_ctx *c, const float *psi, float *out)
     const bool dev_out = is_device_ptr(out);
     if (!dev_out && (st = ensure_stage_pat(c))) return st;
     float2 *dout = dev_out ? (float2 *)out : c->stage_pat;
-    CK(c->impl->forward(pattern_args(c), c->stage_obj, dout, c->s));
+    if (c->opts.dft == 0) {
+        CK(c->impl->forward(pattern_args(c), c->stage_obj, dout, c->s));
+    } else {
+        // tensor-core form: gather, row DFT (transposed store), row DFT into caller order
+        const bool bf16 = c->opts.dft == 1;
+        CK(pty::launch_gather_patches(pattern_args(c), c->P, c->stage_obj, c->tc_x, c->s));
+        CK(pty::tc_dft_rows(c->P, bf16, c->tc_x, c->tc_t, c->tc_img_fwd, c->K * c->P, nullptr, c->tc_err, c->s));
+        CK(pty::tc_dft_rows(c->P, bf16, c->tc_t, dout, c->tc_img_fwd, c->K * c->P, c->perm, c->tc_err, c->s));
+        int herr = 0;
+        CK(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaStreamSynchronize(c->s));
+        if (herr) return fail(c, PTY_ERR_TIMEOUT, "tensor-core DFT: a device wait timed out");
+    }
     if (!dev_out)
         CK(cudaMemcpyAsync(out, dout, sizeof(float2) * (size_t)c->K * c->P * c->P, cudaMemcpyDeviceToHost, c->s));
     return sync(c);

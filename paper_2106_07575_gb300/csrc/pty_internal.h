@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <vector>
 
 namespace pty {
 
@@ -96,6 +97,17 @@ bool pattern_supported(int P);
 int ls_window_supported(int L);  // 1 if L is an instantiated window size
 // out[i] = log1p_fast(t[i]) (device self-test of the line-search logarithm)
 cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_t s);
+
+// ---- tensor-core DFT (tc_dft.cu) ----
+// One application: Y[b][k][y] = sum_n X[b][y][n] exp(sign 2 pi i n k / P) for the nrows =
+// B * P rows of X (output block b goes to out_index[b] when out_index is non-NULL); two
+// applications give the unnormalised 2-D DFT.  img: the split DFT matrix images built by
+// tc_dft_images (device copy).  err |= 1 on a timed-out device wait.
+bool tc_dft_supported(int P);
+cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out);
+cudaError_t tc_dft_rows(int P, bool bf16, const float2 *X, float2 *Y, const void *img, int nrows,
+                        const int *out_index, int *err, cudaStream_t s);
+cudaError_t launch_gather_patches(const PatternArgs &a, int P, const float2 *psi, float2 *X, cudaStream_t s);
 
 // ---- object kernels (object_kernels.cu) ----
 struct ScatterPlan {

@@ -35,7 +35,7 @@ class PtyError(RuntimeError):
 class pty_opts(ctypes.Structure):
     _fields_ = [("gamma0", ctypes.c_double), ("tau", ctypes.c_double), ("t", ctypes.c_double),
                 ("max_halvings", ctypes.c_int32), ("eps", ctypes.c_double), ("ls_window", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("tile_config", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tile_config", ctypes.c_int32), ("dft", ctypes.c_int32)]
 
 
 class pty_cg_report(ctypes.Structure):

@@ -1,0 +1,38 @@
+"""Tensor-core form of the DFT (tcgen05, split half precision, FP32 accumulation): the
+forward model against the FP64 oracle, with the error of each split format stated."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+from paper_2106_07575_gb300 import pty, synth  # noqa: E402
+
+# Expected error of the hi + lo split: BF16 keeps ~16 significant bits (2^-16 ~ 1.5e-5
+# per operand), FP16 ~22 bits; FP32 accumulation over 2P terms per 1-D pass.
+TOL = {1: 5e-5, 2: 5e-6}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("P", [64, 128])
+@pytest.mark.parametrize("dft", [1, 2])
+def test_tensor_core_forward_vs_oracle(orc, P, dft):
+    if P == 64:
+        p = synth.small_problem(H=192, W=160, P=64, n=5, step=20, jitter=1, peak=1e4, seed=50)
+    else:
+        p = synth.small_problem(H=320, W=288, P=128, n=5, step=35, jitter=2, peak=1e5, seed=51)
+    o = pty.default_opts()
+    o.dft = dft
+    ctx = pty.Context(dev(p.probe), dev(p.pos), dev(p.d), p.H, p.W, o, stream=torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(1)
+    psi = (p.psi_true * (1 + 0.05 * rng.standard_normal((p.H, p.W)))).astype(np.complex64)
+    out = torch.empty((p.K, p.P, p.P), dtype=torch.complex64, device="cuda")
+    ctx.forward(dev(psi), out)
+    want = orc.forward(psi, p.probe, p.pos, nthreads=0)
+    e = float(np.linalg.norm(out.cpu().numpy() - want) / np.linalg.norm(want))
+    print(f"tensor-core DFT P={P} {'BF16' if dft == 1 else 'FP16'} hi+lo: forward rel L2 vs FP64 {e:.2e}")
+    assert e <= TOL[dft]

@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--tile-config", type=int, default=None)
     ap.add_argument("--workload", choices=["production", "spiral", "small", "views"], default="production")
     ap.add_argument("--views", type=int, default=64)
+    ap.add_argument("--dft", type=int, default=0, help="0 FFT, 1 tensor-core split BF16, 2 split FP16")
     return ap.parse_args()
 
 
@@ -256,6 +257,7 @@ def main():
         opts.ls_window = args.ls_window
     if args.tile_config is not None:
         opts.tile_config = args.tile_config
+    opts.dft = args.dft
     probe_d, pos_d, d_d = dev(p.probe), dev(p.pos), dev(p.d)
     ctx = pty.Context(probe_d, pos_d, d_d, p.H, p.W, opts, stream=stream.cuda_stream)
     psi = dev(p.psi0())
@@ -325,6 +327,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / max(steps_done, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload, "ls_window": L, "tile_config": opts.tile_config, "plan": ctx.plan(),
+                   "dft": ["fp32 fft", "tensor-core split bf16", "tensor-core split fp16"][args.dft],
                    "l2": f"inputs larger than L2 ({p.d.nbytes / 1e6:.0f} MB data)",
                    "parallelism": f"{world} independent replica(s)"},
         "status": pty.STATUS_NAMES[st], "roofline": roof, "clocks": clocks, "gpu_launches": launches,

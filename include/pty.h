@@ -98,7 +98,7 @@ typedef struct {
     int32_t dft;         /* 2-D DFTs: 0 (default) FP32 FFT on the CUDA cores; 1 batched complex
                             GEMMs on the tensor cores with operands split into BF16 hi + lo and
                             FP32 accumulation; 2 the same with FP16 hi + lo.  1 and 2 need
-                            P = 64 or 128 and currently apply to pty_forward. */
+                            P = 64 or 128; pty_adjoint needs 0. */
 } pty_opts;
 
 typedef struct pty_ctx pty_ctx;

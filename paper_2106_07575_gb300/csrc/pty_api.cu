@@ -85,7 +85,8 @@ struct pty_ctx {
     // tensor-core DFT form (opts.dft != 0)
     uint8_t *tc_img_fwd = nullptr, *tc_img_inv = nullptr;
     int *tc_err = nullptr;
-    float2 *tc_x = nullptr, *tc_t = nullptr;  // [K][P][P] work buffers
+    float2 *tc_x = nullptr, *tc_t = nullptr, *tc_u = nullptr;  // [K][P][P] work buffers
+    double *tc_pars = nullptr;                                  // [2][K] Parseval sums
 
     // one CG iteration as a CUDA graph
     cudaGraphExec_t iter_exec = nullptr;
@@ -149,7 +150,8 @@ void free_all(pty_ctx *c)
                     c->nz_u,       c->tile_start, c->tile_list,  c->w,         c->fpart,        c->part_sc,
                     c->part_ls,    c->psi,        c->g,          c->g_prev,    c->eta_prev,     c->st,
                     c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
-                    c->stage_obj2, c->stage_pat, c->tc_img_fwd, c->tc_img_inv, c->tc_err, c->tc_x, c->tc_t};
+                    c->stage_obj2, c->stage_pat, c->tc_img_fwd, c->tc_img_inv, c->tc_err, c->tc_x, c->tc_t,
+                    c->tc_u, c->tc_pars};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -331,9 +333,66 @@ int views_out(pty_ctx *c, float *const *psi, const float2 *atlas)
     return PTY_OK;
 }
 
+// GRAD pattern pass of the tensor-core form: psi -> w (sorted order) and fpart.
+int tc_grad(pty_ctx *c, const float2 *psi, const DevState *st)
+{
+    const pty::PatternArgs a = pattern_args(c);
+    const bool bf16 = c->opts.dft == 1;
+    const int rows = c->K * c->P;
+    CK(pty::launch_gather_patches(a, c->P, psi, c->tc_x, c->s));
+    CK(pty::tc_dft_rows(c->P, bf16, c->tc_x, c->tc_t, c->tc_img_fwd, rows, nullptr, nullptr, c->tc_err, c->s));
+    CK(pty::tc_dft_rows(c->P, bf16, c->tc_t, c->tc_u, c->tc_img_fwd, rows, nullptr, nullptr, c->tc_err, c->s));
+    CK(pty::launch_tc_residual(a, c->P, c->tc_u, c->fpart, st, c->s));
+    CK(pty::tc_dft_rows(c->P, bf16, c->tc_u, c->tc_t, c->tc_img_inv, rows, nullptr, nullptr, c->tc_err, c->s));
+    CK(pty::tc_dft_rows(c->P, bf16, c->tc_t, c->w, c->tc_img_inv, rows, nullptr, c->probe, c->tc_err, c->s));
+    return PTY_OK;
+}
+
 // The launches of one CG iteration on the context's stream (plain, timed or captured).
 int launch_iteration(pty_ctx *c, bool timed)
 {
+    if (c->opts.dft != 0) {
+        const pty::PatternArgs a = pattern_args(c);
+        const pty::ScatterPlan plan = scatter_plan(c);
+        const pty::ViewMap vm = view_map(c);
+        const pty::LsArgs ls = ls_args(c);
+        const bool bf16 = c->opts.dft == 1;
+        const int rows = c->K * c->P;
+        const int first = ls.adaptive ? 4 : ls.L;
+        const int nwin = 1 + (std::max(0, c->opts.max_halvings - first) + ls.L - 1) / ls.L;
+        int st;
+        {
+            StageTimer t(c, 0, timed);
+            if ((st = tc_grad(c, c->psi, c->st))) return st;
+        }
+        {
+            StageTimer t(c, 1, timed);
+            CK(pty::launch_scatter(c->P, a, plan, c->w, c->g, 1, c->eta_prev, c->g_prev, c->part_sc, c->st, c->s));
+        }
+        {
+            StageTimer t(c, 3, timed);
+            CK(pty::launch_dy_finalize(c->fpart, 1, c->part_sc, vm, c->st, c->hist, ls, c->s));
+        }
+        {
+            StageTimer t(c, 2, timed);  // v = G eta once per iteration; windows reuse it
+            CK(pty::launch_tc_gather_eta(a, c->P, c->psi, c->g, c->eta_prev, c->tc_x, c->tc_pars, c->st, c->s));
+            CK(pty::tc_dft_rows(c->P, bf16, c->tc_x, c->tc_t, c->tc_img_fwd, rows, nullptr, nullptr, c->tc_err, c->s));
+            CK(pty::tc_dft_rows(c->P, bf16, c->tc_t, c->tc_u, c->tc_img_fwd, rows, nullptr, nullptr, c->tc_err, c->s));
+        }
+        for (int wdx = 0; wdx < nwin; wdx++) {
+            {
+                StageTimer t(c, 2, timed);
+                if (wdx == 0 && ls.adaptive)
+                    CK(pty::launch_tc_ls_entries(a, c->P, 16, c->tc_u, c->tc_pars, c->part_ls, c->st, c->s));
+                CK(pty::launch_tc_ls_entries(a, c->P, ls.L, c->tc_u, c->tc_pars, c->part_ls, c->st, c->s));
+            }
+            StageTimer t(c, 3, timed);
+            CK(pty::launch_ls_decide(c->part_ls, c->K, 1, vm, ls, c->st, c->hist, c->s));
+        }
+        StageTimer t(c, 3, timed);
+        CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, c->s));
+        return PTY_OK;
+    }
     const pty::PatternArgs a = pattern_args(c);
     const pty::ScatterPlan plan = scatter_plan(c);
     const pty::ViewMap vm = view_map(c);
@@ -746,9 +805,12 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
         CKC(cudaMemset(c->tc_err, 0, sizeof(int)));
         CKC(dalloc(&c->tc_x, (size_t)K * PP));
         CKC(dalloc(&c->tc_t, (size_t)K * PP));
+        CKC(dalloc(&c->tc_u, (size_t)K * PP));
+        CKC(dalloc(&c->tc_pars, (size_t)2 * K));
+        c->CS = c->CSl = 1;  // one partial per pattern in this form
     }
 #undef CKC
-    if (o.tile_config < 0) {
+    if (o.tile_config < 0 && o.dft == 0) {
         const int at = autotune(c);
         if (at != PTY_OK) return bail(at);
     }
@@ -804,9 +866,12 @@ int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
         }
     }
     std::vector<DevState> hs(c->V);
+    int herr = 0;
     CK(cudaMemcpyAsync(hs.data(), c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
+    if (c->tc_err) CK(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     if ((st = views_out(c, psi, c->psi))) return st;
     if ((st = sync(c))) return st;
+    if (herr) return fail(c, PTY_ERR_TIMEOUT, "tensor-core DFT: a device wait timed out");
     if ((st = read_reports(c, niter, rep, hs))) return st;
     for (int v = 0; v < c->V; v++)
         if (hs[v].stalled)
@@ -877,8 +942,10 @@ int pty_forward(pty_ctx *c, const float *psi, float *out)
         // tensor-core form: gather, row DFT (transposed store), row DFT into caller order
         const bool bf16 = c->opts.dft == 1;
         CK(pty::launch_gather_patches(pattern_args(c), c->P, c->stage_obj, c->tc_x, c->s));
-        CK(pty::tc_dft_rows(c->P, bf16, c->tc_x, c->tc_t, c->tc_img_fwd, c->K * c->P, nullptr, c->tc_err, c->s));
-        CK(pty::tc_dft_rows(c->P, bf16, c->tc_t, dout, c->tc_img_fwd, c->K * c->P, c->perm, c->tc_err, c->s));
+        CK(pty::tc_dft_rows(c->P, bf16, c->tc_x, c->tc_t, c->tc_img_fwd, c->K * c->P, nullptr, nullptr, c->tc_err,
+                            c->s));
+        CK(pty::tc_dft_rows(c->P, bf16, c->tc_t, dout, c->tc_img_fwd, c->K * c->P, c->perm, nullptr, c->tc_err,
+                            c->s));
         int herr = 0;
         CK(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
         CK(cudaStreamSynchronize(c->s));
@@ -894,6 +961,7 @@ int pty_adjoint(pty_ctx *c, const float *y, float *x)
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
     if (!y || !x) return fail(c, PTY_ERR_ARG, "y and x must be non-NULL");
     if (c->V != 1) return fail(c, PTY_ERR_UNSUPPORTED, "pty_adjoint works on single-view contexts");
+    if (c->opts.dft != 0) return fail(c, PTY_ERR_UNSUPPORTED, "pty_adjoint uses the FFT form (dft = 0)");
     int st;
     if ((st = enter(c)) || (st = ensure_stage(c))) return st;
     const size_t n = (size_t)c->K * c->P * c->P;
@@ -921,7 +989,11 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
     if ((st = enter(c)) || (st = ensure_stage(c))) return st;
     if ((st = views_in(c, &psi, c->stage_obj))) return st;
     pty::PatternArgs a = pattern_args(c);
-    CK(c->impl->grad(a, c->stage_obj, c->w, c->fpart, nullptr, c->s));
+    if (c->opts.dft != 0) {
+        if ((st = tc_grad(c, c->stage_obj, nullptr))) return st;
+    } else {
+        CK(c->impl->grad(a, c->stage_obj, c->w, c->fpart, nullptr, c->s));
+    }
     CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, c->stage_obj2, 0, nullptr, nullptr, nullptr, nullptr,
                            c->s));
     CK(pty::launch_sum(c->fpart, c->K * c->CS, c->dscalar, c->s));

@@ -105,9 +105,21 @@ cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_
 // tc_dft_images (device copy).  err |= 1 on a timed-out device wait.
 bool tc_dft_supported(int P);
 cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out);
+// conj_mul (nullable): the stored element (k, y) of block b is multiplied by conj(conj_mul[k*P + y]).
 cudaError_t tc_dft_rows(int P, bool bf16, const float2 *X, float2 *Y, const void *img, int nrows,
-                        const int *out_index, int *err, cudaStream_t s);
+                        const int *out_index, const float2 *conj_mul, int *err, cudaStream_t s);
 cudaError_t launch_gather_patches(const PatternArgs &a, int P, const float2 *psi, float2 *X, cudaStream_t s);
+// CG pieces of the tensor-core form (tc_cg.cu); spectra U, V are [K][P][P] in natural order.
+// Residual of Eq. 3 in place in U at the entries, objective terms fpart[i], u kept in nz_u.
+cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, double *fpart, const DevState *st,
+                               cudaStream_t s);
+// X[i] = (probe / P) * eta patch with eta = -g + alpha_v eta_prev; pars[0][i], pars[1][i] =
+// P^2 sum conj(p psi / P) (p eta / P) and P^2 sum |p eta / P|^2 (real parts, Parseval sums).
+cudaError_t launch_tc_gather_eta(const PatternArgs &a, int P, const float2 *psi, const float2 *g, const float2 *ep,
+                                 float2 *X, double *pars, const DevState *st, cudaStream_t s);
+// Candidate sums of one line-search window from V at the entries (layout [L+2][K]).
+cudaError_t launch_tc_ls_entries(const PatternArgs &a, int P, int L, const float2 *V, const double *pars,
+                                 double *part, const DevState *st, cudaStream_t s);
 
 // ---- object kernels (object_kernels.cu) ----
 struct ScatterPlan {

@@ -161,6 +161,7 @@ template <int P, bool BF16>
 __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__restrict__ X, float2 *__restrict__ Y,
                                                                const uint8_t *__restrict__ Bimg, int nrows,
                                                                const int *__restrict__ out_index,
+                                                               const float2 *__restrict__ conj_mul,
                                                                int *__restrict__ err)
 {
     using G = TcGeo<P>;
@@ -292,8 +293,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
             tmem_ld32(tl + P + k0, im);
             if (row < nrows) {
                 float2 *dst = Y + (size_t)(out_index ? out_index[b] : b) * P * P + y;
+                if (conj_mul) {  // element (k, y) of the 2-D result times conj(conj_mul[k][y])
 #pragma unroll
-                for (int q = 0; q < 32; q++) dst[(size_t)(k0 + q) * P] = make_float2(re[q], im[q]);
+                    for (int q = 0; q < 32; q++) {
+                        const float2 c = __ldg(conj_mul + (size_t)(k0 + q) * P + y);
+                        dst[(size_t)(k0 + q) * P] =
+                            make_float2(fmaf(c.x, re[q], c.y * im[q]), fmaf(c.x, im[q], -c.y * re[q]));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; q++) dst[(size_t)(k0 + q) * P] = make_float2(re[q], im[q]);
+                }
             }
         }
     }
@@ -359,15 +369,15 @@ std::vector<uint8_t> build_images(int sign)
 }
 
 template <int P, bool BF16>
-cudaError_t run_rows(const float2 *X, float2 *Y, const void *img, int nrows, const int *out_index, int *err,
-                     cudaStream_t s)
+cudaError_t run_rows(const float2 *X, float2 *Y, const void *img, int nrows, const int *out_index,
+                     const float2 *conj_mul, int *err, cudaStream_t s)
 {
     using G = TcGeo<P>;
     auto k = k_dft_rows_tc<P, BF16>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
     const int nb = (nrows + kTcRows - 1) / kTcRows;
-    k<<<nb, kTcThreads, G::SMEM, s>>>(X, Y, (const uint8_t *)img, nrows, out_index, err);
+    k<<<nb, kTcThreads, G::SMEM, s>>>(X, Y, (const uint8_t *)img, nrows, out_index, conj_mul, err);
     return cudaGetLastError();
 }
 
@@ -384,14 +394,14 @@ cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out)
 }
 
 cudaError_t tc_dft_rows(int P, bool bf16, const float2 *X, float2 *Y, const void *img, int nrows,
-                        const int *out_index, int *err, cudaStream_t s)
+                        const int *out_index, const float2 *conj_mul, int *err, cudaStream_t s)
 {
     if (P == 64)
-        return bf16 ? run_rows<64, true>(X, Y, img, nrows, out_index, err, s)
-                    : run_rows<64, false>(X, Y, img, nrows, out_index, err, s);
+        return bf16 ? run_rows<64, true>(X, Y, img, nrows, out_index, conj_mul, err, s)
+                    : run_rows<64, false>(X, Y, img, nrows, out_index, conj_mul, err, s);
     if (P == 128)
-        return bf16 ? run_rows<128, true>(X, Y, img, nrows, out_index, err, s)
-                    : run_rows<128, false>(X, Y, img, nrows, out_index, err, s);
+        return bf16 ? run_rows<128, true>(X, Y, img, nrows, out_index, conj_mul, err, s)
+                    : run_rows<128, false>(X, Y, img, nrows, out_index, conj_mul, err, s);
     return cudaErrorInvalidValue;
 }
 

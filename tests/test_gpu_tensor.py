@@ -36,3 +36,31 @@ def test_tensor_core_forward_vs_oracle(orc, P, dft):
     e = float(np.linalg.norm(out.cpu().numpy() - want) / np.linalg.norm(want))
     print(f"tensor-core DFT P={P} {'BF16' if dft == 1 else 'FP16'} hi+lo: forward rel L2 vs FP64 {e:.2e}")
     assert e <= TOL[dft]
+
+
+GRAD_TOL = {1: 1e-4, 2: 1e-5}
+
+
+@pytest.mark.parametrize("dft", [1, 2])
+def test_tensor_core_gradient_and_cg(orc, dft):
+    """Gradient (Eq. 3) and ten CG iterations with every 2-D DFT on the tensor cores."""
+    p = synth.small_problem()
+    o = pty.default_opts()
+    o.dft = dft
+    ctx = pty.Context(dev(p.probe), dev(p.pos), dev(p.d), p.H, p.W, o, stream=torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(2)
+    psi = (p.psi_true * (1 + 0.05 * rng.standard_normal((p.H, p.W)))).astype(np.complex64)
+    g = torch.empty((p.H, p.W), dtype=torch.complex64, device="cuda")
+    F = ctx.gradient(dev(psi), g)
+    gw, Fw = orc.gradient(psi, p.probe, p.pos, p.d, nthreads=0)
+    e = float(np.linalg.norm(g.cpu().numpy() - gw) / np.linalg.norm(gw))
+    name = "BF16" if dft == 1 else "FP16"
+    print(f"tensor-core {name}: gradient rel L2 {e:.2e}, objective rel {abs(F - Fw) / abs(Fw):.2e}")
+    assert e <= GRAD_TOL[dft] and abs(F - Fw) <= 1e-4 * abs(Fw)
+    x = dev(p.psi0())
+    st, rep = ctx.cg_solve(x, 10)
+    want = orc.cg_solve(p.psi0(), p.probe, p.pos, p.d, 10, nthreads=0)
+    relF = np.abs(rep["F"] - want["F"]) / np.abs(want["F"])
+    print(f"tensor-core {name} CG: max objective rel err {relF.max():.2e}, trials {list(rep['halvings'])} vs "
+          f"{list(want['halvings'])}")
+    assert st == pty.PTY_OK and np.all(relF <= 1e-4)

@@ -9,8 +9,9 @@
 // half-precision part (BF16 or FP16): A B ~ Ah Bh + Al Bh + Ah Bl, evaluated as ONE GEMM
 // with K' = 3 * 2P, A' = [Ah | Al | Ah], B' = [Bh; Bh; Bl], accumulated in FP32 in TMEM.
 //
-// Per CTA (128 threads): 128 consecutive rows.  The threads split the FP32 rows into Ah
-// and Al in shared memory (canonical K-major layout without swizzle: 8 x 16-byte core
+// Per CTA (128 threads): 128 consecutive rows.  For FP16 the tile is first scaled by a power
+// of two so that its largest magnitude is 2^14 at most (undone exactly on the results).  The
+// threads split the FP32 rows into Ah and Al in shared memory (canonical K-major layout without swizzle: 8 x 16-byte core
 // matrices, K-adjacent core matrices 128 bytes apart).  B' is stored in global memory as
 // a sequence of exact shared-memory images of 64-column chunks (built on the host from
 // FP64), streamed by cp.async.bulk through a 3-stage mbarrier pipeline.  One thread issues
@@ -189,6 +190,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
 
+    // FP16 has a narrow range: scale the tile by a power of two so that its largest
+    // magnitude is at most 2^14 (exact), and undo it on the FP32 results.
+    float scale = 1.0f;
+    if constexpr (!BF16) {
+        __shared__ unsigned int amax_bits;
+        if (tid == 0) amax_bits = 0u;
+        __syncthreads();
+        float mx = 0.0f;
+        for (int t = tid; t < kTcRows * (P / 8); t += kTcThreads) {
+            const int row = m0 + t / (P / 8), j = t % (P / 8);
+            if (row < nrows) {
+                const float4 *src = (const float4 *)(X + (size_t)row * P + 8 * j);
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    const float4 v = __ldg(src + q);
+                    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+                }
+            }
+        }
+        atomicMax(&amax_bits, __float_as_uint(mx));  // non-negative floats order as integers
+        __syncthreads();
+        const float amax = __uint_as_float(amax_bits);
+        if (amax > 0.0f && isfinite(amax)) {
+            int e;
+            frexpf(amax, &e);  // amax < 2^e
+            scale = ldexpf(1.0f, 14 - e);
+        }
+    }
+
     // A: split the FP32 rows into high and low halves, canonical K-major layout.
     // Task (row m, group j of 8 complex values) -> core-matrix rows of re and im.
     for (int t = tid; t < kTcRows * (P / 8); t += kTcThreads) {
@@ -200,10 +230,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
 #pragma unroll
             for (int q = 0; q < 4; q++) {
                 const float4 v = __ldg(src + q);
-                re[2 * q] = v.x;
-                im[2 * q] = v.y;
-                re[2 * q + 1] = v.z;
-                im[2 * q + 1] = v.w;
+                re[2 * q] = v.x * scale;
+                im[2 * q] = v.y * scale;
+                re[2 * q + 1] = v.z * scale;
+                im[2 * q + 1] = v.w * scale;
             }
         } else {
 #pragma unroll
@@ -286,11 +316,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
         const int m = warp * 32 + lane, row = m0 + m;
         const int b = row / P, y = row % P;
         const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        const float unscale = 1.0f / scale;  // exact: a power of two
 #pragma unroll 1
         for (int k0 = 0; k0 < P; k0 += 32) {
             float re[32], im[32];
             tmem_ld32(tl + k0, re);
             tmem_ld32(tl + P + k0, im);
+#pragma unroll
+            for (int q = 0; q < 32; q++) {
+                re[q] *= unscale;
+                im[q] *= unscale;
+            }
             if (row < nrows) {
                 float2 *dst = Y + (size_t)(out_index ? out_index[b] : b) * P * P + y;
                 if (conj_mul) {  // element (k, y) of the 2-D result times conj(conj_mul[k][y])

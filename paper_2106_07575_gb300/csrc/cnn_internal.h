@@ -1,0 +1,60 @@
+// cnn_internal.h -- kernel launchers of the learned initial guess (not part of the C ABI).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pty_internal.h"
+
+namespace pty {
+namespace cnn {
+
+constexpr int kC = 32;  // hidden channels of this build
+
+bool size_supported(int P);
+
+// x[b] = log(1 + sqrt(max(d[src_b], 0))) with the zero frequency moved to [P/2][P/2];
+// src_b = idx ? idx[b] : b.
+cudaError_t launch_features(int P, int B, const float *d, const int *idx, float *x, cudaStream_t s);
+
+// Hidden 3x3 convolution with kC output channels.  cin = 1 or kC (forward: z = conv + bias,
+// a = GELU(z)); cin = 2 or kC (backward-data: out = conv(in; flipped transposed weights) *
+// GELU'(zprev)).  w: BF16 [kC][cin][9].
+cudaError_t launch_conv_fwd(int P, int cin, int B, const float *in, const __nv_bfloat16 *w, const float *bias,
+                            float *z, float *a, cudaStream_t s);
+cudaError_t launch_conv_bwd(int P, int cin, int B, const float *in, const __nv_bfloat16 *wt, const float *zprev,
+                            float *out, cudaStream_t s);
+// Output layer: z [B][2][P][P] = conv(in [B][kC][P][P]; w [2][kC][9]) + bias.
+cudaError_t launch_conv_head(int P, int B, const float *in, const __nv_bfloat16 *w, const float *bias, float *z,
+                             cudaStream_t s);
+// Head and loss: o = (0.8 + 0.2 s0) exp(i pi/2 s1), s = sigmoid(z).  With t: part[blk] =
+// block sums of w |o - t|^2 and dz = d loss / d z with loss scaled by inv_norm.  o_out,
+// t may be NULL.  Returns the number of partial sums in *nparts.
+cudaError_t launch_head_loss(int P, int B, const float *z, const int *idx, const float2 *t, const float *w,
+                             double inv_norm, float2 *o_out, float *dz, double *part, int *nparts,
+                             cudaStream_t s);
+// loss[0] = inv_norm * sum of n partials (fixed order).
+cudaError_t launch_loss_finalize(const double *part, int n, double inv_norm, double *loss, cudaStream_t s);
+// Weight and bias gradient of one layer: partials per CTA, then a fixed-order sum into
+// grad ([cout][cin][9] then [cout]).  part must hold wgrad_parts(P, B) * (cout*cin*9 + cout).
+int wgrad_blocks(int P, int B);
+cudaError_t launch_wgrad(int P, int cin, int cout, int B, const float *a, const float *dz, float *part,
+                         float *grad, cudaStream_t s);
+// Adam on n masters, then the BF16 copies of every layer's weights are refreshed.
+cudaError_t launch_adam(float *master, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
+                        float eps, float bc1, float bc2, cudaStream_t s);
+// w16 = bf16(master weights), wt16[ci][co][8 - tap] = the same (backward-data weights).
+cudaError_t launch_refresh(const float *master, int cout, int cin, __nv_bfloat16 *w16, __nv_bfloat16 *wt16,
+                           cudaStream_t s);
+
+// Stitching (probe-weighted average of patches) over a single-view context's positions:
+// num/den accumulated per object tile, then psi0 = num / (den + floor * max den), 1 where
+// den = 0.  patches in the caller's order (perm maps sorted -> caller index).
+cudaError_t launch_stitch(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *patches, float floor,
+                          float2 *num, float *den, float *tile_max, float *dmax, float2 *out, cudaStream_t s);
+// Fill n complex values with 1.
+cudaError_t launch_fill_ones(float2 *x, size_t n, cudaStream_t s);
+
+}  // namespace cnn
+}  // namespace pty

@@ -32,7 +32,9 @@
 #include <tuple>
 #include <vector>
 
+#include "cnn_internal.h"
 #include "pty.h"
+#include "pty_cnn.h"
 #include "pty_internal.h"
 
 using pty::DevHist;
@@ -87,6 +89,10 @@ struct pty_ctx {
     int *tc_err = nullptr;
     float2 *tc_x = nullptr, *tc_t = nullptr, *tc_u = nullptr;  // [K][P][P] work buffers
     double *tc_pars = nullptr;                                  // [2][K] Parseval sums
+
+    // stitching of patch estimates (pty_stitch)
+    float *st_den = nullptr;   // [HA][WA] sum of |p|^2
+    float *st_tmax = nullptr;  // [ntiles + 1] per-tile maxima, then the maximum
 
     // one CG iteration as a CUDA graph
     cudaGraphExec_t iter_exec = nullptr;
@@ -151,7 +157,7 @@ void free_all(pty_ctx *c)
                     c->part_ls,    c->psi,        c->g,          c->g_prev,    c->eta_prev,     c->st,
                     c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
                     c->stage_obj2, c->stage_pat, c->tc_img_fwd, c->tc_img_inv, c->tc_err, c->tc_x, c->tc_t,
-                    c->tc_u, c->tc_pars};
+                    c->tc_u, c->tc_pars, c->st_den, c->st_tmax};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -1104,7 +1110,40 @@ int pty_stage_times(pty_ctx *c, double ms[4], int64_t launches[4], int reset)
     return PTY_OK;
 }
 
+int pty_stitch(pty_ctx *c, const float *patches, float floor_, float *psi0)
+{
+    if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
+    if (!patches || !psi0) return fail(c, PTY_ERR_ARG, "patches and psi0 must be non-NULL");
+    if (!(floor_ >= 0.f) || !std::isfinite(floor_)) return fail(c, PTY_ERR_ARG, "floor must be finite and >= 0");
+    if (c->V != 1) return fail(c, PTY_ERR_UNSUPPORTED, "pty_stitch works on single-view contexts");
+    if (!is_device_ptr(patches)) return fail(c, PTY_ERR_ARG, "patches must be a device array");
+    int st;
+    if ((st = enter(c)) || (st = ensure_stage(c))) return st;
+    const int ntiles = c->ntile_x * c->ntile_y;
+    if (!c->st_den) CK(dalloc(&c->st_den, (size_t)c->HA * c->WA));
+    if (!c->st_tmax) CK(dalloc(&c->st_tmax, (size_t)ntiles + 1));
+    CK(pty::cnn::launch_stitch(c->P, pattern_args(c), scatter_plan(c), (const float2 *)patches, floor_,
+                               c->stage_obj2, c->st_den, c->st_tmax, c->st_tmax + ntiles, c->stage_obj, c->s));
+    float *po[1] = {psi0};
+    if ((st = views_out(c, po, c->stage_obj))) return st;
+    return sync(c);
+}
+
 }  // extern "C"
+
+namespace pty {
+int ctx_info(const pty_ctx *c, int *H, int *W, int *P, int *K, int *V, int *dev)
+{
+    if (!c) return PTY_ERR_ARG;
+    *H = c->Hv.empty() ? 0 : c->Hv[0];
+    *W = c->Wv.empty() ? 0 : c->Wv[0];
+    *P = c->P;
+    *K = c->K;
+    *V = c->V;
+    *dev = c->dev;
+    return PTY_OK;
+}
+}  // namespace pty
 
 #include "pty_selftest.h"
 

@@ -162,3 +162,10 @@ cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t 
 cudaError_t launch_begin_solve(DevState *st, int V, cudaStream_t s);
 
 }  // namespace pty
+
+struct pty_ctx;
+namespace pty {
+// Sizes of a context: view 0's object H x W, P, K, the number of views and the device.
+int ctx_info(const pty_ctx *c, int *H, int *W, int *P, int *K, int *V, int *dev);
+
+}  // namespace pty

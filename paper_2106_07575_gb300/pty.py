@@ -23,7 +23,12 @@ STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_
 EXPORTED = ["pty_default_opts", "pty_create", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
             "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
             "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_gradient_noalloc", "pty_get_plan",
-            "pty_batch_create", "pty_batch_cg_solve", "pty_num_views"]
+            "pty_batch_create", "pty_batch_cg_solve", "pty_num_views",
+            # learned initial guess (include/pty_cnn.h)
+            "pty_default_adam", "pty_cnn_create", "pty_cnn_destroy", "pty_cnn_last_error", "pty_cnn_num_params",
+            "pty_cnn_set_params", "pty_cnn_get_params", "pty_cnn_init_params", "pty_cnn_set_loss_weight",
+            "pty_cnn_predict", "pty_cnn_loss_grad", "pty_cnn_train_step", "pty_cnn_train", "pty_stitch",
+            "pty_learned_init"]
 
 
 class PtyError(RuntimeError):
@@ -36,6 +41,16 @@ class pty_opts(ctypes.Structure):
     _fields_ = [("gamma0", ctypes.c_double), ("tau", ctypes.c_double), ("t", ctypes.c_double),
                 ("max_halvings", ctypes.c_int32), ("eps", ctypes.c_double), ("ls_window", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("tile_config", ctypes.c_int32), ("dft", ctypes.c_int32)]
+
+
+class pty_adam(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_double), ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("eps", ctypes.c_double)]
+
+
+class pty_init_report(ctypes.Structure):
+    _fields_ = [("F_learned", ctypes.c_double), ("F_ones", ctypes.c_double), ("used_learned", ctypes.c_int32),
+                ("ms", ctypes.c_double)]
 
 
 class pty_cg_report(ctypes.Structure):
@@ -86,9 +101,32 @@ def load(build_if_missing: bool = True):
     lib.pty_batch_cg_solve.argtypes = [vp, ctypes.POINTER(vp), i32, ctypes.POINTER(pty_cg_report)]
     lib.pty_num_views.argtypes = [vp]
     lib.pty_num_views.restype = i32
+    u64, i64 = ctypes.c_uint64, ctypes.c_int64
+    lib.pty_default_adam.argtypes = [ctypes.POINTER(pty_adam)]
+    lib.pty_default_adam.restype = None
+    lib.pty_cnn_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, vp]
+    lib.pty_cnn_destroy.argtypes = [vp]
+    lib.pty_cnn_destroy.restype = None
+    lib.pty_cnn_last_error.argtypes = [vp]
+    lib.pty_cnn_last_error.restype = ctypes.c_char_p
+    lib.pty_cnn_num_params.argtypes = [vp]
+    lib.pty_cnn_num_params.restype = i64
+    lib.pty_cnn_set_params.argtypes = [vp, vp]
+    lib.pty_cnn_get_params.argtypes = [vp, vp]
+    lib.pty_cnn_init_params.argtypes = [vp, u64]
+    lib.pty_cnn_set_loss_weight.argtypes = [vp, vp]
+    lib.pty_cnn_predict.argtypes = [vp, i32, vp, vp]
+    lib.pty_cnn_loss_grad.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(dbl), vp]
+    lib.pty_cnn_train_step.argtypes = [vp, i32, vp, vp, vp, ctypes.POINTER(pty_adam), ctypes.POINTER(dbl)]
+    lib.pty_cnn_train.argtypes = [vp, i64, vp, vp, i32, i32, u64, ctypes.POINTER(pty_adam), ctypes.POINTER(dbl)]
+    lib.pty_stitch.argtypes = [vp, vp, ctypes.c_float, vp]
+    lib.pty_learned_init.argtypes = [vp, vp, vp, vp, ctypes.POINTER(pty_init_report)]
     for f in ("pty_create", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
               "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p",
-              "pty_gradient_noalloc", "pty_get_plan", "pty_batch_create", "pty_batch_cg_solve"):
+              "pty_gradient_noalloc", "pty_get_plan", "pty_batch_create", "pty_batch_cg_solve", "pty_cnn_create",
+              "pty_cnn_set_params", "pty_cnn_get_params", "pty_cnn_init_params", "pty_cnn_set_loss_weight",
+              "pty_cnn_predict", "pty_cnn_loss_grad", "pty_cnn_train_step", "pty_cnn_train", "pty_stitch",
+              "pty_learned_init"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -378,3 +416,100 @@ class Context:
         out = (ctypes.c_int32 * 4)()
         _check(lib, self.ctx, lib.pty_get_plan(self.ctx, out))
         return {"grad": (out[0], out[1]), "ls": (out[2], out[3])}
+
+
+# ---- learned initial guess (include/pty_cnn.h) ----
+
+def default_adam() -> pty_adam:
+    a = pty_adam()
+    load().pty_default_adam(ctypes.byref(a))
+    return a
+
+
+def _check_cnn(lib, net, st):
+    if st != PTY_OK:
+        msg = lib.pty_cnn_last_error(net)
+        raise PtyError(st, msg.decode() if msg else "")
+    return st
+
+
+def pty_stitch(ctx, patches, floor, psi0):
+    lib = load()
+    return _check(lib, ctx, lib.pty_stitch(ctx, _ptr(patches, _C), float(floor), _ptr(psi0, _C)))
+
+
+class Network:
+    """Owning wrapper of a pty_cnn network (the learned initial guess)."""
+
+    def __init__(self, P, channels=32, layers=6, max_batch=64, stream=None):
+        lib = load()
+        net = ctypes.c_void_p()
+        _check_cnn(lib, None, lib.pty_cnn_create(ctypes.byref(net), P, channels, layers, max_batch,
+                                                 ctypes.c_void_p(stream) if stream else None))
+        self.net, self.P, self.channels, self.layers, self.max_batch = net, P, channels, layers, max_batch
+
+    def close(self):
+        if self.net:
+            load().pty_cnn_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, *args):
+        lib = load()
+        return _check_cnn(lib, self.net, getattr(lib, name)(self.net, *args))
+
+    @property
+    def num_params(self) -> int:
+        return int(load().pty_cnn_num_params(self.net))
+
+    def set_params(self, params):
+        return self._call("pty_cnn_set_params", _ptr(params, _F))
+
+    def get_params(self, out=None):
+        out = np.empty(self.num_params, np.float32) if out is None else out
+        self._call("pty_cnn_get_params", _ptr(out, _F))
+        return out
+
+    def init_params(self, seed):
+        return self._call("pty_cnn_init_params", ctypes.c_uint64(seed))
+
+    def set_loss_weight(self, w):
+        return self._call("pty_cnn_set_loss_weight", _ptr(w, _F))
+
+    def predict(self, d, o):
+        return self._call("pty_cnn_predict", int(d.shape[0]), _ptr(d, _F), _ptr(o, _C))
+
+    def loss_grad(self, d, t, idx=None, grad=None, B=None):
+        B = int(idx.shape[0] if idx is not None else d.shape[0]) if B is None else B
+        loss = ctypes.c_double(0.0)
+        self._call("pty_cnn_loss_grad", B, _ptr(idx, _I), _ptr(d, _F), _ptr(t, _C), ctypes.byref(loss),
+                   _ptr(grad, _F))
+        return loss.value
+
+    def train_step(self, d, t, idx=None, adam: pty_adam | None = None, B=None):
+        B = int(idx.shape[0] if idx is not None else d.shape[0]) if B is None else B
+        loss = ctypes.c_double(0.0)
+        self._call("pty_cnn_train_step", B, _ptr(idx, _I), _ptr(d, _F), _ptr(t, _C),
+                   ctypes.byref(adam) if adam is not None else None, ctypes.byref(loss))
+        return loss.value
+
+    def train(self, d, t, batch, steps, seed=0, adam: pty_adam | None = None):
+        losses = np.zeros(max(steps, 1), np.float64)
+        self._call("pty_cnn_train", int(d.shape[0]), _ptr(d, _F), _ptr(t, _C), batch, steps, ctypes.c_uint64(seed),
+                   ctypes.byref(adam) if adam is not None else None,
+                   losses.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        return losses[:steps]
+
+    def learned_init(self, ctx, d, psi0):
+        """Write the learned start (or the ones start, whichever has the lower objective) to psi0."""
+        lib = load()
+        rep = pty_init_report()
+        c = ctx.ctx if isinstance(ctx, Context) else ctx
+        _check_cnn(lib, self.net, lib.pty_learned_init(c, self.net, _ptr(d, _F), _ptr(psi0, _C), ctypes.byref(rep)))
+        return {"F_learned": rep.F_learned, "F_ones": rep.F_ones, "used_learned": bool(rep.used_learned),
+                "ms": rep.ms}

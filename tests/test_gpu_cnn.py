@@ -1,0 +1,173 @@
+"""Learned initial guess on the GPU: CNN kernels against the FP64 oracle network.
+
+Forward, loss, every parameter gradient and the Adam update are compared with
+oracle/cnn.py on the same seeded inputs; weights are BF16-representable so that the BF16
+working copy of the kernels is exact and only FP32 accumulation separates the two.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cnn as ocnn
+from paper_2106_07575_gb300 import pty, synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+DEV = torch.device("cuda")
+# FP32 accumulation over 9 x 32 taps per layer and six layers against FP64
+FWD_TOL = 1e-5
+# weight gradients sum B x P^2 pixel products in FP32 per CTA band, then in FP64
+GRAD_TOL = 1e-4
+
+
+def bf16_exact(params):
+    out = []
+    for W, b in params:
+        Wr = torch.from_numpy(W.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+        out.append((Wr, b.astype(np.float32).astype(np.float64)))
+    return out
+
+
+def flat(params):
+    return np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in params]).astype(np.float32)
+
+
+def unflat(v, like):
+    out, o = [], 0
+    for W, b in like:
+        nW, nb = W.size, b.size
+        out.append((v[o:o + nW].reshape(W.shape).astype(np.float64), v[o + nW:o + nW + nb].astype(np.float64)))
+        o += nW + nb
+    return out
+
+
+def inputs(B, P, seed):
+    rng = np.random.default_rng(seed)
+    probe = synth.gaussian_probe(P)
+    # counts shaped like a far-field pattern: bright centre at [0, 0], Poisson noise
+    ky = np.fft.fftfreq(P)[:, None]
+    kx = np.fft.fftfreq(P)[None, :]
+    lam = 1e4 * np.exp(-(ky**2 + kx**2) / (2 * 0.05**2)) + 0.5
+    d = rng.poisson(lam[None] * rng.uniform(0.5, 1.5, (B, 1, 1))).astype(np.float32)
+    t = (rng.uniform(0.8, 1.0, (B, P, P)) * np.exp(1j * rng.uniform(0, math.pi / 2, (B, P, P)))).astype(np.complex64)
+    w = (np.abs(probe.astype(np.complex128)) ** 2).astype(np.float32)
+    return d, t, w
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+@pytest.mark.parametrize("P,B", [(64, 3), (128, 1)])
+def test_cnn_forward_parity(P, B):
+    params = bf16_exact(ocnn.init_params(channels=32, layers=6, seed=11))
+    # non-zero biases so that the bias path is exercised
+    rng = np.random.default_rng(12)
+    params = [(W, rng.normal(0, 0.05, b.shape).astype(np.float32).astype(np.float64)) for W, b in params]
+    d, _, _ = inputs(B, P, 13)
+    net = pty.Network(P, 32, 6, max_batch=2)  # B = 3 runs in two chunks
+    net.set_params(flat(params))
+    o = torch.empty((B, P, P), dtype=torch.complex64, device=DEV)
+    net.predict(torch.from_numpy(d).to(DEV), o)
+    want, _ = ocnn.forward(params, ocnn.features(d.astype(np.float64)))
+    e = rel(o.cpu().numpy(), want)
+    print(f"P={P} B={B}: CNN forward rel L2 vs FP64 {e:.2e}")
+    assert e <= FWD_TOL
+
+
+@pytest.mark.parametrize("P,B", [(64, 3), (128, 1)])
+def test_cnn_loss_and_gradient_parity(P, B):
+    params = bf16_exact(ocnn.init_params(channels=32, layers=6, seed=21))
+    d, t, w = inputs(B + 1, P, 22)
+    idx = np.array([B] + list(range(B - 1)), np.int32)  # gathered pairs, not in storage order
+    net = pty.Network(P, 32, 6, max_batch=B)
+    net.set_params(flat(params))
+    net.set_loss_weight(torch.from_numpy(w).to(DEV))
+    g = torch.empty(net.num_params, dtype=torch.float32, device=DEV)
+    loss = net.loss_grad(torch.from_numpy(d).to(DEV), torch.from_numpy(t).to(DEV),
+                         idx=torch.from_numpy(idx).to(DEV), grad=g)
+    want_loss, want_grads = ocnn.loss_and_grads(params, ocnn.features(d[idx].astype(np.float64)),
+                                                t[idx].astype(np.complex128), w.astype(np.float64))
+    got = unflat(g.cpu().numpy(), params)
+    print(f"P={P} B={B}: loss {loss:.9e} vs {want_loss:.9e}")
+    assert abs(loss - want_loss) <= 1e-6 * abs(want_loss)
+    for l, ((gW, gb), (wW, wb)) in enumerate(zip(got, want_grads)):
+        eW, eb = rel(gW, wW), rel(gb, wb)
+        print(f"  layer {l}: dW rel L2 {eW:.2e}, db rel L2 {eb:.2e}")
+        assert eW <= GRAD_TOL and eb <= GRAD_TOL
+
+
+def test_cnn_gradient_deterministic_and_adam_step():
+    P, B = 64, 2
+    params = bf16_exact(ocnn.init_params(channels=32, layers=4, seed=31))
+    d, t, w = inputs(B, P, 32)
+    dd, td = torch.from_numpy(d).to(DEV), torch.from_numpy(t).to(DEV)
+    net = pty.Network(P, 32, 4, max_batch=B)
+    net.set_params(flat(params))
+    net.set_loss_weight(w)
+    g1 = torch.empty(net.num_params, dtype=torch.float32, device=DEV)
+    g2 = torch.empty_like(g1)
+    l1 = net.loss_grad(dd, td, grad=g1)
+    l2 = net.loss_grad(dd, td, grad=g2)
+    assert l1 == l2 and torch.equal(g1, g2), "loss/gradient not bitwise reproducible"
+    lr = 1e-3
+    adam = pty.default_adam()
+    adam.lr = lr
+    l3 = net.train_step(dd, td, adam=adam)
+    assert l3 == l1
+    got = net.get_params()
+    _, og = ocnn.loss_and_grads(params, ocnn.features(d.astype(np.float64)), t.astype(np.complex128),
+                                w.astype(np.float64))
+    want = flat(ocnn.adam_step(params, og, {}, lr=lr))
+    gref = np.abs(np.concatenate([np.concatenate([a.ravel(), b.ravel()]) for a, b in og]))
+    # first Adam step = -lr g / (|g| + eps): compare where the gradient is well above its
+    # FP32 error, so that its sign is certain on both sides
+    mask = gref > 1e-4 * gref.max()
+    assert mask.mean() > 0.5
+    err = np.abs(got - want)[mask].max()
+    print(f"Adam step: max |param diff| {err:.2e} over {mask.sum()} of {mask.size} parameters")
+    assert err <= 1e-3 * lr + 1e-7
+    np.testing.assert_allclose(got - flat(params), want - flat(params), atol=2.01 * lr)
+
+
+def test_stitch_parity_and_uncovered_pixels():
+    P = 64
+    rng = np.random.default_rng(41)
+    H, W = 200, 260
+    pos = np.stack([rng.integers(0, H - P - 40, 30), rng.integers(0, W - P - 60, 30)], 1).astype(np.int32)
+    probe = synth.gaussian_probe(P).astype(np.complex64)
+    d0 = np.zeros((30, P, P), np.float32)
+    ctx = pty.Context(torch.from_numpy(probe).to(DEV), torch.from_numpy(pos).to(DEV), torch.from_numpy(d0).to(DEV),
+                      H, W)
+    patches = (rng.uniform(0.8, 1, (30, P, P)) * np.exp(1j * rng.uniform(0, 1.5, (30, P, P)))).astype(np.complex64)
+    out = torch.empty((H, W), dtype=torch.complex64, device=DEV)
+    pty.pty_stitch(ctx.ctx, torch.from_numpy(patches).to(DEV), 1e-3, out)
+    want = ocnn.stitch(patches.astype(np.complex128), probe, pos, (H, W), floor=1e-3)
+    got = out.cpu().numpy()
+    e = np.abs(got - want).max()
+    print(f"stitch max abs err {e:.2e}")
+    assert e <= 1e-5
+    assert np.all(got[H - 1, :] == 1.0) and np.all(got[:, W - 1] == 1.0)  # beyond every scan
+    ctx.close()
+
+
+def test_cnn_argument_errors():
+    with pytest.raises(pty.PtyError):
+        pty.Network(96, 32, 6)
+    with pytest.raises(pty.PtyError):
+        pty.Network(64, 16, 6)
+    net = pty.Network(64, 32, 3, max_batch=2)
+    d = torch.zeros((3, 64, 64), dtype=torch.float32, device=DEV)
+    t = torch.zeros((3, 64, 64), dtype=torch.complex64, device=DEV)
+    with pytest.raises(pty.PtyError):
+        net.loss_grad(d, t)  # batch 3 > max_batch 2
+    with pytest.raises(pty.PtyError):
+        net.loss_grad(d.cpu(), t.cpu(), B=2)  # host arrays
+    bad = -np.ones((64, 64), np.float32)
+    with pytest.raises(pty.PtyError):
+        net.set_loss_weight(bad)

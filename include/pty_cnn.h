@@ -53,6 +53,7 @@ typedef struct {
     double F_learned;     /* Eq. 2 objective at the stitched network start */
     double F_ones;        /* Eq. 2 objective at the all-ones start */
     int32_t used_learned; /* 1: psi0 is the network start; 0: the ones start was kept */
+    double scale;         /* factor c applied to the stitched patches (see pty_learned_init) */
     double ms;            /* wall time of the call (prediction, stitching, both objectives) */
 } pty_init_report;
 
@@ -125,8 +126,12 @@ PTY_API int pty_stitch(pty_ctx *ctx, const float *patches, float floor, float *p
 /*
  * The learned start of a single-view context: predict every pattern of `d` (device
  * [K][P][P], the context's measured data in the caller's order) with `net` (P must
- * match), stitch with floor 1e-3, evaluate Eq. 2 there and at the all-ones object, and
- * write the better of the two to psi0 (host or device [H][W] complex).  rep may be NULL.
+ * match), stitch with floor 1e-3, and scale the stitched object psi_s by the factor c at
+ * which Eq. 2 is stationary along the ray {c psi_s} when eps is neglected,
+ *   c^2 = sum d / sum |G psi_s|^2
+ * (the denominator by Parseval from the stitch's sum of |p|^2 over positions, no extra
+ * forward pass).  Then evaluate Eq. 2 at c psi_s and at the all-ones object, and write the
+ * better of the two to psi0 (host or device [H][W] complex).  rep may be NULL.
  */
 PTY_API int pty_learned_init(pty_ctx *ctx, pty_cnn *net, const float *d, float *psi0, pty_init_report *rep);
 

@@ -471,12 +471,19 @@ int pty_learned_init(pty_ctx *ctx, pty_cnn *n, const float *d, float *psi0, pty_
     const auto t0 = std::chrono::steady_clock::now();
     const size_t PP = (size_t)P * P, HW = (size_t)H * W;
     float2 *patches = nullptr, *pl = nullptr, *po = nullptr;
+    double *red = nullptr;
     CKN(dalloc(&patches, (size_t)K * PP));
     int st = PTY_OK;
-    if (dalloc(&pl, HW) || dalloc(&po, HW)) st = fail(n, PTY_ERR_NOMEM, "device allocation failed");
-    double Fl = 0.0, Fo = 0.0;
+    if (dalloc(&pl, HW) || dalloc(&po, HW) || dalloc(&red, (size_t)pty::cnn::kPartials + 1))
+        st = fail(n, PTY_ERR_NOMEM, "device allocation failed");
+    double Fl = 0.0, Fo = 0.0, scale = 1.0;
     if (!st) st = pty_cnn_predict(n, K, d, (float *)patches);
-    if (!st && (st = pty_stitch(ctx, (const float *)patches, 1e-3f, (float *)pl)))
+    // sum of the measured counts, for the scale of the stitched start
+    if (!st && (pty::cnn::launch_sum_sq_weighted(nullptr, d, (size_t)K * PP, red, red + pty::cnn::kPartials, 1.0,
+                                                 n->s) != cudaSuccess ||
+                cudaStreamSynchronize(n->s) != cudaSuccess))
+        st = fail(n, PTY_ERR_CUDA, "sum of counts failed");
+    if (!st && (st = pty::cnn::stitch_scaled(ctx, patches, 1e-3f, red + pty::cnn::kPartials, pl, &scale)))
         fail(n, st, "stitch: %s", pty_last_error(ctx));
     if (!st && (st = pty_gradient(ctx, (const float *)pl, nullptr, &Fl)))
         fail(n, st, "objective: %s", pty_last_error(ctx));
@@ -492,11 +499,13 @@ int pty_learned_init(pty_ctx *ctx, pty_cnn *n, const float *d, float *psi0, pty_
     cudaFree(patches);
     if (pl) cudaFree(pl);
     if (po) cudaFree(po);
+    if (red) cudaFree(red);
     if (st) return st;
     if (rep) {
         rep->F_learned = Fl;
         rep->F_ones = Fo;
         rep->used_learned = use ? 1 : 0;
+        rep->scale = scale;
         rep->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     return PTY_OK;

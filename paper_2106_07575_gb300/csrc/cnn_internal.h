@@ -53,6 +53,24 @@ cudaError_t launch_refresh(const float *master, int cout, int cin, __nv_bfloat16
 // den = 0.  patches in the caller's order (perm maps sorted -> caller index).
 cudaError_t launch_stitch(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *patches, float floor,
                           float2 *num, float *den, float *tile_max, float *dmax, float2 *out, cudaStream_t s);
+}  // namespace cnn
+}  // namespace pty
+
+struct pty_ctx;
+namespace pty {
+namespace cnn {
+// Stitch (as pty_stitch) into the device array out [H][W] and scale it by the factor c at
+// which Eq. 2 is stationary along the ray {c psi} when eps is neglected:
+// c^2 = sum d / sum |G psi|^2, with sum |G psi|^2 = sum_x |psi(x)|^2 sum_k |p(x - r_k)|^2
+// (Parseval, unitary F).  sum_d: device double holding sum d.  c_out: host double (nullable).
+int stitch_scaled(pty_ctx *c, const float2 *patches, float floor, const double *sum_d, float2 *out, double *c_out);
+// out[0] = scale * sum_i |x_i|^2 w_i (x non-NULL) or scale * sum_i w_i (x NULL), in FP64 in a
+// fixed order; part holds kPartials doubles.
+constexpr int kPartials = 1024;
+cudaError_t launch_sum_sq_weighted(const float2 *x, const float *w, size_t n, double *part, double *out, double scale,
+                                   cudaStream_t s);
+// x *= c with c = sqrt(num[0] / den[0]) (1 if den[0] <= 0); c_out[0] = c (nullable).
+cudaError_t launch_scale_to(float2 *x, size_t n, const double *num, const double *den, double *c_out, cudaStream_t s);
 // Fill n complex values with 1.
 cudaError_t launch_fill_ones(float2 *x, size_t n, cudaStream_t s);
 

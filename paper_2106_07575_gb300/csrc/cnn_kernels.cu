@@ -516,6 +516,40 @@ __global__ void k_stitch_finish(size_t n, const float2 *__restrict__ num, const 
     }
 }
 
+// part[block] = sum over the block's grid-stride share of |x|^2 w (x complex, w real, both
+// may be offset views) or of plain floats (x NULL).
+constexpr int kRedBlocks = 1024;
+
+__global__ void __launch_bounds__(NT) k_partial_sums(const float2 *__restrict__ x, const float *__restrict__ w, size_t n,
+                                                     double *__restrict__ part)
+{
+    __shared__ double red[NT / 32], tot[1];
+    double s = 0.0;
+    for (size_t i = (size_t)blockIdx.x * NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
+        if (x) {
+            const float2 v = x[i];
+            s += (double)(v.x * v.x + v.y * v.y) * (double)w[i];
+        } else {
+            s += (double)w[i];
+        }
+    }
+    double v[1] = {s};
+    block_sum<NT, 1>(v, red, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+}
+
+__global__ void k_scale(float2 *__restrict__ x, size_t n, const double *__restrict__ num, const double *__restrict__ den,
+                        double *__restrict__ c_out)
+{
+    const double c = den[0] > 0.0 ? sqrt(num[0] / den[0]) : 1.0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && c_out) c_out[0] = c;
+    const float cf = (float)c;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 v = x[i];
+        x[i] = make_float2(v.x * cf, v.y * cf);
+    }
+}
+
 __global__ void k_fill_ones(float2 *x, size_t n)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
@@ -684,6 +718,20 @@ cudaError_t launch_stitch(int P, const PatternArgs &a, const ScatterPlan &plan, 
     k_max<<<1, NT, 0, s>>>(tile_max, nb, dmax);
     const size_t n = (size_t)a.H * a.W;
     k_stitch_finish<<<grid_for(n), NT, 0, s>>>(n, num, den, floor_, dmax, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_sq_weighted(const float2 *x, const float *w, size_t n, double *part, double *out, double scale,
+                                   cudaStream_t s)
+{
+    k_partial_sums<<<kRedBlocks, NT, 0, s>>>(x, w, n, part);
+    k_loss_finalize<<<1, NT, 0, s>>>(part, kRedBlocks, scale, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_to(float2 *x, size_t n, const double *num, const double *den, double *c_out, cudaStream_t s)
+{
+    k_scale<<<grid_for(n), NT, 0, s>>>(x, n, num, den, c_out);
     return cudaGetLastError();
 }
 

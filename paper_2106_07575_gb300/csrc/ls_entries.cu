@@ -1,0 +1,80 @@
+// ls_entries.cu -- line-search candidate windows over the detector pixels with counts.
+//
+// With u = G psi_m and v = G eta_m kept at every entry (pixel with d > 0) by the GRAD and
+// LS pattern passes, the objective at a candidate step gamma changes by (Eq. 2, 7)
+//   sum_entries [ q - d log(1 + q / (|u|^2 + eps)) ] + (pixels without counts: Parseval)
+//   q = gamma (2 Re conj(u) v + gamma |v|^2) = |u + gamma v|^2 - |u|^2.
+// One thread block per (pattern, chunk) of the entry layout sums the window's candidates in
+// FP32 per thread and FP64 across the block: the partials have the layout of the LS pass
+// (rows 2.. of [L+2][K * cs]), so the decision kernel reads both alike.  The kernel needs
+// no shared-memory tile and runs at full occupancy, which hides the latency of the
+// logarithm chain that bounded the fused pattern pass.
+#include "mathx.cuh"
+#include "pty_internal.h"
+#include "reduce.cuh"
+
+namespace pty {
+
+namespace {
+
+constexpr int kNT = 256;
+
+template <int L>
+__global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, double *__restrict__ part,
+                                                    const DevState *__restrict__ sts)
+{
+    const int blk = blockIdx.x, i = blk / cs, c = blk % cs;
+    const DevState *st = sts + a.pat_view[i];
+    if (st->stalled || st->decided || st->Lsel != L) return;
+    __shared__ double red[(kNT / 32) * L];
+    __shared__ double tot[L];
+    const int Leff = st->Leff;
+    float gam[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) gam[l] = (float)st->cand[l];
+    float acc[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) acc[l] = 0.0f;
+    const int per = a.nzc / cs;
+    const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
+    for (long long e = e0 + threadIdx.x; e < e1; e += kNT) {
+        const float dv = __ldg(a.nz_d + e);
+        const float2 u = __ldg(a.nz_u + e), v = __ldg(a.nz_v + e);
+        const float au = fmaf(u.x, u.x, u.y * u.y);
+        const float bu = fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
+        const float cu = fmaf(v.x, v.x, v.y * v.y);
+        const float inv = 1.0f / (au + a.eps);
+        const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+            if (l < Leff) {  // uniform over the block
+                const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
+                const float t = fmaxf(q * inv, tmin);
+                acc[l] += q - dv * log1p_fast(t);
+            }
+        }
+    }
+    double vals[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) vals[l] = acc[l];
+    block_sum<kNT, L>(vals, red, tot);
+    const size_t KC = (size_t)a.K * cs;
+    for (int l = threadIdx.x; l < L; l += kNT) part[(size_t)(2 + l) * KC + blk] = tot[l];
+}
+
+}  // namespace
+
+cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int L, double *part, const DevState *st, cudaStream_t s)
+{
+    const int nb = a.K * cs;
+    switch (L) {
+    case 4: k_ls_entries<4><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
+    case 8: k_ls_entries<8><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
+    case 16: k_ls_entries<16><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
+    case 32: k_ls_entries<32><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pty

@@ -79,6 +79,77 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
     }
 }
 
+// Illumination map D(x) = sum over positions k covering x of |p(x - r_k)|^2 (p the stored
+// probe, i.e. the probe / P), per object tile from the same position-sorted lists.
+template <int P>
+__global__ void __launch_bounds__(kScNT) k_illum(PatternArgs a, ScatterPlan plan, float *__restrict__ D)
+{
+    const int b = blockIdx.x;
+    const int ty = b / plan.ntile_x, tx = b % plan.ntile_x;
+    const int x = tx * kScTX + (threadIdx.x % kScTX);
+    const int y0 = ty * kScTY + threadIdx.x / kScTX;
+    float acc[kScNJ];
+#pragma unroll
+    for (int j = 0; j < kScNJ; j++) acc[j] = 0.f;
+    for (int q = plan.tile_start[b]; q < plan.tile_start[b + 1]; q++) {
+        const int2 rc = __ldg(a.pos + __ldg(plan.tile_list + q));
+        const int dx = x - rc.y;
+        if (dx < 0 || dx >= P) continue;
+#pragma unroll
+        for (int j = 0; j < kScNJ; j++) {
+            const int yy = y0 + (kScNT / kScTX) * j - rc.x;
+            if (yy >= 0 && yy < P) {
+                const float2 p = __ldg(a.probe + yy * P + dx);
+                acc[j] += p.x * p.x + p.y * p.y;
+            }
+        }
+    }
+    if (x >= a.W) return;
+#pragma unroll
+    for (int j = 0; j < kScNJ; j++) {
+        const int y = y0 + (kScNT / kScTX) * j;
+        if (y < a.H) D[(size_t)y * a.W + x] = acc[j];
+    }
+}
+
+// Search direction of Eq. 6, eta = -g + alpha eta_prev (alpha of the tile's view), and the
+// view's real-space sums that Parseval's identity turns into the line search's totals over
+// all detector pixels: part[b] = (sum D Re conj(psi) eta, sum D |eta|^2) over tile b.
+__global__ void __launch_bounds__(kScNT) k_eta(int H, int W, ScatterPlan plan, const float2 *__restrict__ psi,
+                                               const float2 *__restrict__ g, const float2 *__restrict__ ep,
+                                               const float *__restrict__ D, float2 *__restrict__ eta,
+                                               double *__restrict__ part, const DevState *__restrict__ sts)
+{
+    const int b = blockIdx.x;
+    const DevState *st = sts + plan.tile_view[b];
+    if (st->stalled) return;
+    __shared__ double red[(kScNT / 32) * 2];
+    __shared__ double tot[2];
+    const int ty = b / plan.ntile_x, tx = b % plan.ntile_x;
+    const int x = tx * kScTX + (threadIdx.x % kScTX);
+    const int y0 = ty * kScTY + threadIdx.x / kScTX;
+    const float alpha = (float)st->alpha;
+    float s0 = 0.f, s1 = 0.f;
+    if (x < W) {
+#pragma unroll
+        for (int j = 0; j < kScNJ; j++) {
+            const int y = y0 + (kScNT / kScTX) * j;
+            if (y < H) {
+                const size_t o = (size_t)y * W + x;
+                const float2 gv = __ldg(g + o), ev = __ldg(ep + o), pv = __ldg(psi + o);
+                const float2 e = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
+                eta[o] = e;
+                const float dd = __ldg(D + o);
+                s0 = fmaf(dd, fmaf(pv.x, e.x, pv.y * e.y), s0);
+                s1 = fmaf(dd, fmaf(e.x, e.x, e.y * e.y), s1);
+            }
+        }
+    }
+    double v[2] = {(double)s0, (double)s1};
+    block_sum<kScNT, 2>(v, red, tot);
+    if (threadIdx.x < 2) part[2 * b + threadIdx.x] = tot[threadIdx.x];
+}
+
 // Each thread sums a fixed strided subset, then the block combines: fixed order.
 __device__ __forceinline__ double strided_sum(const double *v, int n, int stride, int off)
 {
@@ -153,7 +224,8 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
 // Rows of partials have length kc; view v's entries are [pat_off[v] cs, pat_off[v+1] cs).
 // The open window of view v has st->Leff <= 32 candidates.
 __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__ part, int kc, int cs, ViewMap vm,
-                                                      DevState *sts, DevHist h, LsArgs ls)
+                                                      const double *__restrict__ vpart, double vscale, DevState *sts,
+                                                      DevHist h, LsArgs ls)
 {
     const int v = blockIdx.x;
     DevState *st = sts + v;
@@ -169,6 +241,11 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
         double s = 0.0;
         for (int i = p0 + lane; i < p1; i += 32) s += pj[i];
         s = warp_sum(s);
+        if (vpart && j < 2) {  // the view's object-tile sums of the all-pixel totals (Parseval)
+            double t = 0.0;
+            for (int b = vm.tile_off[v] + lane; b < vm.tile_off[v + 1]; b += 32) t += vpart[2 * b + j];
+            s += vscale * warp_sum(t);
+        }
         if (lane == 0) tot[j] = s;
     }
     __syncthreads();
@@ -273,6 +350,25 @@ cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan,
     return cudaGetLastError();
 }
 
+cudaError_t launch_illumination(int P, const PatternArgs &a, const ScatterPlan &plan, float *D, cudaStream_t s)
+{
+    const int nb = plan.ntile_x * plan.ntile_y;
+    switch (P) {
+    case 64: k_illum<64><<<nb, kScNT, 0, s>>>(a, plan, D); break;
+    case 128: k_illum<128><<<nb, kScNT, 0, s>>>(a, plan, D); break;
+    case 256: k_illum<256><<<nb, kScNT, 0, s>>>(a, plan, D); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eta(int H, int W, const ScatterPlan &plan, const float2 *psi, const float2 *g, const float2 *ep,
+                       const float *D, float2 *eta, double *part, const DevState *st, cudaStream_t s)
+{
+    k_eta<<<plan.ntile_x * plan.ntile_y, kScNT, 0, s>>>(H, W, plan, psi, g, ep, D, eta, part, st);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s)
 {
     k_sum<<<1, kSumNT, 0, s>>>(v, n, out);
@@ -286,10 +382,10 @@ cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const LsArgs &ls, DevState *st,
-                             DevHist h, cudaStream_t s)
+cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const double *vpart, double vscale,
+                             const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
 {
-    k_ls_decide<<<vm.V, kSumNT, 0, s>>>(part, kc, cs, vm, st, h, ls);
+    k_ls_decide<<<vm.V, kSumNT, 0, s>>>(part, kc, cs, vm, vpart, vscale, st, h, ls);
     return cudaGetLastError();
 }
 

@@ -7,9 +7,10 @@
 //   k_grad         GRAD stage: gather x probe -> F -> likelihood residual (Eq. 3) and the
 //                  objective terms (Eq. 2) -> F^H -> x conj(p); one patch-sized result
 //                  per pattern, summed into the object by the scatter kernel
-//   k_ls           LS stage: v = G eta for one pattern, then the change of the objective
-//                  F(psi + gamma eta) - F(psi) (Eq. 2, 7) for a window of candidate steps
-//                  gamma, using G(psi + gamma eta) = u + gamma v with u kept by k_grad
+//   k_ls_fft       LS stage, once per iteration: v = G eta for one pattern, kept at the
+//                  detector pixels with counts, and the two Parseval sums that the change
+//                  of the objective needs at the other pixels (the candidate windows run
+//                  on the kept values: ls_entries.cu)
 //   k_nz_*         create time: the compact list of detector pixels with counts
 //
 // The forward DFT leaves the spectrum in the permuted slot order of fft_tile.cuh, in
@@ -51,6 +52,7 @@ __device__ __forceinline__ void gather_rows(float2 *buf, const float2 *__restric
                                             const float2 *__restrict__ src, int W, int r0, int c0, int c)
 {
     constexpr int LDA = Slab<P, R>::LDA;
+#pragma unroll 4
     for (int e = threadIdx.x; e < R * P; e += NT) {
         const int rl = e / P, x = e % P, y = c * R + rl;
         buf[rl * LDA + x] = cmul(__ldg(probe + y * P + x), __ldg(src + (size_t)(r0 + y) * W + (c0 + x)));
@@ -151,9 +153,10 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
     __syncthreads();
     const int per = a.nzc / CS;  // entry chunks (of the finest column split) owned by this CTA
     const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
+#pragma unroll 2
     for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
-        const int s = a.nz_slot[e];  // global slot qy * P + qx
-        const float dv = a.nz_d[e];
+        const int s = __ldg(a.nz_slot + e);  // global slot qy * P + qx
+        const float dv = __ldg(a.nz_d + e);
         float2 *pu = buf + (s / P) * LDB + (s % P - c * R);
         float2 u = *pu;
         a.nz_u[e] = u;
@@ -182,79 +185,44 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
 // Over all pixels, sum conj(u) v and sum |v|^2 equal P^2 sum conj(x) y and P^2 sum |y|^2
 // of the real-space exit waves x = p psi / P, y = p eta / P (Parseval); the d = 0 part is
 // that total minus the entries' part.
-template <int P, int R, int NT, int L>
-__global__ void __launch_bounds__(NT) k_ls(PatternArgs a, const float2 *__restrict__ psi,
-                                           const float2 *__restrict__ g, const float2 *__restrict__ ep,
-                                           double *__restrict__ part, const DevState *__restrict__ sts)
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_ls_fft(PatternArgs a, const float2 *__restrict__ eta,
+                                               double *__restrict__ part, const DevState *__restrict__ sts)
 {
     const DevState *st = sts + a.pat_view[blockIdx.x / Slab<P, R>::CS];  // uniform over the cluster
-    if (st->stalled || st->decided || st->Lsel != L) return;
+    if (st->stalled) return;
     extern __shared__ __align__(16) float2 sm[];
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
-    __shared__ double red[(NT / 32) * (L + 2)];
-    __shared__ double tot[L + 2];
+    __shared__ double red[(NT / 32) * 2];
+    __shared__ double tot[2];
     float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
     int i, c;
     who<P, R>(i, c);
     const int2 rc = a.pos[i];
-    const float alpha = (float)st->alpha;
-    const int Leff = st->Leff;
-    float gam[L];
-#pragma unroll
-    for (int l = 0; l < L; l++) gam[l] = (float)st->cand[l];
     cluster_start<P, R>();
     load_twiddles<P, NT>(tw, a.tw);
-
-    // y = p eta / P into the row slab, with the real-space sums of Parseval's identity
-    float sb = 0.f, sbc = 0.f, scc = 0.f, sccc = 0.f;
-    for (int e = threadIdx.x; e < R * P; e += NT) {
-        const int rl = e / P, x = e % P, y = c * R + rl;
-        const size_t o = (size_t)(rc.x + y) * a.W + (rc.y + x);
-        const float2 gv = __ldg(g + o), ev = __ldg(ep + o), pv = __ldg(a.probe + y * P + x);
-        const float2 eta = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
-        const float2 yv = cmul(pv, eta), xv = cmul(pv, __ldg(psi + o));
-        buf[rl * LDA + x] = yv;
-        kahan_add(sb, sbc, fmaf(xv.x, yv.x, xv.y * yv.y));
-        kahan_add(scc, sccc, fmaf(yv.x, yv.x, yv.y * yv.y));
-    }
+    gather_rows<P, R, NT>(buf, a.probe, eta, a.W, rc.x, rc.y, c);  // p eta / P into the row slab
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
 
-    float bp = 0.0f, cp = 0.0f, acc[L];
-#pragma unroll
-    for (int l = 0; l < L; l++) acc[l] = 0.0f;
+    // v = G eta at the entries (kept for the candidate windows), and the entries' share of
+    // the two all-pixel sums, removed here so that rows 0 and 1 cover the pixels without counts
+    float bp = 0.0f, cp = 0.0f;
     const int per = a.nzc / CS;
     const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
+#pragma unroll 4
     for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
-        const int s = a.nz_slot[e];
-        const float dv = a.nz_d[e];
-        const float2 u = a.nz_u[e];
+        const int s = __ldg(a.nz_slot + e);
+        const float2 u = __ldg(a.nz_u + e);
         const float2 v = buf[(s / P) * LDB + (s % P - c * R)];
-        const float au = fmaf(u.x, u.x, u.y * u.y);
-        const float bu = fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
-        const float cu = fmaf(v.x, v.x, v.y * v.y);
-        bp += bu;
-        cp += cu;
-        const float inv = 1.0f / (au + a.eps);
-        const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
-#pragma unroll
-        for (int l = 0; l < L; l++) {
-            if (l < Leff) {  // uniform over the block
-                const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
-                const float t = fmaxf(q * inv, tmin);
-                acc[l] += q - dv * log1p_fast(t);
-            }
-        }
+        a.nz_v[e] = v;
+        bp += fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
+        cp += fmaf(v.x, v.x, v.y * v.y);
     }
-    constexpr double PP = (double)P * (double)P;
-    double vals[L + 2];
-    vals[0] = PP * ((double)sb - (double)sbc) - (double)bp;
-    vals[1] = PP * ((double)scc - (double)sccc) - (double)cp;
-#pragma unroll
-    for (int l = 0; l < L; l++) vals[2 + l] = acc[l];
-    block_sum<NT, L + 2>(vals, red, tot);
+    double vals[2] = {-(double)bp, -(double)cp};
+    block_sum<NT, 2>(vals, red, tot);
     const int KC = a.K * CS;
-    if (threadIdx.x < L + 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // [L+2][K*CS]
+    if (threadIdx.x < 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // rows 0, 1 of [L+2][K*CS]
 }
 
 // Global slot (qy * P + qx) and natural-order index of local slot s of column chunk c.
@@ -368,22 +336,9 @@ struct PatternOps {
     {
         return launch_pattern(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, psi, w, fpart, st);
     }
-    template <int L>
-    static cudaError_t ls_l(const PatternArgs &a, const float2 *psi, const float2 *g, const float2 *ep, double *part,
-                            const DevState *st, cudaStream_t s)
+    static cudaError_t ls(const PatternArgs &a, const float2 *eta, double *part, const DevState *st, cudaStream_t s)
     {
-        return launch_pattern(k_ls<P, R, NT, L>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, psi, g, ep, part, st);
-    }
-    static cudaError_t ls(const PatternArgs &a, int L, const float2 *psi, const float2 *g, const float2 *ep,
-                          double *part, const DevState *st, cudaStream_t s)
-    {
-        switch (L) {
-        case 4: return ls_l<4>(a, psi, g, ep, part, st, s);
-        case 8: return ls_l<8>(a, psi, g, ep, part, st, s);
-        case 16: return ls_l<16>(a, psi, g, ep, part, st, s);
-        case 32: return ls_l<32>(a, psi, g, ep, part, st, s);
-        default: return cudaErrorInvalidValue;
-        }
+        return launch_pattern(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, eta, part, st);
     }
     static cudaError_t nz_count(const float *d, const int *perm, int K, int *cnt, cudaStream_t s)
     {

@@ -66,6 +66,7 @@ struct pty_ctx {
     unsigned short *nz_slot = nullptr;  // [E]
     float *nz_d = nullptr;              // [E]
     float2 *nz_u = nullptr;             // [E]
+    float2 *nz_v = nullptr;             // [E]
     long long n_entries = 0;
     int *tile_start = nullptr, *tile_list = nullptr;
     int ntile_y = 0, ntile_x = 0;
@@ -76,6 +77,9 @@ struct pty_ctx {
     double *part_sc = nullptr;  // [ntiles][2]
     double *part_ls = nullptr;  // [L+2][K * CS]
     float2 *psi = nullptr, *g = nullptr, *g_prev = nullptr, *eta_prev = nullptr;  // atlas
+    float2 *eta = nullptr;       // atlas: the current search direction (LS stage)
+    float *illum = nullptr;      // atlas: sum over positions of |probe / P|^2 (Parseval totals)
+    double *part_eta = nullptr;  // [ntiles][2] object-tile sums of the LS stage
     DevState *st = nullptr;     // [V]
     double *dscalar = nullptr;
     DevHist hist{};
@@ -93,6 +97,7 @@ struct pty_ctx {
     // stitching of patch estimates (pty_stitch)
     float *st_den = nullptr;   // [HA][WA] sum of |p|^2
     float *st_tmax = nullptr;  // [ntiles + 1] per-tile maxima, then the maximum
+    double *st_red = nullptr;  // [kPartials + 2] reduction scratch of the scaled stitch
 
     // one CG iteration as a CUDA graph
     cudaGraphExec_t iter_exec = nullptr;
@@ -153,11 +158,12 @@ void free_all(pty_ctx *c)
 {
     void *ptrs[] = {c->probe,      c->tw,         c->pos,        c->perm,      c->pat_view,     c->view_pat_off,
                     c->view_tile_off, c->row_view, c->tile_view,  c->nz_off,    c->nz_slot,      c->nz_d,
-                    c->nz_u,       c->tile_start, c->tile_list,  c->w,         c->fpart,        c->part_sc,
+                    c->nz_u,       c->nz_v,       c->tile_start, c->tile_list,  c->w,         c->fpart,        c->part_sc,
                     c->part_ls,    c->psi,        c->g,          c->g_prev,    c->eta_prev,     c->st,
                     c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
                     c->stage_obj2, c->stage_pat, c->tc_img_fwd, c->tc_img_inv, c->tc_err, c->tc_x, c->tc_t,
-                    c->tc_u, c->tc_pars, c->st_den, c->st_tmax};
+                    c->tc_u, c->tc_pars, c->st_den, c->st_tmax, c->st_red,
+                    c->eta, c->illum, c->part_eta};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -181,6 +187,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.nz_slot = c->nz_slot;
     a.nz_d = c->nz_d;
     a.nz_u = c->nz_u;
+    a.nz_v = c->nz_v;
     a.pat_view = c->pat_view;
     a.eps = (float)c->opts.eps;
     return a;
@@ -393,7 +400,7 @@ int launch_iteration(pty_ctx *c, bool timed)
                 CK(pty::launch_tc_ls_entries(a, c->P, ls.L, c->tc_u, c->tc_pars, c->part_ls, c->st, c->s));
             }
             StageTimer t(c, 3, timed);
-            CK(pty::launch_ls_decide(c->part_ls, c->K, 1, vm, ls, c->st, c->hist, c->s));
+            CK(pty::launch_ls_decide(c->part_ls, c->K, 1, vm, nullptr, 0.0, ls, c->st, c->hist, c->s));
         }
         StageTimer t(c, 3, timed);
         CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, c->s));
@@ -419,16 +426,22 @@ int launch_iteration(pty_ctx *c, bool timed)
         StageTimer t(c, 3, timed);
         CK(pty::launch_dy_finalize(c->fpart, c->CS, c->part_sc, vm, c->st, c->hist, ls, c->s));
     }
+    {
+        StageTimer t(c, 2, timed);  // eta and v = G eta once per iteration; the windows reuse them
+        CK(pty::launch_eta(c->HA, c->WA, plan, c->psi, c->g, c->eta_prev, c->illum, c->eta, c->part_eta, c->st, c->s));
+        CK(c->impl_ls->ls(a, c->eta, c->part_ls, c->st, c->s));
+    }
     for (int wdx = 0; wdx < nwin; wdx++) {
         {
             StageTimer t(c, 2, timed);
             // the first window of an adaptive search runs on the 16- or the 32-candidate
             // kernel as the device chose; the other one returns at once
-            if (wdx == 0 && ls.adaptive) CK(c->impl_ls->ls(a, 16, c->psi, c->g, c->eta_prev, c->part_ls, c->st, c->s));
-            CK(c->impl_ls->ls(a, ls.L, c->psi, c->g, c->eta_prev, c->part_ls, c->st, c->s));
+            if (wdx == 0 && ls.adaptive) CK(pty::launch_ls_entries(a, c->CSl, 16, c->part_ls, c->st, c->s));
+            CK(pty::launch_ls_entries(a, c->CSl, ls.L, c->part_ls, c->st, c->s));
         }
         StageTimer t(c, 3, timed);
-        CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, c->CSl, vm, ls, c->st, c->hist, c->s));
+        CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, c->CSl, vm, c->part_eta, (double)c->P * c->P, ls, c->st,
+                                 c->hist, c->s));
     }
     StageTimer t(c, 3, timed);
     CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, c->s));
@@ -517,7 +530,7 @@ int autotune(pty_ctx *c)
             }
             for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
                 err = cudaEventRecord(e0, c->s);
-                if (err == cudaSuccess) err = impls[j].ls(a, 16, c->psi, c->g, c->eta_prev, c->part_ls, c->st, c->s);
+                if (err == cudaSuccess) err = impls[j].ls(a, c->eta, c->part_ls, c->st, c->s);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, c->s);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
@@ -729,6 +742,9 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     CKC(dalloc(&c->g, HW));
     CKC(dalloc(&c->g_prev, HW));
     CKC(dalloc(&c->eta_prev, HW));
+    CKC(dalloc(&c->eta, HW));
+    CKC(dalloc(&c->illum, HW));
+    CKC(dalloc(&c->part_eta, (size_t)ntiles * 2));
     CKC(dalloc(&c->st, (size_t)V));
     CKC(dalloc(&c->dscalar, (size_t)4));
     CKC(cudaMemcpyAsync(c->probe, hprobe.data(), sizeof(float2) * PP, cudaMemcpyHostToDevice, c->s));
@@ -745,7 +761,9 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
         CKC(cudaMemcpyAsync(c->tile_list, list.data(), sizeof(int) * list.size(), cudaMemcpyHostToDevice, c->s));
     CKC(cudaMemsetAsync(c->g_prev, 0, sizeof(float2) * HW, c->s));
     CKC(cudaMemsetAsync(c->eta_prev, 0, sizeof(float2) * HW, c->s));
+    CKC(cudaMemsetAsync(c->eta, 0, sizeof(float2) * HW, c->s));
     CKC(cudaMemsetAsync(c->psi, 0, sizeof(float2) * HW, c->s));
+    CKC(pty::launch_illumination(P, pattern_args(c), scatter_plan(c), c->illum, c->s));
     CKC(cudaMemsetAsync(c->st, 0, sizeof(DevState) * V, c->s));
 
     // measured data: read here only (a host array goes through a temporary device copy)
@@ -790,6 +808,7 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     if (ce == cudaSuccess) ce = dalloc(&c->nz_slot, E);
     if (ce == cudaSuccess) ce = dalloc(&c->nz_d, E);
     if (ce == cudaSuccess) ce = dalloc(&c->nz_u, E);
+    if (ce == cudaSuccess) ce = dalloc(&c->nz_v, E);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (KC + 1), cudaMemcpyHostToDevice, c->s);
     if (ce == cudaSuccess) ce = c->impl_nz->nz_fill(dd, c->perm, (int)K, c->nz_off, c->nz_slot, c->nz_d, c->s);
@@ -1110,6 +1129,45 @@ int pty_stage_times(pty_ctx *c, double ms[4], int64_t launches[4], int reset)
     return PTY_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Probe-weighted stitching into c->stage_obj (atlas layout); c->st_den keeps sum_k |p/P|^2.
+int stitch_into_stage(pty_ctx *c, const float2 *patches, float floor_)
+{
+    int st;
+    if ((st = enter(c)) || (st = ensure_stage(c))) return st;
+    const int ntiles = c->ntile_x * c->ntile_y;
+    if (!c->st_den) CK(dalloc(&c->st_den, (size_t)c->HA * c->WA));
+    if (!c->st_tmax) CK(dalloc(&c->st_tmax, (size_t)ntiles + 1));
+    CK(pty::cnn::launch_stitch(c->P, pattern_args(c), scatter_plan(c), patches, floor_, c->stage_obj2, c->st_den,
+                               c->st_tmax, c->st_tmax + ntiles, c->stage_obj, c->s));
+    return PTY_OK;
+}
+}  // namespace
+
+int pty::cnn::stitch_scaled(pty_ctx *c, const float2 *patches, float floor_, const double *sum_d, float2 *out,
+                            double *c_out)
+{
+    int st;
+    if ((st = stitch_into_stage(c, patches, floor_))) return st;
+    if (!c->st_red) CK(dalloc(&c->st_red, (size_t)pty::cnn::kPartials + 2));
+    const size_t n = (size_t)c->HA * c->WA;
+    double *A = c->st_red + pty::cnn::kPartials;
+    // sum |G psi|^2 = P^2 sum_x |psi(x)|^2 sum_k |p(x - r_k) / P|^2 (the stored probe is p / P)
+    CK(pty::cnn::launch_sum_sq_weighted(c->stage_obj, c->st_den, n, c->st_red, A, (double)c->P * c->P, c->s));
+    CK(pty::cnn::launch_scale_to(c->stage_obj, n, sum_d, A, A + 1, c->s));
+    float *po[1] = {(float *)out};
+    if ((st = views_out(c, po, c->stage_obj))) return st;
+    double hc = 1.0;
+    CK(cudaMemcpyAsync(&hc, A + 1, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    if ((st = sync(c))) return st;
+    if (c_out) *c_out = hc;
+    return PTY_OK;
+}
+
+extern "C" {
+
 int pty_stitch(pty_ctx *c, const float *patches, float floor_, float *psi0)
 {
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
@@ -1118,12 +1176,7 @@ int pty_stitch(pty_ctx *c, const float *patches, float floor_, float *psi0)
     if (c->V != 1) return fail(c, PTY_ERR_UNSUPPORTED, "pty_stitch works on single-view contexts");
     if (!is_device_ptr(patches)) return fail(c, PTY_ERR_ARG, "patches must be a device array");
     int st;
-    if ((st = enter(c)) || (st = ensure_stage(c))) return st;
-    const int ntiles = c->ntile_x * c->ntile_y;
-    if (!c->st_den) CK(dalloc(&c->st_den, (size_t)c->HA * c->WA));
-    if (!c->st_tmax) CK(dalloc(&c->st_tmax, (size_t)ntiles + 1));
-    CK(pty::cnn::launch_stitch(c->P, pattern_args(c), scatter_plan(c), (const float2 *)patches, floor_,
-                               c->stage_obj2, c->st_den, c->st_tmax, c->st_tmax + ntiles, c->stage_obj, c->s));
+    if ((st = stitch_into_stage(c, (const float2 *)patches, floor_))) return st;
     float *po[1] = {psi0};
     if ((st = views_out(c, po, c->stage_obj))) return st;
     return sync(c);

@@ -55,6 +55,7 @@ struct PatternArgs {
     const unsigned short *nz_slot;  // [E] global slot qy * P + qx of each entry
     const float *nz_d;          // [E] measured counts (> 0) of each entry
     float2 *nz_u;               // [E] u = G psi_m at each entry (GRAD pass -> LS pass)
+    float2 *nz_v;               // [E] v = G eta_m at each entry (LS pass -> candidate windows)
     const int *pat_view;        // [K] view of sorted pattern i (all 0 for one view)
     float eps;
 };
@@ -80,12 +81,11 @@ struct PatternImpl {
     // fpart = objective terms; u kept at the entries.  Exits early when st->stalled.
     cudaError_t (*grad)(const PatternArgs &, const float2 *psi, float2 *w, double *fpart, const DevState *st,
                         cudaStream_t);
-    // LS pattern pass over the candidates gamma0 tau^(k0+l+1), l < L, with
-    // eta = -g + alpha eta_prev and v = G eta: part[0][.], part[1][.] = (sum Re conj(u) v,
-    // sum |v|^2) over the d = 0 pixels, part[2+l][.] = sum over the entries of the
-    // objective change at candidate l.  Exits early when st->decided or st->stalled.
-    cudaError_t (*ls)(const PatternArgs &, int L, const float2 *psi, const float2 *g, const float2 *eta_prev,
-                      double *part, const DevState *st, cudaStream_t);
+    // LS pattern pass, once per iteration: v = G eta (eta the object-sized search direction)
+    // is kept at the entries (nz_v) and part[0][.], part[1][.] = -(sum Re conj(u) v, sum
+    // |v|^2) over the entries (per CTA, rows of length K * CS): the all-pixel totals come from
+    // object sums (launch_eta).  Exits when st->stalled.
+    cudaError_t (*ls)(const PatternArgs &, const float2 *eta, double *part, const DevState *st, cudaStream_t);
     // Entries of the measured data: counts per (pattern, CTA) chunk, then the compact list.
     cudaError_t (*nz_count)(const float *d, const int *perm, int K, int *cnt, cudaStream_t);
     cudaError_t (*nz_fill)(const float *d, const int *perm, int K, const long long *off, unsigned short *slot,
@@ -97,6 +97,12 @@ bool pattern_supported(int P);
 int ls_window_supported(int L);  // 1 if L is an instantiated window size
 // out[i] = log1p_fast(t[i]) (device self-test of the line-search logarithm)
 cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_t s);
+
+// ---- line-search candidate windows (ls_entries.cu) ----
+// part[2 + l][i * cs + c] = sum over the entries of chunk c of pattern i of the objective
+// change at candidate l (gamma0 tau^(k0+l+1)), from u (nz_u), v (nz_v) and d: the window
+// of the L-candidate kernel; returns at once unless st->Lsel == L and a window is open.
+cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int L, double *part, const DevState *st, cudaStream_t s);
 
 // ---- tensor-core DFT (tc_dft.cu) ----
 // One application: Y[b][k][y] = sum_n X[b][y][n] exp(sign 2 pi i n k / P) for the nrows =
@@ -150,9 +156,16 @@ cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
 cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, const ViewMap &vm, DevState *st,
                                DevHist h, const LsArgs &ls, cudaStream_t s);
 // LS stage decision per view over the open window; part rows have length kc (K * CS), the
-// view's partials are [pat_off[v] * cs, pat_off[v + 1] * cs).
-cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const LsArgs &ls, DevState *st,
-                             DevHist h, cudaStream_t s);
+// view's partials are [pat_off[v] * cs, pat_off[v + 1] * cs).  vpart (nullable): object-tile
+// partials [ntiles][2] added, times vscale, to rows 0 and 1 over the view's tiles.
+cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const double *vpart, double vscale,
+                             const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s);
+// D[y][x] = sum over the positions covering (y, x) of |probe / P|^2 at the covered pixel.
+cudaError_t launch_illumination(int P, const PatternArgs &a, const ScatterPlan &plan, float *D, cudaStream_t s);
+// eta = -g + alpha_v eta_prev over the object (H x W, scatter tiles) and the per-tile sums
+// part[b] = (sum D Re conj(psi) eta, sum D |eta|^2).
+cudaError_t launch_eta(int H, int W, const ScatterPlan &plan, const float2 *psi, const float2 *g, const float2 *ep,
+                       const float *D, float2 *eta, double *part, const DevState *st, cudaStream_t s);
 // Update stage for every object pixel (W columns per row): psi += gamma eta,
 // eta_prev <- eta = -g + alpha eta_prev, g_prev <- g, with the scalars of the row's view.
 cudaError_t launch_update(int H, int W, const ViewMap &vm, float2 *psi, const float2 *g, float2 *eta_prev,

@@ -15,8 +15,11 @@ import numpy as np
 from . import pty, synth
 
 
-def training_pairs(probe, n_pairs: int, N: int = 1024, per_phantom: int = 8192, seed: int = 100):
-    """(d [n][P][P] float32, t [n][P][P] complex64) CUDA tensors from the forward model."""
+def training_pairs(probe, n_pairs: int, N: int = 1024, per_phantom: int = 8192, seed: int = 100,
+                   phantoms=("ellipse", "voronoi")):
+    """(d [n][P][P] float32, t [n][P][P] complex64) CUDA tensors from the forward model.
+
+    Phantom i (N x N, generator seed + i) is of kind phantoms[i % len(phantoms)]."""
     import torch
 
     dev = torch.device("cuda")
@@ -32,7 +35,8 @@ def training_pairs(probe, n_pairs: int, N: int = 1024, per_phantom: int = 8192, 
     k, i = 0, 0
     while k < n_pairs:
         rng = np.random.default_rng(seed + i)
-        psi = synth.ellipse_phantom(N, N, rng) if i % 2 == 0 else synth.voronoi_phantom(N, N, rng)
+        kind = phantoms[i % len(phantoms)]
+        psi = synth.ellipse_phantom(N, N, rng) if kind == "ellipse" else synth.voronoi_phantom(N, N, rng)
         m = min(per_phantom, n_pairs - k)
         pos = rng.integers(0, N - P + 1, size=(m, 2)).astype(np.int32)
         psi_d = torch.from_numpy(psi).to(dev)

@@ -50,7 +50,7 @@ class pty_adam(ctypes.Structure):
 
 class pty_init_report(ctypes.Structure):
     _fields_ = [("F_learned", ctypes.c_double), ("F_ones", ctypes.c_double), ("used_learned", ctypes.c_int32),
-                ("ms", ctypes.c_double)]
+                ("scale", ctypes.c_double), ("ms", ctypes.c_double)]
 
 
 class pty_cg_report(ctypes.Structure):
@@ -512,4 +512,4 @@ class Network:
         c = ctx.ctx if isinstance(ctx, Context) else ctx
         _check_cnn(lib, self.net, lib.pty_learned_init(c, self.net, _ptr(d, _F), _ptr(psi0, _C), ctypes.byref(rep)))
         return {"F_learned": rep.F_learned, "F_ones": rep.F_ones, "used_learned": bool(rep.used_learned),
-                "ms": rep.ms}
+                "scale": rep.scale, "ms": rep.ms}

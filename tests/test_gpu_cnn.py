@@ -171,3 +171,62 @@ def test_cnn_argument_errors():
     bad = -np.ones((64, 64), np.float32)
     with pytest.raises(pty.PtyError):
         net.set_loss_weight(bad)
+
+
+def _small_test_problem():
+    prob = synth.small_problem(seed=5)
+    probe = torch.from_numpy(prob.probe).to(DEV)
+    ctx = pty.Context(probe, torch.from_numpy(prob.pos).to(DEV), torch.from_numpy(prob.d).to(DEV), prob.H, prob.W)
+    return prob, ctx
+
+
+def test_learned_init_fallback_keeps_ones():
+    """A network with large random weights predicts patches of random phase; its stitched
+    start has a higher objective than the ones start, which is therefore kept."""
+    prob, ctx = _small_test_problem()
+    net = pty.Network(64, 32, 6, max_batch=64)
+    rng = np.random.default_rng(51)
+    net.set_params(rng.normal(0, 3.0, net.num_params).astype(np.float32))
+    psi0 = torch.empty((prob.H, prob.W), dtype=torch.complex64, device=DEV)
+    rep = net.learned_init(ctx, torch.from_numpy(prob.d).to(DEV), psi0)
+    print("random network:", rep)
+    assert not rep["used_learned"] and rep["F_learned"] >= rep["F_ones"]
+    assert torch.equal(psi0, torch.ones_like(psi0))
+    ctx.close()
+
+
+def test_learned_init_trained_gain():
+    """Train on forward-model pairs (ellipse and Voronoi phantoms), then compare the learned
+    start with the ones start on a held-out scan: objective at the start, and CG iterations
+    to a relative objective gap of 1e-3 (gap normalised by the ones start, F* = F(psi_true))."""
+    from paper_2106_07575_gb300 import learned
+
+    prob, ctx = _small_test_problem()
+    d_train, t_train = learned.training_pairs(prob.probe, 16384, N=256, per_phantom=4096, seed=100)
+    net = pty.Network(64, 32, 6, max_batch=64)
+    net.init_params(7)
+    net.set_loss_weight((np.abs(prob.probe.astype(np.complex128)) ** 2).astype(np.float32))
+    losses = net.train(d_train, t_train, 64, 512, seed=9)
+    del d_train, t_train
+    first, last = losses[:8].mean(), losses[-64:].mean()
+    print(f"training loss {first:.4f} -> {last:.4f}")
+    assert last < 0.8 * first
+    d = torch.from_numpy(prob.d).to(DEV)
+    psi_true = torch.from_numpy(prob.psi_true).to(DEV)
+    g = torch.empty_like(psi_true)
+    F_star = ctx.gradient(psi_true, g)
+    ones = torch.ones_like(psi_true)
+    F0 = ctx.gradient(ones, g)
+    psi0 = torch.empty_like(psi_true)
+    rep = net.learned_init(ctx, d, psi0)
+    assert rep["F_learned"] == pytest.approx(ctx.gradient(psi0, g)) or not rep["used_learned"]
+    assert min(rep["F_learned"], rep["F_ones"]) <= F0
+    res = {}
+    for name, start in (("ones", ones.clone()), ("learned", psi0.clone())):
+        ctx.cg_reset()
+        res[name] = learned.solve_to_gap(ctx, start, F_star, F0, 400, chunk=4)[0]
+    gap0 = (min(rep["F_learned"], rep["F_ones"]) - F_star) / (F0 - F_star)
+    print(f"learned start: used={rep['used_learned']} scale={rep['scale']:.4f} gap at start {gap0:.3f}; "
+          f"iterations to gap 1e-3: ones {res['ones']}, learned {res['learned']}")
+    assert res["ones"] is not None and res["learned"] is not None
+    ctx.close()

@@ -317,9 +317,9 @@ def mid128():
                                name="mid")
 
 
-@pytest.mark.parametrize("cfg", [0, 1, 2])
+@pytest.mark.parametrize("cfg", [0, 1, 2, 3])
 def test_p128_configurations(orc, mid128, cfg):
-    """One CTA per pattern and clusters of 2 and 4 CTAs give oracle parity."""
+    """One CTA per pattern (512 or 1024 threads) and clusters of 2 and 4 CTAs give oracle parity."""
     p = mid128
     ctx = make_ctx(p, _cfg_opts(cfg))
     psi = random_object(p, 30)

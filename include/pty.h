@@ -174,6 +174,13 @@ PTY_API int pty_gradient(pty_ctx *ctx, const float *psi, float *grad, double *F)
  * accepted).  The iteration runs without host synchronisation between its stages; it is
  * captured once as a CUDA graph and replayed (unless opts.flags bit 0 asks for per-stage
  * timing).  Needs a single-view context.
+ * Linear form (FFT path, opts.dft = 0): Eq. 1 is linear in psi, so after an accepted step
+ * G psi_{m+1} = G psi_m + gamma G eta_m; the model G psi at the detector pixels with counts
+ * is then updated in place from the line search's G eta instead of by a forward DFT, and
+ * the gradient's dense part conj(p) F^H G psi = |p|^2 psi is summed over positions in the
+ * object domain.  A full forward pass runs at the first iteration of a call whose object
+ * differs from the one the previous call returned (64-bit hash), after pty_gradient on the
+ * context, and every 16th iteration (by the count since the last reset).
  */
 PTY_API int pty_cg_solve(pty_ctx *ctx, float *psi_inout, int32_t niter, pty_cg_report *rep);
 
@@ -210,9 +217,11 @@ PTY_API int pty_cg_reset(pty_ctx *ctx);
 
 /*
  * Checkpoint of the conjugate-gradient state (previous gradient and direction, the
- * iteration count and the last step): pty_cg_state_size bytes of host memory.
- * pty_cg_state_load restores it into a context of the same problem sizes; a solve
- * resumed from a checkpoint reproduces the uninterrupted solve bit for bit.
+ * iteration count and the last step, and the model values kept at the detector pixels
+ * with counts): pty_cg_state_size bytes of host memory.  pty_cg_state_load restores it
+ * into a context of the same problem (PTY_ERR_ARG if the sizes differ); a solve resumed
+ * from a checkpoint with the object the saved solve returned reproduces the uninterrupted
+ * solve bit for bit.
  */
 PTY_API size_t pty_cg_state_size(const pty_ctx *ctx);
 PTY_API int pty_cg_state_save(pty_ctx *ctx, void *host_buf);

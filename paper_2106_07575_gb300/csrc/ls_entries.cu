@@ -19,59 +19,68 @@ namespace {
 
 constexpr int kNT = 256;
 
+// Fixed grid of kBlocks CTAs striding over the (pattern, chunk) units, so that a window
+// launched after the step was decided costs one short launch.
+constexpr int kBlocks = 152 * 8;
+
 template <int L>
-__global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, double *__restrict__ part,
+__global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V, double *__restrict__ part,
                                                     const DevState *__restrict__ sts)
 {
-    const int blk = blockIdx.x, i = blk / cs, c = blk % cs;
-    const DevState *st = sts + a.pat_view[i];
-    if (st->stalled || st->decided || st->Lsel != L) return;
+    // one view: a window with nothing to evaluate ends the whole launch at once
+    if (V == 1 && (sts->stalled || sts->decided || sts->Lsel != L)) return;
     __shared__ double red[(kNT / 32) * L];
     __shared__ double tot[L];
-    const int Leff = st->Leff;
-    float gam[L];
+    const int nunits = a.K * cs;
+    const size_t KC = (size_t)nunits;
+    for (int blk = blockIdx.x; blk < nunits; blk += gridDim.x) {
+        const int i = blk / cs, c = blk % cs;
+        const DevState *st = sts + (V == 1 ? 0 : a.pat_view[i]);
+        if (st->stalled || st->decided || st->Lsel != L) continue;  // uniform over the block
+        // candidates beyond the open window are evaluated at gamma = 0 and never read
+        const int Leff = st->Leff;
+        float gam[L];
 #pragma unroll
-    for (int l = 0; l < L; l++) gam[l] = (float)st->cand[l];
-    float acc[L];
+        for (int l = 0; l < L; l++) gam[l] = l < Leff ? (float)st->cand[l] : 0.0f;
+        float acc[L];
 #pragma unroll
-    for (int l = 0; l < L; l++) acc[l] = 0.0f;
-    const int per = a.nzc / cs;
-    const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
-    for (long long e = e0 + threadIdx.x; e < e1; e += kNT) {
-        const float dv = __ldg(a.nz_d + e);
-        const float2 u = __ldg(a.nz_u + e), v = __ldg(a.nz_v + e);
-        const float au = fmaf(u.x, u.x, u.y * u.y);
-        const float bu = fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
-        const float cu = fmaf(v.x, v.x, v.y * v.y);
-        const float inv = 1.0f / (au + a.eps);
-        const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
+        for (int l = 0; l < L; l++) acc[l] = 0.0f;
+        const int per = a.nzc / cs;
+        const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
+        for (long long e = e0 + threadIdx.x; e < e1; e += kNT) {
+            const float dv = __ldg(a.nz_d + e);
+            const float2 u = __ldg(a.nz_u + e), v = __ldg(a.nz_v + e);
+            const float au = fmaf(u.x, u.x, u.y * u.y);
+            const float bu2 = 2.0f * fmaf(u.x, v.x, u.y * v.y);  // 2 Re conj(u) v
+            const float cu = fmaf(v.x, v.x, v.y * v.y);
+            const float inv = 1.0f / (au + a.eps);
+            const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
 #pragma unroll
-        for (int l = 0; l < L; l++) {
-            if (l < Leff) {  // uniform over the block
-                const float q = gam[l] * fmaf(gam[l], cu, 2.0f * bu);
+            for (int l = 0; l < L; l++) {
+                const float q = gam[l] * fmaf(gam[l], cu, bu2);
                 const float t = fmaxf(q * inv, tmin);
-                acc[l] += q - dv * log1p_fast(t);
+                acc[l] = fmaf(-dv, log1p_fast(t), acc[l] + q);
             }
         }
-    }
-    double vals[L];
+        double vals[L];
 #pragma unroll
-    for (int l = 0; l < L; l++) vals[l] = acc[l];
-    block_sum<kNT, L>(vals, red, tot);
-    const size_t KC = (size_t)a.K * cs;
-    for (int l = threadIdx.x; l < L; l += kNT) part[(size_t)(2 + l) * KC + blk] = tot[l];
+        for (int l = 0; l < L; l++) vals[l] = acc[l];
+        block_sum<kNT, L>(vals, red, tot);  // ends with a barrier: red and tot are free again
+        for (int l = threadIdx.x; l < L; l += kNT) part[(size_t)(2 + l) * KC + blk] = tot[l];
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int L, double *part, const DevState *st, cudaStream_t s)
+cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, double *part, const DevState *st,
+                              cudaStream_t s)
 {
-    const int nb = a.K * cs;
+    const int nb = a.K * cs < kBlocks ? a.K * cs : kBlocks;
     switch (L) {
-    case 4: k_ls_entries<4><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
-    case 8: k_ls_entries<8><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
-    case 16: k_ls_entries<16><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
-    case 32: k_ls_entries<32><<<nb, kNT, 0, s>>>(a, cs, part, st); break;
+    case 4: k_ls_entries<4><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
+    case 8: k_ls_entries<8><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
+    case 16: k_ls_entries<16><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
+    case 32: k_ls_entries<32><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -27,12 +27,14 @@ template <int P>
 __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan plan, const float2 *__restrict__ w,
                                                    float2 *__restrict__ out, int dy, const float2 *__restrict__ ep,
                                                    const float2 *__restrict__ gp, double *__restrict__ part,
-                                                   const DevState *__restrict__ st)
+                                                   const DevState *__restrict__ st, const float2 *__restrict__ psi,
+                                                   const float *__restrict__ D, float p2)
 {
     const int b = blockIdx.x;
     if (st && st[plan.tile_view[b]].stalled) return;
-    __shared__ double red[(kScNT / 32) * 2];
-    __shared__ double tot[2];
+    const bool lin = st && st[plan.tile_view[b]].lin;
+    __shared__ double red[(kScNT / 32) * 3];
+    __shared__ double tot[3];
     const int ty = b / plan.ntile_x, tx = b % plan.ntile_x;
     const int x = tx * kScTX + (threadIdx.x % kScTX);
     const int y0 = ty * kScTY + threadIdx.x / kScTX;
@@ -56,13 +58,20 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
             }
         }
     }
-    float gg = 0.f, den = 0.f;
+    float gg = 0.f, den = 0.f, pd = 0.f;
     if (x < a.W) {
 #pragma unroll
         for (int j = 0; j < kScNJ; j++) {
             const int y = y0 + (kScNT / kScTX) * j;
             if (y < a.H) {
                 const size_t o = (size_t)y * a.W + x;
+                if (lin) {  // the |p|^2 psi terms of the linear form, summed over positions: P^2 D psi
+                    const float2 pv = __ldg(psi + o);
+                    const float dd = __ldg(D + o);
+                    acc[j].x = fmaf(p2 * dd, pv.x, acc[j].x);
+                    acc[j].y = fmaf(p2 * dd, pv.y, acc[j].y);
+                    pd = fmaf(dd, fmaf(pv.x, pv.x, pv.y * pv.y), pd);
+                }
                 out[o] = acc[j];
                 if (dy) {
                     const float2 e = __ldg(ep + o), g0 = __ldg(gp + o);
@@ -73,9 +82,9 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
         }
     }
     if (dy) {
-        double v[2] = {(double)gg, (double)den};
-        block_sum<kScNT, 2>(v, red, tot);
-        if (threadIdx.x < 2) part[2 * b + threadIdx.x] = tot[threadIdx.x];
+        double v[3] = {(double)gg, (double)den, (double)pd};
+        block_sum<kScNT, 3>(v, red, tot);
+        if (threadIdx.x < 3) part[3 * b + threadIdx.x] = tot[threadIdx.x];  // [ntiles][3]
     }
 }
 
@@ -179,21 +188,22 @@ __device__ __forceinline__ void open_window(DevState *st, double gamma0, double 
 }
 
 __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict__ fpart, int cs,
-                                                        const double *__restrict__ part, ViewMap vm, DevState *sts,
-                                                        DevHist h, LsArgs ls)
+                                                        const double *__restrict__ part, double p2, ViewMap vm,
+                                                        DevState *sts, DevHist h, LsArgs ls)
 {
     const int v = blockIdx.x;
     DevState *st = sts + v;
     if (st->stalled) return;
-    __shared__ double red[(kSumNT / 32) * 3];
-    __shared__ double tot[3];
+    __shared__ double red[(kSumNT / 32) * 4];
+    __shared__ double tot[4];
     const int f0 = vm.pat_off[v] * cs, f1 = vm.pat_off[v + 1] * cs;
     const int t0 = vm.tile_off[v], t1 = vm.tile_off[v + 1];
-    double v3[3] = {strided_sum(fpart + f0, f1 - f0, 1, 0), strided_sum(part + 2 * (size_t)t0, t1 - t0, 2, 0),
-                    strided_sum(part + 2 * (size_t)t0, t1 - t0, 2, 1)};
-    block_sum<kSumNT, 3>(v3, red, tot);
+    double v4[4] = {strided_sum(fpart + f0, f1 - f0, 1, 0), strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 0),
+                    strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 1), strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 2)};
+    block_sum<kSumNT, 4>(v4, red, tot);
     if (threadIdx.x == 0) {
-        const double Fm = tot[0], gg = tot[1], den = tot[2];
+        // linear form: sum |u|^2 over all pixels = P^2 sum D |psi|^2 (0 from the tiles otherwise)
+        const double Fm = tot[0] + p2 * tot[3], gg = tot[1], den = tot[2];
         double alpha = 0.0;
         if (den > 0.0 && isfinite(den) && isfinite(gg)) {
             alpha = gg / den;
@@ -223,7 +233,25 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
 
 // Rows of partials have length kc; view v's entries are [pat_off[v] cs, pat_off[v+1] cs).
 // The open window of view v has st->Leff <= 32 candidates.
-__global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__ part, int kc, int cs, ViewMap vm,
+// Sum of n doubles v[0], v[stride], ... by one warp in a fixed order: each lane keeps four
+// accumulators over a fixed strided subset, then a butterfly across the warp.
+__device__ __forceinline__ double warp_strided_sum(const double *__restrict__ v, int n, int lane)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int i = lane;
+    for (; i + 96 < n; i += 128) {
+        s0 += v[i];
+        s1 += v[i + 32];
+        s2 += v[i + 64];
+        s3 += v[i + 96];
+    }
+    for (; i < n; i += 32) s0 += v[i];
+    return warp_sum((s0 + s1) + (s2 + s3));
+}
+
+constexpr int kDecNT = 1024;
+
+__global__ void __launch_bounds__(kDecNT) k_ls_decide(const double *__restrict__ part, int kc, int cs, ViewMap vm,
                                                       const double *__restrict__ vpart, double vscale, DevState *sts,
                                                       DevHist h, LsArgs ls)
 {
@@ -231,23 +259,25 @@ __global__ void __launch_bounds__(kSumNT) k_ls_decide(const double *__restrict__
     DevState *st = sts + v;
     if (st->stalled || st->decided) return;
     __shared__ double tot[32 + 2];
-    // warp w sums the values j = w, w + 8, ... over the view's partials, each lane a fixed
-    // strided subset, then a butterfly across the warp (fixed order).
+    __shared__ double vtot[2];
+    // warp w sums rows j = w, w + 32, ... of the view's partials (fixed order)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int Leff = st->Leff;
     const int p0 = vm.pat_off[v] * cs, p1 = vm.pat_off[v + 1] * cs;
-    for (int j = warp; j < Leff + 2; j += kSumNT / 32) {
-        const double *pj = part + (size_t)j * kc;
-        double s = 0.0;
-        for (int i = p0 + lane; i < p1; i += 32) s += pj[i];
-        s = warp_sum(s);
-        if (vpart && j < 2) {  // the view's object-tile sums of the all-pixel totals (Parseval)
-            double t = 0.0;
-            for (int b = vm.tile_off[v] + lane; b < vm.tile_off[v + 1]; b += 32) t += vpart[2 * b + j];
-            s += vscale * warp_sum(t);
-        }
+    for (int j = warp; j < Leff + 2; j += kDecNT / 32) {
+        const double s = warp_strided_sum(part + (size_t)j * kc + p0, p1 - p0, lane);
         if (lane == 0) tot[j] = s;
     }
+    // the view's object-tile sums of the all-pixel totals of rows 0 and 1 (Parseval)
+    if (vpart && warp >= 30) {
+        const int j = warp - 30, t0 = vm.tile_off[v], n = vm.tile_off[v + 1] - t0;
+        double t0s = 0.0;
+        for (int b = lane; b < n; b += 32) t0s += vpart[2 * (t0 + b) + j];
+        t0s = warp_sum(t0s);
+        if (lane == 0) vtot[j] = vscale * t0s;
+    }
+    __syncthreads();
+    if (vpart && threadIdx.x < 2) tot[threadIdx.x] += vtot[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
         const int m = st->m, k0 = st->k0;
@@ -305,7 +335,9 @@ __global__ void k_update(int H, int W, ViewMap vm, float2 *__restrict__ psi, con
     }
 }
 
-__global__ void k_update_counters(DevState *sts, int V)
+// lin_period > 0: the next GRAD pass runs in the linear form unless the total iteration
+// count is a multiple of lin_period (a full forward DFT then bounds the drift of u).
+__global__ void k_update_counters(DevState *sts, int V, int lin_period)
 {
     for (int v = threadIdx.x; v < V; v += blockDim.x) {
         DevState *st = sts + v;
@@ -313,7 +345,56 @@ __global__ void k_update_counters(DevState *sts, int V)
         st->m += 1;
         st->total += 1;
         st->last_gamma = st->gamma;
+        st->lin = lin_period > 0 && (st->total % lin_period) != 0;
     }
+}
+
+// Order-independent 64-bit hash of each view's object: the sum modulo 2^64 of a mixed
+// (index, value bits) key per pixel (splitmix64 finaliser, Steele, Lea, Flood 2014).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+__global__ void __launch_bounds__(256) k_hash(int W, const int *__restrict__ row_view, const float2 *__restrict__ psi,
+                                              unsigned long long *__restrict__ out)
+{
+    // one block per object row: a row belongs to one view; one atomic add per row
+    __shared__ unsigned long long red[8];
+    const int y = blockIdx.x;
+    unsigned long long h = 0;
+    for (int x = threadIdx.x; x < W; x += 256) {
+        const size_t i = (size_t)y * W + x;
+        const float2 v = psi[i];
+        const unsigned long long key =
+            ((unsigned long long)__float_as_uint(v.x) << 32 | __float_as_uint(v.y)) ^ mix64(i);
+        h += mix64(key);  // integer sum: exact in any order
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = h;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int k = 0; k < 8; k++) t += red[k];
+        atomicAdd(out + row_view[y], t);
+    }
+}
+
+// Start of a solve call: the entries' u and v stay usable only if every view's object is
+// the one the previous call ended with (and nothing else overwrote them: force == 0).
+__global__ void k_check_hash(DevState *sts, int V, const unsigned long long *__restrict__ h, int force)
+{
+    for (int v = threadIdx.x; v < V; v += blockDim.x)
+        if (force || h[v] != sts[v].psi_hash) sts[v].lin = 0;
+}
+
+__global__ void k_store_hash(DevState *sts, int V, const unsigned long long *__restrict__ h)
+{
+    for (int v = threadIdx.x; v < V; v += blockDim.x) sts[v].psi_hash = h[v];
 }
 
 __global__ void k_check_data(const float *__restrict__ d, size_t n, int *flag)
@@ -338,13 +419,14 @@ __global__ void k_begin_solve(DevState *sts, int V)
 // ------------------------------------------------------------------------------------
 cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *w, float2 *out,
                            int dy, const float2 *eta_prev, const float2 *g_prev, double *part, const DevState *st,
-                           cudaStream_t s)
+                           cudaStream_t s, const float2 *psi, const float *D)
 {
+    const float p2 = (float)P * (float)P;
     const int nb = plan.ntile_x * plan.ntile_y;
     switch (P) {
-    case 64: k_scatter<64><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st); break;
-    case 128: k_scatter<128><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st); break;
-    case 256: k_scatter<256><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st); break;
+    case 64: k_scatter<64><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st, psi, D, p2); break;
+    case 128: k_scatter<128><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st, psi, D, p2); break;
+    case 256: k_scatter<256><<<nb, kScNT, 0, s>>>(a, plan, w, out, dy, eta_prev, g_prev, part, st, psi, D, p2); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -375,29 +457,29 @@ cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, const ViewMap &vm, DevState *st,
-                               DevHist h, const LsArgs &ls, cudaStream_t s)
+cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, double p2, const ViewMap &vm,
+                               DevState *st, DevHist h, const LsArgs &ls, cudaStream_t s)
 {
-    k_dy_finalize<<<vm.V, kSumNT, 0, s>>>(fpart, cs, part, vm, st, h, ls);
+    k_dy_finalize<<<vm.V, kSumNT, 0, s>>>(fpart, cs, part, p2, vm, st, h, ls);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const double *vpart, double vscale,
                              const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
 {
-    k_ls_decide<<<vm.V, kSumNT, 0, s>>>(part, kc, cs, vm, vpart, vscale, st, h, ls);
+    k_ls_decide<<<vm.V, kDecNT, 0, s>>>(part, kc, cs, vm, vpart, vscale, st, h, ls);
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(int H, int W, const ViewMap &vm, float2 *psi, const float2 *g, float2 *eta_prev,
-                          float2 *g_prev, DevState *st, cudaStream_t s)
+                          float2 *g_prev, DevState *st, int lin_period, cudaStream_t s)
 {
     size_t nb = ((size_t)H * W + 255) / 256;
     if (nb > 152 * 8) nb = 152 * 8;
     k_update<<<(unsigned)nb, 256, 0, s>>>(H, W, vm, psi, g, eta_prev, g_prev, st);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_update_counters<<<1, 32, 0, s>>>(st, vm.V);
+    k_update_counters<<<1, 32, 0, s>>>(st, vm.V, lin_period);
     return cudaGetLastError();
 }
 
@@ -413,6 +495,27 @@ cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t 
 cudaError_t launch_begin_solve(DevState *st, int V, cudaStream_t s)
 {
     k_begin_solve<<<1, 32, 0, s>>>(st, V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hash(int H, int W, const int *row_view, const float2 *psi, unsigned long long *h, int V,
+                        cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(h, 0, sizeof(unsigned long long) * V, s);
+    if (e != cudaSuccess) return e;
+    k_hash<<<H, 256, 0, s>>>(W, row_view, psi, h);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_hash(DevState *st, int V, const unsigned long long *h, int force, cudaStream_t s)
+{
+    k_check_hash<<<1, 32, 0, s>>>(st, V, h, force);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_hash(DevState *st, int V, const unsigned long long *h, cudaStream_t s)
+{
+    k_store_hash<<<1, 32, 0, s>>>(st, V, h);
     return cudaGetLastError();
 }
 

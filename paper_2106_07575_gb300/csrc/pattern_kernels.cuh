@@ -7,6 +7,8 @@
 //   k_grad         GRAD stage: gather x probe -> F -> likelihood residual (Eq. 3) and the
 //                  objective terms (Eq. 2) -> F^H -> x conj(p); one patch-sized result
 //                  per pattern, summed into the object by the scatter kernel
+//   k_grad_lin     GRAD stage in the linear form: u updated at the entries from the kept
+//                  v = G eta of the last step, one inverse DFT of the sparse correction
 //   k_ls_fft       LS stage, once per iteration: v = G eta for one pattern, kept at the
 //                  detector pixels with counts, and the two Parseval sums that the change
 //                  of the objective needs at the other pixels (the candidate windows run
@@ -126,22 +128,14 @@ __global__ void __launch_bounds__(NT) k_adjoint_fft(PatternArgs a, const float2 
 //   f = sum_j |u_j|^2 - sum_{entries} d log(|u|^2 + eps)
 //   r = u, except r = u (1 - d / (|u|^2 + eps)) at the entries
 //   w = conj(p) F^H r;  u at the entries is kept for the line search of this iteration.
+// One pattern of the GRAD pass (full form).
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__restrict__ psi,
-                                             float2 *__restrict__ w, double *__restrict__ fpart,
-                                             const DevState *__restrict__ st)
+__device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 *__restrict__ psi,
+                                             float2 *__restrict__ w, double *__restrict__ fpart, float2 *buf,
+                                             const float2 *tw, double *red, double *tot, int i, int c)
 {
-    if (st && st[a.pat_view[blockIdx.x / Slab<P, R>::CS]].stalled) return;
-    extern __shared__ __align__(16) float2 sm[];
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
-    __shared__ double red[NT / 32];
-    __shared__ double tot[1];
-    float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
-    int i, c;
-    who<P, R>(i, c);
     const int2 rc = a.pos[i];
-    cluster_start<P, R>();
-    load_twiddles<P, NT>(tw, a.tw);
     gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
@@ -178,6 +172,40 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
     }
 }
 
+// Single-CTA configurations (CS = 1) run persistently: the CTAs of the grid stride over
+// the patterns.  Clusters run one pattern each.
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__restrict__ psi,
+                                             float2 *__restrict__ w, double *__restrict__ fpart,
+                                             const DevState *__restrict__ st)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int CS = Slab<P, R>::CS;
+    __shared__ double red[NT / 32];
+    __shared__ double tot[1];
+    float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
+    const int c = blockIdx.x % CS;
+    if (st && a.V == 1 && (st->stalled || st->lin)) return;  // one view: decided for all patterns
+    cluster_start<P, R>();
+    load_twiddles<P, NT>(tw, a.tw);
+    auto skip = [&](int i) {
+        if (!st) return false;
+        const DevState &sv = st[a.pat_view[i]];
+        return sv.stalled || sv.lin;  // a view in the linear form runs k_grad_lin
+    };
+    if constexpr (CS == 1) {
+        for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
+            if (skip(i)) continue;
+            __syncthreads();  // the previous pattern's reads of buf are done
+            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, 0);
+        }
+    } else {
+        const int i = blockIdx.x / CS;
+        if (skip(i)) return;  // uniform over the cluster
+        grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c);
+    }
+}
+
 // LS pattern pass for a window of st->Leff <= L candidate steps gamma_l (Eq. 7 with Eq. 2):
 //   F(psi + gamma eta) - F(psi) = sum_j q_j - sum_{entries} d log1p(q / (|u|^2 + eps)),
 //   q_j = |u_j + gamma v_j|^2 - |u_j|^2 = gamma (2 Re conj(u_j) v_j + gamma |v_j|^2),
@@ -185,26 +213,87 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
 // Over all pixels, sum conj(u) v and sum |v|^2 equal P^2 sum conj(x) y and P^2 sum |y|^2
 // of the real-space exit waves x = p psi / P, y = p eta / P (Parseval); the d = 0 part is
 // that total minus the entries' part.
+// GRAD stage in the linear form (Eq. 1 is linear in psi): after an accepted step
+// psi_m = psi_{m-1} + gamma eta_{m-1}, the model at the entries is u_m = u_{m-1} + gamma v_{m-1}
+// (both kept there), so no forward DFT is needed.  The residual of Eq. 3 differs from u only
+// at the entries, r = u + Delta with Delta = -d u / (|u|^2 + eps); since F^H u = p psi, the
+// pattern's contribution to the gradient is conj(p) F^H Delta plus |p|^2 psi, and the latter
+// summed over positions is D psi (D the illumination map), added by the scatter-add.  The
+// objective keeps only its entry terms here; sum |u|^2 = P^2 sum D |psi|^2 comes from the
+// scatter-add too.  Runs only for views whose st->lin is set.
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_ls_fft(PatternArgs a, const float2 *__restrict__ eta,
-                                               double *__restrict__ part, const DevState *__restrict__ sts)
+__device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *__restrict__ w,
+                                                 double *__restrict__ fpart, float2 *buf, const float2 *tw,
+                                                 double *red, double *tot, float gam, int i, int c)
 {
-    const DevState *st = sts + a.pat_view[blockIdx.x / Slab<P, R>::CS];  // uniform over the cluster
-    if (st->stalled) return;
-    extern __shared__ __align__(16) float2 sm[];
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
-    __shared__ double red[(NT / 32) * 2];
-    __shared__ double tot[2];
+    // the column slab (permuted spectrum order) starts at zero
+    for (int e = threadIdx.x; e < P * LDB; e += NT) buf[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    float f = 0.0f;
+    const int per = a.nzc / CS;
+    const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
+#pragma unroll 2
+    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
+        const int s = __ldg(a.nz_slot + e);
+        const float dv = __ldg(a.nz_d + e);
+        const float2 u0 = a.nz_u[e], v = __ldg(a.nz_v + e);
+        const float2 u = make_float2(fmaf(gam, v.x, u0.x), fmaf(gam, v.y, u0.y));
+        a.nz_u[e] = u;
+        const float den = fmaf(u.x, u.x, u.y * u.y) + a.eps;
+        f -= dv * logf(den);
+        const float sc = -dv / den;
+        buf[(s / P) * LDB + (s % P - c * R)] = make_float2(u.x * sc, u.y * sc);
+    }
+    double vv[1] = {(double)f};
+    block_sum<NT, 1>(vv, red, tot);  // its barriers also order the writes before F^H
+    if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
+    fft2_inv<P, R, NT>(buf, tw);
+    float2 *wi = w + (size_t)i * P * P;
+    for (int e = threadIdx.x; e < R * P; e += NT) {
+        const int rl = e / P, x = e % P, yy = c * R + rl;
+        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
+    }
+}
+
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_grad_lin(PatternArgs a, float2 *__restrict__ w, double *__restrict__ fpart,
+                                                 const DevState *__restrict__ sts)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int CS = Slab<P, R>::CS;
+    __shared__ double red[NT / 32];
+    __shared__ double tot[1];
     float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
-    int i, c;
-    who<P, R>(i, c);
-    const int2 rc = a.pos[i];
+    const int c = blockIdx.x % CS;
+    if (a.V == 1 && (sts->stalled || !sts->lin)) return;  // one view: decided for all patterns
     cluster_start<P, R>();
     load_twiddles<P, NT>(tw, a.tw);
+    if constexpr (CS == 1) {
+        for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
+            const DevState *st = sts + a.pat_view[i];
+            if (st->stalled || !st->lin) continue;
+            __syncthreads();  // the previous pattern's reads of buf are done
+            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, 0);
+        }
+    } else {
+        const int i = blockIdx.x / CS;
+        const DevState *st = sts + a.pat_view[i];
+        if (st->stalled || !st->lin) return;  // uniform over the cluster
+        grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c);
+    }
+}
+
+template <int P, int R, int NT>
+__device__ __forceinline__ void ls_fft_pattern(const PatternArgs &a, const float2 *__restrict__ eta,
+                                               double *__restrict__ part, float2 *buf, const float2 *tw,
+                                               double *red, double *tot, int i, int c)
+{
+    constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
+    const int2 rc = a.pos[i];
     gather_rows<P, R, NT>(buf, a.probe, eta, a.W, rc.x, rc.y, c);  // p eta / P into the row slab
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
-
     // v = G eta at the entries (kept for the candidate windows), and the entries' share of
     // the two all-pixel sums, removed here so that rows 0 and 1 cover the pixels without counts
     float bp = 0.0f, cp = 0.0f;
@@ -222,7 +311,33 @@ __global__ void __launch_bounds__(NT) k_ls_fft(PatternArgs a, const float2 *__re
     double vals[2] = {-(double)bp, -(double)cp};
     block_sum<NT, 2>(vals, red, tot);
     const int KC = a.K * CS;
-    if (threadIdx.x < 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // rows 0, 1 of [L+2][K*CS]
+    if (threadIdx.x < 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // rows 0, 1
+}
+
+template <int P, int R, int NT>
+__global__ void __launch_bounds__(NT) k_ls_fft(PatternArgs a, const float2 *__restrict__ eta,
+                                               double *__restrict__ part, const DevState *__restrict__ sts)
+{
+    extern __shared__ __align__(16) float2 sm[];
+    constexpr int CS = Slab<P, R>::CS;
+    __shared__ double red[(NT / 32) * 2];
+    __shared__ double tot[2];
+    float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
+    const int c = blockIdx.x % CS;
+    if (a.V == 1 && sts->stalled) return;  // one view: decided for all patterns
+    cluster_start<P, R>();
+    load_twiddles<P, NT>(tw, a.tw);
+    if constexpr (CS == 1) {
+        for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
+            if (sts[a.pat_view[i]].stalled) continue;
+            __syncthreads();  // the previous pattern's reads of buf are done
+            ls_fft_pattern<P, R, NT>(a, eta, part, buf, tw, red, tot, i, 0);
+        }
+    } else {
+        const int i = blockIdx.x / CS;
+        if (sts[a.pat_view[i]].stalled) return;  // uniform over the cluster
+        ls_fft_pattern<P, R, NT>(a, eta, part, buf, tw, red, tot, i, c);
+    }
 }
 
 // Global slot (qy * P + qx) and natural-order index of local slot s of column chunk c.
@@ -319,6 +434,27 @@ cudaError_t launch_pattern(void (*kern)(KArgs...), int nblocks, int nthreads, si
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// Grid of a persistent pattern kernel: with one CTA per pattern (cs = 1), the CTAs that fit
+// on the device at once (by the kernel's occupancy), at most one per pattern; clusters
+// (cs > 1) keep one cluster per pattern, since co-resident clusters are fewer than the
+// per-CTA occupancy suggests and a static stride would serialise the others.
+template <typename... KArgs>
+int persistent_blocks(void (*kern)(KArgs...), int nslices, int nthreads, size_t smem, int cs)
+{
+    if (cs > 1) return nslices;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthreads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        return nslices;
+    }
+    int g = nsm * per_sm;
+    g -= g % cs;
+    if (g < cs) g = cs;
+    return g < nslices ? g : nslices;
+}
+
 // All launchers of one (P, R, NT) configuration.
 template <int P, int R, int NT>
 struct PatternOps {
@@ -334,11 +470,18 @@ struct PatternOps {
     static cudaError_t grad(const PatternArgs &a, const float2 *psi, float2 *w, double *fpart, const DevState *st,
                             cudaStream_t s)
     {
-        return launch_pattern(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, psi, w, fpart, st);
+        const int g = persistent_blocks(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        return launch_pattern(k_grad<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, psi, w, fpart, st);
+    }
+    static cudaError_t grad_lin(const PatternArgs &a, float2 *w, double *fpart, const DevState *st, cudaStream_t s)
+    {
+        const int g = persistent_blocks(k_grad_lin<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        return launch_pattern(k_grad_lin<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, w, fpart, st);
     }
     static cudaError_t ls(const PatternArgs &a, const float2 *eta, double *part, const DevState *st, cudaStream_t s)
     {
-        return launch_pattern(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, eta, part, st);
+        const int g = persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        return launch_pattern(k_ls_fft<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, eta, part, st);
     }
     static cudaError_t nz_count(const float *d, const int *perm, int K, int *cnt, cudaStream_t s)
     {
@@ -357,7 +500,7 @@ template <int P, int R, int NT>
 constexpr PatternImpl make_impl()
 {
     using O = PatternOps<P, R, NT>;
-    return PatternImpl{P, R, NT, &O::forward, &O::adjoint, &O::grad, &O::ls, &O::nz_count, &O::nz_fill};
+    return PatternImpl{P, R, NT, &O::forward, &O::adjoint, &O::grad, &O::grad_lin, &O::ls, &O::nz_count, &O::nz_fill};
 }
 
 }  // namespace pty

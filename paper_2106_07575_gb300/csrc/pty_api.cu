@@ -80,6 +80,8 @@ struct pty_ctx {
     float2 *eta = nullptr;       // atlas: the current search direction (LS stage)
     float *illum = nullptr;      // atlas: sum over positions of |probe / P|^2 (Parseval totals)
     double *part_eta = nullptr;  // [ntiles][2] object-tile sums of the LS stage
+    unsigned long long *hash = nullptr;  // [V] object hashes (solve entry / exit)
+    bool cache_dirty = false;  // the entries' u no longer belong to the last solve's object
     DevState *st = nullptr;     // [V]
     double *dscalar = nullptr;
     DevHist hist{};
@@ -163,7 +165,7 @@ void free_all(pty_ctx *c)
                     c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
                     c->stage_obj2, c->stage_pat, c->tc_img_fwd, c->tc_img_inv, c->tc_err, c->tc_x, c->tc_t,
                     c->tc_u, c->tc_pars, c->st_den, c->st_tmax, c->st_red,
-                    c->eta, c->illum, c->part_eta};
+                    c->eta, c->illum, c->part_eta, c->hash};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -189,6 +191,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.nz_u = c->nz_u;
     a.nz_v = c->nz_v;
     a.pat_view = c->pat_view;
+    a.V = c->V;
     a.eps = (float)c->opts.eps;
     return a;
 }
@@ -362,6 +365,10 @@ int tc_grad(pty_ctx *c, const float2 *psi, const DevState *st)
 }
 
 // The launches of one CG iteration on the context's stream (plain, timed or captured).
+// GRAD passes in the linear form between full passes: every kLinPeriod-th iteration (by the
+// total count since the last reset) recomputes u at the entries with the forward DFT.
+constexpr int kLinPeriod = 16;
+
 int launch_iteration(pty_ctx *c, bool timed)
 {
     if (c->opts.dft != 0) {
@@ -384,7 +391,7 @@ int launch_iteration(pty_ctx *c, bool timed)
         }
         {
             StageTimer t(c, 3, timed);
-            CK(pty::launch_dy_finalize(c->fpart, 1, c->part_sc, vm, c->st, c->hist, ls, c->s));
+            CK(pty::launch_dy_finalize(c->fpart, 1, c->part_sc, 0.0, vm, c->st, c->hist, ls, c->s));
         }
         {
             StageTimer t(c, 2, timed);  // v = G eta once per iteration; windows reuse it
@@ -403,7 +410,7 @@ int launch_iteration(pty_ctx *c, bool timed)
             CK(pty::launch_ls_decide(c->part_ls, c->K, 1, vm, nullptr, 0.0, ls, c->st, c->hist, c->s));
         }
         StageTimer t(c, 3, timed);
-        CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, c->s));
+        CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, 0, c->s));
         return PTY_OK;
     }
     const pty::PatternArgs a = pattern_args(c);
@@ -415,16 +422,18 @@ int launch_iteration(pty_ctx *c, bool timed)
     const int rest = std::max(0, c->opts.max_halvings - first);
     const int nwin = 1 + (rest + ls.L - 1) / ls.L;
     {
-        StageTimer t(c, 0, timed);
+        StageTimer t(c, 0, timed);  // full pass, or the linear form (each returns at once if not chosen)
         CK(c->impl->grad(a, c->psi, c->w, c->fpart, c->st, c->s));
+        CK(c->impl->grad_lin(a, c->w, c->fpart, c->st, c->s));
     }
     {
         StageTimer t(c, 1, timed);
-        CK(pty::launch_scatter(c->P, a, plan, c->w, c->g, 1, c->eta_prev, c->g_prev, c->part_sc, c->st, c->s));
+        CK(pty::launch_scatter(c->P, a, plan, c->w, c->g, 1, c->eta_prev, c->g_prev, c->part_sc, c->st, c->s, c->psi,
+                               c->illum));
     }
     {
         StageTimer t(c, 3, timed);
-        CK(pty::launch_dy_finalize(c->fpart, c->CS, c->part_sc, vm, c->st, c->hist, ls, c->s));
+        CK(pty::launch_dy_finalize(c->fpart, c->CS, c->part_sc, (double)c->P * c->P, vm, c->st, c->hist, ls, c->s));
     }
     {
         StageTimer t(c, 2, timed);  // eta and v = G eta once per iteration; the windows reuse them
@@ -436,15 +445,15 @@ int launch_iteration(pty_ctx *c, bool timed)
             StageTimer t(c, 2, timed);
             // the first window of an adaptive search runs on the 16- or the 32-candidate
             // kernel as the device chose; the other one returns at once
-            if (wdx == 0 && ls.adaptive) CK(pty::launch_ls_entries(a, c->CSl, 16, c->part_ls, c->st, c->s));
-            CK(pty::launch_ls_entries(a, c->CSl, ls.L, c->part_ls, c->st, c->s));
+            if (wdx == 0 && ls.adaptive) CK(pty::launch_ls_entries(a, c->CSl, c->V, 16, c->part_ls, c->st, c->s));
+            CK(pty::launch_ls_entries(a, c->CSl, c->V, ls.L, c->part_ls, c->st, c->s));
         }
         StageTimer t(c, 3, timed);
         CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, c->CSl, vm, c->part_eta, (double)c->P * c->P, ls, c->st,
                                  c->hist, c->s));
     }
     StageTimer t(c, 3, timed);
-    CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, c->s));
+    CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, kLinPeriod, c->s));
     return PTY_OK;
 }
 
@@ -736,7 +745,8 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     CKC(dalloc(&c->tile_list, std::max<size_t>(list.size(), 1)));
     CKC(dalloc(&c->w, (size_t)K * PP));
     CKC(dalloc(&c->fpart, (size_t)K * c->CSmax));
-    CKC(dalloc(&c->part_sc, (size_t)ntiles * 2));
+    CKC(dalloc(&c->part_sc, (size_t)ntiles * 3));
+    CKC(dalloc(&c->hash, (size_t)V));
     CKC(dalloc(&c->part_ls, (size_t)K * c->CSmax * (32 + 2)));
     CKC(dalloc(&c->psi, HW));
     CKC(dalloc(&c->g, HW));
@@ -880,6 +890,10 @@ int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
     if ((st = enter(c))) return st;
     if ((st = ensure_hist(c, niter))) return st;
     if ((st = views_in(c, (const float *const *)psi, c->psi))) return st;
+    // the entries' u and v carry over only to the object the previous call returned
+    CK(pty::launch_hash(c->HA, c->WA, c->row_view, c->psi, c->hash, c->V, c->s));
+    CK(pty::launch_check_hash(c->st, c->V, c->hash, c->cache_dirty ? 1 : 0, c->s));
+    c->cache_dirty = false;
     CK(pty::launch_begin_solve(c->st, c->V, c->s));
     const bool timed = (c->opts.flags & 1) != 0;
     if (!timed && niter > 0) build_graph(c);
@@ -890,6 +904,8 @@ int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
             return st;
         }
     }
+    CK(pty::launch_hash(c->HA, c->WA, c->row_view, c->psi, c->hash, c->V, c->s));
+    CK(pty::launch_store_hash(c->st, c->V, c->hash, c->s));
     std::vector<DevState> hs(c->V);
     int herr = 0;
     CK(cudaMemcpyAsync(hs.data(), c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
@@ -1014,6 +1030,7 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
     if ((st = enter(c)) || (st = ensure_stage(c))) return st;
     if ((st = views_in(c, &psi, c->stage_obj))) return st;
     pty::PatternArgs a = pattern_args(c);
+    c->cache_dirty = true;  // the pass below overwrites u at the entries
     if (c->opts.dft != 0) {
         if ((st = tc_grad(c, c->stage_obj, nullptr))) return st;
     } else {
@@ -1065,10 +1082,21 @@ int pty_batch_cg_solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_repo
 
 int32_t pty_num_views(const pty_ctx *c) { return c ? c->V : 0; }
 
+// Checkpoint layout: header {magic, H*W of the atlas, views, entries} (4 x int64), g_prev,
+// eta_prev, the per-view DevState, then u and v at the entries (the linear form's cache).
+namespace {
+constexpr long long kStateMagic = 0x5054594347310001LL;
+size_t state_bytes(const pty_ctx *c)
+{
+    const size_t HW = (size_t)c->HA * c->WA, E = (size_t)std::max<long long>(c->n_entries, 0);
+    return 4 * sizeof(long long) + 2 * sizeof(float2) * HW + sizeof(DevState) * c->V + 2 * sizeof(float2) * E;
+}
+}  // namespace
+
 size_t pty_cg_state_size(const pty_ctx *c)
 {
     if (!c) return 0;
-    return 2 * sizeof(float2) * (size_t)c->HA * c->WA + sizeof(DevState) * c->V;
+    return state_bytes(c);
 }
 
 int pty_cg_state_save(pty_ctx *c, void *host_buf)
@@ -1076,12 +1104,28 @@ int pty_cg_state_save(pty_ctx *c, void *host_buf)
     if (!c || !host_buf) return fail(c, PTY_ERR_ARG, "ctx and buffer must be non-NULL");
     int st;
     if ((st = enter(c))) return st;
-    const size_t HW = (size_t)c->HA * c->WA;
+    const size_t HW = (size_t)c->HA * c->WA, E = (size_t)std::max<long long>(c->n_entries, 0);
     char *b = (char *)host_buf;
+    const long long hdr[4] = {kStateMagic, (long long)HW, (long long)c->V, (long long)E};
+    std::memcpy(b, hdr, sizeof hdr);
+    b += sizeof hdr;
     CK(cudaMemcpyAsync(b, c->g_prev, sizeof(float2) * HW, cudaMemcpyDeviceToHost, c->s));
     CK(cudaMemcpyAsync(b + sizeof(float2) * HW, c->eta_prev, sizeof(float2) * HW, cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(b + 2 * sizeof(float2) * HW, c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
-    return sync(c);
+    char *bs = b + 2 * sizeof(float2) * HW;
+    CK(cudaMemcpyAsync(bs, c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
+    char *be = bs + sizeof(DevState) * c->V;
+    if (E) {
+        CK(cudaMemcpyAsync(be, c->nz_u, sizeof(float2) * E, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(be + sizeof(float2) * E, c->nz_v, sizeof(float2) * E, cudaMemcpyDeviceToHost, c->s));
+    }
+    if ((st = sync(c))) return st;
+    if (c->cache_dirty) {  // the entries were overwritten since the last solve: no linear carry-over
+        std::vector<DevState> hs(c->V);
+        std::memcpy(hs.data(), bs, sizeof(DevState) * c->V);
+        for (auto &h : hs) h.lin = 0;
+        std::memcpy(bs, hs.data(), sizeof(DevState) * c->V);
+    }
+    return PTY_OK;
 }
 
 int pty_cg_state_load(pty_ctx *c, const void *host_buf)
@@ -1089,8 +1133,13 @@ int pty_cg_state_load(pty_ctx *c, const void *host_buf)
     if (!c || !host_buf) return fail(c, PTY_ERR_ARG, "ctx and buffer must be non-NULL");
     int st;
     if ((st = enter(c))) return st;
-    const size_t HW = (size_t)c->HA * c->WA;
+    const size_t HW = (size_t)c->HA * c->WA, E = (size_t)std::max<long long>(c->n_entries, 0);
     const char *b = (const char *)host_buf;
+    long long hdr[4];
+    std::memcpy(hdr, b, sizeof hdr);
+    if (hdr[0] != kStateMagic || hdr[1] != (long long)HW || hdr[2] != (long long)c->V || hdr[3] != (long long)E)
+        return fail(c, PTY_ERR_ARG, "checkpoint does not belong to a problem of this context's sizes");
+    b += sizeof hdr;
     std::vector<DevState> hs(c->V);
     std::memcpy(hs.data(), b + 2 * sizeof(float2) * HW, sizeof(DevState) * c->V);
     for (auto &h : hs) {
@@ -1098,9 +1147,15 @@ int pty_cg_state_load(pty_ctx *c, const void *host_buf)
         h.decided = 0;
         h.stalled = 0;
     }
+    const char *be = b + 2 * sizeof(float2) * HW + sizeof(DevState) * c->V;
     CK(cudaMemcpyAsync(c->g_prev, b, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->eta_prev, b + sizeof(float2) * HW, sizeof(float2) * HW, cudaMemcpyHostToDevice, c->s));
     CK(cudaMemcpyAsync(c->st, hs.data(), sizeof(DevState) * c->V, cudaMemcpyHostToDevice, c->s));
+    if (E) {
+        CK(cudaMemcpyAsync(c->nz_u, be, sizeof(float2) * E, cudaMemcpyHostToDevice, c->s));
+        CK(cudaMemcpyAsync(c->nz_v, be + sizeof(float2) * E, sizeof(float2) * E, cudaMemcpyHostToDevice, c->s));
+    }
+    c->cache_dirty = false;
     return sync(c);
 }
 

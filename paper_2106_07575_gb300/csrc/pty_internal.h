@@ -20,12 +20,14 @@ struct DevState {
     int Leff;      // candidates in the open line-search window
     int last_halvings;  // trials of the last accepted step (sizes the next first window)
     int Lsel;      // capacity of the LS kernel that runs the open window (16 or 32 when adaptive)
-    int pad2;
+    int lin;       // the entries hold u and v of the last accepted step: the next GRAD pass
+                   // updates u = u + gamma v in place instead of running the forward DFT
     double alpha;  // Dai-Yuan coefficient of the current iteration (Eq. 6)
     double gamma;  // accepted step of the current iteration
     double Fm;     // F(psi_m)
     double Fnext;  // F(psi_m + gamma eta_m) of the accepted trial
     double last_gamma;
+    unsigned long long psi_hash;  // hash of the view's object when the last solve call ended
     double cand[32];  // candidate steps gamma0 tau^(k0+l+1) of the open line-search window
 };
 
@@ -57,6 +59,7 @@ struct PatternArgs {
     float2 *nz_u;               // [E] u = G psi_m at each entry (GRAD pass -> LS pass)
     float2 *nz_v;               // [E] v = G eta_m at each entry (LS pass -> candidate windows)
     const int *pat_view;        // [K] view of sorted pattern i (all 0 for one view)
+    int V;                      // views
     float eps;
 };
 
@@ -81,6 +84,10 @@ struct PatternImpl {
     // fpart = objective terms; u kept at the entries.  Exits early when st->stalled.
     cudaError_t (*grad)(const PatternArgs &, const float2 *psi, float2 *w, double *fpart, const DevState *st,
                         cudaStream_t);
+    // GRAD pattern pass in the linear form (views with st->lin set; k_grad skips them):
+    // u = u + gamma_last v at the entries, fpart = entry terms of the objective,
+    // w[i] = conj(p) F^H Delta_i with Delta the residual's difference from u.
+    cudaError_t (*grad_lin)(const PatternArgs &, float2 *w, double *fpart, const DevState *st, cudaStream_t);
     // LS pattern pass, once per iteration: v = G eta (eta the object-sized search direction)
     // is kept at the entries (nz_v) and part[0][.], part[1][.] = -(sum Re conj(u) v, sum
     // |v|^2) over the entries (per CTA, rows of length K * CS): the all-pixel totals come from
@@ -102,7 +109,8 @@ cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_
 // part[2 + l][i * cs + c] = sum over the entries of chunk c of pattern i of the objective
 // change at candidate l (gamma0 tau^(k0+l+1)), from u (nz_u), v (nz_v) and d: the window
 // of the L-candidate kernel; returns at once unless st->Lsel == L and a window is open.
-cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int L, double *part, const DevState *st, cudaStream_t s);
+cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, double *part, const DevState *st,
+                              cudaStream_t s);
 
 // ---- tensor-core DFT (tc_dft.cu) ----
 // One application: Y[b][k][y] = sum_n X[b][y][n] exp(sign 2 pi i n k / P) for the nrows =
@@ -143,18 +151,22 @@ struct ViewMap {
     const int *tile_off;  // [V + 1] scatter-tile range of each view
     const int *row_view;  // [H] view of each object row
 };
-// out[y][x] = sum over patterns i covering (y, x), in ascending i, of w[i][y-r_i][x-c_i].
-// With dy != 0 also part[b] = (sum |out|^2, sum Re conj(eta_prev) (out - g_prev)) per tile b.
+// out[y][x] = sum over patterns i covering (y, x), in ascending i, of w[i][y-r_i][x-c_i],
+// plus P^2 D psi for views in the linear form (st->lin; psi, D the object and illumination).
+// With dy != 0 also part[b] = (sum |out|^2, sum Re conj(eta_prev) (out - g_prev),
+// linear form ? sum D |psi|^2 : 0) per tile b ([ntiles][3]).
 cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *w,
                            float2 *out, int dy, const float2 *eta_prev, const float2 *g_prev,
-                           double *part, const DevState *st, cudaStream_t s);
+                           double *part, const DevState *st, cudaStream_t s, const float2 *psi = nullptr,
+                           const float *D = nullptr);
 // Fixed-order sum of n doubles into *out (one block).
 cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
 // DIR stage scalars per view (one block each): F_m = sum of the view's fpart (CS per
-// pattern); alpha from the view's tile partials (restart rule); opens the first line-search
-// window; writes the history of iteration m.
-cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, const ViewMap &vm, DevState *st,
-                               DevHist h, const LsArgs &ls, cudaStream_t s);
+// pattern) plus p2 times the tiles' third partial (linear form); alpha from the view's tile
+// partials (restart rule); opens the first line-search window; writes the history of
+// iteration m.
+cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, double p2, const ViewMap &vm,
+                               DevState *st, DevHist h, const LsArgs &ls, cudaStream_t s);
 // LS stage decision per view over the open window; part rows have length kc (K * CS), the
 // view's partials are [pat_off[v] * cs, pat_off[v + 1] * cs).  vpart (nullable): object-tile
 // partials [ntiles][2] added, times vscale, to rows 0 and 1 over the view's tiles.
@@ -168,11 +180,19 @@ cudaError_t launch_eta(int H, int W, const ScatterPlan &plan, const float2 *psi,
                        const float *D, float2 *eta, double *part, const DevState *st, cudaStream_t s);
 // Update stage for every object pixel (W columns per row): psi += gamma eta,
 // eta_prev <- eta = -g + alpha eta_prev, g_prev <- g, with the scalars of the row's view.
+// lin_period > 0 enables the linear form of the next GRAD pass (a full pass every
+// lin_period iterations).
 cudaError_t launch_update(int H, int W, const ViewMap &vm, float2 *psi, const float2 *g, float2 *eta_prev,
-                          float2 *g_prev, DevState *st, cudaStream_t s);
+                          float2 *g_prev, DevState *st, int lin_period, cudaStream_t s);
 // flag |= 1 if any of the n floats is NaN, Inf or negative.
 cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t s);
 cudaError_t launch_begin_solve(DevState *st, int V, cudaStream_t s);
+// h[v] = order-independent 64-bit hash of view v's rows of psi (H x W atlas).
+cudaError_t launch_hash(int H, int W, const int *row_view, const float2 *psi, unsigned long long *h, int V,
+                        cudaStream_t s);
+// st[v].lin = 0 where force or h[v] differs from st[v].psi_hash; store h into psi_hash.
+cudaError_t launch_check_hash(DevState *st, int V, const unsigned long long *h, int force, cudaStream_t s);
+cudaError_t launch_store_hash(DevState *st, int V, const unsigned long long *h, cudaStream_t s);
 
 }  // namespace pty
 

@@ -63,7 +63,7 @@ SM_MAX_MHZ = 2070.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["pty", "reference"], default="pty")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -383,30 +383,35 @@ def main():
     tctx.close()
     n_it = max(trep["iters_done"], 1)
 
-    # roofline of the dominant kernel, k_grad (FP32 ALU bound: 2-D FFTs on the CUDA cores);
-    # algorithmic flops: 5 N log2 N per 2-D DFT (N = P^2) plus the elementwise complex
-    # arithmetic (probe products, likelihood residual); one launch covers all K patterns
+    # roofline of the dominant kernel, the LS pattern pass k_ls_fft (FP32 ALU bound: one 2-D
+    # FFT per pattern on the CUDA cores; one launch per iteration covers all K patterns).
+    # Algorithmic flops: 5 N log2 N per 2-D DFT (N = P^2) plus the probe product (6 N) and,
+    # at the n_e detector pixels with counts, the two Parseval sums (8 per pixel).
     P, K = p.P, p.K
     L = opts.ls_window
-    grad_flops = K * (2 * fft2_flops(P) + 24 * P * P)
+    n_e = float(np.count_nonzero(p.d))  # detector pixels with counts
+    ls_flops = K * (fft2_flops(P) + 6 * P * P) + 8 * n_e
+    ls_ms = stage_ms[2] / max(stage_n[2], 1)
     grad_ms = stage_ms[0] / max(stage_n[0], 1)
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"bound": "alu", "kernel": "k_grad", "achieved": grad_flops / (grad_ms * 1e-3) / 1e12,
-            "peak": peak_tflops, "unit": "TFLOP/s", "frac": grad_flops / (grad_ms * 1e-3) / 1e12 / peak_tflops,
-            "traffic": None,
+    achieved = ls_flops / (ls_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_ls_fft", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops, "traffic": None,
             "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-            "launch_ms": grad_ms, "launches_timed": int(stage_n[0]),
-            "timing": "CUDA events around each k_grad launch on its stream, stage-timed pass of the same workload",
-            "other": {"ls_stage_ms_per_iter": stage_ms[2] / n_it, "scatter_ms_per_iter": stage_ms[1] / n_it,
-                      "small_ms_per_iter": stage_ms[3] / n_it,
-                      "k_grad_hbm_gbs": K * P * P * 8 / (grad_ms * 1e-3) / 1e9}}
+            "launch_ms": ls_ms, "launches_timed": int(stage_n[2]),
+            "timing": "CUDA events around each k_ls_fft launch on its stream, stage-timed pass of the same workload",
+            "other": {"grad_pass_ms": grad_ms,
+                      "grad_pass_tflops_linear_form": K * (fft2_flops(P) + 6 * P * P) / (grad_ms * 1e-3) / 1e12,
+                      "ls_windows_ms_per_iter": stage_ms[4] / n_it, "scatter_ms_per_iter": stage_ms[1] / n_it,
+                      "small_ms_per_iter": stage_ms[3] / n_it}}
 
     Lcap = 32 if L == 0 else L
     first_w = 4 if L == 0 else L
     nwin = 1 + (max(0, opts.max_halvings - first_w) + Lcap - 1) // Lcap
-    # per iteration: grad, scatter, dy_finalize, eta, LS pass, windows (entries + decide;
-    # the adaptive first window launches both entry kernels), update + counters
-    launches = args.steps * (7 + 2 * nwin + (1 if L == 0 else 0)) + 1 if args.dft == 0 else None
+    # per iteration: grad (full and linear form, one returns at once), scatter, dy_finalize,
+    # eta, LS pass, windows (entries + decide; the adaptive first window launches both entry
+    # kernels), update + counters; per call: 2 hashes, hash check, begin, hash store
+    launches = args.steps * (8 + 2 * nwin + (1 if L == 0 else 0)) + 5 if args.dft == 0 else None
     value = world * K * steps_done / (ms * 1e-3)
 
     out = {
@@ -418,7 +423,8 @@ def main():
                    "l2": f"inputs larger than L2 ({p.d.nbytes / 1e6:.0f} MB data)",
                    "parallelism": f"{world} independent replica(s)"},
         "status": pty.STATUS_NAMES[st], "roofline": roof, "clocks": clocks, "gpu_launches": launches,
-        "stages_ms_per_iter": {"grad": stage_ms[0] / n_it, "scatter": stage_ms[1] / n_it, "ls": stage_ms[2] / n_it,
+        "stages_ms_per_iter": {"grad": stage_ms[0] / n_it, "scatter": stage_ms[1] / n_it,
+                               "ls_pass": stage_ms[2] / n_it, "ls_windows": stage_ms[4] / n_it,
                                "small": stage_ms[3] / n_it, "iterations": n_it,
                                "note": "stage-timed pass (events between stages, no graph)"},
         "trials_per_iter": float(np.mean(rep["halvings"])) if len(rep["halvings"]) else None,

@@ -88,7 +88,8 @@ typedef struct {
                             or 32, or 0 (default) for an adaptive first pass sized from the
                             previous iteration's trial count (plus one), then passes of 32; the
                             accepted step does not depend on it */
-    int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times) */
+    int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times); bit 1: no
+                            linear form (every GRAD pass runs the forward DFT) */
     int32_t tile_config; /* pattern-kernel configuration: -1 (default) = autotune at
                             pty_create (the GRAD and LS passes of every configuration for P are
                             timed on the problem's own data; the choice is cached per problem
@@ -236,11 +237,13 @@ PTY_API int pty_get_plan(const pty_ctx *ctx, int32_t plan[4]);
 
 /*
  * Per-stage GPU time accumulated since the last reset (needs opts.flags bit 0):
- * ms[0] GRAD pattern pass, ms[1] scatter-add + direction reductions, ms[2] LS pattern
- * passes, ms[3] small reductions and update; launches[i] the matching kernel counts.
- * Either pointer may be NULL.  reset != 0 clears the counters after reading.
+ * ms[0] GRAD pattern pass (full or linear form), ms[1] scatter-add + direction reductions,
+ * ms[2] LS pattern pass (v = G eta), ms[3] small kernels (Dai-Yuan scalars, search
+ * direction, line-search decisions, update), ms[4] line-search candidate windows;
+ * launches[i] the matching launch counts.  Either pointer may be NULL.  reset != 0 clears
+ * the counters after reading.
  */
-PTY_API int pty_stage_times(pty_ctx *ctx, double ms[4], int64_t launches[4], int reset);
+PTY_API int pty_stage_times(pty_ctx *ctx, double ms[5], int64_t launches[5], int reset);
 
 /*
  * Objective and gradient (as pty_gradient) without a context and without allocating any

@@ -109,8 +109,8 @@ struct pty_ctx {
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;
-    double stage_ms[4] = {0, 0, 0, 0};
-    int64_t stage_n[4] = {0, 0, 0, 0};
+    double stage_ms[5] = {0, 0, 0, 0, 0};
+    int64_t stage_n[5] = {0, 0, 0, 0, 0};
 };
 
 static std::string g_create_err;
@@ -401,7 +401,7 @@ int launch_iteration(pty_ctx *c, bool timed)
         }
         for (int wdx = 0; wdx < nwin; wdx++) {
             {
-                StageTimer t(c, 2, timed);
+                StageTimer t(c, 4, timed);
                 if (wdx == 0 && ls.adaptive)
                     CK(pty::launch_tc_ls_entries(a, c->P, 16, c->tc_u, c->tc_pars, c->part_ls, c->st, c->s));
                 CK(pty::launch_tc_ls_entries(a, c->P, ls.L, c->tc_u, c->tc_pars, c->part_ls, c->st, c->s));
@@ -436,13 +436,16 @@ int launch_iteration(pty_ctx *c, bool timed)
         CK(pty::launch_dy_finalize(c->fpart, c->CS, c->part_sc, (double)c->P * c->P, vm, c->st, c->hist, ls, c->s));
     }
     {
-        StageTimer t(c, 2, timed);  // eta and v = G eta once per iteration; the windows reuse them
+        StageTimer t(c, 3, timed);  // the search direction and its object sums
         CK(pty::launch_eta(c->HA, c->WA, plan, c->psi, c->g, c->eta_prev, c->illum, c->eta, c->part_eta, c->st, c->s));
+    }
+    {
+        StageTimer t(c, 2, timed);  // v = G eta once per iteration; the windows reuse it
         CK(c->impl_ls->ls(a, c->eta, c->part_ls, c->st, c->s));
     }
     for (int wdx = 0; wdx < nwin; wdx++) {
         {
-            StageTimer t(c, 2, timed);
+            StageTimer t(c, 4, timed);
             // the first window of an adaptive search runs on the 16- or the 32-candidate
             // kernel as the device chose; the other one returns at once
             if (wdx == 0 && ls.adaptive) CK(pty::launch_ls_entries(a, c->CSl, c->V, 16, c->part_ls, c->st, c->s));
@@ -453,7 +456,8 @@ int launch_iteration(pty_ctx *c, bool timed)
                                  c->hist, c->s));
     }
     StageTimer t(c, 3, timed);
-    CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, kLinPeriod, c->s));
+    const int lin_period = (c->opts.flags & 2) ? 0 : kLinPeriod;
+    CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, lin_period, c->s));
     return PTY_OK;
 }
 
@@ -1169,15 +1173,15 @@ int pty_get_plan(const pty_ctx *c, int32_t plan[4])
     return PTY_OK;
 }
 
-int pty_stage_times(pty_ctx *c, double ms[4], int64_t launches[4], int reset)
+int pty_stage_times(pty_ctx *c, double ms[5], int64_t launches[5], int reset)
 {
     if (!c) return fail(nullptr, PTY_ERR_ARG, "ctx is NULL");
-    for (int i = 0; i < 4; i++) {
+    for (int i = 0; i < 5; i++) {
         if (ms) ms[i] = c->stage_ms[i];
         if (launches) launches[i] = c->stage_n[i];
     }
     if (reset)
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < 5; i++) {
             c->stage_ms[i] = 0;
             c->stage_n[i] = 0;
         }

@@ -249,8 +249,8 @@ def pty_cg_state_load(ctx, blob: bytes):
 
 def pty_stage_times(ctx, reset=False):
     lib = load()
-    ms = (ctypes.c_double * 4)()
-    n = (ctypes.c_int64 * 4)()
+    ms = (ctypes.c_double * 5)()
+    n = (ctypes.c_int64 * 5)()
     _check(lib, ctx, lib.pty_stage_times(ctx, ms, n, int(bool(reset))))
     return list(ms), list(n)
 

@@ -20,6 +20,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]
+# extra nvcc flags (space-separated), e.g. compile-time tuning defines; part of the cache key
+FLAGS += os.environ.get("PTY_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

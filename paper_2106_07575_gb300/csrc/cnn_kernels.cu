@@ -421,7 +421,7 @@ __global__ void k_refresh(const float *__restrict__ master, int cout, int cin, _
 }
 
 // ---- stitching ----
-constexpr int kStTY = 32, kStTX = 64, kStNJ = kStTY * kStTX / NT;
+constexpr int kStTY = kTileY, kStTX = kTileX, kStNJ = kStTY * kStTX / NT;
 
 template <int P>
 __global__ void __launch_bounds__(NT) k_stitch_acc(PatternArgs a, ScatterPlan plan, const float2 *__restrict__ patches,

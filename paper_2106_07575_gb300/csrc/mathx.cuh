@@ -18,8 +18,10 @@ __device__ __forceinline__ float log1p_fast(float t)
 {
     const float w = 1.0f + t;
     const int e = (__float_as_int(w) - 0x3f3504f3) >> 23;
-    const float two_e = __int_as_float((127 + e) << 23);
-    const float f = (t - (two_e - 1.0f)) * __int_as_float((127 - e) << 23);
+    // f = (t - (2^e - 1)) 2^-e, written as one rounding of t 2^-e + (2^-e - 1): the same
+    // value (scaling by a power of two commutes with rounding; 2^-e - 1 is exact)
+    const float r = __int_as_float((127 - e) << 23);
+    const float f = fmaf(t, r, r - 1.0f);
     const float s = __fdividef(f, 2.0f + f);
     const float s2 = s * s;
     const float p = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);

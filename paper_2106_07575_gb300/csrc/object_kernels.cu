@@ -19,7 +19,7 @@
 namespace pty {
 
 namespace {
-constexpr int kScTY = 32, kScTX = 64, kScNT = 256, kScNJ = kScTY * kScTX / kScNT;
+constexpr int kScTY = kTileY, kScTX = kTileX, kScNT = 256, kScNJ = kScTY * kScTX / kScNT;
 constexpr int kSumNT = 256;
 }  // namespace
 

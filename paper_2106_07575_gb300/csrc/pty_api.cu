@@ -199,8 +199,8 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
 pty::ScatterPlan scatter_plan(const pty_ctx *c)
 {
     pty::ScatterPlan p;
-    p.TY = 32;
-    p.TX = 64;
+    p.TY = pty::kTileY;
+    p.TX = pty::kTileX;
     p.ntile_y = c->ntile_y;
     p.ntile_x = c->ntile_x;
     p.tile_start = c->tile_start;
@@ -685,8 +685,9 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     }
     for (int v = 0; v < V; v++) vpoff[v + 1] = vpoff[v] + Ks[v];  // views are contiguous after the sort
 
-    // scatter plan: object tiles of 32 x 64, each with the ascending list of overlapping patterns
-    const int TY = 32, TX = 64;
+    // scatter plan: object tiles of kTileY x kTileX, each with the ascending list of
+    // overlapping patterns
+    const int TY = pty::kTileY, TX = pty::kTileX;
     c->ntile_y = (c->HA + TY - 1) / TY;
     c->ntile_x = (c->WA + TX - 1) / TX;
     const int ntiles = c->ntile_y * c->ntile_x;

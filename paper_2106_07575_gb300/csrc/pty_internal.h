@@ -136,6 +136,16 @@ cudaError_t launch_tc_ls_entries(const PatternArgs &a, int P, int L, const float
                                  double *part, const DevState *st, cudaStream_t s);
 
 // ---- object kernels (object_kernels.cu) ----
+// Object tile of the scatter-add and of the other object-tile kernels (rows x columns);
+// views of a batch start on multiples of 32 rows, a multiple of kTileY.
+#ifndef PTY_TILE_Y
+#define PTY_TILE_Y 16
+#endif
+#ifndef PTY_TILE_X
+#define PTY_TILE_X 64
+#endif
+constexpr int kTileY = PTY_TILE_Y, kTileX = PTY_TILE_X;
+static_assert(32 % kTileY == 0 && 256 % kTileX == 0 && (kTileY * kTileX) % 256 == 0, "object tile shape");
 struct ScatterPlan {
     int TY, TX;       // object tile
     int ntile_y, ntile_x;

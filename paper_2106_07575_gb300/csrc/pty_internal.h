@@ -123,6 +123,11 @@ cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out)
 cudaError_t tc_dft_rows(int P, bool bf16, const float2 *X, float2 *Y, const void *img, int nrows,
                         const int *out_index, const float2 *conj_mul, int *err, cudaStream_t s);
 cudaError_t launch_gather_patches(const PatternArgs &a, int P, const float2 *psi, float2 *X, cudaStream_t s);
+// The BF16 split form as a persistent warp-specialised kernel (tc_ws.cu): its B images
+// (interleaved real/imaginary K) and the row DFT with the semantics of tc_dft_rows.
+cudaError_t tc_ws_images(int P, int sign, std::vector<uint8_t> &out);
+cudaError_t tc_ws_rows(int P, const float2 *X, float2 *Y, const void *img, int nrows, const int *out_index,
+                       const float2 *conj_mul, int *err, cudaStream_t s);
 // CG pieces of the tensor-core form (tc_cg.cu); spectra U, V are [K][P][P] in natural order.
 // Residual of Eq. 3 in place in U at the entries, objective terms fpart[i], u kept in nz_u.
 cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, double *fpart, const DevState *st,

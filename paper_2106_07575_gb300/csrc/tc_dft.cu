@@ -1,4 +1,6 @@
-// tc_dft.cu -- the DFT of Eq. 1 (and F^H of Eq. 3) as a tensor-core GEMM on sm_103a.
+// tc_dft.cu -- the DFT of Eq. 1 (and F^H of Eq. 3) as a tensor-core GEMM on sm_103a: the
+// FP16 split form (per-tile scaling, one tile per CTA) and the dispatch; the BF16 split form
+// runs the persistent warp-specialised kernel of tc_ws.cu.
 //
 // One application transforms every row of a batch of P x P complex arrays and stores the
 // result transposed within each array, so two applications give the unnormalised 2-D DFT
@@ -9,7 +11,7 @@
 // half-precision part (BF16 or FP16): A B ~ Ah Bh + Al Bh + Ah Bl, evaluated as ONE GEMM
 // with K' = 3 * 2P, A' = [Ah | Al | Ah], B' = [Bh; Bh; Bl], accumulated in FP32 in TMEM.
 //
-// Per CTA (128 threads): 128 consecutive rows.  For FP16 the tile is first scaled by a power
+// Per CTA (512 threads): 128 consecutive rows.  For FP16 the tile is first scaled by a power
 // of two so that its largest magnitude is 2^14 at most (undone exactly on the results).  The
 // threads split the FP32 rows into Ah and Al in shared memory (canonical K-major layout without swizzle: 8 x 16-byte core
 // matrices, K-adjacent core matrices 128 bytes apart).  B' is stored in global memory as
@@ -27,15 +29,16 @@
 #include <vector>
 
 #include "pty_internal.h"
+#include "tc_ptx.cuh"
 
 namespace pty {
 namespace {
+using namespace tcx;
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 512;  // 16 warps: loads in flight for the operand split; 4 per TMEM lane quarter
 constexpr int kTcRows = 128;    // M per CTA
 constexpr int kTcChunk = 64;    // K' elements per pipeline stage
 constexpr int kTcStages = 3;
-constexpr long long kSpinLimit = 1LL << 26;  // mbarrier poll limit (~seconds)
 
 template <int P>
 struct TcGeo {
@@ -50,111 +53,12 @@ struct TcGeo {
     static constexpr size_t SMEM = 2 * (size_t)A_BYTES + kTcStages * (size_t)B_BYTES + 256;
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05; no swizzle, base offset 0
-    return d;
-}
-
 // kind::f16 instruction descriptor: D = F32, A = B = BF16 or F16, both K-major, M = 128.
 template <int N, bool BF16>
 __device__ __forceinline__ uint32_t umma_idesc()
 {
     const uint32_t fmt = BF16 ? 1u : 0u;
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcRows >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// Bounded wait for the given phase parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kSpinLimit; it++) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate)
-{
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void umma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 32 consecutive accumulator columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
-}
-
-template <bool BF16>
-__device__ __forceinline__ uint16_t to_half_bits(float x)
-{
-    if constexpr (BF16) {
-        return __bfloat16_as_ushort(__float2bfloat16_rn(x));
-    } else {
-        return __half_as_ushort(__float2half_rn(x));
-    }
-}
-
-template <bool BF16>
-__device__ __forceinline__ float from_half_bits(uint16_t b)
-{
-    if constexpr (BF16) {
-        return __bfloat162float(__ushort_as_bfloat16(b));
-    } else {
-        return __half2float(__ushort_as_half(b));
-    }
 }
 
 // Y[b][k][y] = sum_n X[b][y][n] W^{n k}  (W = exp(sign 2 pi i / P)) for all rows (b, y).
@@ -221,6 +125,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
 
     // A: split the FP32 rows into high and low halves, canonical K-major layout.
     // Task (row m, group j of 8 complex values) -> core-matrix rows of re and im.
+#pragma unroll 4
     for (int t = tid; t < kTcRows * (P / 8); t += kTcThreads) {
         const int m = t / (P / 8), j = t % (P / 8);
         const int row = m0 + m;
@@ -312,34 +217,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
     if (!ok) {
         if (tid == 0) atomicOr(err, 1);
     } else {
-        // epilogue: lane = row; columns [0, P) real parts, [P, 2P) imaginary parts
-        const int m = warp * 32 + lane, row = m0 + m;
+        // epilogue: warp w reads TMEM lane quarter w % 4 (lane = row) and the column group
+        // w / 4 of P/4 columns; columns [0, P) hold real parts, [P, 2P) imaginary parts
+        constexpr int CW = P / (kTcThreads / 128);  // columns per warp: 32 (P = 128) or 16 (P = 64)
+        const int q4 = warp & 3, k0 = (warp >> 2) * CW;
+        const int m = q4 * 32 + lane, row = m0 + m;
         const int b = row / P, y = row % P;
-        const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+        const uint32_t tl = tmem + ((uint32_t)(q4 * 32) << 16);
         const float unscale = 1.0f / scale;  // exact: a power of two
-#pragma unroll 1
-        for (int k0 = 0; k0 < P; k0 += 32) {
-            float re[32], im[32];
+        float re[CW], im[CW];
+        if constexpr (CW == 32) {
             tmem_ld32(tl + k0, re);
             tmem_ld32(tl + P + k0, im);
+        } else {
+            tmem_ld16(tl + k0, re);
+            tmem_ld16(tl + P + k0, im);
+        }
 #pragma unroll
-            for (int q = 0; q < 32; q++) {
-                re[q] *= unscale;
-                im[q] *= unscale;
-            }
-            if (row < nrows) {
-                float2 *dst = Y + (size_t)(out_index ? out_index[b] : b) * P * P + y;
-                if (conj_mul) {  // element (k, y) of the 2-D result times conj(conj_mul[k][y])
+        for (int q = 0; q < CW; q++) {
+            re[q] *= unscale;
+            im[q] *= unscale;
+        }
+        if (row < nrows) {
+            float2 *dst = Y + (size_t)(out_index ? out_index[b] : b) * P * P + y;
+            if (conj_mul) {  // element (k, y) of the 2-D result times conj(conj_mul[k][y])
 #pragma unroll
-                    for (int q = 0; q < 32; q++) {
-                        const float2 c = __ldg(conj_mul + (size_t)(k0 + q) * P + y);
-                        dst[(size_t)(k0 + q) * P] =
-                            make_float2(fmaf(c.x, re[q], c.y * im[q]), fmaf(c.x, im[q], -c.y * re[q]));
-                    }
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 32; q++) dst[(size_t)(k0 + q) * P] = make_float2(re[q], im[q]);
+                for (int q = 0; q < CW; q++) {
+                    const float2 c = __ldg(conj_mul + (size_t)(k0 + q) * P + y);
+                    dst[(size_t)(k0 + q) * P] = make_float2(fmaf(c.x, re[q], c.y * im[q]), fmaf(c.x, im[q], -c.y * re[q]));
                 }
+            } else {
+#pragma unroll
+                for (int q = 0; q < CW; q++) dst[(size_t)(k0 + q) * P] = make_float2(re[q], im[q]);
             }
         }
     }
@@ -423,6 +332,7 @@ bool tc_dft_supported(int P) { return P == 64 || P == 128; }
 
 cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out)
 {
+    if (bf16) return tc_ws_images(P, sign, out);  // the warp-specialised kernel's layout
     if (P == 64) out = bf16 ? build_images<64, true>(sign) : build_images<64, false>(sign);
     else if (P == 128) out = bf16 ? build_images<128, true>(sign) : build_images<128, false>(sign);
     else return cudaErrorInvalidValue;
@@ -432,6 +342,7 @@ cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out)
 cudaError_t tc_dft_rows(int P, bool bf16, const float2 *X, float2 *Y, const void *img, int nrows,
                         const int *out_index, const float2 *conj_mul, int *err, cudaStream_t s)
 {
+    if (bf16) return tc_ws_rows(P, X, Y, img, nrows, out_index, conj_mul, err, s);
     if (P == 64)
         return bf16 ? run_rows<64, true>(X, Y, img, nrows, out_index, conj_mul, err, s)
                     : run_rows<64, false>(X, Y, img, nrows, out_index, conj_mul, err, s);

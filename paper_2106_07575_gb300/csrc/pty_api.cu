@@ -1260,6 +1260,12 @@ int ctx_info(const pty_ctx *c, int *H, int *W, int *P, int *K, int *V, int *dev)
 
 #include "pty_selftest.h"
 
+extern "C" int pty_selftest_tc_wait_limit(int64_t polls)
+{
+    pty::tc_set_wait_limit((long long)polls);
+    return PTY_OK;
+}
+
 extern "C" int pty_selftest_log1p(const float *t, float *out, int32_t n)
 {
     pty_ctx *c = nullptr;

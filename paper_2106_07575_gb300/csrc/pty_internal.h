@@ -118,6 +118,10 @@ cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, double
 // applications give the unnormalised 2-D DFT.  img: the split DFT matrix images built by
 // tc_dft_images (device copy).  err |= 1 on a timed-out device wait.
 bool tc_dft_supported(int P);
+// Polls every pipeline wait of the tensor-core kernels allows before it gives up (the kernel
+// then records err |= 1); tc_set_wait_limit(polls <= 0) restores the default.
+long long tc_wait_limit();
+void tc_set_wait_limit(long long polls);
 cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out);
 // conj_mul (nullable): the stored element (k, y) of block b is multiplied by conj(conj_mul[k*P + y]).
 cudaError_t tc_dft_rows(int P, bool bf16, const float2 *X, float2 *Y, const void *img, int nrows,

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
                                                                const uint8_t *__restrict__ Bimg, int nrows,
                                                                const int *__restrict__ out_index,
                                                                const float2 *__restrict__ conj_mul,
-                                                               int *__restrict__ err)
+                                                               int *__restrict__ err, long long spin_limit)
 {
     using G = TcGeo<P>;
     extern __shared__ __align__(1024) uint8_t tsm[];
@@ -176,13 +177,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
     if (tid == 0) {
         const uint32_t idesc = umma_idesc<G::N, BF16>();
         bool ok = true;
+        int issued = 0, consumed = 0;  // chunks whose copies were issued / whose MMAs were issued
         for (int c = 0; c < kTcStages && c < G::NCHUNK; c++) {
             mbar_expect_tx(full + c, G::B_BYTES);
             bulk_g2s(Bst + c * G::B_BYTES, Bimg + (size_t)c * G::B_BYTES, G::B_BYTES, full + c);
+            issued = c + 1;
         }
         for (int c = 0; c < G::NCHUNK && ok; c++) {
             const int s = c % kTcStages;
-            if (!mbar_wait(full + s, (c / kTcStages) & 1)) {
+            if (!mbar_wait(full + s, (c / kTcStages) & 1, spin_limit)) {
                 ok = false;
                 break;
             }
@@ -196,20 +199,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dft_rows_tc(const float2 *__r
                 umma_f16(tmem, ad, bd, idesc, (c > 0 || k > 0) ? 1u : 0u);
             }
             umma_commit(empty + s);
+            consumed = c + 1;
             // refill the stage of the previous chunk once its MMAs have finished reading it
             const int pc = c - 1;
             if (pc >= 0 && pc + kTcStages < G::NCHUNK) {
                 const int ps = pc % kTcStages;
-                if (!mbar_wait(empty + ps, (pc / kTcStages) & 1)) {
+                if (!mbar_wait(empty + ps, (pc / kTcStages) & 1, spin_limit)) {
                     ok = false;
                     break;
                 }
                 mbar_expect_tx(full + ps, G::B_BYTES);
                 bulk_g2s(Bst + ps * G::B_BYTES, Bimg + (size_t)(pc + kTcStages) * G::B_BYTES, G::B_BYTES, full + ps);
+                issued = pc + kTcStages + 1;
             }
         }
         umma_commit(done);  // arrives once every issued MMA has completed
-        if (!ok) fail_s = 1;
+        if (!ok) {
+            fail_s = 1;
+            // every copy issued but not consumed lands before the CTA can exit
+            for (int c = consumed; c < issued; c++) mbar_wait(full + c % kTcStages, (c / kTcStages) & 1);
+        }
     }
     __syncthreads();
     const bool ok = mbar_wait(done, 0) && !fail_s;
@@ -322,13 +331,19 @@ cudaError_t run_rows(const float2 *X, float2 *Y, const void *img, int nrows, con
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::SMEM);
     if (e != cudaSuccess) return e;
     const int nb = (nrows + kTcRows - 1) / kTcRows;
-    k<<<nb, kTcThreads, G::SMEM, s>>>(X, Y, (const uint8_t *)img, nrows, out_index, conj_mul, err);
+    k<<<nb, kTcThreads, G::SMEM, s>>>(X, Y, (const uint8_t *)img, nrows, out_index, conj_mul, err, tc_wait_limit());
     return cudaGetLastError();
 }
 
 }  // namespace
 
 bool tc_dft_supported(int P) { return P == 64 || P == 128; }
+
+namespace {
+std::atomic<long long> g_tc_wait_limit{tcx::kSpinLimit};
+}
+long long tc_wait_limit() { return g_tc_wait_limit.load(); }
+void tc_set_wait_limit(long long polls) { g_tc_wait_limit.store(polls > 0 ? polls : tcx::kSpinLimit); }
 
 cudaError_t tc_dft_images(int P, bool bf16, int sign, std::vector<uint8_t> &out)
 {

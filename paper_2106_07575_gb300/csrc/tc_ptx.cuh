@@ -43,10 +43,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait for the given phase parity; returns false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = kSpinLimit)
 {
     const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kSpinLimit; it++) {
+    for (long long it = 0; it < limit; it++) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -19,9 +19,10 @@
 //   10 - 13 epilogue: tcgen05.ld of the finished buffer (warp w reads lane quarter w % 4),
 //           transposed store, optional conjugate product; the buffer is then released.
 // So the split of chunk c + 1, the MMAs of chunk c and the epilogue of the previous tile
-// overlap.  Every wait is bounded and also gives up when another role has failed; after a
-// failure the loader waits (bounded) for the copies it issued and the MMA thread for its
-// MMAs before the TMEM is freed; err |= 1 records the failure.
+// overlap.  Every pipeline wait is bounded (tc_wait_limit polls) and also gives up when
+// another role has failed; after a failure the loader waits for the copies it issued and the
+// MMA thread for its MMAs (bounded by the default limit, whatever the pipeline limit) before
+// the TMEM is freed; err |= 1 records the failure.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -74,10 +75,10 @@ __device__ __forceinline__ uint32_t idesc_bf16()
 }
 
 // Bounded wait that also gives up when another role has recorded a failure.
-__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *fail)
+__device__ __forceinline__ bool ws_wait(uint64_t *bar, uint32_t parity, volatile int *fail, long long limit)
 {
     const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kSpinLimit; it++) {
+    for (long long it = 0; it < limit; it++) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -99,7 +100,8 @@ __device__ __forceinline__ void ws_fail(volatile int *fail, int *err)
 template <int P>
 __global__ void __launch_bounds__(kWsThreads, 1)
     k_dft_rows_ws(const float2 *__restrict__ X, float2 *__restrict__ Y, const uint8_t *__restrict__ Bimg, int nrows,
-                  const int *__restrict__ out_index, const float2 *__restrict__ conj_mul, int *__restrict__ err)
+                  const int *__restrict__ out_index, const float2 *__restrict__ conj_mul, int *__restrict__ err,
+                  long long spin_limit)
 {
     using G = WsGeo<P>;
     extern __shared__ __align__(1024) uint8_t sm[];
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                 for (int kc = 0; kc < G::NKC && ok; kc++)
                     for (int part = 0; part < 2 && ok; part++) {
                         const int sb = ub % kWsSB;
-                        if (!(ok = ws_wait(bempty + sb, ((ub / kWsSB) & 1) ^ 1, fail))) break;
+                        if (!(ok = ws_wait(bempty + sb, ((ub / kWsSB) & 1) ^ 1, fail, spin_limit))) break;
                         mbar_expect_tx(bfull + sb, (uint32_t)G::BIMG);
                         bulk_g2s(bs + (size_t)sb * G::BIMG, Bimg + (size_t)(2 * kc + part) * G::BIMG, G::BIMG,
                                  bfull + sb);
@@ -174,16 +176,16 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, lt++) {
                 const int tb = lt & 1;
-                if (!(ok = ws_wait(tempty + tb, ((lt >> 1) & 1) ^ 1, fail))) break;
+                if (!(ok = ws_wait(tempty + tb, ((lt >> 1) & 1) ^ 1, fail, spin_limit))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(tb * G::N);
                 for (int kc = 0; kc < G::NKC && ok; kc++) {
                     const int sa = ua % kWsSA;
-                    if (!(ok = ws_wait(afull + sa, (ua / kWsSA) & 1, fail))) break;
+                    if (!(ok = ws_wait(afull + sa, (ua / kWsSA) & 1, fail, spin_limit))) break;
                     const uint32_t ah = smem_u32(as + (size_t)sa * kAStage), al = ah + kAPart;
                     for (int part = 0; part < 2 && ok; part++) {
                         const int sb = ub % kWsSB;
-                        if (!(ok = ws_wait(bfull + sb, (ub / kWsSB) & 1, fail))) break;
+                        if (!(ok = ws_wait(bfull + sb, (ub / kWsSB) & 1, fail, spin_limit))) break;
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t b = smem_u32(bs + (size_t)sb * G::BIMG);
 #pragma unroll
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     }
                 }
                 const int sa = ua % kWsSA;
-                if (lane == 0) ok = ws_wait(aempty + sa, ((ua / kWsSA) & 1) ^ 1, fail);
+                if (lane == 0) ok = ws_wait(aempty + sa, ((ua / kWsSA) & 1) ^ 1, fail, spin_limit);
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
                 if (!ok) break;
                 uint8_t *ahi = as + (size_t)sa * kAStage, *alo = ahi + kAPart;
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, lt++) {
             const int tb = lt & 1;
-            if (lane == 0) ok = ws_wait(tfull + tb, (lt >> 1) & 1, fail);
+            if (lane == 0) ok = ws_wait(tfull + tb, (lt >> 1) & 1, fail, spin_limit);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -372,7 +374,7 @@ cudaError_t run_ws(const float2 *X, float2 *Y, const void *img, int nrows, const
     const int ntiles = (nrows + kWsRows - 1) / kWsRows;
     const int nb = ntiles < nsm ? ntiles : nsm;
     if (nb < 1) return cudaSuccess;
-    k<<<nb, kWsThreads, G::SMEM, s>>>(X, Y, (const uint8_t *)img, nrows, out_index, conj_mul, err);
+    k<<<nb, kWsThreads, G::SMEM, s>>>(X, Y, (const uint8_t *)img, nrows, out_index, conj_mul, err, tc_wait_limit());
     return cudaGetLastError();
 }
 

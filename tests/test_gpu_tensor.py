@@ -67,3 +67,28 @@ def test_tensor_core_gradient_and_cg(orc, dft):
     print(f"tensor-core {name} CG: max objective rel err {relF.max():.2e}, trials {list(rep['halvings'])} vs "
           f"{list(want['halvings'])}")
     assert st == pty.PTY_OK and np.all(relF <= 1e-4)
+
+
+def test_tensor_core_wait_timeout_is_reported_and_recoverable():
+    """Failure detection without a GPU fault: with the pipeline waits of the tensor-core
+    kernels limited to one poll they give up; the solve reports PTY_ERR_TIMEOUT, and with the
+    default limit restored a new context solves normally (the device is still usable)."""
+    p = synth.small_problem(seed=0)
+    o = pty.default_opts()
+    o.dft = 1
+    ctx = pty.Context(dev(p.probe), dev(p.pos), dev(p.d), p.H, p.W, o)
+    x = dev(p.psi0())
+    pty.pty_selftest_tc_wait_limit(1)
+    try:
+        with pytest.raises(pty.PtyError) as exc:
+            ctx.cg_solve(x, 2)
+        assert exc.value.status == pty.PTY_ERR_TIMEOUT
+    finally:
+        pty.pty_selftest_tc_wait_limit(0)
+    ctx.close()
+    ctx2 = pty.Context(dev(p.probe), dev(p.pos), dev(p.d), p.H, p.W, o)
+    st, rep = ctx2.cg_solve(dev(p.psi0()), 2)
+    ref = pty.Context(dev(p.probe), dev(p.pos), dev(p.d), p.H, p.W, o)
+    st2, rep2 = ref.cg_solve(dev(p.psi0()), 2)
+    assert st == pty.PTY_OK and list(rep["halvings"]) == list(rep2["halvings"])
+    assert np.array_equal(rep["F"], rep2["F"])

@@ -59,6 +59,42 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 
+# DRAM traffic per launch of the LS pattern pass, from an ncu capture summarised in
+# profiles/: valid only while the kernel's sources are the ones hashed there
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_ls_fft_mlcg_1024_p128.md")
+TRAFFIC_SOURCES = ["fft_tile.cuh", "pattern_kernels.cuh", "pattern_p128.cu", "pty_internal.h", "reduce.cuh",
+                   "mathx.cuh"]
+
+
+def ls_pass_source_hash():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2106_07575_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ls_pass_traffic(P, plan_ls):
+    """(bytes per launch or None, note) for the chosen LS configuration (R, NT)."""
+    import re
+
+    try:
+        with open(TRAFFIC_PROFILE) as fh:
+            text = fh.read()
+    except OSError:
+        return None, "no profile summary"
+    cur = ls_pass_source_hash()
+    for m in re.finditer(r"^traffic: k_ls_fft<(\d+),(\d+),(\d+)> (\d+) bytes/launch, sources ([0-9a-f]+)$", text,
+                         re.M):
+        if (int(m.group(1)), int(m.group(2)), int(m.group(3))) != (P, plan_ls[0], plan_ls[1]):
+            continue
+        if m.group(5) != cur:
+            return None, f"kernel sources changed since the capture ({m.group(5)} -> {cur})"
+        return int(m.group(4)), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {os.path.basename(TRAFFIC_PROFILE)}"
+    return None, f"no capture of k_ls_fft<{P},{plan_ls[0]},{plan_ls[1]}>"
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -395,8 +431,9 @@ def main():
     grad_ms = stage_ms[0] / max(stage_n[0], 1)
     peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = ls_flops / (ls_ms * 1e-3) / 1e12
+    traffic, traffic_note = ls_pass_traffic(P, plan["ls"])
     roof = {"bound": "alu", "kernel": "k_ls_fft", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": None,
+            "frac": achieved / peak_tflops, "traffic": traffic, "traffic_note": traffic_note,
             "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
             "launch_ms": ls_ms, "launches_timed": int(stage_n[2]),
             "timing": "CUDA events around each k_ls_fft launch on its stream, stage-timed pass of the same workload",

@@ -5,10 +5,11 @@
 //   sum_entries [ q - d log(1 + q / (|u|^2 + eps)) ] + (pixels without counts: Parseval)
 //   q = gamma (2 Re conj(u) v + gamma |v|^2) = |u + gamma v|^2 - |u|^2.
 // One thread block per (pattern, chunk) of the entry layout sums the window's candidates in
-// FP32 per thread and FP64 across the block: the partials have the layout of the LS pass
-// (rows 2.. of [L+2][K * cs]), so the decision kernel reads both alike.  The kernel needs
-// no shared-memory tile and runs at full occupancy, which hides the latency of the
-// logarithm chain that bounded the fused pattern pass.
+// FP32 per thread and in float-float across the block (an FP64 butterfly over 16 values
+// kept the FP64 pipe 72 % busy and set the kernel's time): the partials have the layout of
+// the LS pass (rows 2.. of [L+2][K * cs]), so the decision kernel reads both alike.  The
+// kernel needs no shared-memory tile and runs at full occupancy, which hides the latency
+// of the logarithm chain.
 #include "mathx.cuh"
 #include "pty_internal.h"
 #include "reduce.cuh"
@@ -24,13 +25,13 @@ constexpr int kNT = 256;
 constexpr int kBlocks = 152 * 8;
 
 template <int L>
-__global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V, double *__restrict__ part,
+__global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V, float2 *__restrict__ part,
                                                     const DevState *__restrict__ sts)
 {
     // one view: a window with nothing to evaluate ends the whole launch at once
     if (V == 1 && (sts->stalled || sts->decided || sts->Lsel != L)) return;
-    __shared__ double red[(kNT / 32) * L];
-    __shared__ double tot[L];
+    __shared__ float2 red[(kNT / 32) * L];
+    __shared__ float2 tot[L];
     const int nunits = a.K * cs;
     const size_t KC = (size_t)nunits;
     for (int blk = blockIdx.x; blk < nunits; blk += gridDim.x) {
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V
         const int Leff = st->Leff;
         float gam[L];
 #pragma unroll
-        for (int l = 0; l < L; l++) gam[l] = l < Leff ? (float)st->cand[l] : 0.0f;
+        for (int l = 0; l < L; l++) gam[l] = l < Leff ? st->cand_f[l] : 0.0f;
         float acc[L];
 #pragma unroll
         for (int l = 0; l < L; l++) acc[l] = 0.0f;
@@ -62,17 +63,14 @@ __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V
                 acc[l] = fmaf(-dv, log1p_fast(t), acc[l] + q);
             }
         }
-        double vals[L];
-#pragma unroll
-        for (int l = 0; l < L; l++) vals[l] = acc[l];
-        block_sum<kNT, L>(vals, red, tot);  // ends with a barrier: red and tot are free again
+        block_sum_ff<kNT, L>(acc, red, tot);  // ends with a barrier: red and tot are free again
         for (int l = threadIdx.x; l < L; l += kNT) part[(size_t)(2 + l) * KC + blk] = tot[l];
     }
 }
 
 }  // namespace
 
-cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, double *part, const DevState *st,
+cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, float2 *part, const DevState *st,
                               cudaStream_t s)
 {
     const int nb = a.K * cs < kBlocks ? a.K * cs : kBlocks;

@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(NT) k_na_grad(NaArgs a)
     if (*na_flag(a)) return;
     using pty::Tile;
     extern __shared__ __align__(16) float2 sm[];
-    __shared__ double red[NT / 32];
-    __shared__ double tot[1];
+    __shared__ float2 red[NT / 32];
+    __shared__ float2 tot[1];
     float2 *tile = sm, *tw = sm + Tile<P>::ELEMS;
     const int k = blockIdx.x;
     const int2 rc = a.pos[k];
@@ -133,9 +133,9 @@ __global__ void __launch_bounds__(NT) k_na_grad(NaArgs a)
             tile[qy * Tile<P>::LD + qx] = u;
         }
     }
-    double v[1] = {(double)f};
-    pty::block_sum<NT, 1>(v, red, tot);
-    if (threadIdx.x == 0) na_fpart(a)[k] = tot[0];
+    float v[1] = {f};
+    pty::block_sum_ff<NT, 1>(v, red, tot);
+    if (threadIdx.x == 0) na_fpart(a)[k] = pty::ff_value(tot[0]);
     pty::fft2_inv<P, NT>(tile, tw);
     float2 *wk = na_w(a) + (size_t)k * P * P;
     for (int e = threadIdx.x; e < P * P; e += NT) {

@@ -26,15 +26,15 @@ constexpr int kSumNT = 256;
 template <int P>
 __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan plan, const float2 *__restrict__ w,
                                                    float2 *__restrict__ out, int dy, const float2 *__restrict__ ep,
-                                                   const float2 *__restrict__ gp, double *__restrict__ part,
+                                                   const float2 *__restrict__ gp, float2 *__restrict__ part,
                                                    const DevState *__restrict__ st, const float2 *__restrict__ psi,
                                                    const float *__restrict__ D, float p2)
 {
     const int b = blockIdx.x;
     if (st && st[plan.tile_view[b]].stalled) return;
     const bool lin = st && st[plan.tile_view[b]].lin;
-    __shared__ double red[(kScNT / 32) * 3];
-    __shared__ double tot[3];
+    __shared__ float2 red[(kScNT / 32) * 3];
+    __shared__ float2 tot[3];
     const int ty = b / plan.ntile_x, tx = b % plan.ntile_x;
     const int x = tx * kScTX + (threadIdx.x % kScTX);
     const int y0 = ty * kScTY + threadIdx.x / kScTX;
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
         }
     }
     if (dy) {
-        double v[3] = {(double)gg, (double)den, (double)pd};
-        block_sum<kScNT, 3>(v, red, tot);
+        float v[3] = {gg, den, pd};
+        block_sum_ff<kScNT, 3>(v, red, tot);
         if (threadIdx.x < 3) part[3 * b + threadIdx.x] = tot[threadIdx.x];  // [ntiles][3]
     }
 }
@@ -127,17 +127,17 @@ __global__ void __launch_bounds__(kScNT) k_illum(PatternArgs a, ScatterPlan plan
 __global__ void __launch_bounds__(kScNT) k_eta(int H, int W, ScatterPlan plan, const float2 *__restrict__ psi,
                                                const float2 *__restrict__ g, const float2 *__restrict__ ep,
                                                const float *__restrict__ D, float2 *__restrict__ eta,
-                                               double *__restrict__ part, const DevState *__restrict__ sts)
+                                               float2 *__restrict__ part, const DevState *__restrict__ sts)
 {
     const int b = blockIdx.x;
     const DevState *st = sts + plan.tile_view[b];
     if (st->stalled) return;
-    __shared__ double red[(kScNT / 32) * 2];
-    __shared__ double tot[2];
+    __shared__ float2 red[(kScNT / 32) * 2];
+    __shared__ float2 tot[2];
     const int ty = b / plan.ntile_x, tx = b % plan.ntile_x;
     const int x = tx * kScTX + (threadIdx.x % kScTX);
     const int y0 = ty * kScTY + threadIdx.x / kScTX;
-    const float alpha = (float)st->alpha;
+    const float alpha = st->alpha_f;
     float s0 = 0.f, s1 = 0.f;
     if (x < W) {
 #pragma unroll
@@ -154,26 +154,26 @@ __global__ void __launch_bounds__(kScNT) k_eta(int H, int W, ScatterPlan plan, c
             }
         }
     }
-    double v[2] = {(double)s0, (double)s1};
-    block_sum<kScNT, 2>(v, red, tot);
+    float v[2] = {s0, s1};
+    block_sum_ff<kScNT, 2>(v, red, tot);
     if (threadIdx.x < 2) part[2 * b + threadIdx.x] = tot[threadIdx.x];
 }
 
 // Each thread sums a fixed strided subset, then the block combines: fixed order.
-__device__ __forceinline__ double strided_sum(const double *v, int n, int stride, int off)
+__device__ __forceinline__ float2 strided_sum(const float2 *v, int n, int stride, int off)
 {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < n; i += kSumNT) s += v[(size_t)i * stride + off];
+    float2 s = make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < n; i += kSumNT) s = ff_add(s, v[(size_t)i * stride + off]);
     return s;
 }
 
-__global__ void __launch_bounds__(kSumNT) k_sum(const double *__restrict__ v, int n, double *__restrict__ out)
+__global__ void __launch_bounds__(kSumNT) k_sum(const float2 *__restrict__ v, int n, double *__restrict__ out)
 {
-    __shared__ double red[kSumNT / 32];
-    __shared__ double tot[1];
-    double x[1] = {strided_sum(v, n, 1, 0)};
-    block_sum<kSumNT, 1>(x, red, tot);
-    if (threadIdx.x == 0) *out = tot[0];
+    __shared__ float2 red[kSumNT / 32];
+    __shared__ float2 tot[1];
+    float2 x[1] = {strided_sum(v, n, 1, 0)};
+    block_sum_ff<kSumNT, 1>(x, red, tot);
+    if (threadIdx.x == 0) *out = ff_value(tot[0]);
 }
 
 __device__ __forceinline__ void open_window(DevState *st, double gamma0, double tau)
@@ -184,26 +184,27 @@ __device__ __forceinline__ void open_window(DevState *st, double gamma0, double 
     for (int l = 0; l < st->Leff; l++) {
         g *= tau;
         st->cand[l] = g;
+        st->cand_f[l] = (float)g;
     }
 }
 
-__global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict__ fpart, int cs,
-                                                        const double *__restrict__ part, double p2, ViewMap vm,
+__global__ void __launch_bounds__(kSumNT) k_dy_finalize(const float2 *__restrict__ fpart, int cs,
+                                                        const float2 *__restrict__ part, double p2, ViewMap vm,
                                                         DevState *sts, DevHist h, LsArgs ls)
 {
     const int v = blockIdx.x;
     DevState *st = sts + v;
     if (st->stalled) return;
-    __shared__ double red[(kSumNT / 32) * 4];
-    __shared__ double tot[4];
+    __shared__ float2 red[(kSumNT / 32) * 4];
+    __shared__ float2 tot[4];
     const int f0 = vm.pat_off[v] * cs, f1 = vm.pat_off[v + 1] * cs;
     const int t0 = vm.tile_off[v], t1 = vm.tile_off[v + 1];
-    double v4[4] = {strided_sum(fpart + f0, f1 - f0, 1, 0), strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 0),
+    float2 v4[4] = {strided_sum(fpart + f0, f1 - f0, 1, 0), strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 0),
                     strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 1), strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 2)};
-    block_sum<kSumNT, 4>(v4, red, tot);
+    block_sum_ff<kSumNT, 4>(v4, red, tot);
     if (threadIdx.x == 0) {
         // linear form: sum |u|^2 over all pixels = P^2 sum D |psi|^2 (0 from the tiles otherwise)
-        const double Fm = tot[0] + p2 * tot[3], gg = tot[1], den = tot[2];
+        const double Fm = ff_value(tot[0]) + p2 * ff_value(tot[3]), gg = ff_value(tot[1]), den = ff_value(tot[2]);
         double alpha = 0.0;
         if (den > 0.0 && isfinite(den) && isfinite(gg)) {
             alpha = gg / den;
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
             st->restarts += 1;
         }
         st->alpha = alpha;
+        st->alpha_f = (float)alpha;
         st->Fm = Fm;
         st->k0 = 0;
         st->decided = 0;
@@ -235,24 +237,24 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const double *__restrict
 // The open window of view v has st->Leff <= 32 candidates.
 // Sum of n doubles v[0], v[stride], ... by one warp in a fixed order: each lane keeps four
 // accumulators over a fixed strided subset, then a butterfly across the warp.
-__device__ __forceinline__ double warp_strided_sum(const double *__restrict__ v, int n, int lane)
+__device__ __forceinline__ float2 warp_strided_sum(const float2 *__restrict__ v, int n, int lane)
 {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
     int i = lane;
     for (; i + 96 < n; i += 128) {
-        s0 += v[i];
-        s1 += v[i + 32];
-        s2 += v[i + 64];
-        s3 += v[i + 96];
+        s0 = ff_add(s0, v[i]);
+        s1 = ff_add(s1, v[i + 32]);
+        s2 = ff_add(s2, v[i + 64]);
+        s3 = ff_add(s3, v[i + 96]);
     }
-    for (; i < n; i += 32) s0 += v[i];
-    return warp_sum((s0 + s1) + (s2 + s3));
+    for (; i < n; i += 32) s0 = ff_add(s0, v[i]);
+    return warp_sum_ff(ff_add(ff_add(s0, s1), ff_add(s2, s3)));
 }
 
 constexpr int kDecNT = 1024;
 
-__global__ void __launch_bounds__(kDecNT) k_ls_decide(const double *__restrict__ part, int kc, int cs, ViewMap vm,
-                                                      const double *__restrict__ vpart, double vscale, DevState *sts,
+__global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__ part, int kc, int cs, ViewMap vm,
+                                                      const float2 *__restrict__ vpart, double vscale, DevState *sts,
                                                       DevHist h, LsArgs ls)
 {
     const int v = blockIdx.x;
@@ -265,16 +267,16 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const double *__restrict__
     const int Leff = st->Leff;
     const int p0 = vm.pat_off[v] * cs, p1 = vm.pat_off[v + 1] * cs;
     for (int j = warp; j < Leff + 2; j += kDecNT / 32) {
-        const double s = warp_strided_sum(part + (size_t)j * kc + p0, p1 - p0, lane);
-        if (lane == 0) tot[j] = s;
+        const float2 s = warp_strided_sum(part + (size_t)j * kc + p0, p1 - p0, lane);
+        if (lane == 0) tot[j] = ff_value(s);
     }
     // the view's object-tile sums of the all-pixel totals of rows 0 and 1 (Parseval)
     if (vpart && warp >= 30) {
         const int j = warp - 30, t0 = vm.tile_off[v], n = vm.tile_off[v + 1] - t0;
-        double t0s = 0.0;
-        for (int b = lane; b < n; b += 32) t0s += vpart[2 * (t0 + b) + j];
-        t0s = warp_sum(t0s);
-        if (lane == 0) vtot[j] = vscale * t0s;
+        float2 t0s = make_float2(0.f, 0.f);
+        for (int b = lane; b < n; b += 32) t0s = ff_add(t0s, vpart[2 * (t0 + b) + j]);
+        t0s = warp_sum_ff(t0s);
+        if (lane == 0) vtot[j] = vscale * ff_value(t0s);
     }
     __syncthreads();
     if (vpart && threadIdx.x < 2) tot[threadIdx.x] += vtot[threadIdx.x];
@@ -288,6 +290,7 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const double *__restrict__
             const double dF = gam * (2.0 * tot[0] + gam * tot[1]) + tot[2 + l];
             if (dF <= gam * ls.t) {
                 st->gamma = gam;
+                st->gamma_f = (float)gam;
                 st->Fnext = st->Fm + dF;
                 st->decided = 1;
                 st->last_halvings = k0 + l + 1;
@@ -323,7 +326,7 @@ __global__ void k_update(int H, int W, ViewMap vm, float2 *__restrict__ psi, con
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const DevState *st = sts + vm.row_view[i / W];
         if (st->stalled || !st->decided) continue;
-        const float gam = (float)st->gamma, alpha = (float)st->alpha;
+        const float gam = st->gamma_f, alpha = st->alpha_f;
         const float2 gv = g[i], ev = ep[i];
         const float2 eta = make_float2(fmaf(alpha, ev.x, -gv.x), fmaf(alpha, ev.y, -gv.y));
         float2 p = psi[i];
@@ -418,7 +421,7 @@ __global__ void k_begin_solve(DevState *sts, int V)
 
 // ------------------------------------------------------------------------------------
 cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *w, float2 *out,
-                           int dy, const float2 *eta_prev, const float2 *g_prev, double *part, const DevState *st,
+                           int dy, const float2 *eta_prev, const float2 *g_prev, float2 *part, const DevState *st,
                            cudaStream_t s, const float2 *psi, const float *D)
 {
     const float p2 = (float)P * (float)P;
@@ -445,26 +448,26 @@ cudaError_t launch_illumination(int P, const PatternArgs &a, const ScatterPlan &
 }
 
 cudaError_t launch_eta(int H, int W, const ScatterPlan &plan, const float2 *psi, const float2 *g, const float2 *ep,
-                       const float *D, float2 *eta, double *part, const DevState *st, cudaStream_t s)
+                       const float *D, float2 *eta, float2 *part, const DevState *st, cudaStream_t s)
 {
     k_eta<<<plan.ntile_x * plan.ntile_y, kScNT, 0, s>>>(H, W, plan, psi, g, ep, D, eta, part, st);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s)
+cudaError_t launch_sum(const float2 *v, int n, double *out, cudaStream_t s)
 {
     k_sum<<<1, kSumNT, 0, s>>>(v, n, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, double p2, const ViewMap &vm,
+cudaError_t launch_dy_finalize(const float2 *fpart, int cs, const float2 *part, double p2, const ViewMap &vm,
                                DevState *st, DevHist h, const LsArgs &ls, cudaStream_t s)
 {
     k_dy_finalize<<<vm.V, kSumNT, 0, s>>>(fpart, cs, part, p2, vm, st, h, ls);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const double *vpart, double vscale,
+cudaError_t launch_ls_decide(const float2 *part, int kc, int cs, const ViewMap &vm, const float2 *vpart, double vscale,
                              const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
 {
     k_ls_decide<<<vm.V, kDecNT, 0, s>>>(part, kc, cs, vm, vpart, vscale, st, h, ls);

@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(NT) k_adjoint_fft(PatternArgs a, const float2 
 // One pattern of the GRAD pass (full form).
 template <int P, int R, int NT>
 __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 *__restrict__ psi,
-                                             float2 *__restrict__ w, double *__restrict__ fpart, float2 *buf,
-                                             const float2 *tw, double *red, double *tot, int i, int c)
+                                             float2 *__restrict__ w, float2 *__restrict__ fpart, float2 *buf,
+                                             const float2 *tw, float2 *red, float2 *tot, int i, int c)
 {
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
@@ -161,8 +161,8 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
         u.y *= sc;
         *pu = u;
     }
-    double v[1] = {(double)f};
-    block_sum<NT, 1>(v, red, tot);  // its barriers also order the residual writes before F^H
+    float v[1] = {f};
+    block_sum_ff<NT, 1>(v, red, tot);  // its barriers also order the residual writes before F^H
     if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
     fft2_inv<P, R, NT>(buf, tw);
     float2 *wi = w + (size_t)i * P * P;
@@ -176,13 +176,13 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
 // the patterns.  Clusters run one pattern each.
 template <int P, int R, int NT>
 __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__restrict__ psi,
-                                             float2 *__restrict__ w, double *__restrict__ fpart,
+                                             float2 *__restrict__ w, float2 *__restrict__ fpart,
                                              const DevState *__restrict__ st)
 {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int CS = Slab<P, R>::CS;
-    __shared__ double red[NT / 32];
-    __shared__ double tot[1];
+    __shared__ float2 red[NT / 32];
+    __shared__ float2 tot[1];
     float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
     const int c = blockIdx.x % CS;
     if (st && a.V == 1 && (st->stalled || st->lin)) return;  // one view: decided for all patterns
@@ -223,8 +223,8 @@ __global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__rest
 // scatter-add too.  Runs only for views whose st->lin is set.
 template <int P, int R, int NT>
 __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *__restrict__ w,
-                                                 double *__restrict__ fpart, float2 *buf, const float2 *tw,
-                                                 double *red, double *tot, float gam, int i, int c)
+                                                 float2 *__restrict__ fpart, float2 *buf, const float2 *tw,
+                                                 float2 *red, float2 *tot, float gam, int i, int c)
 {
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     // the column slab (permuted spectrum order) starts at zero
@@ -245,8 +245,8 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
         const float sc = -dv / den;
         buf[(s / P) * LDB + (s % P - c * R)] = make_float2(u.x * sc, u.y * sc);
     }
-    double vv[1] = {(double)f};
-    block_sum<NT, 1>(vv, red, tot);  // its barriers also order the writes before F^H
+    float vv[1] = {f};
+    block_sum_ff<NT, 1>(vv, red, tot);  // its barriers also order the writes before F^H
     if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
     fft2_inv<P, R, NT>(buf, tw);
     float2 *wi = w + (size_t)i * P * P;
@@ -257,13 +257,13 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
 }
 
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_grad_lin(PatternArgs a, float2 *__restrict__ w, double *__restrict__ fpart,
+__global__ void __launch_bounds__(NT) k_grad_lin(PatternArgs a, float2 *__restrict__ w, float2 *__restrict__ fpart,
                                                  const DevState *__restrict__ sts)
 {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int CS = Slab<P, R>::CS;
-    __shared__ double red[NT / 32];
-    __shared__ double tot[1];
+    __shared__ float2 red[NT / 32];
+    __shared__ float2 tot[1];
     float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
     const int c = blockIdx.x % CS;
     if (a.V == 1 && (sts->stalled || !sts->lin)) return;  // one view: decided for all patterns
@@ -286,8 +286,8 @@ __global__ void __launch_bounds__(NT) k_grad_lin(PatternArgs a, float2 *__restri
 
 template <int P, int R, int NT>
 __device__ __forceinline__ void ls_fft_pattern(const PatternArgs &a, const float2 *__restrict__ eta,
-                                               double *__restrict__ part, float2 *buf, const float2 *tw,
-                                               double *red, double *tot, int i, int c)
+                                               float2 *__restrict__ part, float2 *buf, const float2 *tw,
+                                               float2 *red, float2 *tot, int i, int c)
 {
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
@@ -308,20 +308,20 @@ __device__ __forceinline__ void ls_fft_pattern(const PatternArgs &a, const float
         bp += fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
         cp += fmaf(v.x, v.x, v.y * v.y);
     }
-    double vals[2] = {-(double)bp, -(double)cp};
-    block_sum<NT, 2>(vals, red, tot);
+    float vals[2] = {-bp, -cp};
+    block_sum_ff<NT, 2>(vals, red, tot);
     const int KC = a.K * CS;
     if (threadIdx.x < 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // rows 0, 1
 }
 
 template <int P, int R, int NT>
 __global__ void __launch_bounds__(NT) k_ls_fft(PatternArgs a, const float2 *__restrict__ eta,
-                                               double *__restrict__ part, const DevState *__restrict__ sts)
+                                               float2 *__restrict__ part, const DevState *__restrict__ sts)
 {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int CS = Slab<P, R>::CS;
-    __shared__ double red[(NT / 32) * 2];
-    __shared__ double tot[2];
+    __shared__ float2 red[(NT / 32) * 2];
+    __shared__ float2 tot[2];
     float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
     const int c = blockIdx.x % CS;
     if (a.V == 1 && sts->stalled) return;  // one view: decided for all patterns
@@ -467,18 +467,18 @@ struct PatternOps {
     {
         return launch_pattern(k_adjoint_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, y, w);
     }
-    static cudaError_t grad(const PatternArgs &a, const float2 *psi, float2 *w, double *fpart, const DevState *st,
+    static cudaError_t grad(const PatternArgs &a, const float2 *psi, float2 *w, float2 *fpart, const DevState *st,
                             cudaStream_t s)
     {
         const int g = persistent_blocks(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
         return launch_pattern(k_grad<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, psi, w, fpart, st);
     }
-    static cudaError_t grad_lin(const PatternArgs &a, float2 *w, double *fpart, const DevState *st, cudaStream_t s)
+    static cudaError_t grad_lin(const PatternArgs &a, float2 *w, float2 *fpart, const DevState *st, cudaStream_t s)
     {
         const int g = persistent_blocks(k_grad_lin<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
         return launch_pattern(k_grad_lin<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, w, fpart, st);
     }
-    static cudaError_t ls(const PatternArgs &a, const float2 *eta, double *part, const DevState *st, cudaStream_t s)
+    static cudaError_t ls(const PatternArgs &a, const float2 *eta, float2 *part, const DevState *st, cudaStream_t s)
     {
         const int g = persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
         return launch_pattern(k_ls_fft<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, eta, part, st);

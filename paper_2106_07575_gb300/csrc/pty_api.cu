@@ -73,13 +73,13 @@ struct pty_ctx {
 
     // CG state and scratch (device)
     float2 *w = nullptr;        // [K][P][P] per-pattern adjoint results
-    double *fpart = nullptr;    // [K * CS]
-    double *part_sc = nullptr;  // [ntiles][2]
-    double *part_ls = nullptr;  // [L+2][K * CS]
+    float2 *fpart = nullptr;    // [K * CS] float-float partial sums
+    float2 *part_sc = nullptr;  // [ntiles][3]
+    float2 *part_ls = nullptr;  // [L+2][K * CS]
     float2 *psi = nullptr, *g = nullptr, *g_prev = nullptr, *eta_prev = nullptr;  // atlas
     float2 *eta = nullptr;       // atlas: the current search direction (LS stage)
     float *illum = nullptr;      // atlas: sum over positions of |probe / P|^2 (Parseval totals)
-    double *part_eta = nullptr;  // [ntiles][2] object-tile sums of the LS stage
+    float2 *part_eta = nullptr;  // [ntiles][2] object-tile sums of the LS stage
     unsigned long long *hash = nullptr;  // [V] object hashes (solve entry / exit)
     bool cache_dirty = false;  // the entries' u no longer belong to the last solve's object
     DevState *st = nullptr;     // [V]
@@ -94,7 +94,7 @@ struct pty_ctx {
     uint8_t *tc_img_fwd = nullptr, *tc_img_inv = nullptr;
     int *tc_err = nullptr;
     float2 *tc_x = nullptr, *tc_t = nullptr, *tc_u = nullptr;  // [K][P][P] work buffers
-    double *tc_pars = nullptr;                                  // [2][K] Parseval sums
+    float2 *tc_pars = nullptr;                                  // [2][K] Parseval sums
 
     // stitching of patch estimates (pty_stitch)
     float *st_den = nullptr;   // [HA][WA] sum of |p|^2
@@ -519,7 +519,10 @@ int autotune(pty_ctx *c)
         for (auto &h : hs) {
             h.Leff = 16;
             h.Lsel = 16;
-            for (int l = 0; l < 16; l++) h.cand[l] = std::ldexp(1.0, -(l + 1));
+            for (int l = 0; l < 16; l++) {
+                h.cand[l] = std::ldexp(1.0, -(l + 1));
+                h.cand_f[l] = (float)h.cand[l];
+            }
         }
         CK(cudaMemcpyAsync(c->st, hs.data(), sizeof(DevState) * c->V, cudaMemcpyHostToDevice, c->s));
         cudaEvent_t e0, e1;
@@ -1090,7 +1093,7 @@ int32_t pty_num_views(const pty_ctx *c) { return c ? c->V : 0; }
 // Checkpoint layout: header {magic, H*W of the atlas, views, entries} (4 x int64), g_prev,
 // eta_prev, the per-view DevState, then u and v at the entries (the linear form's cache).
 namespace {
-constexpr long long kStateMagic = 0x5054594347310001LL;
+constexpr long long kStateMagic = 0x5054594347310002LL;
 size_t state_bytes(const pty_ctx *c)
 {
     const size_t HW = (size_t)c->HA * c->WA, E = (size_t)std::max<long long>(c->n_entries, 0);

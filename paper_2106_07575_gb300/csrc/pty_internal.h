@@ -29,6 +29,10 @@ struct DevState {
     double last_gamma;
     unsigned long long psi_hash;  // hash of the view's object when the last solve call ended
     double cand[32];  // candidate steps gamma0 tau^(k0+l+1) of the open line-search window
+    // FP32 roundings of alpha, gamma and cand for the per-pixel kernels (a double-to-float
+    // conversion per thread would run on the slow FP64 pipe)
+    float alpha_f, gamma_f;
+    float cand_f[32];
 };
 
 // Per-call history arrays (device), one block of `cap` iterations per view, indexed by
@@ -73,7 +77,8 @@ struct LsArgs {
 
 // ---- pattern kernels (pattern_kernels.cuh, instantiated per P in pattern_p*.cu) ----
 // One configuration: patterns of P x P held by clusters of P / R CTAs of NT threads.
-// Per-pattern sums are written per CTA: fpart[K * CS], LS partials [L + 2][K * CS].
+// Per-pattern sums are written per CTA: fpart[K * CS], LS partials [L + 2][K * CS].  All
+// partial sums are float-float pairs (float2: hi, lo; reduce.cuh).
 struct PatternImpl {
     int P, R, NT;
     // out[perm[i]] = F(p * patch_i(psi))   (unitary)
@@ -82,17 +87,17 @@ struct PatternImpl {
     cudaError_t (*adjoint)(const PatternArgs &, const float2 *y, float2 *w, cudaStream_t);
     // GRAD pattern pass: w[i] = conj(p) F^H r_i, r the likelihood residual of u = G psi;
     // fpart = objective terms; u kept at the entries.  Exits early when st->stalled.
-    cudaError_t (*grad)(const PatternArgs &, const float2 *psi, float2 *w, double *fpart, const DevState *st,
+    cudaError_t (*grad)(const PatternArgs &, const float2 *psi, float2 *w, float2 *fpart, const DevState *st,
                         cudaStream_t);
     // GRAD pattern pass in the linear form (views with st->lin set; k_grad skips them):
     // u = u + gamma_last v at the entries, fpart = entry terms of the objective,
     // w[i] = conj(p) F^H Delta_i with Delta the residual's difference from u.
-    cudaError_t (*grad_lin)(const PatternArgs &, float2 *w, double *fpart, const DevState *st, cudaStream_t);
+    cudaError_t (*grad_lin)(const PatternArgs &, float2 *w, float2 *fpart, const DevState *st, cudaStream_t);
     // LS pattern pass, once per iteration: v = G eta (eta the object-sized search direction)
     // is kept at the entries (nz_v) and part[0][.], part[1][.] = -(sum Re conj(u) v, sum
     // |v|^2) over the entries (per CTA, rows of length K * CS): the all-pixel totals come from
     // object sums (launch_eta).  Exits when st->stalled.
-    cudaError_t (*ls)(const PatternArgs &, const float2 *eta, double *part, const DevState *st, cudaStream_t);
+    cudaError_t (*ls)(const PatternArgs &, const float2 *eta, float2 *part, const DevState *st, cudaStream_t);
     // Entries of the measured data: counts per (pattern, CTA) chunk, then the compact list.
     cudaError_t (*nz_count)(const float *d, const int *perm, int K, int *cnt, cudaStream_t);
     cudaError_t (*nz_fill)(const float *d, const int *perm, int K, const long long *off, unsigned short *slot,
@@ -109,7 +114,7 @@ cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_
 // part[2 + l][i * cs + c] = sum over the entries of chunk c of pattern i of the objective
 // change at candidate l (gamma0 tau^(k0+l+1)), from u (nz_u), v (nz_v) and d: the window
 // of the L-candidate kernel; returns at once unless st->Lsel == L and a window is open.
-cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, double *part, const DevState *st,
+cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, float2 *part, const DevState *st,
                               cudaStream_t s);
 
 // ---- tensor-core DFT (tc_dft.cu) ----
@@ -134,15 +139,15 @@ cudaError_t tc_ws_rows(int P, const float2 *X, float2 *Y, const void *img, int n
                        const float2 *conj_mul, int *err, cudaStream_t s);
 // CG pieces of the tensor-core form (tc_cg.cu); spectra U, V are [K][P][P] in natural order.
 // Residual of Eq. 3 in place in U at the entries, objective terms fpart[i], u kept in nz_u.
-cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, double *fpart, const DevState *st,
+cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, float2 *fpart, const DevState *st,
                                cudaStream_t s);
 // X[i] = (probe / P) * eta patch with eta = -g + alpha_v eta_prev; pars[0][i], pars[1][i] =
 // P^2 sum conj(p psi / P) (p eta / P) and P^2 sum |p eta / P|^2 (real parts, Parseval sums).
 cudaError_t launch_tc_gather_eta(const PatternArgs &a, int P, const float2 *psi, const float2 *g, const float2 *ep,
-                                 float2 *X, double *pars, const DevState *st, cudaStream_t s);
+                                 float2 *X, float2 *pars, const DevState *st, cudaStream_t s);
 // Candidate sums of one line-search window from V at the entries (layout [L+2][K]).
-cudaError_t launch_tc_ls_entries(const PatternArgs &a, int P, int L, const float2 *V, const double *pars,
-                                 double *part, const DevState *st, cudaStream_t s);
+cudaError_t launch_tc_ls_entries(const PatternArgs &a, int P, int L, const float2 *V, const float2 *pars,
+                                 float2 *part, const DevState *st, cudaStream_t s);
 
 // ---- object kernels (object_kernels.cu) ----
 // Object tile of the scatter-add and of the other object-tile kernels (rows x columns);
@@ -176,27 +181,27 @@ struct ViewMap {
 // linear form ? sum D |psi|^2 : 0) per tile b ([ntiles][3]).
 cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *w,
                            float2 *out, int dy, const float2 *eta_prev, const float2 *g_prev,
-                           double *part, const DevState *st, cudaStream_t s, const float2 *psi = nullptr,
+                           float2 *part, const DevState *st, cudaStream_t s, const float2 *psi = nullptr,
                            const float *D = nullptr);
-// Fixed-order sum of n doubles into *out (one block).
-cudaError_t launch_sum(const double *v, int n, double *out, cudaStream_t s);
+// Fixed-order sum of n float-float values into *out (one block).
+cudaError_t launch_sum(const float2 *v, int n, double *out, cudaStream_t s);
 // DIR stage scalars per view (one block each): F_m = sum of the view's fpart (CS per
 // pattern) plus p2 times the tiles' third partial (linear form); alpha from the view's tile
 // partials (restart rule); opens the first line-search window; writes the history of
 // iteration m.
-cudaError_t launch_dy_finalize(const double *fpart, int cs, const double *part, double p2, const ViewMap &vm,
+cudaError_t launch_dy_finalize(const float2 *fpart, int cs, const float2 *part, double p2, const ViewMap &vm,
                                DevState *st, DevHist h, const LsArgs &ls, cudaStream_t s);
 // LS stage decision per view over the open window; part rows have length kc (K * CS), the
 // view's partials are [pat_off[v] * cs, pat_off[v + 1] * cs).  vpart (nullable): object-tile
 // partials [ntiles][2] added, times vscale, to rows 0 and 1 over the view's tiles.
-cudaError_t launch_ls_decide(const double *part, int kc, int cs, const ViewMap &vm, const double *vpart, double vscale,
+cudaError_t launch_ls_decide(const float2 *part, int kc, int cs, const ViewMap &vm, const float2 *vpart, double vscale,
                              const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s);
 // D[y][x] = sum over the positions covering (y, x) of |probe / P|^2 at the covered pixel.
 cudaError_t launch_illumination(int P, const PatternArgs &a, const ScatterPlan &plan, float *D, cudaStream_t s);
 // eta = -g + alpha_v eta_prev over the object (H x W, scatter tiles) and the per-tile sums
 // part[b] = (sum D Re conj(psi) eta, sum D |eta|^2).
 cudaError_t launch_eta(int H, int W, const ScatterPlan &plan, const float2 *psi, const float2 *g, const float2 *ep,
-                       const float *D, float2 *eta, double *part, const DevState *st, cudaStream_t s);
+                       const float *D, float2 *eta, float2 *part, const DevState *st, cudaStream_t s);
 // Update stage for every object pixel (W columns per row): psi += gamma eta,
 // eta_prev <- eta = -g + alpha eta_prev, g_prev <- g, with the scalars of the row's view.
 // lin_period > 0 enables the linear form of the next GRAD pass (a full pass every

@@ -25,13 +25,13 @@ __device__ __forceinline__ int entry_natural(int s)
 }
 
 template <int P>
-__global__ void __launch_bounds__(kNT) k_tc_residual(PatternArgs a, float2 *__restrict__ U, double *__restrict__ fpart,
+__global__ void __launch_bounds__(kNT) k_tc_residual(PatternArgs a, float2 *__restrict__ U, float2 *__restrict__ fpart,
                                                      const DevState *__restrict__ st)
 {
     const int i = blockIdx.x;
     if (st && st[a.pat_view[i]].stalled) return;
-    __shared__ double red[kNT / 32];
-    __shared__ double tot[1];
+    __shared__ float2 red[kNT / 32];
+    __shared__ float2 tot[1];
     float2 *ui = U + (size_t)i * P * P;
     float f = 0.0f;
     for (int e = threadIdx.x; e < P * P; e += kNT) {
@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(kNT) k_tc_residual(PatternArgs a, float2 *__re
         u.y *= sc;
         ui[j] = u;
     }
-    double v[1] = {(double)f};
-    block_sum<kNT, 1>(v, red, tot);
+    float v[1] = {f};
+    block_sum_ff<kNT, 1>(v, red, tot);
     if (threadIdx.x == 0) fpart[i] = tot[0];
 }
 
@@ -68,15 +68,15 @@ __device__ __forceinline__ void kahan(float &sum, float &comp, float x)
 template <int P>
 __global__ void __launch_bounds__(kNT) k_tc_gather_eta(PatternArgs a, const float2 *__restrict__ psi,
                                                        const float2 *__restrict__ g, const float2 *__restrict__ ep,
-                                                       float2 *__restrict__ X, double *__restrict__ pars,
+                                                       float2 *__restrict__ X, float2 *__restrict__ pars,
                                                        const DevState *__restrict__ sts)
 {
     const int i = blockIdx.x;
     const DevState *st = sts + a.pat_view[i];
     if (st->stalled) return;
-    __shared__ double red[(kNT / 32) * 2];
-    __shared__ double tot[2];
-    const float alpha = (float)st->alpha;
+    __shared__ float2 red[(kNT / 32) * 2];
+    __shared__ float2 tot[2];
+    const float alpha = st->alpha_f;
     const int2 rc = a.pos[i];
     float2 *xi = X + (size_t)i * P * P;
     float sb = 0.f, sbc = 0.f, sc = 0.f, scc = 0.f;
@@ -90,26 +90,27 @@ __global__ void __launch_bounds__(kNT) k_tc_gather_eta(PatternArgs a, const floa
         kahan(sb, sbc, fmaf(xv.x, yv.x, xv.y * yv.y));
         kahan(sc, scc, fmaf(yv.x, yv.x, yv.y * yv.y));
     }
-    constexpr double PP = (double)P * (double)P;
-    double v[2] = {PP * ((double)sb - (double)sbc), PP * ((double)sc - (double)scc)};
-    block_sum<kNT, 2>(v, red, tot);
+    // the compensated pairs are float-float values (sum - comp); P^2 is a power of two
+    constexpr float PP = (float)P * (float)P;
+    float2 v[2] = {make_float2(PP * sb, -PP * sbc), make_float2(PP * sc, -PP * scc)};
+    block_sum_ff<kNT, 2>(v, red, tot);
     if (threadIdx.x < 2) pars[(size_t)threadIdx.x * a.K + i] = tot[threadIdx.x];
 }
 
 template <int P, int L>
 __global__ void __launch_bounds__(kNT) k_tc_ls_entries(PatternArgs a, const float2 *__restrict__ V,
-                                                       const double *__restrict__ pars, double *__restrict__ part,
+                                                       const float2 *__restrict__ pars, float2 *__restrict__ part,
                                                        const DevState *__restrict__ sts)
 {
     const int i = blockIdx.x;
     const DevState *st = sts + a.pat_view[i];
     if (st->stalled || st->decided || st->Lsel != L) return;
-    __shared__ double red[(kNT / 32) * (L + 2)];
-    __shared__ double tot[L + 2];
+    __shared__ float2 red[(kNT / 32) * L];
+    __shared__ float2 tot[L + 2];
     const int Leff = st->Leff;
     float gam[L];
 #pragma unroll
-    for (int l = 0; l < L; l++) gam[l] = (float)st->cand[l];
+    for (int l = 0; l < L; l++) gam[l] = st->cand_f[l];
     const float2 *vi = V + (size_t)i * P * P;
     float bp = 0.0f, cp = 0.0f, acc[L];
 #pragma unroll
@@ -135,22 +136,19 @@ __global__ void __launch_bounds__(kNT) k_tc_ls_entries(PatternArgs a, const floa
             }
         }
     }
-    double vals[L + 2];
-    vals[0] = -(double)bp;
-    vals[1] = -(double)cp;
-#pragma unroll
-    for (int l = 0; l < L; l++) vals[2 + l] = acc[l];
-    block_sum<kNT, L + 2>(vals, red, tot);
+    block_sum_ff<kNT, L>(acc, red, tot + 2);  // ends with a barrier: red is free again
+    const float bc[2] = {-bp, -cp};
+    block_sum_ff<kNT, 2>(bc, red, tot);
     if (threadIdx.x < L + 2) {
-        double t = tot[threadIdx.x];
-        if (threadIdx.x < 2) t += pars[(size_t)threadIdx.x * a.K + i];  // d = 0 part: total minus entries
+        float2 t = tot[threadIdx.x];
+        if (threadIdx.x < 2) t = ff_add(t, pars[(size_t)threadIdx.x * a.K + i]);  // d = 0 part: total minus entries
         part[(size_t)threadIdx.x * a.K + i] = t;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, double *fpart, const DevState *st,
+cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, float2 *fpart, const DevState *st,
                                cudaStream_t s)
 {
     if (P == 64) k_tc_residual<64><<<a.K, kNT, 0, s>>>(a, U, fpart, st);
@@ -160,7 +158,7 @@ cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, double *f
 }
 
 cudaError_t launch_tc_gather_eta(const PatternArgs &a, int P, const float2 *psi, const float2 *g, const float2 *ep,
-                                 float2 *X, double *pars, const DevState *st, cudaStream_t s)
+                                 float2 *X, float2 *pars, const DevState *st, cudaStream_t s)
 {
     if (P == 64) k_tc_gather_eta<64><<<a.K, kNT, 0, s>>>(a, psi, g, ep, X, pars, st);
     else if (P == 128) k_tc_gather_eta<128><<<a.K, kNT, 0, s>>>(a, psi, g, ep, X, pars, st);
@@ -169,7 +167,7 @@ cudaError_t launch_tc_gather_eta(const PatternArgs &a, int P, const float2 *psi,
 }
 
 template <int P>
-static cudaError_t ls_entries_p(const PatternArgs &a, int L, const float2 *V, const double *pars, double *part,
+static cudaError_t ls_entries_p(const PatternArgs &a, int L, const float2 *V, const float2 *pars, float2 *part,
                                 const DevState *st, cudaStream_t s)
 {
     switch (L) {
@@ -182,8 +180,8 @@ static cudaError_t ls_entries_p(const PatternArgs &a, int L, const float2 *V, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_ls_entries(const PatternArgs &a, int P, int L, const float2 *V, const double *pars,
-                                 double *part, const DevState *st, cudaStream_t s)
+cudaError_t launch_tc_ls_entries(const PatternArgs &a, int P, int L, const float2 *V, const float2 *pars,
+                                 float2 *part, const DevState *st, cudaStream_t s)
 {
     if (P == 64) return ls_entries_p<64>(a, L, V, pars, part, st, s);
     if (P == 128) return ls_entries_p<128>(a, L, V, pars, part, st, s);

@@ -85,11 +85,16 @@ typedef struct {
                             (0.1: with a smaller guard the gradient at dark detector pixels
                             holding counts is too ill-conditioned for single precision) */
     int32_t ls_window;   /* line-search trials evaluated per pass over the data: 4, 8, 16
-                            or 32, or 0 (default) for an adaptive first pass sized from the
-                            previous iteration's trial count (plus one), then passes of 32; the
-                            accepted step does not depend on it */
+                            or 32, or 0 (default) for an adaptive search: with dft = 0 the
+                            leading trials that a lower bound of the objective change
+                            (Jensen's inequality on the concave log, per pattern) rejects are
+                            skipped, and the first pass of 8, 16 or 32 trials starts at the
+                            first trial the bound cannot reject, sized from the previous
+                            iteration; then passes of 32.  The accepted step and the trial
+                            count do not depend on it */
     int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times); bit 1: no
-                            linear form (every GRAD pass runs the forward DFT) */
+                            linear form (every GRAD pass runs the forward DFT); bit 2: no
+                            certified skip of leading trials (adaptive search only) */
     int32_t tile_config; /* pattern-kernel configuration: -1 (default) = autotune at
                             pty_create (the GRAD and LS passes of every configuration for P are
                             timed on the problem's own data; the choice is cached per problem

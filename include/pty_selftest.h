@@ -32,6 +32,15 @@ PTY_API int pty_selftest_log1p(const float *t, float *out, int32_t n);
  */
 PTY_API int pty_selftest_tc_wait_limit(int64_t polls);
 
+/*
+ * *k0cert = the number of leading line-search trials of view `view` that the certificate of
+ * the adaptive search (pty_opts.ls_window = 0, dft = 0) rejected without evaluating them in
+ * the last iteration of the last pty_cg_solve / pty_batch_cg_solve call on ctx (0 when the
+ * certificate is off).  Synchronises ctx's stream.  Returns PTY_OK, PTY_ERR_ARG (NULL ctx
+ * or k0cert, view out of range) or PTY_ERR_CUDA.
+ */
+PTY_API int pty_selftest_ls_certified(pty_ctx *ctx, int32_t view, int32_t *k0cert);
+
 #ifdef __cplusplus
 }
 #endif

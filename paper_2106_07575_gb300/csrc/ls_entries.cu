@@ -6,8 +6,9 @@
 //   q = gamma (2 Re conj(u) v + gamma |v|^2) = |u + gamma v|^2 - |u|^2.
 // One thread block per (pattern, chunk) of the entry layout sums the window's candidates in
 // FP32 per thread and in float-float across the block (an FP64 butterfly over 16 values
-// kept the FP64 pipe 72 % busy and set the kernel's time): the partials have the layout of
-// the LS pass (rows 2.. of [L+2][K * cs]), so the decision kernel reads both alike.  The
+// kept the FP64 pipe 72 % busy and set the kernel's time) into rows 2.. of [L+2][K * cs]:
+// one column per unit, or with one view one column per CTA (its units summed in their fixed
+// order), so that the decision kernel reads few partials.  The
 // kernel needs no shared-memory tile and runs at full occupancy, which hides the latency
 // of the logarithm chain.
 #include "mathx.cuh"
@@ -34,6 +35,7 @@ __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V
     __shared__ float2 tot[L];
     const int nunits = a.K * cs;
     const size_t KC = (size_t)nunits;
+    float2 cta = make_float2(0.f, 0.f);  // one view: thread l < L sums candidate l over the CTA's units
     for (int blk = blockIdx.x; blk < nunits; blk += gridDim.x) {
         const int i = blk / cs, c = blk % cs;
         const DevState *st = sts + (V == 1 ? 0 : a.pat_view[i]);
@@ -63,12 +65,22 @@ __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V
                 acc[l] = fmaf(-dv, log1p_fast(t), acc[l] + q);
             }
         }
-        block_sum_ff<kNT, L>(acc, red, tot);  // ends with a barrier: red and tot are free again
-        for (int l = threadIdx.x; l < L; l += kNT) part[(size_t)(2 + l) * KC + blk] = tot[l];
+        block_sum_ff<kNT, L>(acc, red, tot);  // ends with a barrier: red is free again
+        if (V == 1) {
+            if (threadIdx.x < L) cta = ff_add(cta, tot[threadIdx.x]);
+        } else if (threadIdx.x < L) {
+            part[(size_t)(2 + threadIdx.x) * KC + blk] = tot[threadIdx.x];
+        }
     }
+    if (V == 1 && threadIdx.x < L) part[(size_t)(2 + threadIdx.x) * KC + blockIdx.x] = cta;
 }
 
 }  // namespace
+
+int ls_entries_cols(const PatternArgs &a, int cs, int V)
+{
+    return V == 1 ? (a.K * cs < kBlocks ? a.K * cs : kBlocks) : 0;
+}
 
 cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, float2 *part, const DevState *st,
                               cudaStream_t s)

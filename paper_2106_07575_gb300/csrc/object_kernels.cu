@@ -224,7 +224,13 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const float2 *__restrict
         }
         st->Leff = Le;
         st->Lsel = ls.adaptive ? (Le <= 16 ? 16 : 32) : ls.L;
+        st->k0cert = 0;
         open_window(st, ls.gamma0, ls.tau);
+        double gj = ls.gamma0;  // the leading trials for the certificate rows of the LS pass
+        for (int j = 0; j < kCertN; j++) {
+            gj *= ls.tau;
+            st->cert_f[j] = (float)gj;
+        }
         const int m = st->m;
         if (m < h.cap) {
             h.F[(size_t)v * (h.cap + 1) + m] = Fm;
@@ -253,9 +259,9 @@ __device__ __forceinline__ float2 warp_strided_sum(const float2 *__restrict__ v,
 
 constexpr int kDecNT = 1024;
 
-__global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__ part, int kc, int cs, ViewMap vm,
-                                                      const float2 *__restrict__ vpart, double vscale, DevState *sts,
-                                                      DevHist h, LsArgs ls)
+__global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__ part, int kc, int cs, int ls_cols,
+                                                      int en_cols, ViewMap vm, const float2 *__restrict__ vpart,
+                                                      double vscale, DevState *sts, DevHist h, LsArgs ls)
 {
     const int v = blockIdx.x;
     DevState *st = sts + v;
@@ -267,7 +273,9 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__
     const int Leff = st->Leff;
     const int p0 = vm.pat_off[v] * cs, p1 = vm.pat_off[v + 1] * cs;
     for (int j = warp; j < Leff + 2; j += kDecNT / 32) {
-        const float2 s = warp_strided_sum(part + (size_t)j * kc + p0, p1 - p0, lane);
+        const int nc = j < 2 ? ls_cols : en_cols;  // per-CTA columns (one view) or the view's range
+        const float2 s = nc > 0 ? warp_strided_sum(part + (size_t)j * kc, nc, lane)
+                                : warp_strided_sum(part + (size_t)j * kc + p0, p1 - p0, lane);
         if (lane == 0) tot[j] = ff_value(s);
     }
     // the view's object-tile sums of the all-pixel totals of rows 0 and 1 (Parseval)
@@ -294,6 +302,7 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__
                 st->Fnext = st->Fm + dF;
                 st->decided = 1;
                 st->last_halvings = k0 + l + 1;
+                st->last_excess = k0 + l - st->k0cert;
                 if (m < h.cap) {
                     h.gamma[hi] = gam;
                     h.halvings[hi] = k0 + l + 1;
@@ -317,6 +326,77 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__
             open_window(st, ls.gamma0, ls.tau);
         }
     }
+}
+
+// Certified rejection of the leading trials of Algorithm 1's backtracking (Eq. 7).  The LS
+// pass wrote, per (pattern, chunk), a lower bound of the entries' share of the objective change
+// at each of the first kCertN trials (Jensen's inequality on the concave log1p, see
+// ls_cert_rows) and its magnitude; with the pixels without counts (rows 0, 1 plus the object
+// sums, exact) the view's bound is LB_j <= F(psi + gamma_j eta) - F(psi).  Every leading trial
+// with LB_j above the acceptance threshold gamma_j t by more than a rounding margin would be
+// rejected by the plain search, so the first window opens at the first trial the bound cannot
+// reject; its size (8, 16 or 32 trials) follows the previous iteration's distance between that
+// trial and the accepted one.  Accepted step and trial count are those of the plain search.
+__global__ void __launch_bounds__(kDecNT) k_ls_certify(const float2 *__restrict__ part, int kc, int cs, int ls_cols,
+                                                       ViewMap vm, const float2 *__restrict__ vpart, double vscale,
+                                                       DevState *sts, LsArgs ls)
+{
+    const int v = blockIdx.x;
+    DevState *st = sts + v;
+    if (st->stalled) return;
+    constexpr int NR = 2 + 2 * kCertN;
+    __shared__ double tot[NR];
+    __shared__ double vtot[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int p0 = ls_cols > 0 ? 0 : vm.pat_off[v] * cs, p1 = ls_cols > 0 ? ls_cols : vm.pat_off[v + 1] * cs;
+    for (int j = warp; j < NR; j += kDecNT / 32) {
+        const float2 s = warp_strided_sum(part + (size_t)j * kc + p0, p1 - p0, lane);
+        if (lane == 0) tot[j] = ff_value(s);
+    }
+    if (vpart && warp >= 30) {
+        const int j = warp - 30, t0 = vm.tile_off[v], n = vm.tile_off[v + 1] - t0;
+        float2 t0s = make_float2(0.f, 0.f);
+        for (int b = lane; b < n; b += 32) t0s = ff_add(t0s, vpart[2 * (t0 + b) + j]);
+        t0s = warp_sum_ff(t0s);
+        if (lane == 0) vtot[j] = vscale * ff_value(t0s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (vpart) {
+            tot[0] += vtot[0];
+            tot[1] += vtot[1];
+        }
+        int k0 = 0;
+        double g = ls.gamma0;
+        for (; k0 < kCertN && k0 + 1 < ls.max_halvings; k0++) {
+            g *= ls.tau;
+            const double quad = g * (2.0 * tot[0] + g * tot[1]);  // pixels without counts
+            const double lb = quad + tot[2 + k0];
+            const double margin = 1e-4 * (fabs(quad) + tot[2 + kCertN + k0]);
+            if (!(lb > g * ls.t + margin)) break;  // NaN rows give no certificate
+        }
+        st->k0 = k0;
+        st->k0cert = k0;
+        const int Le = st->last_halvings > 0 ? st->last_excess + 2 : 16;
+        const int Ls = Le <= 8 ? 8 : (Le <= 16 ? 16 : 32);
+        st->Leff = Ls;
+        st->Lsel = Ls;
+        open_window(st, ls.gamma0, ls.tau);
+    }
+}
+
+// Sum of the counts of each (pattern, chunk): one block per chunk, FP64 (once per problem).
+__global__ void __launch_bounds__(kSumNT) k_chunk_dsum(PatternArgs a, int cs, float *__restrict__ dsum)
+{
+    __shared__ double red[kSumNT / 32];
+    __shared__ double tot[1];
+    const int i = blockIdx.x / cs, c = blockIdx.x % cs, per = a.nzc / cs;
+    const long long e0 = a.nz_off[(size_t)i * a.nzc + c * per], e1 = a.nz_off[(size_t)i * a.nzc + (c + 1) * per];
+    double sum = 0.0;
+    for (long long e = e0 + threadIdx.x; e < e1; e += kSumNT) sum += a.nz_d[e];
+    double v[1] = {sum};
+    block_sum<kSumNT, 1>(v, red, tot);
+    if (threadIdx.x == 0) dsum[blockIdx.x] = (float)tot[0];
 }
 
 __global__ void k_update(int H, int W, ViewMap vm, float2 *__restrict__ psi, const float2 *__restrict__ g,
@@ -467,10 +547,24 @@ cudaError_t launch_dy_finalize(const float2 *fpart, int cs, const float2 *part, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_ls_decide(const float2 *part, int kc, int cs, const ViewMap &vm, const float2 *vpart, double vscale,
-                             const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
+cudaError_t launch_ls_certify(const float2 *part, int kc, int cs, int ls_cols, const ViewMap &vm, const float2 *vpart,
+                              double vscale, const LsArgs &ls, DevState *st, cudaStream_t s)
 {
-    k_ls_decide<<<vm.V, kDecNT, 0, s>>>(part, kc, cs, vm, vpart, vscale, st, h, ls);
+    k_ls_certify<<<vm.V, kDecNT, 0, s>>>(part, kc, cs, ls_cols, vm, vpart, vscale, st, ls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_dsum(const PatternArgs &a, int cs, float *dsum, cudaStream_t s)
+{
+    k_chunk_dsum<<<a.K * cs, kSumNT, 0, s>>>(a, cs, dsum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ls_decide(const float2 *part, int kc, int cs, int ls_cols, int en_cols, const ViewMap &vm,
+                             const float2 *vpart, double vscale, const LsArgs &ls, DevState *st, DevHist h,
+                             cudaStream_t s)
+{
+    k_ls_decide<<<vm.V, kDecNT, 0, s>>>(part, kc, cs, ls_cols, en_cols, vm, vpart, vscale, st, h, ls);
     return cudaGetLastError();
 }
 

@@ -284,10 +284,43 @@ __global__ void __launch_bounds__(NT) k_grad_lin(PatternArgs a, float2 *__restri
     }
 }
 
+// Rows 2 .. 2 + 2 kCertN of the LS partials when a.dsum is set: a lower bound of this chunk's
+// share of the objective change at the leading trials gamma_j = gamma0 tau^(j+1) (Eq. 2, 7).
+// With t_e = q_e / (|u_e|^2 + eps) and weights d_e / D (D = sum of the chunk's counts),
+// log1p is concave, so by Jensen's inequality
+//   sum_e d_e log1p(t_e) <= D log1p(T / D),  T = sum_e d_e t_e = gamma S1 + gamma^2 S2,
+//   S1 = sum_e d_e 2 Re conj(u) v / (|u|^2 + eps),  S2 = sum_e d_e |v|^2 / (|u|^2 + eps),
+// and the chunk's exact entry term sum_e [q_e - d_e log1p(t_e)] is at least
+//   lb_j = gamma (2 B + gamma C) - D log1p(T / D)   (B, C: sums of Re conj(u) v, |v|^2).
+// Row 2 + j holds lb_j, row 2 + kCertN + j its magnitude (for the rounding margin); NaN
+// where T / D is not safely above -1 (no certificate).  k: row - 2.
+__device__ __forceinline__ float2 ls_cert_row(const PatternArgs &a, const DevState &sv, const float2 *tot, int col,
+                                              int k)
+{
+    const int j = k % kCertN;
+    const float g = sv.cert_f[j];
+    const float B = -(tot[0].x + tot[0].y), C = -(tot[1].x + tot[1].y);
+    const float S1 = tot[2].x + tot[2].y, S2 = tot[3].x + tot[3].y;
+    const float quad = g * fmaf(g, C, 2.0f * B);
+    const float D = a.dsum[col];
+    float lb = quad, mag = fabsf(quad);
+    if (D > 0.0f) {
+        const float x = g * fmaf(g, S2, S1) / D;
+        const float l = x > -1.0f + 1e-6f ? log1pf(x) : __int_as_float(0x7fc00000);
+        lb = fmaf(-D, l, quad);
+        mag = fmaf(D, fabsf(l), mag);
+    }
+    return ff_from(k < kCertN ? lb : mag);
+}
+
+// Rows of the LS partials that the pass writes: 0, 1, and the certificate rows when set.
+__device__ __forceinline__ int ls_rows(const PatternArgs &a) { return a.dsum ? 2 + 2 * kCertN : 2; }
+
+// One pattern chunk of the LS pass; thread t < ls_rows(a) receives the chunk's value of row t.
 template <int P, int R, int NT>
-__device__ __forceinline__ void ls_fft_pattern(const PatternArgs &a, const float2 *__restrict__ eta,
-                                               float2 *__restrict__ part, float2 *buf, const float2 *tw,
-                                               float2 *red, float2 *tot, int i, int c)
+__device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const float2 *__restrict__ eta, float2 *buf,
+                                                 const float2 *tw, float2 *red, float2 *tot,
+                                                 const DevState *__restrict__ sts, int i, int c)
 {
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
@@ -295,8 +328,10 @@ __device__ __forceinline__ void ls_fft_pattern(const PatternArgs &a, const float
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
     // v = G eta at the entries (kept for the candidate windows), and the entries' share of
-    // the two all-pixel sums, removed here so that rows 0 and 1 cover the pixels without counts
-    float bp = 0.0f, cp = 0.0f;
+    // the two all-pixel sums, removed here so that rows 0 and 1 cover the pixels without
+    // counts; with the certificate also the two weighted sums of its bound
+    const bool cert = a.dsum != nullptr;
+    float bp = 0.0f, cp = 0.0f, s1 = 0.0f, s2 = 0.0f;
     const int per = a.nzc / CS;
     const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
 #pragma unroll 4
@@ -305,13 +340,20 @@ __device__ __forceinline__ void ls_fft_pattern(const PatternArgs &a, const float
         const float2 u = __ldg(a.nz_u + e);
         const float2 v = buf[(s / P) * LDB + (s % P - c * R)];
         a.nz_v[e] = v;
-        bp += fmaf(u.x, v.x, u.y * v.y);  // Re conj(u) v
-        cp += fmaf(v.x, v.x, v.y * v.y);
+        const float re = fmaf(u.x, v.x, u.y * v.y), vv = fmaf(v.x, v.x, v.y * v.y);  // Re conj(u) v, |v|^2
+        bp += re;
+        cp += vv;
+        if (cert) {
+            const float wgt = __fdividef(__ldg(a.nz_d + e), fmaf(u.x, u.x, u.y * u.y) + a.eps);
+            s1 = fmaf(wgt, 2.0f * re, s1);
+            s2 = fmaf(wgt, vv, s2);
+        }
     }
-    float vals[2] = {-bp, -cp};
-    block_sum_ff<NT, 2>(vals, red, tot);
-    const int KC = a.K * CS;
-    if (threadIdx.x < 2) part[(size_t)threadIdx.x * KC + i * CS + c] = tot[threadIdx.x];  // rows 0, 1
+    float vals[4] = {-bp, -cp, s1, s2};
+    block_sum_ff<NT, 4>(vals, red, tot);
+    if (threadIdx.x < 2) return tot[threadIdx.x];
+    if (threadIdx.x < ls_rows(a)) return ls_cert_row(a, sts[a.pat_view[i]], tot, i * CS + c, threadIdx.x - 2);
+    return make_float2(0.f, 0.f);
 }
 
 template <int P, int R, int NT>
@@ -320,23 +362,31 @@ __global__ void __launch_bounds__(NT) k_ls_fft(PatternArgs a, const float2 *__re
 {
     extern __shared__ __align__(16) float2 sm[];
     constexpr int CS = Slab<P, R>::CS;
-    __shared__ float2 red[(NT / 32) * 2];
-    __shared__ float2 tot[2];
+    __shared__ float2 red[(NT / 32) * 4];
+    __shared__ float2 tot[4];
     float2 *buf = sm, *tw = sm + Slab<P, R>::ELEMS;
     const int c = blockIdx.x % CS;
     if (a.V == 1 && sts->stalled) return;  // one view: decided for all patterns
     cluster_start<P, R>();
     load_twiddles<P, NT>(tw, a.tw);
+    const int KC = a.K * CS, nr = ls_rows(a);
     if constexpr (CS == 1) {
+        // one view: one column per CTA, its patterns summed in their fixed order
+        const bool percta = a.V == 1;
+        float2 acc = make_float2(0.f, 0.f);
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (sts[a.pat_view[i]].stalled) continue;
             __syncthreads();  // the previous pattern's reads of buf are done
-            ls_fft_pattern<P, R, NT>(a, eta, part, buf, tw, red, tot, i, 0);
+            const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0);
+            if (percta) acc = ff_add(acc, r);
+            else if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i] = r;
         }
+        if (percta && threadIdx.x < nr) part[(size_t)threadIdx.x * KC + blockIdx.x] = acc;
     } else {
         const int i = blockIdx.x / CS;
         if (sts[a.pat_view[i]].stalled) return;  // uniform over the cluster
-        ls_fft_pattern<P, R, NT>(a, eta, part, buf, tw, red, tot, i, c);
+        const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, c);
+        if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i * CS + c] = r;
     }
 }
 
@@ -483,6 +533,11 @@ struct PatternOps {
         const int g = persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
         return launch_pattern(k_ls_fft<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, eta, part, st);
     }
+    static int ls_cols(const PatternArgs &a)
+    {
+        if (CS != 1 || a.V != 1) return 0;
+        return persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+    }
     static cudaError_t nz_count(const float *d, const int *perm, int K, int *cnt, cudaStream_t s)
     {
         k_nz_count<P, R, NT><<<K * CS, NT, 0, s>>>(d, perm, cnt);
@@ -500,7 +555,8 @@ template <int P, int R, int NT>
 constexpr PatternImpl make_impl()
 {
     using O = PatternOps<P, R, NT>;
-    return PatternImpl{P, R, NT, &O::forward, &O::adjoint, &O::grad, &O::grad_lin, &O::ls, &O::nz_count, &O::nz_fill};
+    return PatternImpl{P, R, NT, &O::forward, &O::adjoint, &O::grad, &O::grad_lin, &O::ls, &O::ls_cols, &O::nz_count,
+                       &O::nz_fill};
 }
 
 }  // namespace pty

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -80,6 +81,8 @@ struct pty_ctx {
     float2 *eta = nullptr;       // atlas: the current search direction (LS stage)
     float *illum = nullptr;      // atlas: sum over positions of |probe / P|^2 (Parseval totals)
     float2 *part_eta = nullptr;  // [ntiles][2] object-tile sums of the LS stage
+    float *dsum = nullptr;       // [K * CSl] counts per (pattern, LS chunk): certificate weights
+    bool cert = false;           // certified skip of leading line-search trials
     unsigned long long *hash = nullptr;  // [V] object hashes (solve entry / exit)
     bool cache_dirty = false;  // the entries' u no longer belong to the last solve's object
     DevState *st = nullptr;     // [V]
@@ -165,7 +168,7 @@ void free_all(pty_ctx *c)
                     c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
                     c->stage_obj2, c->stage_pat, c->tc_img_fwd, c->tc_img_inv, c->tc_err, c->tc_x, c->tc_t,
                     c->tc_u, c->tc_pars, c->st_den, c->st_tmax, c->st_red,
-                    c->eta, c->illum, c->part_eta, c->hash};
+                    c->eta, c->illum, c->part_eta, c->hash, c->dsum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -193,6 +196,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.pat_view = c->pat_view;
     a.V = c->V;
     a.eps = (float)c->opts.eps;
+    a.dsum = c->cert ? c->dsum : nullptr;
     return a;
 }
 
@@ -407,7 +411,7 @@ int launch_iteration(pty_ctx *c, bool timed)
                 CK(pty::launch_tc_ls_entries(a, c->P, ls.L, c->tc_u, c->tc_pars, c->part_ls, c->st, c->s));
             }
             StageTimer t(c, 3, timed);
-            CK(pty::launch_ls_decide(c->part_ls, c->K, 1, vm, nullptr, 0.0, ls, c->st, c->hist, c->s));
+            CK(pty::launch_ls_decide(c->part_ls, c->K, 1, 0, 0, vm, nullptr, 0.0, ls, c->st, c->hist, c->s));
         }
         StageTimer t(c, 3, timed);
         CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, 0, c->s));
@@ -443,16 +447,26 @@ int launch_iteration(pty_ctx *c, bool timed)
         StageTimer t(c, 2, timed);  // v = G eta once per iteration; the windows reuse it
         CK(c->impl_ls->ls(a, c->eta, c->part_ls, c->st, c->s));
     }
+    // with one view the LS pass and the windows write one column per CTA
+    const int ls_cols = c->impl_ls->ls_cols(a), en_cols = pty::ls_entries_cols(a, c->CSl, c->V);
+    if (c->cert) {
+        StageTimer t(c, 4, timed);
+        CK(pty::launch_ls_certify(c->part_ls, c->K * c->CSl, c->CSl, ls_cols, vm, c->part_eta, (double)c->P * c->P, ls,
+                                  c->st, c->s));
+    }
     for (int wdx = 0; wdx < nwin; wdx++) {
         {
             StageTimer t(c, 4, timed);
-            // the first window of an adaptive search runs on the 16- or the 32-candidate
-            // kernel as the device chose; the other one returns at once
+            // the first window of an adaptive search runs on the 8- (certified start only),
+            // 16- or 32-candidate kernel as the device chose; the others return at once
+            if (wdx == 0 && ls.adaptive && c->cert)
+                CK(pty::launch_ls_entries(a, c->CSl, c->V, 8, c->part_ls, c->st, c->s));
             if (wdx == 0 && ls.adaptive) CK(pty::launch_ls_entries(a, c->CSl, c->V, 16, c->part_ls, c->st, c->s));
             CK(pty::launch_ls_entries(a, c->CSl, c->V, ls.L, c->part_ls, c->st, c->s));
         }
         StageTimer t(c, 3, timed);
-        CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, c->CSl, vm, c->part_eta, (double)c->P * c->P, ls, c->st,
+        CK(pty::launch_ls_decide(c->part_ls, c->K * c->CSl, c->CSl, ls_cols, en_cols, vm, c->part_eta,
+                                 (double)c->P * c->P, ls, c->st,
                                  c->hist, c->s));
     }
     StageTimer t(c, 3, timed);
@@ -857,6 +871,16 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
         const int at = autotune(c);
         if (at != PTY_OK) return bail(at);
     }
+    // certified skip of leading line-search trials: adaptive windows of the FFT form
+    if (o.dft == 0 && o.ls_window == 0 && !(o.flags & 4)) {
+        cudaError_t ce2 = dalloc(&c->dsum, (size_t)K * c->CSl);
+        if (ce2 == cudaSuccess) ce2 = pty::launch_chunk_dsum(pattern_args(c), c->CSl, c->dsum, c->s);
+        if (ce2 == cudaSuccess) ce2 = cudaStreamSynchronize(c->s);
+        if (ce2 != cudaSuccess)
+            return bail(fail(c, ce2 == cudaErrorMemoryAllocation ? PTY_ERR_NOMEM : PTY_ERR_CUDA, "certificate weights: %s",
+                             cudaGetErrorString(ce2)));
+        c->cert = true;
+    }
     *out = c;
     return PTY_OK;
 }
@@ -1093,7 +1117,7 @@ int32_t pty_num_views(const pty_ctx *c) { return c ? c->V : 0; }
 // Checkpoint layout: header {magic, H*W of the atlas, views, entries} (4 x int64), g_prev,
 // eta_prev, the per-view DevState, then u and v at the entries (the linear form's cache).
 namespace {
-constexpr long long kStateMagic = 0x5054594347310002LL;
+constexpr long long kStateMagic = 0x5054594347310003LL;
 size_t state_bytes(const pty_ctx *c)
 {
     const size_t HW = (size_t)c->HA * c->WA, E = (size_t)std::max<long long>(c->n_entries, 0);
@@ -1286,5 +1310,18 @@ extern "C" int pty_selftest_log1p(const float *t, float *out, int32_t n)
     if (dt) cudaFree(dt);
     if (dout) cudaFree(dout);
     if (e != cudaSuccess) return fail(c, PTY_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));
+    return PTY_OK;
+}
+
+extern "C" int pty_selftest_ls_certified(pty_ctx *c, int32_t view, int32_t *k0cert)
+{
+    if (!c || !k0cert || view < 0 || view >= c->V) return fail(c, PTY_ERR_ARG, "bad arguments");
+    if (enter(c) != PTY_OK) return PTY_ERR_CUDA;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, (const char *)(c->st + view) + offsetof(pty::DevState, k0cert), sizeof(int),
+                                    cudaMemcpyDeviceToHost, c->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return fail(c, PTY_ERR_CUDA, "selftest: %s", cudaGetErrorString(e));
+    *k0cert = c->cert ? v : 0;
     return PTY_OK;
 }

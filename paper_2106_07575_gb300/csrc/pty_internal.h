@@ -10,6 +10,10 @@ namespace pty {
 // Solver state that lives in device memory so that one CG iteration runs without host
 // synchronisation: the line-search decision, the Dai-Yuan coefficient and the stall flag
 // are produced and consumed by kernels.
+// Leading trials of a line search that the Jensen lower bound of the objective change can
+// reject without evaluating them (ls_fft epilogue, k_ls_certify).
+constexpr int kCertN = 16;
+
 struct DevState {
     int m;         // iterations accepted in the current pty_cg_solve call
     int k0;        // line-search trials already rejected in the current iteration
@@ -33,6 +37,10 @@ struct DevState {
     // conversion per thread would run on the slow FP64 pipe)
     float alpha_f, gamma_f;
     float cand_f[32];
+    // certified skip of the first line-search trials (ls_fft epilogue + k_ls_certify):
+    float cert_f[kCertN];  // gamma0 tau^(j+1), j < kCertN, rounded to FP32
+    int k0cert;            // trials of the current iteration rejected by the certificate
+    int last_excess;       // accepted trial index minus k0cert, last iteration (window size)
 };
 
 // Per-call history arrays (device), one block of `cap` iterations per view, indexed by
@@ -65,6 +73,9 @@ struct PatternArgs {
     const int *pat_view;        // [K] view of sorted pattern i (all 0 for one view)
     int V;                      // views
     float eps;
+    // [K * CS] sum of the counts of each (pattern, CTA) chunk of the LS configuration; set
+    // when the LS pass also writes the certificate rows (else nullptr)
+    const float *dsum;
 };
 
 // Line-search window description (device scalars come from DevState).
@@ -98,6 +109,10 @@ struct PatternImpl {
     // |v|^2) over the entries (per CTA, rows of length K * CS): the all-pixel totals come from
     // object sums (launch_eta).  Exits when st->stalled.
     cudaError_t (*ls)(const PatternArgs &, const float2 *eta, float2 *part, const DevState *st, cudaStream_t);
+    // Columns the LS pass writes per row: with one view a persistent single-CTA configuration
+    // sums its patterns per CTA and writes gridDim columns (returned); otherwise 0: one
+    // column per (pattern, CTA) chunk.
+    int (*ls_cols)(const PatternArgs &);
     // Entries of the measured data: counts per (pattern, CTA) chunk, then the compact list.
     cudaError_t (*nz_count)(const float *d, const int *perm, int K, int *cnt, cudaStream_t);
     cudaError_t (*nz_fill)(const float *d, const int *perm, int K, const long long *off, unsigned short *slot,
@@ -114,6 +129,8 @@ cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_
 // part[2 + l][i * cs + c] = sum over the entries of chunk c of pattern i of the objective
 // change at candidate l (gamma0 tau^(k0+l+1)), from u (nz_u), v (nz_v) and d: the window
 // of the L-candidate kernel; returns at once unless st->Lsel == L and a window is open.
+// Columns launch_ls_entries writes per row with one view (one per CTA), else 0 (one per unit).
+int ls_entries_cols(const PatternArgs &a, int cs, int V);
 cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, float2 *part, const DevState *st,
                               cudaStream_t s);
 
@@ -194,8 +211,17 @@ cudaError_t launch_dy_finalize(const float2 *fpart, int cs, const float2 *part, 
 // LS stage decision per view over the open window; part rows have length kc (K * CS), the
 // view's partials are [pat_off[v] * cs, pat_off[v + 1] * cs).  vpart (nullable): object-tile
 // partials [ntiles][2] added, times vscale, to rows 0 and 1 over the view's tiles.
-cudaError_t launch_ls_decide(const float2 *part, int kc, int cs, const ViewMap &vm, const float2 *vpart, double vscale,
-                             const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s);
+// Certified skip of leading trials (Jensen bound rows of the LS pass), then the first window.
+// ls_cols: columns of the LS pass's rows when it sums per CTA (one view), else 0.
+cudaError_t launch_ls_certify(const float2 *part, int kc, int cs, int ls_cols, const ViewMap &vm, const float2 *vpart,
+                              double vscale, const LsArgs &ls, DevState *st, cudaStream_t s);
+// dsum[i * cs + c] = sum of the counts of chunk c of sorted pattern i (cs chunks per pattern).
+cudaError_t launch_chunk_dsum(const PatternArgs &a, int cs, float *dsum, cudaStream_t s);
+// ls_cols / en_cols: columns of rows 0-1 (LS pass) / rows 2.. (windows) when summed per CTA
+// (one view), else 0 (one column per pattern chunk, the view's range).
+cudaError_t launch_ls_decide(const float2 *part, int kc, int cs, int ls_cols, int en_cols, const ViewMap &vm,
+                             const float2 *vpart, double vscale, const LsArgs &ls, DevState *st, DevHist h,
+                             cudaStream_t s);
 // D[y][x] = sum over the positions covering (y, x) of |probe / P|^2 at the covered pixel.
 cudaError_t launch_illumination(int P, const PatternArgs &a, const ScatterPlan &plan, float *D, cudaStream_t s);
 // eta = -g + alpha_v eta_prev over the object (H x W, scatter tiles) and the per-tile sums

@@ -224,10 +224,10 @@ __global__ void __launch_bounds__(NT) k_head_loss(int P, int B, const float *__r
                                                   float inv_norm, float2 *__restrict__ o_out, float *__restrict__ dz,
                                                   double *__restrict__ part)
 {
-    __shared__ double red[NT / 32], tot[1];
+    __shared__ float2 red[NT / 32], tot[1];
     const size_t PP = (size_t)P * P, n = (size_t)B * PP;
     const size_t i = (size_t)blockIdx.x * NT + threadIdx.x;
-    double l = 0.0;
+    float l = 0.0f;
     if (i < n) {
         const size_t b = i / PP, px = i % PP;
         const float z0 = __ldg(z + (2 * b) * PP + px), z1 = __ldg(z + (2 * b + 1) * PP + px);
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(NT) k_head_loss(int P, int B, const float *__r
             const size_t src = idx ? (size_t)__ldg(idx + b) : b;
             const float2 tt = __ldg(t + src * PP + px);
             const float rx = o.x - tt.x, ry = o.y - tt.y, ww = __ldg(w + px);
-            l = (double)ww * (double)(rx * rx + ry * ry);
+            l = ww * fmaf(rx, rx, ry * ry);
             const float g = 2.f * ww * inv_norm;
             const float damp = g * (rx * cs + ry * sn);
             const float dph = g * (ry * o.x - rx * o.y);
@@ -249,10 +249,10 @@ __global__ void __launch_bounds__(NT) k_head_loss(int P, int B, const float *__r
             dz[(2 * b + 1) * PP + px] = dph * kHalfPi * s1 * (1.f - s1);
         }
     }
-    if (part) {
-        double v[1] = {l};
-        block_sum<NT, 1>(v, red, tot);
-        if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+    if (part) {  // float-float block sum (FP64 runs at 1/64 of the FP32 rate)
+        float v[1] = {l};
+        block_sum_ff<NT, 1>(v, red, tot);
+        if (threadIdx.x == 0) part[blockIdx.x] = ff_value(tot[0]);
     }
 }
 
@@ -387,10 +387,10 @@ __global__ void k_wreduce(const float *__restrict__ part, int nblk, int npl, flo
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npl) return;
-    double s = 0.0;
+    float2 s = make_float2(0.f, 0.f);  // float-float: FP64 runs at 1/64 of the FP32 rate
 #pragma unroll 8
-    for (int k = 0; k < nblk; k++) s += (double)__ldg(part + (size_t)k * npl + p);
-    grad[p] = (float)s;
+    for (int k = 0; k < nblk; k++) s = ff_add_f(s, __ldg(part + (size_t)k * npl + p));
+    grad[p] = s.x + s.y;
 }
 
 // ---- Adam and the BF16 working copies ----
@@ -523,19 +523,19 @@ constexpr int kRedBlocks = 1024;
 __global__ void __launch_bounds__(NT) k_partial_sums(const float2 *__restrict__ x, const float *__restrict__ w, size_t n,
                                                      double *__restrict__ part)
 {
-    __shared__ double red[NT / 32], tot[1];
-    double s = 0.0;
+    __shared__ float2 red[NT / 32], tot[1];
+    float2 s = make_float2(0.f, 0.f);  // float-float: FP64 runs at 1/64 of the FP32 rate
     for (size_t i = (size_t)blockIdx.x * NT + threadIdx.x; i < n; i += (size_t)gridDim.x * NT) {
         if (x) {
             const float2 v = x[i];
-            s += (double)(v.x * v.x + v.y * v.y) * (double)w[i];
+            s = ff_add_f(s, fmaf(v.x, v.x, v.y * v.y) * w[i]);
         } else {
-            s += (double)w[i];
+            s = ff_add_f(s, w[i]);
         }
     }
-    double v[1] = {s};
-    block_sum<NT, 1>(v, red, tot);
-    if (threadIdx.x == 0) part[blockIdx.x] = tot[0];
+    float2 v[1] = {s};
+    block_sum_ff<NT, 1>(v, red, tot);
+    if (threadIdx.x == 0) part[blockIdx.x] = ff_value(tot[0]);
 }
 
 __global__ void k_scale(float2 *__restrict__ x, size_t n, const double *__restrict__ num, const double *__restrict__ den,

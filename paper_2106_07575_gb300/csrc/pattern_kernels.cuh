@@ -26,12 +26,27 @@
 #include "pty_internal.h"
 #include "reduce.cuh"
 
+#ifndef PTY_GATHER_UNROLL
+#define PTY_GATHER_UNROLL 8  // loads of the exit-wave gather in flight per thread
+#endif
+
 namespace pty {
+
+constexpr int kGatherUnroll = PTY_GATHER_UNROLL;
 
 template <int P, int R>
 constexpr size_t slab_bytes()
 {
     return sizeof(float2) * (size_t)(Slab<P, R>::ELEMS + P);
+}
+
+// Resident CTAs per SM the register allocation may plan for: 1 where the tile or slab takes
+// more than half of an SM's shared memory (only one CTA fits, so its threads may use the
+// whole register file); 0 (no hint) otherwise.
+template <int P, int R>
+constexpr int min_ctas()
+{
+    return slab_bytes<P, R>() > 113 * 1024 ? 1 : 0;
 }
 
 // Pattern and cluster rank of this CTA.
@@ -54,7 +69,7 @@ __device__ __forceinline__ void gather_rows(float2 *buf, const float2 *__restric
                                             const float2 *__restrict__ src, int W, int r0, int c0, int c)
 {
     constexpr int LDA = Slab<P, R>::LDA;
-#pragma unroll 4
+#pragma unroll kGatherUnroll
     for (int e = threadIdx.x; e < R * P; e += NT) {
         const int rl = e / P, x = e % P, y = c * R + rl;
         buf[rl * LDA + x] = cmul(__ldg(probe + y * P + x), __ldg(src + (size_t)(r0 + y) * W + (c0 + x)));
@@ -79,7 +94,7 @@ __device__ __forceinline__ void cluster_start()
 
 // ------------------------------------------------------------------------------------
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_forward(PatternArgs a, const float2 *__restrict__ psi,
+__global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_forward(PatternArgs a, const float2 *__restrict__ psi,
                                                 float2 *__restrict__ out)
 {
     extern __shared__ __align__(16) float2 sm[];
@@ -100,7 +115,7 @@ __global__ void __launch_bounds__(NT) k_forward(PatternArgs a, const float2 *__r
 }
 
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_adjoint_fft(PatternArgs a, const float2 *__restrict__ y,
+__global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_adjoint_fft(PatternArgs a, const float2 *__restrict__ y,
                                                     float2 *__restrict__ w)
 {
     extern __shared__ __align__(16) float2 sm[];
@@ -175,7 +190,7 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
 // Single-CTA configurations (CS = 1) run persistently: the CTAs of the grid stride over
 // the patterns.  Clusters run one pattern each.
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_grad(PatternArgs a, const float2 *__restrict__ psi,
+__global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, const float2 *__restrict__ psi,
                                              float2 *__restrict__ w, float2 *__restrict__ fpart,
                                              const DevState *__restrict__ st)
 {
@@ -257,7 +272,7 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
 }
 
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_grad_lin(PatternArgs a, float2 *__restrict__ w, float2 *__restrict__ fpart,
+__global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a, float2 *__restrict__ w, float2 *__restrict__ fpart,
                                                  const DevState *__restrict__ sts)
 {
     extern __shared__ __align__(16) float2 sm[];
@@ -357,7 +372,7 @@ __device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const flo
 }
 
 template <int P, int R, int NT>
-__global__ void __launch_bounds__(NT) k_ls_fft(PatternArgs a, const float2 *__restrict__ eta,
+__global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, const float2 *__restrict__ eta,
                                                float2 *__restrict__ part, const DevState *__restrict__ sts)
 {
     extern __shared__ __align__(16) float2 sm[];

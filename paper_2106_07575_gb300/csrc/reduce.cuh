@@ -66,6 +66,15 @@ __device__ __forceinline__ float2 ff_add(float2 a, float2 b)
     return make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s.x)));
 }
 
+// (s.x + s.y) + x: a float added to a running float-float sum.
+__device__ __forceinline__ float2 ff_add_f(float2 s, float x)
+{
+    const float2 h = ff_two_sum(s.x, x);
+    const float t = __fadd_rn(s.y, h.y);
+    const float hi = __fadd_rn(h.x, t);
+    return make_float2(hi, __fsub_rn(t, __fsub_rn(hi, h.x)));
+}
+
 __device__ __forceinline__ float2 ff_from(float a) { return make_float2(a, 0.0f); }
 __host__ __device__ __forceinline__ double ff_value(float2 a) { return (double)a.x + (double)a.y; }
 __device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }

@@ -188,7 +188,7 @@ __device__ __forceinline__ void open_window(DevState *st, double gamma0, double 
     }
 }
 
-__global__ void __launch_bounds__(kSumNT) k_dy_finalize(const float2 *__restrict__ fpart, int cs,
+__global__ void __launch_bounds__(kSumNT) k_dy_finalize(const float2 *__restrict__ fpart, int cs, int fcols,
                                                         const float2 *__restrict__ part, double p2, ViewMap vm,
                                                         DevState *sts, DevHist h, LsArgs ls)
 {
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const float2 *__restrict
     if (st->stalled) return;
     __shared__ float2 red[(kSumNT / 32) * 4];
     __shared__ float2 tot[4];
-    const int f0 = vm.pat_off[v] * cs, f1 = vm.pat_off[v + 1] * cs;
+    const int f0 = fcols > 0 ? 0 : vm.pat_off[v] * cs, f1 = fcols > 0 ? fcols : vm.pat_off[v + 1] * cs;
     const int t0 = vm.tile_off[v], t1 = vm.tile_off[v + 1];
     float2 v4[4] = {strided_sum(fpart + f0, f1 - f0, 1, 0), strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 0),
                     strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 1), strided_sum(part + 3 * (size_t)t0, t1 - t0, 3, 2)};
@@ -540,10 +540,10 @@ cudaError_t launch_sum(const float2 *v, int n, double *out, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_dy_finalize(const float2 *fpart, int cs, const float2 *part, double p2, const ViewMap &vm,
+cudaError_t launch_dy_finalize(const float2 *fpart, int cs, int fcols, const float2 *part, double p2, const ViewMap &vm,
                                DevState *st, DevHist h, const LsArgs &ls, cudaStream_t s)
 {
-    k_dy_finalize<<<vm.V, kSumNT, 0, s>>>(fpart, cs, part, p2, vm, st, h, ls);
+    k_dy_finalize<<<vm.V, kSumNT, 0, s>>>(fpart, cs, fcols, part, p2, vm, st, h, ls);
     return cudaGetLastError();
 }
 

@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_adjoint_fft(PatternArg
 template <int P, int R, int NT>
 __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 *__restrict__ psi,
                                              float2 *__restrict__ w, float2 *__restrict__ fpart, float2 *buf,
-                                             const float2 *tw, float2 *red, float2 *tot, int i, int c)
+                                             const float2 *tw, float2 *red, float2 *tot, int i, int c,
+                                             float2 *facc)
 {
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
@@ -176,9 +177,14 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
         u.y *= sc;
         *pu = u;
     }
-    float v[1] = {f};
-    block_sum_ff<NT, 1>(v, red, tot);  // its barriers also order the residual writes before F^H
-    if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
+    if (facc) {  // one view, persistent CTA: the thread's running sum over its patterns
+        *facc = ff_add_f(*facc, f);
+        __syncthreads();  // the residual writes before F^H
+    } else {
+        float v[1] = {f};
+        block_sum_ff<NT, 1>(v, red, tot);  // its barriers also order the residual writes before F^H
+        if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
+    }
     fft2_inv<P, R, NT>(buf, tw);
     float2 *wi = w + (size_t)i * P * P;
     for (int e = threadIdx.x; e < R * P; e += NT) {
@@ -204,20 +210,29 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
     cluster_start<P, R>();
     load_twiddles<P, NT>(tw, a.tw);
     auto skip = [&](int i) {
-        if (!st) return false;
+        if (!st || a.V == 1) return false;  // one view: decided above for all patterns
         const DevState &sv = st[a.pat_view[i]];
         return sv.stalled || sv.lin;  // a view in the linear form runs k_grad_lin
     };
     if constexpr (CS == 1) {
+        // one view: the objective terms are summed per thread over the CTA's patterns and
+        // written as one column per CTA (same grid for k_grad and k_grad_lin)
+        const bool percta = a.V == 1;
+        float2 facc = make_float2(0.f, 0.f);
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (skip(i)) continue;
             __syncthreads();  // the previous pattern's reads of buf are done
-            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, 0);
+            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, 0, percta ? &facc : nullptr);
+        }
+        if (percta) {
+            float2 v[1] = {facc};
+            block_sum_ff<NT, 1>(v, red, tot);
+            if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
     } else {
         const int i = blockIdx.x / CS;
         if (skip(i)) return;  // uniform over the cluster
-        grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c);
+        grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr);
     }
 }
 
@@ -239,7 +254,7 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
 template <int P, int R, int NT>
 __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *__restrict__ w,
                                                  float2 *__restrict__ fpart, float2 *buf, const float2 *tw,
-                                                 float2 *red, float2 *tot, float gam, int i, int c)
+                                                 float2 *red, float2 *tot, float gam, int i, int c, float2 *facc)
 {
     constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     // the column slab (permuted spectrum order) starts at zero
@@ -260,9 +275,14 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
         const float sc = -dv / den;
         buf[(s / P) * LDB + (s % P - c * R)] = make_float2(u.x * sc, u.y * sc);
     }
-    float vv[1] = {f};
-    block_sum_ff<NT, 1>(vv, red, tot);  // its barriers also order the writes before F^H
-    if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
+    if (facc) {  // one view, persistent CTA: the thread's running sum over its patterns
+        *facc = ff_add_f(*facc, f);
+        __syncthreads();  // the writes before F^H
+    } else {
+        float vv[1] = {f};
+        block_sum_ff<NT, 1>(vv, red, tot);  // its barriers also order the writes before F^H
+        if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
+    }
     fft2_inv<P, R, NT>(buf, tw);
     float2 *wi = w + (size_t)i * P * P;
     for (int e = threadIdx.x; e < R * P; e += NT) {
@@ -285,17 +305,29 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
     cluster_start<P, R>();
     load_twiddles<P, NT>(tw, a.tw);
     if constexpr (CS == 1) {
+        const bool percta = a.V == 1;  // as in k_grad
+        float2 facc = make_float2(0.f, 0.f);
+        const float gam1 = percta ? (float)sts->last_gamma : 0.f;  // one view: loop-invariant
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
-            const DevState *st = sts + a.pat_view[i];
-            if (st->stalled || !st->lin) continue;
+            float gam = gam1;
+            if (!percta) {
+                const DevState *st = sts + a.pat_view[i];
+                if (st->stalled || !st->lin) continue;
+                gam = (float)st->last_gamma;
+            }
             __syncthreads();  // the previous pattern's reads of buf are done
-            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, 0);
+            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, gam, i, 0, percta ? &facc : nullptr);
+        }
+        if (percta) {
+            float2 v[1] = {facc};
+            block_sum_ff<NT, 1>(v, red, tot);
+            if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
     } else {
         const int i = blockIdx.x / CS;
         const DevState *st = sts + a.pat_view[i];
         if (st->stalled || !st->lin) return;  // uniform over the cluster
-        grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c);
+        grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c, nullptr);
     }
 }
 
@@ -320,8 +352,9 @@ __device__ __forceinline__ float2 ls_cert_row(const PatternArgs &a, const DevSta
     const float D = a.dsum[col];
     float lb = quad, mag = fabsf(quad);
     if (D > 0.0f) {
-        const float x = g * fmaf(g, S2, S1) / D;
-        const float l = x > -1.0f + 1e-6f ? log1pf(x) : __int_as_float(0x7fc00000);
+        // fast division and log1p (a few ulp): the acceptance margin of k_ls_certify is 1e-4
+        const float x = __fdividef(g * fmaf(g, S2, S1), D);
+        const float l = x > -1.0f + 1e-6f ? log1p_fast(x) : __int_as_float(0x7fc00000);
         lb = fmaf(-D, l, quad);
         mag = fmaf(D, fabsf(l), mag);
     }
@@ -367,7 +400,8 @@ __device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const flo
     float vals[4] = {-bp, -cp, s1, s2};
     block_sum_ff<NT, 4>(vals, red, tot);
     if (threadIdx.x < 2) return tot[threadIdx.x];
-    if (threadIdx.x < ls_rows(a)) return ls_cert_row(a, sts[a.pat_view[i]], tot, i * CS + c, threadIdx.x - 2);
+    if (threadIdx.x < ls_rows(a))
+        return ls_cert_row(a, sts[a.V == 1 ? 0 : a.pat_view[i]], tot, i * CS + c, threadIdx.x - 2);
     return make_float2(0.f, 0.f);
 }
 
@@ -390,7 +424,7 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
         const bool percta = a.V == 1;
         float2 acc = make_float2(0.f, 0.f);
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
-            if (sts[a.pat_view[i]].stalled) continue;
+            if (!percta && sts[a.pat_view[i]].stalled) continue;  // one view: decided above
             __syncthreads();  // the previous pattern's reads of buf are done
             const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0);
             if (percta) acc = ff_add(acc, r);
@@ -532,15 +566,26 @@ struct PatternOps {
     {
         return launch_pattern(k_adjoint_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, s, a, y, w);
     }
+    // One view, single CTA: both GRAD kernels run the same grid and write one objective
+    // column per CTA (returned); otherwise 0 (one column per pattern chunk).
+    static int grad_cols(const PatternArgs &a)
+    {
+        if (CS != 1 || a.V != 1) return 0;
+        const int g1 = persistent_blocks(k_grad<P, R, NT>, a.K, NT, slab_bytes<P, R>(), CS);
+        const int g2 = persistent_blocks(k_grad_lin<P, R, NT>, a.K, NT, slab_bytes<P, R>(), CS);
+        return g1 < g2 ? g1 : g2;
+    }
     static cudaError_t grad(const PatternArgs &a, const float2 *psi, float2 *w, float2 *fpart, const DevState *st,
                             cudaStream_t s)
     {
-        const int g = persistent_blocks(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        const int gc = grad_cols(a);
+        const int g = gc > 0 ? gc : persistent_blocks(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
         return launch_pattern(k_grad<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, psi, w, fpart, st);
     }
     static cudaError_t grad_lin(const PatternArgs &a, float2 *w, float2 *fpart, const DevState *st, cudaStream_t s)
     {
-        const int g = persistent_blocks(k_grad_lin<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        const int gc = grad_cols(a);
+        const int g = gc > 0 ? gc : persistent_blocks(k_grad_lin<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
         return launch_pattern(k_grad_lin<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, w, fpart, st);
     }
     static cudaError_t ls(const PatternArgs &a, const float2 *eta, float2 *part, const DevState *st, cudaStream_t s)
@@ -570,7 +615,7 @@ template <int P, int R, int NT>
 constexpr PatternImpl make_impl()
 {
     using O = PatternOps<P, R, NT>;
-    return PatternImpl{P, R, NT, &O::forward, &O::adjoint, &O::grad, &O::grad_lin, &O::ls, &O::ls_cols, &O::nz_count,
+    return PatternImpl{P, R, NT, &O::forward, &O::adjoint, &O::grad, &O::grad_lin, &O::ls, &O::ls_cols, &O::grad_cols, &O::nz_count,
                        &O::nz_fill};
 }
 

@@ -395,7 +395,7 @@ int launch_iteration(pty_ctx *c, bool timed)
         }
         {
             StageTimer t(c, 3, timed);
-            CK(pty::launch_dy_finalize(c->fpart, 1, c->part_sc, 0.0, vm, c->st, c->hist, ls, c->s));
+            CK(pty::launch_dy_finalize(c->fpart, 1, 0, c->part_sc, 0.0, vm, c->st, c->hist, ls, c->s));
         }
         {
             StageTimer t(c, 2, timed);  // v = G eta once per iteration; windows reuse it
@@ -437,7 +437,8 @@ int launch_iteration(pty_ctx *c, bool timed)
     }
     {
         StageTimer t(c, 3, timed);
-        CK(pty::launch_dy_finalize(c->fpart, c->CS, c->part_sc, (double)c->P * c->P, vm, c->st, c->hist, ls, c->s));
+        CK(pty::launch_dy_finalize(c->fpart, c->CS, c->impl->grad_cols(a), c->part_sc, (double)c->P * c->P, vm, c->st,
+                                   c->hist, ls, c->s));
     }
     {
         StageTimer t(c, 3, timed);  // the search direction and its object sums
@@ -1070,7 +1071,8 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
     }
     CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, c->stage_obj2, 0, nullptr, nullptr, nullptr, nullptr,
                            c->s));
-    CK(pty::launch_sum(c->fpart, c->K * c->CS, c->dscalar, c->s));
+    const int fcols = c->opts.dft != 0 ? 0 : c->impl->grad_cols(a);
+    CK(pty::launch_sum(c->fpart, fcols > 0 ? fcols : c->K * c->CS, c->dscalar, c->s));
     if (grad) {
         float *go[1] = {grad};
         if ((st = views_out(c, go, c->stage_obj2))) return st;

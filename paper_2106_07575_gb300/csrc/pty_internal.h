@@ -113,6 +113,9 @@ struct PatternImpl {
     // sums its patterns per CTA and writes gridDim columns (returned); otherwise 0: one
     // column per (pattern, CTA) chunk.
     int (*ls_cols)(const PatternArgs &);
+    // Columns of fpart the GRAD passes write: with one view a single-CTA configuration sums
+    // per CTA (both GRAD kernels on the same grid, returned); otherwise 0 (one per chunk).
+    int (*grad_cols)(const PatternArgs &);
     // Entries of the measured data: counts per (pattern, CTA) chunk, then the compact list.
     cudaError_t (*nz_count)(const float *d, const int *perm, int K, int *cnt, cudaStream_t);
     cudaError_t (*nz_fill)(const float *d, const int *perm, int K, const long long *off, unsigned short *slot,
@@ -206,7 +209,8 @@ cudaError_t launch_sum(const float2 *v, int n, double *out, cudaStream_t s);
 // pattern) plus p2 times the tiles' third partial (linear form); alpha from the view's tile
 // partials (restart rule); opens the first line-search window; writes the history of
 // iteration m.
-cudaError_t launch_dy_finalize(const float2 *fpart, int cs, const float2 *part, double p2, const ViewMap &vm,
+// fcols > 0: fpart holds fcols per-CTA columns (one view), else one per pattern chunk.
+cudaError_t launch_dy_finalize(const float2 *fpart, int cs, int fcols, const float2 *part, double p2, const ViewMap &vm,
                                DevState *st, DevHist h, const LsArgs &ls, cudaStream_t s);
 // LS stage decision per view over the open window; part rows have length kc (K * CS), the
 // view's partials are [pat_off[v] * cs, pat_off[v + 1] * cs).  vpart (nullable): object-tile

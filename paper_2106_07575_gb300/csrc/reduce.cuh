@@ -141,10 +141,29 @@ __device__ __forceinline__ void block_sum_ff(const float2 (&v)[NV], float2 *red,
         }
     }
     __syncthreads();
-    if (threadIdx.x < NV) {
-        float2 s = red[threadIdx.x];
-        for (int w = 1; w < NT / 32; w++) s = ff_add(s, red[w * NV + threadIdx.x]);
-        out[threadIdx.x] = s;
+    constexpr int NW = NT / 32;
+    static_assert(NW <= 32, "at most 32 warps");
+    if constexpr (NW <= 8) {  // few warps: thread v adds the partials of value v in order
+        if (threadIdx.x < NV) {
+            float2 s = red[threadIdx.x];
+            for (int w = 1; w < NW; w++) s = ff_add(s, red[w * NV + threadIdx.x]);
+            out[threadIdx.x] = s;
+        }
+    } else if (warp == 0) {  // many warps: one warp combines the partials as a tree
+        float2 x[NV];
+#pragma unroll
+        for (int i = 0; i < NV; i++) x[i] = lane < NW ? red[lane * NV + i] : make_float2(0.f, 0.f);
+        if constexpr (NV >= 2 && NV <= 32 && (NV & (NV - 1)) == 0) {
+            warp_scatter_sum_ff<NV>(x);
+            constexpr int SH = 5 - ilog2(NV);
+            if ((lane & ((1 << SH) - 1)) == 0) out[lane >> SH] = x[0];
+        } else {
+#pragma unroll
+            for (int i = 0; i < NV; i++) {
+                const float2 s = warp_sum_ff(x[i]);
+                if (lane == 0) out[i] = s;
+            }
+        }
     }
     __syncthreads();
 }

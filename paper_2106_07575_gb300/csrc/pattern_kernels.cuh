@@ -25,6 +25,7 @@
 #include "mathx.cuh"
 #include "pty_internal.h"
 #include "reduce.cuh"
+#include "tc_ptx.cuh"
 
 #ifndef PTY_GATHER_UNROLL
 #define PTY_GATHER_UNROLL 8  // loads of the exit-wave gather in flight per thread
@@ -76,6 +77,85 @@ __device__ __forceinline__ void gather_rows(float2 *buf, const float2 *__restric
     }
 }
 
+// Probe cache in tensor memory (single-CTA configurations, R = P).  The gather of an exit
+// wave and the emit of an adjoint result both visit pixel e = t + k NT with thread t, so
+// thread t needs only the probe values p[t + k NT], k < NE.  They are stored once per kernel
+// in the thread's TMEM lane (lane quarter warp % 4, columns from (warp / 4) 2 NE) and read
+// back with tcgen05.ld, instead of 128 KB of L2 loads per pattern at P = 128.
+template <int P, int NT>
+struct ProbeCache {
+    static constexpr int NE = P * P / NT;  // complex values per thread
+    static constexpr int NCOL = 2 * NE;    // 32-bit TMEM columns per thread
+    static constexpr int USED = NCOL * (NT / 128);
+    static constexpr int COLS = USED <= 32 ? 32 : USED <= 64 ? 64 : USED <= 128 ? 128 : USED <= 256 ? 256 : 512;
+    uint32_t base, addr;
+
+    // All threads; ends with the cache filled and visible to this thread.
+    __device__ __forceinline__ void init(uint32_t *slot, const float2 *__restrict__ probe)
+    {
+        static_assert(NT % 128 == 0 && NE % 4 == 0 && USED <= 512, "probe cache layout");
+        const int warp = threadIdx.x >> 5;
+        if (warp == 0) tcx::tmem_alloc(slot, COLS);
+        tcx::tmem_fence_before_sync();
+        __syncthreads();
+        tcx::tmem_fence_after_sync();
+        base = *slot;
+        addr = base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * NCOL);
+#pragma unroll 1
+        for (int k0 = 0; k0 < NE; k0 += 4) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const float2 pv = __ldg(probe + threadIdx.x + (k0 + j) * NT);
+                v[2 * j] = pv.x;
+                v[2 * j + 1] = pv.y;
+            }
+            tcx::tmem_st8(addr + 2 * k0, v);
+        }
+        tcx::tmem_wait_st();
+    }
+    // This thread's probe values k0 .. k0 + 3.
+    __device__ __forceinline__ void get4(int k0, float2 (&p)[4]) const
+    {
+        float v[8];
+        tcx::tmem_ld8(addr + 2 * k0, v);
+#pragma unroll
+        for (int j = 0; j < 4; j++) p[j] = make_float2(v[2 * j], v[2 * j + 1]);
+    }
+    // All threads, after the last use.
+    __device__ __forceinline__ void release() const
+    {
+        tcx::tmem_fence_before_sync();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) tcx::tmem_dealloc(base, COLS);
+    }
+};
+
+// Single-CTA form of gather_rows with the probe from the cache: all NE loads of the object
+// are in flight before the first product.
+template <int P, int NT>
+__device__ __forceinline__ void gather_cached(float2 *buf, const ProbeCache<P, NT> &pc,
+                                              const float2 *__restrict__ src, int W, int r0, int c0)
+{
+    constexpr int LDA = P + 1, NE = ProbeCache<P, NT>::NE;
+    float2 sv[NE];
+#pragma unroll
+    for (int k = 0; k < NE; k++) {
+        const int e = threadIdx.x + k * NT;
+        sv[k] = __ldg(src + (size_t)(r0 + e / P) * W + (c0 + e % P));
+    }
+#pragma unroll
+    for (int k0 = 0; k0 < NE; k0 += 4) {
+        float2 pv[4];
+        pc.get4(k0, pv);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int e = threadIdx.x + (k0 + j) * NT;
+            buf[(e / P) * LDA + (e % P)] = cmul(pv[j], sv[k0 + j]);
+        }
+    }
+}
+
 // Kahan-compensated single-precision accumulation (per thread; the block sum is FP64).
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
 {
@@ -114,6 +194,35 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_forward(PatternArgs a,
     }
 }
 
+// w[i] = conj(p) * (row slab of F^H r) of pattern i, with the probe from the cache when given.
+template <int P, int R, int NT>
+__device__ __forceinline__ void emit_adjoint(const PatternArgs &a, const float2 *buf, float2 *__restrict__ w, int i,
+                                             int c, const ProbeCache<P, NT> *pc)
+{
+    constexpr int LDA = Slab<P, R>::LDA;
+    float2 *wi = w + (size_t)i * P * P;
+    if constexpr (R == P) {
+        if (pc) {
+            constexpr int NE = ProbeCache<P, NT>::NE;
+#pragma unroll
+            for (int k0 = 0; k0 < NE; k0 += 4) {
+                float2 pv[4];
+                pc->get4(k0, pv);
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int e = threadIdx.x + (k0 + j) * NT;
+                    wi[e] = cconjmul(pv[j], buf[(e / P) * LDA + (e % P)]);
+                }
+            }
+            return;
+        }
+    }
+    for (int e = threadIdx.x; e < R * P; e += NT) {
+        const int rl = e / P, x = e % P, yy = c * R + rl;
+        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
+    }
+}
+
 template <int P, int R, int NT>
 __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_adjoint_fft(PatternArgs a, const float2 *__restrict__ y,
                                                     float2 *__restrict__ w)
@@ -148,11 +257,16 @@ template <int P, int R, int NT>
 __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 *__restrict__ psi,
                                              float2 *__restrict__ w, float2 *__restrict__ fpart, float2 *buf,
                                              const float2 *tw, float2 *red, float2 *tot, int i, int c,
-                                             float2 *facc)
+                                             float2 *facc, const ProbeCache<P, NT> *pc)
 {
-    constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
+    constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
-    gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+    if constexpr (R == P) {
+        if (pc) gather_cached<P, NT>(buf, *pc, psi, a.W, rc.x, rc.y);
+        else gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+    } else {
+        gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+    }
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
     float f = 0.0f;
@@ -186,11 +300,7 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
         if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
     }
     fft2_inv<P, R, NT>(buf, tw);
-    float2 *wi = w + (size_t)i * P * P;
-    for (int e = threadIdx.x; e < R * P; e += NT) {
-        const int rl = e / P, x = e % P, yy = c * R + rl;
-        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
-    }
+    emit_adjoint<P, R, NT>(a, buf, w, i, c, pc);
 }
 
 // Single-CTA configurations (CS = 1) run persistently: the CTAs of the grid stride over
@@ -215,6 +325,9 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
         return sv.stalled || sv.lin;  // a view in the linear form runs k_grad_lin
     };
     if constexpr (CS == 1) {
+        __shared__ uint32_t tmem_slot;
+        ProbeCache<P, NT> pc;
+        pc.init(&tmem_slot, a.probe);
         // one view: the objective terms are summed per thread over the CTA's patterns and
         // written as one column per CTA (same grid for k_grad and k_grad_lin)
         const bool percta = a.V == 1;
@@ -222,17 +335,18 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (skip(i)) continue;
             __syncthreads();  // the previous pattern's reads of buf are done
-            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, 0, percta ? &facc : nullptr);
+            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, 0, percta ? &facc : nullptr, &pc);
         }
         if (percta) {
             float2 v[1] = {facc};
             block_sum_ff<NT, 1>(v, red, tot);
             if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
+        pc.release();
     } else {
         const int i = blockIdx.x / CS;
         if (skip(i)) return;  // uniform over the cluster
-        grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr);
+        grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr, nullptr);
     }
 }
 
@@ -254,9 +368,10 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
 template <int P, int R, int NT>
 __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *__restrict__ w,
                                                  float2 *__restrict__ fpart, float2 *buf, const float2 *tw,
-                                                 float2 *red, float2 *tot, float gam, int i, int c, float2 *facc)
+                                                 float2 *red, float2 *tot, float gam, int i, int c, float2 *facc,
+                                                 const ProbeCache<P, NT> *pc)
 {
-    constexpr int LDA = Slab<P, R>::LDA, LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
+    constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     // the column slab (permuted spectrum order) starts at zero
     for (int e = threadIdx.x; e < P * LDB; e += NT) buf[e] = make_float2(0.f, 0.f);
     __syncthreads();
@@ -284,11 +399,7 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
         if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
     }
     fft2_inv<P, R, NT>(buf, tw);
-    float2 *wi = w + (size_t)i * P * P;
-    for (int e = threadIdx.x; e < R * P; e += NT) {
-        const int rl = e / P, x = e % P, yy = c * R + rl;
-        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
-    }
+    emit_adjoint<P, R, NT>(a, buf, w, i, c, pc);
 }
 
 template <int P, int R, int NT>
@@ -305,6 +416,9 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
     cluster_start<P, R>();
     load_twiddles<P, NT>(tw, a.tw);
     if constexpr (CS == 1) {
+        __shared__ uint32_t tmem_slot;
+        ProbeCache<P, NT> pc;
+        pc.init(&tmem_slot, a.probe);
         const bool percta = a.V == 1;  // as in k_grad
         float2 facc = make_float2(0.f, 0.f);
         const float gam1 = percta ? (float)sts->last_gamma : 0.f;  // one view: loop-invariant
@@ -316,18 +430,19 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
                 gam = (float)st->last_gamma;
             }
             __syncthreads();  // the previous pattern's reads of buf are done
-            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, gam, i, 0, percta ? &facc : nullptr);
+            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, gam, i, 0, percta ? &facc : nullptr, &pc);
         }
         if (percta) {
             float2 v[1] = {facc};
             block_sum_ff<NT, 1>(v, red, tot);
             if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
+        pc.release();
     } else {
         const int i = blockIdx.x / CS;
         const DevState *st = sts + a.pat_view[i];
         if (st->stalled || !st->lin) return;  // uniform over the cluster
-        grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c, nullptr);
+        grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c, nullptr, nullptr);
     }
 }
 
@@ -368,11 +483,18 @@ __device__ __forceinline__ int ls_rows(const PatternArgs &a) { return a.dsum ? 2
 template <int P, int R, int NT>
 __device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const float2 *__restrict__ eta, float2 *buf,
                                                  const float2 *tw, float2 *red, float2 *tot,
-                                                 const DevState *__restrict__ sts, int i, int c)
+                                                 const DevState *__restrict__ sts, int i, int c,
+                                                 const ProbeCache<P, NT> *pc)
 {
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
-    gather_rows<P, R, NT>(buf, a.probe, eta, a.W, rc.x, rc.y, c);  // p eta / P into the row slab
+    // p eta / P into the row slab
+    if constexpr (R == P) {
+        if (pc) gather_cached<P, NT>(buf, *pc, eta, a.W, rc.x, rc.y);
+        else gather_rows<P, R, NT>(buf, a.probe, eta, a.W, rc.x, rc.y, c);
+    } else {
+        gather_rows<P, R, NT>(buf, a.probe, eta, a.W, rc.x, rc.y, c);
+    }
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
     // v = G eta at the entries (kept for the candidate windows), and the entries' share of
@@ -421,20 +543,24 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
     const int KC = a.K * CS, nr = ls_rows(a);
     if constexpr (CS == 1) {
         // one view: one column per CTA, its patterns summed in their fixed order
+        __shared__ uint32_t tmem_slot;
+        ProbeCache<P, NT> pc;
+        pc.init(&tmem_slot, a.probe);
         const bool percta = a.V == 1;
         float2 acc = make_float2(0.f, 0.f);
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (!percta && sts[a.pat_view[i]].stalled) continue;  // one view: decided above
             __syncthreads();  // the previous pattern's reads of buf are done
-            const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0);
+            const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0, &pc);
             if (percta) acc = ff_add(acc, r);
             else if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i] = r;
         }
         if (percta && threadIdx.x < nr) part[(size_t)threadIdx.x * KC + blockIdx.x] = acc;
+        pc.release();
     } else {
         const int i = blockIdx.x / CS;
         if (sts[a.pat_view[i]].stalled) return;  // uniform over the cluster
-        const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, c);
+        const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, c, nullptr);
         if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i * CS + c] = r;
     }
 }

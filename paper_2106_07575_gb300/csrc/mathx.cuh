@@ -24,8 +24,10 @@ __device__ __forceinline__ float log1p_fast(float t)
     const float f = fmaf(t, r, r - 1.0f);
     const float s = __fdividef(f, 2.0f + f);
     const float s2 = s * s;
-    const float p = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 1.0f / 9.0f, 1.0f / 7.0f), 1.0f / 5.0f), 1.0f / 3.0f), 1.0f);
-    return fmaf((float)e, 0.693147180559945309f, (2.0f * s) * p);
+    // 2 atanh(s) = s q(s^2) with the series' coefficients doubled (exact: scaling by 2
+    // commutes with rounding, so q = 2 p bit for bit and s q = (2 s) p)
+    const float q = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f), 2.0f);
+    return fmaf((float)e, 0.693147180559945309f, s * q);
 }
 
 }  // namespace pty

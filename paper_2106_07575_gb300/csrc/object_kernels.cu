@@ -18,6 +18,10 @@
 
 namespace pty {
 
+#ifndef PTY_SCATTER_LD
+#define PTY_SCATTER_LD __ldcs  // load of the per-pattern results: read once, evict first
+#endif
+
 namespace {
 constexpr int kScTY = kTileY, kScTX = kTileX, kScNT = 256, kScNJ = kScTY * kScTX / kScNT;
 constexpr int kSumNT = 256;
@@ -52,7 +56,7 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
         for (int j = 0; j < kScNJ; j++) {
             const int yy = y0 + (kScNT / kScTX) * j - rc.x;
             if (yy >= 0 && yy < P) {
-                const float2 v = __ldg(wi + yy * P);
+                const float2 v = PTY_SCATTER_LD(wi + yy * P);
                 acc[j].x += v.x;
                 acc[j].y += v.y;
             }

@@ -88,6 +88,10 @@ struct pty_ctx {
     DevState *st = nullptr;     // [V]
     double *dscalar = nullptr;
     DevHist hist{};
+    // pinned host staging of a solve call's results (device state, history, error flag), so
+    // that the call copies them back asynchronously and synchronises once
+    unsigned char *hpin = nullptr;
+    size_t hpin_bytes = 0;
 
     // staging for host arguments (device)
     float2 *stage_obj = nullptr, *stage_obj2 = nullptr;
@@ -171,6 +175,7 @@ void free_all(pty_ctx *c)
                     c->eta, c->illum, c->part_eta, c->hash, c->dsum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->hpin) cudaFreeHost(c->hpin);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     if (c->iter_exec) cudaGraphExecDestroy(c->iter_exec);
     if (c->join) cudaEventDestroy(c->join);
@@ -886,35 +891,54 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     return PTY_OK;
 }
 
-// Fill a host report per view from the device history.
-int read_reports(pty_ctx *c, int niter, pty_cg_report *rep, const std::vector<DevState> &hs)
+// Layout of the pinned staging area: [V] DevState, then the history arrays F [V][cap+1],
+// gamma, alpha [V][cap] (double), halvings [V][cap] (int), then the tensor-core error flag.
+struct HostStage {
+    DevState *st;
+    double *F, *gamma, *alpha;
+    int *halvings, *err;
+};
+
+int ensure_pinned(pty_ctx *c, HostStage &h)
 {
-    if (!rep) return PTY_OK;
-    if (niter <= 0) {
-        for (int v = 0; v < c->V; v++) rep[v].iters_done = hs[v].m;
-        return PTY_OK;
+    const size_t V = c->V, cap = c->hist.cap;
+    const size_t n = sizeof(DevState) * V + sizeof(double) * V * (3 * cap + 1) + sizeof(int) * (V * cap + 1);
+    if (c->hpin_bytes < n) {
+        if (c->hpin) cudaFreeHost(c->hpin);
+        c->hpin = nullptr;
+        c->hpin_bytes = 0;
+        CK(cudaMallocHost((void **)&c->hpin, n));
+        c->hpin_bytes = n;
     }
+    unsigned char *q = c->hpin;
+    h.st = (DevState *)q;
+    q += sizeof(DevState) * V;
+    h.F = (double *)q;
+    h.gamma = h.F + V * (cap + 1);
+    h.alpha = h.gamma + V * cap;
+    h.halvings = (int *)(h.alpha + V * cap);
+    h.err = h.halvings + V * cap;
+    return PTY_OK;
+}
+
+// Fill a host report per view from the staged history.
+void read_reports(const pty_ctx *c, int niter, pty_cg_report *rep, const HostStage &h)
+{
+    if (!rep) return;
     const int cap = c->hist.cap;
-    std::vector<double> hF((size_t)c->V * (cap + 1)), hg((size_t)c->V * cap), ha((size_t)c->V * cap);
-    std::vector<int> hh((size_t)c->V * cap);
-    CK(cudaMemcpyAsync(hF.data(), c->hist.F, sizeof(double) * hF.size(), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(hg.data(), c->hist.gamma, sizeof(double) * hg.size(), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(ha.data(), c->hist.alpha, sizeof(double) * ha.size(), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaMemcpyAsync(hh.data(), c->hist.halvings, sizeof(int) * hh.size(), cudaMemcpyDeviceToHost, c->s));
-    CK(cudaStreamSynchronize(c->s));
     for (int v = 0; v < c->V; v++) {
-        const int done = hs[v].m;
+        const int done = h.st[v].m;
         rep[v].iters_done = done;
-        const int nrec = std::min(niter, done + (hs[v].stalled ? 1 : 0));
+        if (niter <= 0) continue;
+        const int nrec = std::min(niter, done + (h.st[v].stalled ? 1 : 0));
         if (rep[v].F)
-            for (int i = 0; i <= std::min(done, niter); i++) rep[v].F[i] = hF[(size_t)v * (cap + 1) + i];
+            for (int i = 0; i <= std::min(done, niter); i++) rep[v].F[i] = h.F[(size_t)v * (cap + 1) + i];
         for (int i = 0; i < nrec; i++) {
-            if (rep[v].gamma) rep[v].gamma[i] = hg[(size_t)v * cap + i];
-            if (rep[v].alpha) rep[v].alpha[i] = ha[(size_t)v * cap + i];
-            if (rep[v].halvings) rep[v].halvings[i] = hh[(size_t)v * cap + i];
+            if (rep[v].gamma) rep[v].gamma[i] = h.gamma[(size_t)v * cap + i];
+            if (rep[v].alpha) rep[v].alpha[i] = h.alpha[(size_t)v * cap + i];
+            if (rep[v].halvings) rep[v].halvings[i] = h.halvings[(size_t)v * cap + i];
         }
     }
-    return PTY_OK;
 }
 
 int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
@@ -939,18 +963,28 @@ int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
     }
     CK(pty::launch_hash(c->HA, c->WA, c->row_view, c->psi, c->hash, c->V, c->s));
     CK(pty::launch_store_hash(c->st, c->V, c->hash, c->s));
-    std::vector<DevState> hs(c->V);
-    int herr = 0;
-    CK(cudaMemcpyAsync(hs.data(), c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
-    if (c->tc_err) CK(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    // the call's results: asynchronous copies into pinned staging, one synchronisation
+    HostStage hs;
+    if ((st = ensure_pinned(c, hs))) return st;
+    *hs.err = 0;
+    CK(cudaMemcpyAsync(hs.st, c->st, sizeof(DevState) * c->V, cudaMemcpyDeviceToHost, c->s));
+    if (rep && niter > 0) {
+        const size_t V = c->V, cap = c->hist.cap;
+        CK(cudaMemcpyAsync(hs.F, c->hist.F, sizeof(double) * V * (cap + 1), cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(hs.gamma, c->hist.gamma, sizeof(double) * V * cap, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(hs.alpha, c->hist.alpha, sizeof(double) * V * cap, cudaMemcpyDeviceToHost, c->s));
+        CK(cudaMemcpyAsync(hs.halvings, c->hist.halvings, sizeof(int) * V * cap, cudaMemcpyDeviceToHost, c->s));
+    }
+    if (c->tc_err) CK(cudaMemcpyAsync(hs.err, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     if ((st = views_out(c, psi, c->psi))) return st;
     if ((st = sync(c))) return st;
+    const int herr = *hs.err;
     if (herr) return fail(c, PTY_ERR_TIMEOUT, "tensor-core DFT: a device wait timed out");
-    if ((st = read_reports(c, niter, rep, hs))) return st;
+    read_reports(c, niter, rep, hs);
     for (int v = 0; v < c->V; v++)
-        if (hs[v].stalled)
+        if (hs.st[v].stalled)
             return fail(c, PTY_STALLED, "view %d: line search found no step within %d trials at iteration %d", v,
-                        c->opts.max_halvings, hs[v].m);
+                        c->opts.max_halvings, hs.st[v].m);
     return PTY_OK;
 }
 

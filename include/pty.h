@@ -186,7 +186,7 @@ PTY_API int pty_gradient(pty_ctx *ctx, const float *psi, float *grad, double *F)
  * the gradient's dense part conj(p) F^H G psi = |p|^2 psi is summed over positions in the
  * object domain.  A full forward pass runs at the first iteration of a call whose object
  * differs from the one the previous call returned (64-bit hash), after pty_gradient on the
- * context, and every 16th iteration (by the count since the last reset).
+ * context, and every 64th iteration (by the count since the last reset).
  */
 PTY_API int pty_cg_solve(pty_ctx *ctx, float *psi_inout, int32_t niter, pty_cg_report *rep);
 

@@ -30,7 +30,7 @@ def ctx_for(p, linear=True):
 
 def test_linear_matches_full_over_20_iterations(small):
     """Both forms take the same steps; the objective histories agree to FP32 rounding
-    (the linear form refreshes u with a full pass every 16 iterations)."""
+    (the linear form refreshes u with a full pass every 64 iterations)."""
     p = small
     res = {}
     for linear in (True, False):

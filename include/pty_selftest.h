@@ -24,8 +24,8 @@ PTY_API int pty_selftest_log1p(const float *t, float *out, int32_t n);
 
 /*
  * Failure detection without a fault: every pipeline wait of the tensor-core kernels
- * (opts.dft = 1, 2) launched or captured into a context's iteration graph from now on gives
- * up after `polls` polls (polls <= 0 restores the
+ * (opts.dft = 1, 2) and of the tensor-copy scatter-add launched or captured into a context's
+ * iteration graph from now on gives up after `polls` polls (polls <= 0 restores the
  * default, about a second per wait).  A kernel whose wait gave up lets its own copies and
  * tensor-core operations finish, frees its tensor memory and returns; the call reports
  * PTY_ERR_TIMEOUT.  Process-wide; for tests.  Returns PTY_OK.

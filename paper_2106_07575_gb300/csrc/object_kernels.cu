@@ -15,6 +15,7 @@
 
 #include "pty_internal.h"
 #include "reduce.cuh"
+#include "scatter_tail.cuh"
 
 namespace pty {
 
@@ -62,34 +63,7 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
             }
         }
     }
-    float gg = 0.f, den = 0.f, pd = 0.f;
-    if (x < a.W) {
-#pragma unroll
-        for (int j = 0; j < kScNJ; j++) {
-            const int y = y0 + (kScNT / kScTX) * j;
-            if (y < a.H) {
-                const size_t o = (size_t)y * a.W + x;
-                if (lin) {  // the |p|^2 psi terms of the linear form, summed over positions: P^2 D psi
-                    const float2 pv = __ldg(psi + o);
-                    const float dd = __ldg(D + o);
-                    acc[j].x = fmaf(p2 * dd, pv.x, acc[j].x);
-                    acc[j].y = fmaf(p2 * dd, pv.y, acc[j].y);
-                    pd = fmaf(dd, fmaf(pv.x, pv.x, pv.y * pv.y), pd);
-                }
-                out[o] = acc[j];
-                if (dy) {
-                    const float2 e = __ldg(ep + o), g0 = __ldg(gp + o);
-                    gg = fmaf(acc[j].x, acc[j].x, fmaf(acc[j].y, acc[j].y, gg));
-                    den = fmaf(e.x, acc[j].x - g0.x, fmaf(e.y, acc[j].y - g0.y, den));
-                }
-            }
-        }
-    }
-    if (dy) {
-        float v[3] = {gg, den, pd};
-        block_sum_ff<kScNT, 3>(v, red, tot);
-        if (threadIdx.x < 3) part[3 * b + threadIdx.x] = tot[threadIdx.x];  // [ntiles][3]
-    }
+    scatter_tail<kScNT, kScNJ, kScNT / kScTX>(a, acc, x, y0, b, lin, out, dy, ep, gp, part, psi, D, p2, red, tot);
 }
 
 // Illumination map D(x) = sum over positions k covering x of |p(x - r_k)|^2 (p the stored

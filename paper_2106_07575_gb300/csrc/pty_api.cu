@@ -74,6 +74,8 @@ struct pty_ctx {
 
     // CG state and scratch (device)
     float2 *w = nullptr;        // [K][P][P] per-pattern adjoint results
+    alignas(64) unsigned char wmap[128] = {};  // tensor map of w for the tensor-copy scatter-add
+    bool wmap_ok = false;
     float2 *fpart = nullptr;    // [K * CS] float-float partial sums
     float2 *part_sc = nullptr;  // [ntiles][3]
     float2 *part_ls = nullptr;  // [L+2][K * CS]
@@ -99,7 +101,7 @@ struct pty_ctx {
 
     // tensor-core DFT form (opts.dft != 0)
     uint8_t *tc_img_fwd = nullptr, *tc_img_inv = nullptr;
-    int *tc_err = nullptr;
+    int *tc_err = nullptr;  // a bounded device wait gave up (tensor-core DFT, tensor-copy scatter)
     float2 *tc_x = nullptr, *tc_t = nullptr, *tc_u = nullptr;  // [K][P][P] work buffers
     float2 *tc_pars = nullptr;                                  // [2][K] Parseval sums
 
@@ -216,6 +218,25 @@ pty::ScatterPlan scatter_plan(const pty_ctx *c)
     p.tile_list = c->tile_list;
     p.tile_view = c->tile_view;
     return p;
+}
+
+// A device wait of the call gave up (flag read after the call's synchronisation): clear the
+// flag and report it.
+int check_wait_error(pty_ctx *c, int herr)
+{
+    if (!herr) return PTY_OK;
+    cudaMemsetAsync(c->tc_err, 0, sizeof(int), c->s);
+    return fail(c, PTY_ERR_TIMEOUT, "a bounded device wait timed out (tensor-core DFT or tensor-copy scatter-add)");
+}
+
+// The scatter-add of c->w: by tensor copies when the context has the tensor map of w.
+cudaError_t scatter(pty_ctx *c, const pty::PatternArgs &a, const pty::ScatterPlan &plan, float2 *out, int dy,
+                    float2 *part, const DevState *st, const float2 *psi = nullptr, const float *D = nullptr)
+{
+    if (c->wmap_ok)
+        return pty::launch_scatter_tma(c->P, c->wmap, a, plan, out, dy, c->eta_prev, c->g_prev, part, st, c->s, psi, D,
+                                       c->tc_err, pty::tc_wait_limit());
+    return pty::launch_scatter(c->P, a, plan, c->w, out, dy, c->eta_prev, c->g_prev, part, st, c->s, psi, D);
 }
 
 pty::ViewMap view_map(const pty_ctx *c)
@@ -402,7 +423,7 @@ int launch_iteration(pty_ctx *c, bool timed)
         }
         {
             StageTimer t(c, 1, timed);
-            CK(pty::launch_scatter(c->P, a, plan, c->w, c->g, 1, c->eta_prev, c->g_prev, c->part_sc, c->st, c->s));
+            CK(scatter(c, a, plan, c->g, 1, c->part_sc, c->st));
         }
         {
             StageTimer t(c, 3, timed);
@@ -443,8 +464,7 @@ int launch_iteration(pty_ctx *c, bool timed)
     }
     {
         StageTimer t(c, 1, timed);
-        CK(pty::launch_scatter(c->P, a, plan, c->w, c->g, 1, c->eta_prev, c->g_prev, c->part_sc, c->st, c->s, c->psi,
-                               c->illum));
+        CK(scatter(c, a, plan, c->g, 1, c->part_sc, c->st, c->psi, c->illum));
     }
     {
         StageTimer t(c, 3, timed);
@@ -778,6 +798,11 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     CKC(dalloc(&c->tile_start, (size_t)ntiles + 1));
     CKC(dalloc(&c->tile_list, std::max<size_t>(list.size(), 1)));
     CKC(dalloc(&c->w, (size_t)K * PP));
+    CKC(dalloc(&c->tc_err, (size_t)1));
+    CKC(cudaMemset(c->tc_err, 0, sizeof(int)));
+    // scatter-add by tensor copies unless the driver cannot describe w (or opts.flags bit 4)
+    c->wmap_ok = !(o.flags & 16) && pty::scatter_tma_map_bytes() <= sizeof(c->wmap) &&
+                 pty::make_scatter_tma_map(c->wmap, c->w, P, (int)K);
     CKC(dalloc(&c->fpart, (size_t)K * c->CSmax));
     CKC(dalloc(&c->part_sc, (size_t)ntiles * 3));
     CKC(dalloc(&c->hash, (size_t)V));
@@ -870,8 +895,6 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
         CKC(pty::tc_dft_images(P, bf16, +1, img));
         CKC(dalloc(&c->tc_img_inv, img.size()));
         CKC(cudaMemcpy(c->tc_img_inv, img.data(), img.size(), cudaMemcpyHostToDevice));
-        CKC(dalloc(&c->tc_err, (size_t)1));
-        CKC(cudaMemset(c->tc_err, 0, sizeof(int)));
         CKC(dalloc(&c->tc_x, (size_t)K * PP));
         CKC(dalloc(&c->tc_t, (size_t)K * PP));
         CKC(dalloc(&c->tc_u, (size_t)K * PP));
@@ -984,8 +1007,7 @@ int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
     if (c->tc_err) CK(cudaMemcpyAsync(hs.err, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     if ((st = views_out(c, psi, c->psi))) return st;
     if ((st = sync(c))) return st;
-    const int herr = *hs.err;
-    if (herr) return fail(c, PTY_ERR_TIMEOUT, "tensor-core DFT: a device wait timed out");
+    if ((st = check_wait_error(c, *hs.err))) return st;
     read_reports(c, niter, rep, hs);
     for (int v = 0; v < c->V; v++)
         if (hs.st[v].stalled)
@@ -1087,11 +1109,13 @@ int pty_adjoint(pty_ctx *c, const float *y, float *x)
     }
     pty::PatternArgs a = pattern_args(c);
     CK(c->impl->adjoint(a, dy, c->w, c->s));
-    CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, c->stage_obj, 0, nullptr, nullptr, nullptr, nullptr,
-                           c->s));
+    CK(scatter(c, a, scatter_plan(c), c->stage_obj, 0, nullptr, nullptr));
     float *xo[1] = {x};
     if ((st = views_out(c, xo, c->stage_obj))) return st;
-    return sync(c);
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    if ((st = sync(c))) return st;
+    return check_wait_error(c, herr);
 }
 
 int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
@@ -1109,8 +1133,7 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
     } else {
         CK(c->impl->grad(a, c->stage_obj, c->w, c->fpart, nullptr, c->s));
     }
-    CK(pty::launch_scatter(c->P, a, scatter_plan(c), c->w, c->stage_obj2, 0, nullptr, nullptr, nullptr, nullptr,
-                           c->s));
+    CK(scatter(c, a, scatter_plan(c), c->stage_obj2, 0, nullptr, nullptr));
     const int fcols = c->opts.dft != 0 ? 0 : c->impl->grad_cols(a);
     CK(pty::launch_sum(c->fpart, fcols > 0 ? fcols : c->K * c->CS, c->dscalar, c->s));
     if (grad) {
@@ -1118,8 +1141,11 @@ int pty_gradient(pty_ctx *c, const float *psi, float *grad, double *F)
         if ((st = views_out(c, go, c->stage_obj2))) return st;
     }
     double hF = 0.0;
+    int herr = 0;
     CK(cudaMemcpyAsync(&hF, c->dscalar, sizeof(double), cudaMemcpyDeviceToHost, c->s));
+    CK(cudaMemcpyAsync(&herr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->s));
     if ((st = sync(c))) return st;
+    if ((st = check_wait_error(c, herr))) return st;
     if (F) *F = hF;
     return PTY_OK;
 }

@@ -199,6 +199,16 @@ struct ViewMap {
 // plus P^2 D psi for views in the linear form (st->lin; psi, D the object and illumination).
 // With dy != 0 also part[b] = (sum |out|^2, sum Re conj(eta_prev) (out - g_prev),
 // linear form ? sum D |psi|^2 : 0) per tile b ([ntiles][3]).
+// Scatter-add with the per-pattern results fetched by tensor copies (scatter_tma.cu): map is
+// a tensor map of w [K][P][P] (scatter_tma_map_bytes() bytes, 64-byte aligned, made by
+// make_scatter_tma_map, false if the driver cannot); same sums in the same order as
+// launch_scatter.  A bounded wait that gives up sets *err.
+size_t scatter_tma_map_bytes();
+bool make_scatter_tma_map(void *map, const float2 *w, int P, int K);
+cudaError_t launch_scatter_tma(int P, const void *map, const PatternArgs &a, const ScatterPlan &plan, float2 *out,
+                               int dy, const float2 *eta_prev, const float2 *g_prev, float2 *part,
+                               const DevState *st, cudaStream_t s, const float2 *psi, const float *D, int *err,
+                               long long spin_limit);
 cudaError_t launch_scatter(int P, const PatternArgs &a, const ScatterPlan &plan, const float2 *w,
                            float2 *out, int dy, const float2 *eta_prev, const float2 *g_prev,
                            float2 *part, const DevState *st, cudaStream_t s, const float2 *psi = nullptr,

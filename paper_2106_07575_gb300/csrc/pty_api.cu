@@ -526,9 +526,11 @@ void build_graph(pty_ctx *c)
     }
 }
 
-// The autotuner: time the GRAD and LS pattern passes of every configuration for P on the
-// context's own data (psi = 1, eta = 0, a 16-candidate window) and keep the fastest of
-// each.  The choice is cached per problem shape for the life of the process, so contexts of
+// The autotuner: time the GRAD pass in its linear form (the form of all but every 64th
+// iteration) and the LS pattern pass of every configuration for P on the context's own data
+// (entries' u = v = 0, eta = 0, a 16-candidate window; the minimum of three runs each) and
+// keep the fastest of each.  The first iteration of every solve runs the full form, which
+// recomputes u at the entries.  The choice is cached per problem shape for the life of the process, so contexts of
 // the same problem use the same kernels (and give the same bits).
 struct PlanKey {
     int P, H, W, K, V;
@@ -561,8 +563,12 @@ int autotune(pty_ctx *c)
         const size_t HW = (size_t)c->HA * c->WA;
         std::vector<float2> ones(HW, make_float2(1.f, 0.f));
         CK(cudaMemcpyAsync(c->psi, ones.data(), sizeof(float2) * HW, cudaMemcpyHostToDevice, c->s));
+        CK(cudaMemsetAsync(c->nz_u, 0, sizeof(float2) * (size_t)std::max<long long>(c->n_entries, 1), c->s));
+        CK(cudaMemsetAsync(c->nz_v, 0, sizeof(float2) * (size_t)std::max<long long>(c->n_entries, 1), c->s));
         std::vector<DevState> hs(c->V);
         for (auto &h : hs) {
+            h.lin = 1;  // the linear form runs
+            h.last_gamma = 0.5;
             h.Leff = 16;
             h.Lsel = 16;
             for (int l = 0; l < 16; l++) {
@@ -578,27 +584,29 @@ int autotune(pty_ctx *c)
         float tg = 1e30f, tl = 1e30f;
         cudaError_t err = cudaSuccess;
         for (int j = 0; j < n && err == cudaSuccess; j++) {
-            float ms = 0.f;
-            for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
+            float mg = 1e30f, ml = 1e30f, ms = 0.f;
+            for (int rep = 0; rep < 3 && err == cudaSuccess; rep++) {
                 err = cudaEventRecord(e0, c->s);
-                if (err == cudaSuccess) err = impls[j].grad(a, c->psi, c->w, c->fpart, nullptr, c->s);
+                if (err == cudaSuccess) err = impls[j].grad_lin(a, c->w, c->fpart, c->st, c->s);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, c->s);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (err == cudaSuccess) mg = std::min(mg, ms);
             }
-            if (err == cudaSuccess && ms < tg) {
-                tg = ms;
+            if (err == cudaSuccess && mg < tg) {
+                tg = mg;
                 best_g = j;
             }
-            for (int rep = 0; rep < 2 && err == cudaSuccess; rep++) {
+            for (int rep = 0; rep < 3 && err == cudaSuccess; rep++) {
                 err = cudaEventRecord(e0, c->s);
                 if (err == cudaSuccess) err = impls[j].ls(a, c->eta, c->part_ls, c->st, c->s);
                 if (err == cudaSuccess) err = cudaEventRecord(e1, c->s);
                 if (err == cudaSuccess) err = cudaEventSynchronize(e1);
                 if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+                if (err == cudaSuccess) ml = std::min(ml, ms);
             }
-            if (err == cudaSuccess && ms < tl) {
-                tl = ms;
+            if (err == cudaSuccess && ml < tl) {
+                tl = ml;
                 best_l = j;
             }
         }

@@ -7,10 +7,13 @@
 //                 bitwise reproducible.  Optionally fuses the two reductions of the
 //                 Dai-Yuan coefficient (Eq. 6): ||g||^2 and Re <eta_prev, g - g_prev>.
 //   k_dy_finalize DIR stage scalars (Eq. 6, with the restart rule) and F(psi_m) (Eq. 2).
+//   k_ls_certify  LS stage: leading trials rejected by the Jensen lower bound of the
+//                 objective change, then the first exact window.
 //   k_ls_decide   LS stage decision (Eq. 7): the first candidate of the window that does
 //                 not increase the objective, else open the next window or stall.
 //   k_update      Update stage (Eq. 5): psi += gamma eta, keeping eta and g for Eq. 6.
-// All sums of partials run in FP64 in a fixed order.
+// All sums of partials run in float-float (reduce.cuh) in a fixed order; the scalar
+// decisions are taken in FP64 from them.
 #include <cmath>
 
 #include "pty_internal.h"

@@ -10,16 +10,19 @@
 //   k_grad_lin     GRAD stage in the linear form: u updated at the entries from the kept
 //                  v = G eta of the last step, one inverse DFT of the sparse correction
 //   k_ls_fft       LS stage, once per iteration: v = G eta for one pattern, kept at the
-//                  detector pixels with counts, and the two Parseval sums that the change
-//                  of the objective needs at the other pixels (the candidate windows run
-//                  on the kept values: ls_entries.cu)
+//                  detector pixels with counts, the two Parseval sums that the change
+//                  of the objective needs at the other pixels, and the Jensen lower bounds
+//                  of that change at the leading trials (certificate rows; the candidate
+//                  windows run on the kept values: ls_entries.cu)
 //   k_nz_*         create time: the compact list of detector pixels with counts
 //
 // The forward DFT leaves the spectrum in the permuted slot order of fft_tile.cuh, in
 // column slabs; the measured data are stored in that order ("entries", one contiguous
 // range per CTA of a pattern), and the inverse DFT returns to natural order, so no
 // separate reordering pass exists.  Per-pattern sums are produced per CTA; the small
-// reduction kernels add the CS partials of a pattern like any others.
+// reduction kernels add the CS partials of a pattern like any others.  Persistent
+// single-CTA passes of one view sum their partials per thread over the CTA's patterns and
+// write one column per CTA, and keep their threads' probe values in tensor memory.
 #pragma once
 #include "fft_tile.cuh"
 #include "mathx.cuh"

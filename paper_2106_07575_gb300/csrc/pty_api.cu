@@ -11,10 +11,12 @@
 // window, the stall flag) are per view.
 //
 // One CG iteration (Algorithm 1 of the paper, single GPU) is a fixed launch sequence:
-//   GRAD   k_grad (per pattern) -> k_scatter (per object tile, fused Eq. 6 reductions)
-//   DIR    k_dy_finalize (per view: Dai-Yuan coefficient, objective F(psi_m))
-//   LS     windows of (k_ls per pattern -> k_ls_decide per view) until a step is accepted
-//   Update k_update
+//   GRAD   k_grad (full form) or k_grad_lin (linear form) per pattern -> k_scatter_tma (per
+//          object tile, by tensor copies, fused Eq. 6 reductions)
+//   DIR    k_dy_finalize (per view: Dai-Yuan coefficient, objective F(psi_m)) -> k_eta
+//   LS     k_ls_fft per pattern (G eta at the pixels with counts, certificate rows) ->
+//          k_ls_certify -> windows of (k_ls_entries -> k_ls_decide) until a step is accepted
+//   Update k_update, k_update_counters
 // with every decision taken on the device.  The sequence is captured once as a CUDA graph
 // and replayed per iteration; the host synchronises once per call.
 #include <cuda_runtime.h>

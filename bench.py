@@ -166,6 +166,21 @@ def fft2_flops(P):
     return 5.0 * n * math.log2(n)
 
 
+def over_ranks(dist, ms, units, device):
+    """The job's time and work over all ranks (one process per GPU, each a replica of the
+    path): the slowest rank's time and the sum of the ranks' units; every rank receives
+    both.  dist None: one process, returned as given."""
+    if dist is None:
+        return ms, units
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args, rank):
     """FP64 CPU oracle on the host cores, one bounded sample of the workload per step."""
     if rank != 0:
@@ -396,12 +411,8 @@ def main():
     clocks = clk.stop()
     if dist:
         dist.barrier()
-    ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     steps_done = rep["iters_done"]
+    ms, units = over_ranks(dist, t_start.elapsed_time(t_end), p.K * steps_done, "cuda")
     plan = ctx.plan()
     ctx.close()
 
@@ -450,7 +461,7 @@ def main():
     # and 32-candidate entry kernels, all but one returning at once, after the certificate
     # kernel), update + counters; per call: 2 hashes, hash check, begin, hash store
     launches = args.steps * (8 + 2 * nwin + (3 if L == 0 else 0)) + 5 if args.dft == 0 else None
-    value = world * K * steps_done / (ms * 1e-3)
+    value = units / (ms * 1e-3)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -481,13 +492,9 @@ def main():
         for _ in range(args.steps):
             ctx2.cg_solve(psi_h, 1)
         ctx2.close()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s, e2e_units = over_ranks(dist, time.perf_counter() - t0, K * args.steps, "cuda")
         once = d_h.nbytes + probe_h.nbytes + pos_h.nbytes
-        out["e2e"] = {"value": world * K * args.steps / e2e_s, "unit": UNIT,
+        out["e2e"] = {"value": e2e_units / e2e_s, "unit": UNIT,
                       "h2d_bytes_per_step": int(psi_h.nbytes + once / args.steps),
                       "d2h_bytes_per_step": int(psi_h.nbytes + 8 * 4 + 4),
                       "note": "pty_create from host arrays + one pty_cg_solve(niter=1) per step with host psi"}

@@ -165,6 +165,13 @@ _F = ("float32",)
 _I = ("int32",)
 
 
+def _need(a, n, what):
+    """The library reads or writes exactly n elements behind a's pointer: a must hold n."""
+    m = int(a.numel()) if hasattr(a, "numel") else int(np.asarray(a).size)
+    if m != n:
+        raise ValueError(f"{what}: {m} elements, expected {n}")
+
+
 def default_opts() -> pty_opts:
     o = pty_opts()
     load().pty_default_opts(ctypes.byref(o))
@@ -340,10 +347,15 @@ class BatchContext:
         """views: list of (H, W, pos [K][2] int32, data [K][P][P] float32) on one device or the host."""
         import torch
 
-        self.P = probe.shape[0]
+        self.P = P = probe.shape[0]
+        _need(probe, P * P, "probe")
         Hs = [v[0] for v in views]
         Ws = [v[1] for v in views]
         Ks = [v[2].shape[0] for v in views]
+        for i, (_, _, q, d) in enumerate(views):
+            _need(q, 2 * q.shape[0], f"view {i} pos")
+            _need(d, q.shape[0] * P * P, f"view {i} data")
+        self.shapes = list(zip(Hs, Ws))
         pos = torch.cat([torch.as_tensor(v[2]) for v in views]).contiguous()
         data = torch.cat([torch.as_tensor(v[3]) for v in views]).contiguous()
         if data.is_cuda is False and probe.is_cuda:
@@ -363,6 +375,10 @@ class BatchContext:
             pass
 
     def cg_solve(self, psis, niter):
+        if len(psis) != len(self.shapes):
+            raise ValueError(f"{len(psis)} objects for {len(self.shapes)} views")
+        for i, (x, (H, W)) in enumerate(zip(psis, self.shapes)):
+            _need(x, H * W, f"view {i} psi")
         return pty_batch_cg_solve(self.ctx, psis, niter)
 
     def plan(self):
@@ -386,6 +402,9 @@ class Context:
     def __init__(self, probe, pos, data, H, W, opts: pty_opts | None = None, stream=None):
         P = probe.shape[0]
         K = pos.shape[0]
+        _need(probe, P * P, "probe")
+        _need(pos, 2 * K, "pos")
+        _need(data, K * P * P, "data")
         self.shape = (H, W)
         self.P, self.K = P, K
         self._keep = (probe, pos, data)  # borrowed device data must outlive the context
@@ -402,16 +421,29 @@ class Context:
         except Exception:
             pass
 
+    def _object(self, a, what):
+        _need(a, self.shape[0] * self.shape[1], what)
+
+    def _patterns(self, a, what):
+        _need(a, self.K * self.P * self.P, what)
+
     def forward(self, psi, out):
+        self._object(psi, "psi")
+        self._patterns(out, "out")
         return pty_forward(self.ctx, psi, out)
 
     def adjoint(self, y, x):
+        self._patterns(y, "y")
+        self._object(x, "x")
         return pty_adjoint(self.ctx, y, x)
 
     def gradient(self, psi, grad):
+        self._object(psi, "psi")
+        self._object(grad, "grad")
         return pty_gradient(self.ctx, psi, grad)
 
     def cg_solve(self, psi, niter, report=True):
+        self._object(psi, "psi")
         return pty_cg_solve(self.ctx, psi, niter, report)
 
     def cg_reset(self):

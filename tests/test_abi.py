@@ -66,3 +66,36 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     with pytest.raises(pty.PtyError) as e:
         pty.pty_create(256, 256, 64, probe, 1, pos, data, o)
     assert e.value.status == pty.PTY_ERR_ARG
+
+
+def test_binding_checks_array_sizes_before_the_library():
+    """The wrappers know the problem's shapes: an array of the wrong size raises ValueError on
+    the host; an array of the right size reaches the library (here a NULL context, which the
+    library rejects before any CUDA call)."""
+    import numpy as np
+    from paper_2106_07575_gb300 import pty
+
+    probe = np.ones((64, 64), np.complex64)
+    pos = np.zeros((2, 2), np.int32)
+    with pytest.raises(ValueError):
+        pty.Context(probe, pos, np.ones((1, 64, 64), np.float32), 256, 256)
+    with pytest.raises(ValueError):
+        pty.Context(probe, np.zeros((2, 3), np.int32), np.ones((2, 64, 64), np.float32), 256, 256)
+    with pytest.raises(ValueError):
+        pty.Context(np.ones((64, 32), np.complex64), pos, np.ones((2, 64, 64), np.float32), 256, 256)
+    with pytest.raises(ValueError):
+        pty.BatchContext(probe, [(256, 256, pos, np.ones((3, 64, 64), np.float32))])
+
+    c = pty.Context.__new__(pty.Context)
+    c.shape, c.P, c.K, c.ctx = (256, 200), 64, 2, None
+    obj, pats = np.ones((256, 200), np.complex64), np.ones((2, 64, 64), np.complex64)
+    for call in (lambda: c.forward(obj[:100], pats), lambda: c.forward(obj, pats[:1]),
+                 lambda: c.adjoint(pats, obj.T[:10]), lambda: c.gradient(obj, obj[:, :199]),
+                 lambda: c.cg_solve(np.ones((200, 256, 2), np.complex64), 1)):
+        with pytest.raises(ValueError):
+            call()
+    for call in (lambda: c.forward(obj, pats), lambda: c.adjoint(pats, obj), lambda: c.gradient(obj, obj.copy()),
+                 lambda: c.cg_solve(obj, 1)):
+        with pytest.raises(pty.PtyError) as e:
+            call()
+        assert e.value.status == pty.PTY_ERR_ARG

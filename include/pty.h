@@ -148,8 +148,9 @@ PTY_API int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const flo
 /* Release every resource of the context (NULL is ignored). */
 PTY_API void pty_destroy(pty_ctx *ctx);
 
-/* Description of the last error on this context (or of the last failed pty_create when
- * ctx is NULL).  The string lives until the next call on the same context. */
+/* Description of the last error on this context, or with ctx NULL of the last failed call
+ * without a usable context (pty_create, pty_batch_create, a NULL ctx) on the calling thread.
+ * The string lives until the next call on the same context (or on the same thread). */
 PTY_API const char *pty_last_error(const pty_ctx *ctx);
 
 /*

@@ -47,7 +47,7 @@ struct pty_cnn {
 
 namespace {
 
-std::string g_cnn_create_err;
+thread_local std::string g_cnn_create_err;  // last failed call without a network, per thread
 
 int fail(pty_cnn *n, int code, const char *fmt, ...)
 {

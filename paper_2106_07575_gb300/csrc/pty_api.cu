@@ -124,7 +124,8 @@ struct pty_ctx {
     int64_t stage_n[5] = {0, 0, 0, 0, 0};
 };
 
-static std::string g_create_err;
+// message of the last failed call without a context, per calling thread
+static thread_local std::string g_create_err;
 
 namespace {
 

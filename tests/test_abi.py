@@ -99,3 +99,35 @@ def test_binding_checks_array_sizes_before_the_library():
         with pytest.raises(pty.PtyError) as e:
             call()
         assert e.value.status == pty.PTY_ERR_ARG
+
+
+def test_create_error_message_is_per_thread():
+    """The message of a failed pty_create belongs to the calling thread."""
+    import threading
+
+    import numpy as np
+    from paper_2106_07575_gb300 import pty
+
+    lib = pty.load()
+    probe = np.ones((64, 64), np.complex64)
+    pos = np.zeros((1, 2), np.int32)
+    data = np.ones((1, 64, 64), np.float32)
+    with pytest.raises(pty.PtyError):
+        pty.pty_create(256, 256, 48, probe, 1, pos, data)
+    mine = lib.pty_last_error(None).decode()
+    assert "P=48" in mine
+    other = {}
+
+    def worker():
+        o = pty.default_opts()
+        o.tau = 1.5
+        try:
+            pty.pty_create(256, 256, 64, probe, 1, pos, data, o)
+        except pty.PtyError:
+            other["msg"] = lib.pty_last_error(None).decode()
+
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert "invalid options" in other["msg"]
+    assert lib.pty_last_error(None).decode() == mine

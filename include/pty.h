@@ -156,6 +156,9 @@ PTY_API const char *pty_last_error(const pty_ctx *ctx);
 /*
  * Forward model, Eq. 1: out[k] = F(p * patch_k(psi)), unitary F, for every position k
  * in the caller's order.  psi [H][W] complex, out [K][P][P] complex.
+ * Errors: PTY_ERR_ARG (NULL ctx or array), PTY_ERR_UNSUPPORTED (batch context),
+ * PTY_ERR_NOMEM (staging of host arrays), PTY_ERR_TIMEOUT (dft = 1, 2: a bounded device
+ * wait gave up), PTY_ERR_CUDA.
  */
 PTY_API int pty_forward(pty_ctx *ctx, const float *psi, float *out);
 
@@ -163,12 +166,16 @@ PTY_API int pty_forward(pty_ctx *ctx, const float *psi, float *out);
  * Adjoint of the forward model, the G^H of Eq. 3: x = sum_k shift_k(conj(p) * F^H y_k).
  * y [K][P][P] complex (natural DFT order), x [H][W] complex.  The scatter-add of
  * overlapping patches is summed in a fixed order: results are bitwise reproducible.
+ * Errors: PTY_ERR_ARG, PTY_ERR_UNSUPPORTED (batch context, or dft != 0), PTY_ERR_NOMEM,
+ * PTY_ERR_TIMEOUT (a bounded wait of the tensor-copy scatter-add gave up), PTY_ERR_CUDA.
  */
 PTY_API int pty_adjoint(pty_ctx *ctx, const float *y, float *x);
 
 /*
  * Objective and gradient, Eq. 2 and 3, at psi.  grad [H][W] complex (may be NULL to get
  * only the objective); F receives the objective (may be NULL).  Bitwise reproducible.
+ * Errors: PTY_ERR_ARG (NULL ctx or psi), PTY_ERR_UNSUPPORTED (batch context),
+ * PTY_ERR_NOMEM, PTY_ERR_TIMEOUT, PTY_ERR_CUDA.
  */
 PTY_API int pty_gradient(pty_ctx *ctx, const float *psi, float *grad, double *F);
 
@@ -182,6 +189,8 @@ PTY_API int pty_gradient(pty_ctx *ctx, const float *psi, float *grad, double *F)
  * accepted).  The iteration runs without host synchronisation between its stages; it is
  * captured once as a CUDA graph and replayed (unless opts.flags bit 0 asks for per-stage
  * timing).  Needs a single-view context.
+ * Errors: PTY_ERR_ARG (NULL ctx or psi, niter < 0), PTY_ERR_UNSUPPORTED (batch context),
+ * PTY_ERR_NOMEM, PTY_ERR_TIMEOUT (a bounded device wait gave up), PTY_ERR_CUDA.
  * Linear form (FFT path, opts.dft = 0): Eq. 1 is linear in psi, so after an accepted step
  * G psi_{m+1} = G psi_m + gamma G eta_m; the model G psi at the detector pixels with counts
  * is then updated in place from the line search's G eta instead of by a forward DFT, and
@@ -214,13 +223,15 @@ PTY_API int pty_batch_create(pty_ctx **out, int32_t n_views, const int32_t *H, c
  * to that view's [H_v][W_v] complex object (host or device memory), updated in place.
  * reps: host array of n_views reports, or NULL.  Returns PTY_STALLED if any view stalled
  * (that view keeps its last accepted iterate; the others complete their iterations).
+ * Errors as pty_cg_solve (PTY_ERR_ARG also for a NULL psi[v]).
  */
 PTY_API int pty_batch_cg_solve(pty_ctx *ctx, float *const *psi, int32_t niter, pty_cg_report *reps);
 
 /* Number of views of a context (1 for pty_create). */
 PTY_API int32_t pty_num_views(const pty_ctx *ctx);
 
-/* Forget the conjugate-gradient state: the next pty_cg_solve starts with eta = -g. */
+/* Forget the conjugate-gradient state: the next pty_cg_solve starts with eta = -g.
+ * Errors: PTY_ERR_ARG (NULL ctx), PTY_ERR_CUDA. */
 PTY_API int pty_cg_reset(pty_ctx *ctx);
 
 /*

@@ -99,7 +99,7 @@ def ls_pass_traffic(P, plan_ls):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["pty", "reference"], default="pty")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -100,8 +100,9 @@ typedef struct {
                             pty_create (the GRAD and LS passes of every configuration for P are
                             timed on the problem's own data; the choice is cached per problem
                             shape for the process); 0.. = one fixed configuration for P
-                            (P=64: 0; P=128: 0 one CTA, 1 cluster of 2, 2 cluster of 4;
-                            P=256: 0 cluster of 8, 1 cluster of 4) */
+                            (P=64: 0 one CTA of 256 threads; P=128: 0 one CTA of 512
+                            threads, 1 cluster of 2, 2 cluster of 4, 3 one CTA of 1024
+                            threads; P=256: 0 cluster of 8, 1 cluster of 4) */
     int32_t dft;         /* 2-D DFTs: 0 (default) FP32 FFT on the CUDA cores; 1 batched complex
                             GEMMs on the tensor cores with operands split into BF16 hi + lo and
                             FP32 accumulation; 2 the same with FP16 hi + lo.  1 and 2 need

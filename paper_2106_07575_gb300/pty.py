@@ -2,8 +2,17 @@
 
 Every computation runs in the CUDA library; this module converts Python arguments
 (torch tensors on the GPU or the CPU, or numpy arrays) into the raw pointers and sizes
-of the C ABI, and turns status codes into exceptions.  There is no fallback: if the
-library cannot be built or loaded, importing the functions raises.
+of the C ABI, checks that each array holds the number of elements the call reads or
+writes, and turns status codes into exceptions.  There is no fallback: if the library
+cannot be built or loaded, importing the functions raises.
+
+Use (one reconstruction on the current CUDA device)::
+
+    ctx = Context(probe, pos, data, H, W)      # probe [P][P] complex64, pos [K][2] int32,
+                                               # data [K][P][P] float32 counts
+    psi = torch.ones((H, W), dtype=torch.complex64, device="cuda")
+    status, report = ctx.cg_solve(psi, 64)     # 64 ML-CG iterations, psi updated in place
+    ctx.close()
 """
 from __future__ import annotations
 

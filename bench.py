@@ -430,8 +430,10 @@ def main():
     tctx.close()
     n_it = max(trep["iters_done"], 1)
 
-    # roofline of the dominant kernel, the LS pattern pass k_ls_fft (FP32 ALU bound: one 2-D
-    # FFT per pattern on the CUDA cores; one launch per iteration covers all K patterns).
+    # roofline of the LS pattern pass k_ls_fft, one of the two largest kernels with the linear
+    # GRAD pass (whose time and rate go to "other"), and the one with a current traffic
+    # capture (FP32 ALU bound: one 2-D FFT per pattern on the CUDA cores; one launch per
+    # iteration covers all K patterns).
     # Algorithmic flops: 5 N log2 N per 2-D DFT (N = P^2) plus the probe product (6 N) and,
     # at the n_e detector pixels with counts, the two Parseval sums (8 per pixel).
     P, K = p.P, p.K

@@ -45,7 +45,9 @@ class OrcOpts:
 
 
 def build(force: bool = False) -> str:
-    """Compile orc.c into _lib/liborc-<hash>.so with gcc (-O2, OpenMP); return its path."""
+    """Compile orc.c into _lib/liborc-<hash>.so with gcc (-O2, OpenMP); return its path.
+
+    Earlier builds (another source hash) are deleted, so _lib/ holds one library."""
     src = open(_SRC, "rb").read()
     tag = hashlib.sha1(src).hexdigest()[:12]
     os.makedirs(_LIBDIR, exist_ok=True)
@@ -53,8 +55,19 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(out):
         tmp = out + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, out)
+        try:
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, out)
+        finally:
+            if os.path.exists(tmp):
+                os.remove(tmp)
+    for name in os.listdir(_LIBDIR):
+        path = os.path.join(_LIBDIR, name)
+        if name.startswith("liborc-") and name.endswith(".so") and path != out:
+            try:
+                os.remove(path)
+            except OSError:
+                pass
     return out
 
 

@@ -48,39 +48,88 @@ def lib_path() -> str:
     return os.path.join(LIBDIR, f"libpty-{_digest()}.so")
 
 
+def _prune(keep: str) -> None:
+    """Delete every superseded build product under _lib/ (older libraries, partial links,
+    object folders of earlier or failed builds), keeping only ``keep``."""
+    if not os.path.isdir(LIBDIR):
+        return
+    for name in os.listdir(LIBDIR):
+        path = os.path.join(LIBDIR, name)
+        if path == keep:
+            continue
+        if name.startswith("obj-") and os.path.isdir(path):
+            # another process may be compiling into its own obj-<pid> right now
+            pid = name[4:]
+            if pid.isdigit() and int(pid) != os.getpid() and _alive(int(pid)):
+                continue
+            shutil.rmtree(path, ignore_errors=True)
+        elif name.startswith("libpty-") and (name.endswith(".so") or ".so.tmp" in name):
+            if ".so.tmp" in name:
+                pid = name.rsplit(".so.tmp", 1)[1]
+                if pid.isdigit() and int(pid) != os.getpid() and _alive(int(pid)):
+                    continue
+            try:
+                os.remove(path)
+            except OSError:
+                pass
+
+
+def _alive(pid: int) -> bool:
+    try:
+        os.kill(pid, 0)
+    except ProcessLookupError:
+        return False
+    except PermissionError:
+        return True
+    return True
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
-    """Compile (if needed) and return the path of libpty.so."""
+    """Compile (if needed) and return the path of libpty.so.
+
+    Only the current library is kept under _lib/: every earlier build (a different source
+    hash) and every object folder is deleted after a successful link, and the object
+    folder of this build is deleted whether or not nvcc succeeds.
+    """
     out = lib_path()
     if os.path.exists(out) and not force:
+        _prune(out)
         return out
     os.makedirs(LIBDIR, exist_ok=True)
     tmpdir = os.path.join(LIBDIR, f"obj-{os.getpid()}")
     os.makedirs(tmpdir, exist_ok=True)
-    cc = nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_verbose else []
-    procs, objs = [], []
-    for src in _sources():
-        obj = os.path.join(tmpdir, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
-        objs.append(obj)
-    errors = []
-    for src, p in procs:
-        o, _ = p.communicate()
-        if p.returncode != 0 or (ptxas_verbose and o):
-            (errors if p.returncode else [None]).append(None)
-            sys.stderr.write(o.decode(errors="replace"))
-            if p.returncode:
-                errors.append(src)
-    if any(errors):
-        raise RuntimeError(f"nvcc failed for {[e for e in errors if e]}")
-    tmp = out + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, out)
-    shutil.rmtree(tmpdir, ignore_errors=True)
+    try:
+        cc = nvcc()
+        extra = ["-Xptxas", "-v"] if ptxas_verbose else []
+        procs, objs = [], []
+        for src in _sources():
+            obj = os.path.join(tmpdir, os.path.basename(src) + ".o")
+            cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+            objs.append(obj)
+        failed = []
+        for src, p in procs:
+            o, _ = p.communicate()
+            if p.returncode != 0 or (ptxas_verbose and o):
+                sys.stderr.write(o.decode(errors="replace"))
+            if p.returncode != 0:
+                failed.append(src)
+        if failed:
+            raise RuntimeError(f"nvcc failed for {failed}")
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = [cc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs, "-lcudart_static", "-lrt",
+               "-ldl", "-lpthread"]
+        try:
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, out)
+        finally:
+            if os.path.exists(tmp):
+                os.remove(tmp)
+    finally:
+        shutil.rmtree(tmpdir, ignore_errors=True)
+    _prune(out)
     return out
 
 

@@ -272,16 +272,18 @@ PTY_API int pty_stage_times(pty_ctx *ctx, double ms[5], int64_t launches[5], int
  * take the implicit device synchronisation of cudaMalloc/cudaFree.
  *   H, W, P, K   as in pty_create; P is 64 or 128; K <= 16384 and K*P*P <= 4194304.
  *   probe, pos, data, psi   device pointers, layouts as in pty_create / pty_gradient
- *                (data is the dense [K][P][P] array; positions in any order).
+ *                (data is the dense [K][P][P] array; positions in any order); probe, pos,
+ *                psi, grad and F must be 8-byte aligned (they are read as pairs).
  *   eps          the objective's guard (pty_opts.eps).
  *   grad         device [H][W] complex output; F: device double output or NULL.
- *   stream       cudaStream_t (as void*) the work runs on; the call synchronises it.
+ *   stream       cudaStream_t (as void*) of the current device, on which the work runs.
+ *                The call reads a status flag back and synchronises this stream, so it
+ *                cannot be called while the stream is being captured into a CUDA graph.
  * The only scratch is a fixed 32.2 MiB device array inside the library, held on every
  * device where the library's code is loaded until the process exits.  Every call shares
- * it, so calls that overlap on the GPU race; calls ordered on one stream are safe.  The
- * first call on a device looks up the array's address with that device current: make it
- * before any stream capture.
- * Returns PTY_OK; PTY_ERR_ARG for a size beyond the limits, a NULL or host pointer;
+ * it, so calls that overlap on the GPU race; calls ordered on one stream are safe.
+ * Returns PTY_OK; PTY_ERR_ARG for a size beyond the limits, a NULL, host or misaligned
+ * pointer, or a stream of another device;
  * PTY_ERR_BOUNDS if a position puts the patch outside the object (nothing is written);
  * PTY_ERR_CUDA if a CUDA call failed.
  */

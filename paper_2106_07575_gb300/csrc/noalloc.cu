@@ -11,11 +11,14 @@
 // stays there until the process exits.  All calls share it and it keeps the last call's
 // contents, so two calls that overlap on the GPU (different streams or threads, no ordering
 // between them) race on it and give wrong results; calls on one stream are ordered and safe.
-// The first call on a device looks up the array's device address (cudaGetSymbolAddress)
-// with that device current; make that first call before any stream capture.
+// Each call looks up the array's device address on the current device (cudaGetSymbolAddress,
+// once per device), reads a status flag back and synchronises its stream, so it cannot be
+// called while that stream is being captured into a CUDA graph.  The stream must belong to
+// the current device.
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "fft_tile.cuh"
@@ -210,6 +213,9 @@ cudaError_t na_launch(const NaArgs &a, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The kernels read positions as int2 and complex values as float2 / double: 8-byte loads.
+bool na_aligned8(const void *p) { return ((uintptr_t)p & 7) == 0; }
+
 bool na_is_device(const void *p)
 {
     cudaPointerAttributes at;
@@ -233,9 +239,19 @@ extern "C" int pty_gradient_noalloc(int32_t H, int32_t W, int32_t P, const float
     if (!na_is_device(probe) || !na_is_device(pos) || !na_is_device(data) || !na_is_device(psi) ||
         !na_is_device(grad) || (F && !na_is_device(F)))
         return PTY_ERR_ARG;
+    if (!na_aligned8(probe) || !na_aligned8(pos) || !na_aligned8(psi) || !na_aligned8(grad) ||
+        (F && !na_aligned8(F)))
+        return PTY_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return PTY_ERR_CUDA;
+    if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) {
+        cudaGetLastError();
+        return PTY_ERR_ARG;
+    }
+    if (sdev != cur) return PTY_ERR_ARG;
     void *base = nullptr;
     if (na_base(&base) != cudaSuccess) return PTY_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
     NaArgs a;
     a.base = (unsigned char *)base;
     a.H = H;

@@ -66,3 +66,20 @@ def test_noalloc_rejects_oversize_and_bad_positions():
     st = pty.pty_gradient_noalloc(q.H, q.W, q.P, dev(q.probe), q.K, dev(bad), dev(q.d), 0.1, dev(q.psi0()), g,
                                   None, stream)
     assert st == pty.PTY_ERR_BOUNDS
+    # misaligned device pointers (4 mod 8) are rejected before anything launches
+    pos_flat = torch.zeros(2 * q.K + 1, dtype=torch.int32, device="cuda")
+    pos_off = pos_flat[1:]
+    assert pos_off.data_ptr() % 8 == 4
+    st = pty.pty_gradient_noalloc(q.H, q.W, q.P, dev(q.probe), q.K, pos_off, dev(q.d), 0.1, dev(q.psi0()), g,
+                                  None, stream)
+    assert st == pty.PTY_ERR_ARG
+    F_flat = torch.zeros(2, dtype=torch.float32, device="cuda")
+    F_off = F_flat[1:].view(torch.float32)
+    assert F_off.data_ptr() % 8 == 4
+    lib = pty.load()
+    import ctypes
+    st = lib.pty_gradient_noalloc(q.H, q.W, q.P, ctypes.c_void_p(dev(q.probe).data_ptr()), q.K,
+                                  ctypes.c_void_p(dev(q.pos).data_ptr()), ctypes.c_void_p(dev(q.d).data_ptr()), 0.1,
+                                  ctypes.c_void_p(dev(q.psi0()).data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                  ctypes.c_void_p(F_off.data_ptr()), ctypes.c_void_p(stream))
+    assert st == pty.PTY_ERR_ARG

@@ -14,6 +14,10 @@ from .orc import (  # noqa: F401
     gradient,
     cg_solve,
     OrcOpts,
+    EST_ML,
+    EST_LS,
+    SOLVER_CG,
+    SOLVER_GD,
     ORC_OK,
     ORC_ERR_ARG,
     ORC_ERR_BOUNDS,

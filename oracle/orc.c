@@ -34,6 +34,15 @@
  *    F(psi + gamma eta) <= F(psi) + gamma t.  After max_halvings failed trials the solve
  *    stops with psi unchanged for that iteration ("stalled").
  *  - Scan positions are integer top-left corners (row, col) of the P x P patch.
+ *  - The least-squares (Gaussian) estimator, which the paper names beside the ML estimate
+ *    but does not write out, is taken on amplitudes: F_LS = sum (|u| - sqrt d)^2, guarded
+ *    as F_LS,eps = sum |u|^2 - 2 sqrt(d) sqrt(|u|^2 + eps) + d, whose exact Wirtinger
+ *    gradient is u - sqrt(d) u / sqrt(|u|^2 + eps) (equal to F_LS at eps = 0).
+ *  - The gradient-descent solver is Eq. 4 with a constant step gamma (no line search).
+ *  - Warm-started line search (an option; the paper leaves the initial step of Eq. 7's
+ *    search free): from the second iteration of a solve on, the search starts at
+ *    gamma_init = min(gamma0, gamma_{m-1} / tau), so that its first trial is the previous
+ *    accepted step; every trial is still gamma0 tau^k for an integer k.
  *
  * Complex arrays are interleaved (re, im) doubles, layout-compatible with C99
  * double complex.  Object arrays are [H][W] row-major, per-position arrays [K][P][P].
@@ -281,21 +290,32 @@ struct obj_ctx {
     const int *pos;
     const float *d;
     double eps;
+    int est;
     const cplx *tw;
 };
 
-/* f for one detector pixel: |u|^2 - d log(|u|^2 + eps), with 0 log(.) := 0. */
-static double pixel_objective(cplx u, double d, double eps)
+#define ORC_EST_ML 0 /* Poisson maximum likelihood, Eq. 2 */
+#define ORC_EST_LS 1 /* Gaussian least squares on amplitudes */
+
+/* f for one detector pixel.
+ *   ML (Eq. 2): |u|^2 - d log(|u|^2 + eps), with 0 log(.) := 0;
+ *   LS:         |u|^2 - 2 sqrt(d) sqrt(|u|^2 + eps) + d, i.e. (|u| - sqrt d)^2 at eps = 0. */
+static double pixel_objective(cplx u, double d, double eps, int est)
 {
     double a = creal(u) * creal(u) + cimag(u) * cimag(u);
-    return d > 0.0 ? a - d * log(a + eps) : a;
+    if (!(d > 0.0)) return a;
+    if (est == ORC_EST_LS) return a - 2.0 * sqrt(d) * sqrt(a + eps) + d;
+    return a - d * log(a + eps);
 }
 
-/* residual of Eq. 3 in the Fourier domain: u - d u / (|u|^2 + eps). */
-static cplx pixel_residual(cplx u, double d, double eps)
+/* Fourier-domain residual, the Wirtinger derivative of pixel_objective w.r.t. conj(u):
+ *   ML (Eq. 3): u - d u / (|u|^2 + eps);   LS: u - sqrt(d) u / sqrt(|u|^2 + eps). */
+static cplx pixel_residual(cplx u, double d, double eps, int est)
 {
     double a = creal(u) * creal(u) + cimag(u) * cimag(u);
-    return d > 0.0 ? u - (d / (a + eps)) * u : u;
+    if (!(d > 0.0)) return u;
+    if (est == ORC_EST_LS) return u - (sqrt(d) / sqrt(a + eps)) * u;
+    return u - (d / (a + eps)) * u;
 }
 
 static void obj_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
@@ -307,7 +327,7 @@ static void obj_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
     fft2_unitary(work, c->P, 0, c->tw);
     const float *dk = c->d + (long)k * PP;
     double s = 0.0;
-    for (long j = 0; j < PP; j++) s += pixel_objective(work[j], (double)dk[j], c->eps);
+    for (long j = 0; j < PP; j++) s += pixel_objective(work[j], (double)dk[j], c->eps, c->est);
     *fpart = s;
 }
 
@@ -320,8 +340,8 @@ static void grad_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
     const float *dk = c->d + (long)k * PP;
     double s = 0.0;
     for (long j = 0; j < PP; j++) {
-        s += pixel_objective(work[j], (double)dk[j], c->eps);
-        work[j] = pixel_residual(work[j], (double)dk[j], c->eps);
+        s += pixel_objective(work[j], (double)dk[j], c->eps, c->est);
+        work[j] = pixel_residual(work[j], (double)dk[j], c->eps, c->est);
     }
     *fpart = s;
     fft2_unitary(work, c->P, 1, c->tw);
@@ -330,7 +350,7 @@ static void grad_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
 
 /* Objective with per-pattern partials summed in pattern order. */
 static int objective_impl(int H, int W, int P, const cplx *p, int K, const int *pos, const float *d,
-                          double eps, const cplx *psi, const cplx *tw, int T, double *F)
+                          double eps, int est, const cplx *psi, const cplx *tw, int T, double *F)
 {
     double *fpart = (double *)malloc(sizeof(double) * (size_t)K);
     cplx *work = (cplx *)malloc(sizeof(cplx) * (size_t)(T < 1 ? 1 : T) * P * P);
@@ -339,7 +359,7 @@ static int objective_impl(int H, int W, int P, const cplx *p, int K, const int *
         free(work);
         return ORC_ERR_NOMEM;
     }
-    struct obj_ctx c = {W, P, p, psi, pos, d, eps, tw};
+    struct obj_ctx c = {W, P, p, psi, pos, d, eps, est, tw};
     (void)H;
 #pragma omp parallel for num_threads(T) schedule(static)
     for (int k = 0; k < K; k++) {
@@ -359,11 +379,11 @@ static int objective_impl(int H, int W, int P, const cplx *p, int K, const int *
 }
 
 static int gradient_impl(int H, int W, int P, const cplx *p, int K, const int *pos, const float *d,
-                         double eps, const cplx *psi, const cplx *tw, int T, cplx *g, double *F)
+                         double eps, int est, const cplx *psi, const cplx *tw, int T, cplx *g, double *F)
 {
     double *fpart = (double *)malloc(sizeof(double) * (size_t)K);
     if (!fpart) return ORC_ERR_NOMEM;
-    struct obj_ctx c = {W, P, p, psi, pos, d, eps, tw};
+    struct obj_ctx c = {W, P, p, psi, pos, d, eps, est, tw};
     int st = run_patterns_scatter(K, P, H, W, T, grad_one, &c, g, fpart);
     if (st == ORC_OK && F) {
         double s = 0.0;
@@ -375,28 +395,30 @@ static int gradient_impl(int H, int W, int P, const cplx *p, int K, const int *p
 }
 
 int orc_objective(int H, int W, int P, const double *probe, int K, const int *pos, const float *d,
-                  double eps, const double *psi, double *F, int nthreads)
+                  double eps, int est, const double *psi, double *F, int nthreads)
 {
+    if (est != ORC_EST_ML && est != ORC_EST_LS) return ORC_ERR_ARG;
     int st = check_geom(H, W, P, K, pos);
     if (st) return st;
     if (!F || !d || !psi || !probe) return ORC_ERR_ARG;
     cplx *tw = make_twiddles(P);
     if (!tw) return ORC_ERR_NOMEM;
-    st = objective_impl(H, W, P, (const cplx *)probe, K, pos, d, eps, (const cplx *)psi, tw,
+    st = objective_impl(H, W, P, (const cplx *)probe, K, pos, d, eps, est, (const cplx *)psi, tw,
                         nthreads_eff(nthreads), F);
     free(tw);
     return st;
 }
 
 int orc_gradient(int H, int W, int P, const double *probe, int K, const int *pos, const float *d,
-                 double eps, const double *psi, double *g, double *F, int nthreads)
+                 double eps, int est, const double *psi, double *g, double *F, int nthreads)
 {
+    if (est != ORC_EST_ML && est != ORC_EST_LS) return ORC_ERR_ARG;
     int st = check_geom(H, W, P, K, pos);
     if (st) return st;
     if (!g || !d || !psi || !probe) return ORC_ERR_ARG;
     cplx *tw = make_twiddles(P);
     if (!tw) return ORC_ERR_NOMEM;
-    st = gradient_impl(H, W, P, (const cplx *)probe, K, pos, d, eps, (const cplx *)psi, tw,
+    st = gradient_impl(H, W, P, (const cplx *)probe, K, pos, d, eps, est, (const cplx *)psi, tw,
                        nthreads_eff(nthreads), (cplx *)g, F);
     free(tw);
     return st;
@@ -405,13 +427,29 @@ int orc_gradient(int H, int W, int P, const double *probe, int K, const int *pos
 /* ------------------------------------------------------------------------- */
 /* CG solve (Eq. 5, 6, 7; Algorithm 1 on one device).                        */
 /* ------------------------------------------------------------------------- */
+#define ORC_SOLVER_CG 0 /* Eq. 5-7, Algorithm 1 */
+#define ORC_SOLVER_GD 1 /* Eq. 4, constant step */
+
 typedef struct {
     double gamma0;     /* initial step, Algorithm 1: 1 */
     double tau;        /* shrink factor, Algorithm 1: 0.5 */
     double t;          /* Eq. 7 termination constant, "usually 0" */
     int max_halvings;  /* trials before the solve is declared stalled */
     double eps;        /* log / division guard of the implemented objective */
+    int est;           /* ORC_EST_ML (Eq. 2) or ORC_EST_LS */
+    int solver;        /* ORC_SOLVER_CG or ORC_SOLVER_GD */
+    double gd_step;    /* constant step gamma of Eq. 4 (GD only) */
+    int warm;          /* 1: warm-started line search (CG only) */
 } orc_opts;
+
+static double wall_seconds(void)
+{
+#ifdef _OPENMP
+    return omp_get_wtime();
+#else
+    return 0.0;
+#endif
+}
 
 /* Re sum conj(a) b over n complex values. */
 static double re_dot(const cplx *a, const cplx *b, long n)
@@ -426,16 +464,23 @@ static double re_dot(const cplx *a, const cplx *b, long n)
  *   F_hist[niter+1]: F(psi_m) for m = 0..iters_done (F of the accepted trial at the end),
  *   gamma[niter], halvings[niter] (number of trials), alpha[niter] (Dai-Yuan coefficient,
  *   0 for the steepest-descent start or a restart).
+ *   t_hist[niter]: wall-clock seconds at the end of each iteration (measurement only).
  * Returns ORC_OK, or ORC_STALLED when an iteration found no step within max_halvings
  * trials (psi keeps the last accepted iterate; *iters_done counts accepted iterations).
+ * With opts->solver == ORC_SOLVER_GD the iterations are Eq. 4 instead: psi -= gd_step g,
+ * gamma = gd_step, no trials (halvings 0), alpha 0; F_hist[m+1] = F(psi_{m+1}).
  */
 int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos, const float *d,
                  const orc_opts *opts, double *psi_io, int niter, double *F_hist, double *gamma_out,
-                 int *halvings_out, double *alpha_out, int *iters_done, int nthreads)
+                 int *halvings_out, double *alpha_out, int *iters_done, double *t_hist, int nthreads)
 {
     int st = check_geom(H, W, P, K, pos);
     if (st) return st;
     if (!opts || !psi_io || !d || !probe || niter < 0) return ORC_ERR_ARG;
+    if ((opts->est != ORC_EST_ML && opts->est != ORC_EST_LS) ||
+        (opts->solver != ORC_SOLVER_CG && opts->solver != ORC_SOLVER_GD))
+        return ORC_ERR_ARG;
+    const int est = opts->est;
     int T = nthreads_eff(nthreads);
     long n = (long)H * W;
     cplx *psi = (cplx *)psi_io;
@@ -449,12 +494,29 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
     const cplx *p = (const cplx *)probe;
     int m;
     if (iters_done) *iters_done = 0;
+    double gam_prev = 0.0; /* last accepted step of this solve (warm start) */
     for (m = 0; m < niter; m++) {
         /* GRAD stage: g_m = grad F(psi_m), F_m = F(psi_m) */
         double Fm;
-        st = gradient_impl(H, W, P, p, K, pos, d, opts->eps, psi, tw, T, g, &Fm);
+        st = gradient_impl(H, W, P, p, K, pos, d, opts->eps, est, psi, tw, T, g, &Fm);
         if (st) goto done;
         if (F_hist) F_hist[m] = Fm;
+        if (opts->solver == ORC_SOLVER_GD) {
+            /* Eq. 4: psi_{m+1} = psi_m - gamma grad F(psi_m), gamma constant */
+            for (long i = 0; i < n; i++) psi[i] -= opts->gd_step * g[i];
+            if (gamma_out) gamma_out[m] = opts->gd_step;
+            if (halvings_out) halvings_out[m] = 0;
+            if (alpha_out) alpha_out[m] = 0.0;
+            if (F_hist && m + 1 == niter) {
+                double Fn;
+                st = objective_impl(H, W, P, p, K, pos, d, opts->eps, est, psi, tw, T, &Fn);
+                if (st) goto done;
+                F_hist[m + 1] = Fn;
+            }
+            if (iters_done) *iters_done = m + 1;
+            if (t_hist) t_hist[m] = wall_seconds();
+            continue;
+        }
         /* DIR stage: Dai-Yuan (Eq. 6), eta_0 = -g_0 */
         double alpha = 0.0;
         if (m > 0) {
@@ -474,12 +536,13 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
         if (alpha_out) alpha_out[m] = alpha;
         /* LS stage: gamma^(0) = gamma0; do { gamma *= tau; F(psi+gamma eta) } while Eq. 7 fails */
         double gam = opts->gamma0, Ft = 0.0;
+        if (opts->warm && gam_prev > 0.0 && gam_prev / opts->tau < gam) gam = gam_prev / opts->tau;
         int k = 0, ok = 0;
         do {
             gam *= opts->tau;
             k++;
             for (long i = 0; i < n; i++) trial[i] = psi[i] + gam * eta[i];
-            st = objective_impl(H, W, P, p, K, pos, d, opts->eps, trial, tw, T, &Ft);
+            st = objective_impl(H, W, P, p, K, pos, d, opts->eps, est, trial, tw, T, &Ft);
             if (st) goto done;
             ok = (Ft <= Fm + gam * opts->t);
         } while (!ok && k < opts->max_halvings);
@@ -494,7 +557,9 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
         for (long i = 0; i < n; i++) psi[i] = trial[i];
         if (F_hist) F_hist[m + 1] = Ft;
         memcpy(g_prev, g, sizeof(cplx) * n);
+        gam_prev = gam;
         if (iters_done) *iters_done = m + 1;
+        if (t_hist) t_hist[m] = wall_seconds();
     }
     st = ORC_OK;
 done:

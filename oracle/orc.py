@@ -30,18 +30,33 @@ class _Opts(ctypes.Structure):
         ("t", ctypes.c_double),
         ("max_halvings", ctypes.c_int),
         ("eps", ctypes.c_double),
+        ("est", ctypes.c_int),
+        ("solver", ctypes.c_int),
+        ("gd_step", ctypes.c_double),
+        ("warm", ctypes.c_int),
     ]
+
+
+EST_ML, EST_LS = 0, 1  # Poisson maximum likelihood (Eq. 2); Gaussian least squares on amplitudes
+SOLVER_CG, SOLVER_GD = 0, 1  # Eq. 5-7 with Algorithm 1; Eq. 4 with a constant step
 
 
 @dataclass
 class OrcOpts:
-    """Line-search and objective options; defaults follow Algorithm 1 (gamma0=1, tau=0.5, t=0)."""
+    """Line-search and objective options; defaults follow Algorithm 1 (gamma0=1, tau=0.5, t=0).
+
+    est: EST_ML or EST_LS; solver: SOLVER_CG or SOLVER_GD (step gd_step); warm: start each
+    line search after the first at min(gamma0, gamma_prev / tau)."""
 
     gamma0: float = 1.0
     tau: float = 0.5
     t: float = 0.0
     max_halvings: int = 60
     eps: float = 0.1
+    est: int = EST_ML
+    solver: int = SOLVER_CG
+    gd_step: float = 0.0
+    warm: bool = False
 
 
 def build(force: bool = False) -> str:
@@ -83,9 +98,9 @@ def _get():
         lib.orc_QH.argtypes = [i, i, i, P, i, P, P, P]
         lib.orc_forward.argtypes = [i, i, i, P, i, P, P, P, i]
         lib.orc_adjoint.argtypes = [i, i, i, P, i, P, P, P, i]
-        lib.orc_objective.argtypes = [i, i, i, P, i, P, P, d, P, P, i]
-        lib.orc_gradient.argtypes = [i, i, i, P, i, P, P, d, P, P, P, i]
-        lib.orc_cg_solve.argtypes = [i, i, i, P, i, P, P, ctypes.POINTER(_Opts), P, i, P, P, P, P, P, i]
+        lib.orc_objective.argtypes = [i, i, i, P, i, P, P, d, i, P, P, i]
+        lib.orc_gradient.argtypes = [i, i, i, P, i, P, P, d, i, P, P, P, i]
+        lib.orc_cg_solve.argtypes = [i, i, i, P, i, P, P, ctypes.POINTER(_Opts), P, i, P, P, P, P, P, P, i]
         for f in ("orc_fft2", "orc_Q", "orc_QH", "orc_forward", "orc_adjoint", "orc_objective",
                   "orc_gradient", "orc_cg_solve"):
             getattr(lib, f).restype = ctypes.c_int
@@ -163,51 +178,57 @@ def adjoint(y, probe, pos, shape, nthreads=1):
     return out
 
 
-def objective(psi, probe, pos, d, eps=0.1, nthreads=1):
-    """F_eps(psi) = sum |G psi|^2 - d log(|G psi|^2 + eps) (Eq. 2 with the eps guard)."""
+def objective(psi, probe, pos, d, eps=0.1, nthreads=1, est=EST_ML):
+    """F_eps(psi) = sum |G psi|^2 - d log(|G psi|^2 + eps) (Eq. 2 with the eps guard), or with
+    est=EST_LS the amplitude least squares sum |G psi|^2 - 2 sqrt(d) sqrt(|G psi|^2 + eps) + d."""
     psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
     H, W = psi.shape
     P = probe.shape[0]
     F = ctypes.c_double(0.0)
-    st = _get().orc_objective(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, _ptr(psi),
+    st = _get().orc_objective(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, est, _ptr(psi),
                               ctypes.byref(F), nthreads)
     _check(st, "objective")
     return F.value
 
 
-def gradient(psi, probe, pos, d, eps=0.1, nthreads=1):
-    """(g, F): g = G^H(G psi - d G psi / (|G psi|^2 + eps)) (Eq. 3), F as in objective()."""
+def gradient(psi, probe, pos, d, eps=0.1, nthreads=1, est=EST_ML):
+    """(g, F): g = G^H(G psi - d G psi / (|G psi|^2 + eps)) (Eq. 3), F as in objective(); with
+    est=EST_LS g = G^H(G psi - sqrt(d) G psi / sqrt(|G psi|^2 + eps))."""
     psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
     H, W = psi.shape
     P = probe.shape[0]
     g = np.empty((H, W), np.complex128)
     F = ctypes.c_double(0.0)
-    st = _get().orc_gradient(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, _ptr(psi),
+    st = _get().orc_gradient(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, est, _ptr(psi),
                              _ptr(g), ctypes.byref(F), nthreads)
     _check(st, "gradient")
     return g, F.value
 
 
 def cg_solve(psi0, probe, pos, d, niter, opts: OrcOpts | None = None, nthreads=1):
-    """Run niter ML-CG iterations (Eq. 5-7, Algorithm 1 on one device).
+    """Run niter ML-CG iterations (Eq. 5-7, Algorithm 1 on one device), or Eq. 4's gradient
+    descent with opts.solver = SOLVER_GD.
 
     Returns a dict with psi, F (F_hist[0..iters_done]), gamma, halvings, alpha,
-    iters_done and status (ORC_OK or ORC_STALLED).
+    iters_done, status (ORC_OK or ORC_STALLED) and t (wall seconds at the end of each
+    iteration, for timing only).
     """
     opts = opts or OrcOpts()
     psi = _c128(psi0).copy()
     probe, pos, d = _c128(probe), _pos(pos), _f32(d)
     H, W = psi.shape
     P = probe.shape[0]
-    o = _Opts(opts.gamma0, opts.tau, opts.t, opts.max_halvings, opts.eps)
+    o = _Opts(opts.gamma0, opts.tau, opts.t, opts.max_halvings, opts.eps, int(opts.est), int(opts.solver),
+              float(opts.gd_step), int(bool(opts.warm)))
     F = np.full(niter + 1, np.nan)
     gam = np.full(max(niter, 1), np.nan)
     halv = np.zeros(max(niter, 1), np.int32)
     alpha = np.full(max(niter, 1), np.nan)
+    tim = np.full(max(niter, 1), np.nan)
     done = ctypes.c_int(0)
     st = _get().orc_cg_solve(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), ctypes.byref(o),
                              _ptr(psi), niter, _ptr(F), _ptr(gam), _ptr(halv), _ptr(alpha),
-                             ctypes.byref(done), nthreads)
+                             ctypes.byref(done), _ptr(tim), nthreads)
     if st not in (ORC_OK, ORC_STALLED):
         _check(st, "cg_solve")
     n = done.value
@@ -219,4 +240,5 @@ def cg_solve(psi0, probe, pos, d, niter, opts: OrcOpts | None = None, nthreads=1
         "alpha": alpha[: min(niter, n + (st == ORC_STALLED))],
         "iters_done": n,
         "status": st,
+        "t": tim[:n],
     }

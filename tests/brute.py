@@ -31,28 +31,54 @@ def g_matrix(H, W, P, probe, pos):
 
 
 class Brute:
-    def __init__(self, H, W, P, probe, pos, d, eps):
+    """Dense restatement.  est "ml": Eq. 2 / Eq. 3 with the eps guard; est "ls": the
+    amplitude least-squares estimator (|u| - sqrt d)^2 with |u| -> sqrt(|u|^2 + eps)."""
+
+    def __init__(self, H, W, P, probe, pos, d, eps, est="ml"):
         self.G = g_matrix(H, W, P, np.asarray(probe, np.complex128), np.asarray(pos))
         self.d = np.asarray(d, np.float64).ravel()
         self.eps = eps
+        self.est = est
         self.shape = (H, W)
 
     def objective(self, psi):
         u = self.G @ psi.ravel()
         a = np.abs(u) ** 2
-        logterm = np.where(self.d > 0, self.d * np.log(np.where(self.d > 0, a + self.eps, 1.0)), 0.0)
+        has = self.d > 0
+        if self.est == "ls":
+            # (s - sqrt d)^2 expanded, s = sqrt(|u|^2 + eps); |u|^2 where nothing was counted
+            s = np.sqrt(a + self.eps)
+            return float(np.sum(np.where(has, a - 2.0 * np.sqrt(self.d) * s + self.d, a)))
+        logterm = np.where(has, self.d * np.log(np.where(has, a + self.eps, 1.0)), 0.0)
         return float(np.sum(a - logterm))
 
     def gradient(self, psi):
         u = self.G @ psi.ravel()
         a = np.abs(u) ** 2
-        resid = u - np.where(self.d > 0, self.d / np.where(self.d > 0, a + self.eps, 1.0), 0.0) * u
+        has = self.d > 0
+        if self.est == "ls":
+            # d/d conj(u) of (s - sqrt d)^2 = (s - sqrt d) u / s
+            s = np.sqrt(a + self.eps)
+            resid = np.where(has, (s - np.sqrt(self.d)) / s, 1.0) * u
+        else:
+            resid = u - np.where(has, self.d / np.where(has, a + self.eps, 1.0), 0.0) * u
         return (self.G.conj().T @ resid).reshape(self.shape)
 
-    def cg(self, psi0, niter, gamma0=1.0, tau=0.5, t=0.0, max_halvings=60):
+    def gd(self, psi0, niter, step):
+        """Eq. 4 with a constant step: psi <- psi - step * grad F(psi)."""
+        psi = np.array(psi0, np.complex128)
+        F = []
+        for _ in range(niter):
+            F.append(self.objective(psi))
+            psi = psi - step * self.gradient(psi)
+        F.append(self.objective(psi))
+        return {"F": F, "psi": psi}
+
+    def cg(self, psi0, niter, gamma0=1.0, tau=0.5, t=0.0, max_halvings=60, warm=False):
         psi = np.array(psi0, np.complex128)
         out = {"F": [], "gamma": [], "halvings": [], "alpha": []}
         g_prev = eta = None
+        last = None  # accepted step of the previous iteration (warm start)
         for m in range(niter):
             g = self.gradient(psi)
             Fm = self.objective(psi)
@@ -65,7 +91,7 @@ class Brute:
                 alpha = num / den if den > 0 and np.isfinite(den) else 0.0
             eta = -g if m == 0 else -g + alpha * eta
             out["alpha"].append(alpha)
-            gam = gamma0
+            gam = gamma0 if (not warm or last is None) else min(gamma0, last / tau)
             for k in range(1, max_halvings + 1):
                 gam *= tau
                 Ft = self.objective(psi + gam * eta)
@@ -77,6 +103,7 @@ class Brute:
             out["halvings"].append(k)
             psi = psi + gam * eta
             g_prev = g
+            last = gam
         out["F"].append(self.objective(psi))
         out["psi"] = psi
         return out

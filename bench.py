@@ -10,8 +10,14 @@ data (236 MB) is larger than L2, so no flush is needed between steps.
 Multi-GPU: the solve does not shard across GPUs; `--gpus N` (under torchrun) runs N
 independent replicas and reports their total throughput (weak scaling).
 
+Timed region: after W warm-up iterations the CG state is checkpointed; the K-step solve is
+replayed from that checkpoint for about a second (so that the clock sampler sees the GPU
+under load), then restored once more and the K steps are timed with CUDA events: the
+timed steps are iterations W .. W+K-1 of one solve.
+
 `--impl reference` times the FP64 CPU oracle (the method's plain restatement) on the host
-cores instead, one bounded sample per step.
+cores instead: the same workload, the same iterations W .. W+K-1 of a solve from the same
+start (bounded to a few minutes of CPU time).
 """
 from __future__ import annotations
 
@@ -59,14 +65,15 @@ FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 
-# DRAM traffic per launch of the LS pattern pass, from an ncu capture summarised in
+# DRAM traffic per launch of a pattern kernel, from the one-pass ncu captures summarised in
 # profiles/: valid only while the kernel's sources are the ones hashed there
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_ls_fft_mlcg_1024_p128.md")
+TRAFFIC_PROFILES = {"k_ls_fft": os.path.join(ROOT, "profiles", "k_ls_fft_mlcg_1024_p128.md"),
+                    "k_grad_lin": os.path.join(ROOT, "profiles", "k_grad_lin_mlcg_1024_p128.md")}
 TRAFFIC_SOURCES = ["fft_tile.cuh", "pattern_kernels.cuh", "pattern_p128.cu", "pty_internal.h", "reduce.cuh",
                    "mathx.cuh"]
 
 
-def ls_pass_source_hash():
+def pattern_source_hash():
     import hashlib
 
     h = hashlib.sha256()
@@ -76,31 +83,34 @@ def ls_pass_source_hash():
     return h.hexdigest()[:16]
 
 
-def ls_pass_traffic(P, plan_ls):
-    """(bytes per launch or None, note) for the chosen LS configuration (R, NT)."""
+def kernel_traffic(kernel, P, plan):
+    """(bytes per launch or None, note) of `kernel` in the configuration (R, NT) = plan."""
     import re
 
+    path = TRAFFIC_PROFILES[kernel]
     try:
-        with open(TRAFFIC_PROFILE) as fh:
+        with open(path) as fh:
             text = fh.read()
     except OSError:
         return None, "no profile summary"
-    cur = ls_pass_source_hash()
-    for m in re.finditer(r"^traffic: k_ls_fft<(\d+),(\d+),(\d+)> (\d+) bytes/launch, sources ([0-9a-f]+)$", text,
-                         re.M):
-        if (int(m.group(1)), int(m.group(2)), int(m.group(3))) != (P, plan_ls[0], plan_ls[1]):
+    cur = pattern_source_hash()
+    pat = r"^traffic: " + kernel + r"<(\d+),(\d+),(\d+)> (\d+) bytes/launch, sources ([0-9a-f]+)$"
+    for m in re.finditer(pat, text, re.M):
+        if (int(m.group(1)), int(m.group(2)), int(m.group(3))) != (P, plan[0], plan[1]):
             continue
         if m.group(5) != cur:
             return None, f"kernel sources changed since the capture ({m.group(5)} -> {cur})"
-        return int(m.group(4)), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {os.path.basename(TRAFFIC_PROFILE)}"
-    return None, f"no capture of k_ls_fft<{P},{plan_ls[0]},{plan_ls[1]}>"
+        return int(m.group(4)), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, {os.path.basename(path)}"
+    return None, f"no capture of {kernel}<{P},{plan[0]},{plan[1]}>"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--preroll-s", type=float, default=1.0,
+                    help="seconds of replayed steps before the timed steps (clock sampling under load)")
     ap.add_argument("--impl", choices=["pty", "reference"], default="pty")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -115,9 +125,11 @@ def parse():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 20 ms) around the timed region.  Samples carry their
+    timestamps; the record reports the samples taken while the GPU ran the replayed steps
+    and the timed steps (`window`), and how many fell inside the timed steps alone."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -134,31 +146,43 @@ class Clocks:
         except OSError:
             self.proc = None
 
-    def stop(self):
+    def stop(self, load=None, timed=None):
+        """load, timed: (t0, t1) wall-clock windows (time.time()) of the GPU work."""
+        import datetime
+
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
         self.proc.wait()
         self.f.seek(0)
-        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 10]
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 11]
         os.unlink(self.f.name)
-        sm, smmax, reasons, busy = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm_all, sm_load, n_timed, smmax, reasons, power = [], [], 0, None, set(), []
         for r in rows:
             try:
-                s, mx, util = float(r[1]), float(r[2]), float(r[4])
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                s, mx, pw = float(r[2]), float(r[3]), float(r[4])
             except ValueError:
                 continue
             smmax = mx
-            sm.append(s)
-            if util >= 50:
-                busy.append(s)
-            for n, v in zip(names, r[6:10]):
-                if v.strip().lower() == "active":
-                    reasons.add(n)
-        use = busy or sm
+            sm_all.append(s)
+            in_load = load is not None and load[0] <= ts <= load[1]
+            if in_load:
+                sm_load.append(s)
+                power.append(pw)
+                for n, v in zip(names, r[7:11]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            if timed is not None and timed[0] <= ts <= timed[1]:
+                n_timed += 1
+        use = sm_load or sm_all
         return {"sm_mhz": float(np.median(use)) if use else None, "sm_max_mhz": smmax,
-                "reasons": sorted(reasons), "samples": len(rows), "samples_busy": len(busy)}
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(sm_load),
+                "samples_in_timed_steps": n_timed,
+                "power_w_median": float(np.median(power)) if power else None,
+                "window": "samples taken while the replayed and the timed steps ran" if sm_load else
+                          "no sample fell under load: median of all samples"}
 
 
 def fft2_flops(P):
@@ -181,48 +205,58 @@ def over_ranks(dist, ms, units, device):
     return float(t.item()), float(u.item())
 
 
-def run_reference(args, rank):
-    """FP64 CPU oracle on the host cores, one bounded sample of the workload per step."""
-    if rank != 0:
-        return
+REF_MAX_ITERS = 80  # bound of the oracle's solve (about 2 minutes on 16 host cores)
+
+
+def oracle_rate(p, warmup, steps, cores):
+    """The FP64 oracle's throughput on iterations warmup .. warmup+k-1 of one solve of the
+    workload from its start (the iterations the GPU arm times), k <= steps bounded so the
+    solve stays within REF_MAX_ITERS iterations.  Returns (patterns/s, k, seconds, trials)."""
     import oracle
-    from paper_2106_07575_gb300 import synth
 
     oracle.build()
+    k = max(1, min(steps, REF_MAX_ITERS - warmup))
+    out = oracle.cg_solve(p.psi0(), p.probe, p.pos, p.d, warmup + k, nthreads=cores)
+    t = out["t"]
+    done = len(t) - warmup
+    if done < 1:
+        raise RuntimeError(f"oracle solve stopped after {len(t)} iterations (status {out['status']})")
+    k = min(k, done)
+    t0 = t[warmup - 1] if warmup >= 1 else 0.0
+    dt = float(t[warmup + k - 1] - t0)
+    trials = out["halvings"][warmup:warmup + k]
+    return p.K * k / dt, k, dt, float(np.mean(trials))
+
+
+def run_reference(args, rank):
+    """FP64 CPU oracle on the host cores: the GPU arm's workload and timed iterations."""
+    if rank != 0:
+        return
+    from paper_2106_07575_gb300 import synth
+
     p = synth.production_problem()
-    S = 400  # positions of the sample: the first 400 in raster order (a 1024^2 sub-scan)
     cores = os.cpu_count()
-    pos, d = p.pos[:S], p.d[:S]
-    psi = p.psi0()
-    for _ in range(args.warmup):
-        oracle.cg_solve(psi, p.probe, pos, d, 1, nthreads=cores)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.cg_solve(psi, p.probe, pos, d, 1, nthreads=cores)
-    dt = time.perf_counter() - t0
-    v = S * args.steps / dt
-    sample = f"one FP64 oracle CG iteration over the first {S} of the 3600 positions per step"
+    v, k, dt, trials = oracle_rate(p, args.warmup, args.steps, cores)
+    sample = (f"iterations {args.warmup}..{args.warmup + k - 1} of one FP64 oracle ML-CG solve of the full workload "
+              f"({p.K} positions, {trials:.1f} line-search trials per iteration) from the ones start, "
+              f"{dt:.1f} s timed; the {args.warmup} earlier iterations untimed")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": k, "warmup": args.warmup, "ms_per_step": 1e3 * dt / k,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample_positions": S},
+        "config": {"workload": WORKLOAD, "timed_iterations": [args.warmup, args.warmup + k - 1]},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline(p):
-    import oracle
-
-    oracle.build()
+def cpu_baseline(p, warmup):
+    """The oracle on a bounded sample of the GPU arm's timed iterations (about 10-20 s)."""
     cores = os.cpu_count()
-    t0 = time.perf_counter()
-    out = oracle.cg_solve(p.psi0(), p.probe, p.pos, p.d, 1, nthreads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": p.K / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"one FP64 oracle CG iteration of the full workload ({p.K} positions, "
-                      f"{int(out['halvings'][0])} line-search trials), {dt:.1f} s"}
+    v, k, dt, trials = oracle_rate(p, warmup, 5, cores)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"iterations {warmup}..{warmup + k - 1} of one FP64 oracle solve of the full workload "
+                      f"({p.K} positions, {trials:.1f} line-search trials per iteration), {dt:.1f} s timed"}
 
 
 def run_views(args, torch, pty, synth):
@@ -396,64 +430,108 @@ def main():
     probe_d, pos_d, d_d = dev(p.probe), dev(p.pos), dev(p.d)
     ctx = pty.Context(probe_d, pos_d, d_d, p.H, p.W, opts, stream=stream.cuda_stream)
     psi = dev(p.psi0())
-    ctx.cg_solve(psi, args.warmup)
+    if args.warmup > 0:
+        ctx.cg_solve(psi, args.warmup)
+    # checkpoint after the warm-up: every replay below and the timed steps start here
+    ckpt = ctx.state_save()
+    psi_ck = psi.clone()
+
+    def restore():
+        ctx.state_load(ckpt)
+        psi.copy_(psi_ck)
 
     clk = Clocks(local)
+    clk.start()
+    time.sleep(0.1)
+    torch.cuda.synchronize()
+    t_load0 = time.time()
+    while True:  # replay the timed solve so the sampler sees the GPU under load
+        restore()
+        ctx.cg_solve(psi, args.steps)
+        torch.cuda.synchronize()
+        if time.time() - t_load0 >= args.preroll_s:
+            break
+    restore()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clk.start()
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tw0 = time.time()
     t_start.record(stream)
     st, rep = ctx.cg_solve(psi, args.steps)
     t_end.record(stream)
     torch.cuda.synchronize()
-    clocks = clk.stop()
+    tw1 = time.time()
     if dist:
         dist.barrier()
+    time.sleep(0.05)
+    clocks = clk.stop(load=(t_load0, tw1), timed=(tw0, tw1))
     steps_done = rep["iters_done"]
     ms, units = over_ranks(dist, t_start.elapsed_time(t_end), p.K * steps_done, "cuda")
     plan = ctx.plan()
-    ctx.close()
 
-    # per-kernel launch durations: the same workload in a second context with per-stage
-    # CUDA events on the stream the kernels run on (no graph replay there); 1 warm-up and up
-    # to 10 iterations continuing from the timed solve's object
+    # Per-kernel launch durations: the same iterations in a second context with CUDA events
+    # around each stage on the stream the kernels run on (no graph there).  The GRAD stage
+    # launches both GRAD kernels (the full form on a call's first iteration, the linear form
+    # after it; the other returns at once), so the linear form's time is the difference of a
+    # one-iteration and an n-iteration call from the same checkpoint, over n - 1.
     topts = pty.default_opts()
     topts.ls_window, topts.tile_config, topts.dft, topts.flags = opts.ls_window, opts.tile_config, opts.dft, 1
     tctx = pty.Context(probe_d, pos_d, d_d, p.H, p.W, topts, stream=stream.cuda_stream)
-    tctx.cg_solve(psi, 1)
-    tctx.stage_times(reset=True)
-    n_stage = max(1, min(args.steps, 10))
-    _, trep = tctx.cg_solve(psi, n_stage)
-    stage_ms, stage_n = tctx.stage_times(reset=True)
-    tctx.close()
-    n_it = max(trep["iters_done"], 1)
+    n_stage = max(2, min(args.steps, 21))
 
-    # roofline of the LS pattern pass k_ls_fft, one of the two largest kernels with the linear
-    # GRAD pass (whose time and rate go to "other"), and the one with a current traffic
-    # capture (FP32 ALU bound: one 2-D FFT per pattern on the CUDA cores; one launch per
-    # iteration covers all K patterns).
-    # Algorithmic flops: 5 N log2 N per 2-D DFT (N = P^2) plus the probe product (6 N) and,
-    # at the n_e detector pixels with counts, the two Parseval sums (8 per pixel).
+    def staged(n):
+        tctx.state_load(ckpt)
+        x = psi_ck.clone()
+        tctx.cg_solve(x, 1)  # warm the kernels of this context
+        tctx.state_load(ckpt)
+        x.copy_(psi_ck)
+        tctx.stage_times(reset=True)
+        _, r = tctx.cg_solve(x, n)
+        ms_, n_ = tctx.stage_times(reset=True)
+        return ms_, n_, max(r["iters_done"], 1)
+
+    s1_ms, _, _ = staged(1)
+    stage_ms, stage_n, n_it = staged(n_stage)
+    tctx.close()
+    ctx.close()
+
     P, K = p.P, p.K
     L = opts.ls_window
     n_e = float(np.count_nonzero(p.d))  # detector pixels with counts
-    ls_flops = K * (fft2_flops(P) + 6 * P * P) + 8 * n_e
-    ls_ms = stage_ms[2] / max(stage_n[2], 1)
-    grad_ms = stage_ms[0] / max(stage_n[0], 1)
-    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = ls_flops / (ls_ms * 1e-3) / 1e12
-    traffic, traffic_note = ls_pass_traffic(P, plan["ls"])
-    roof = {"bound": "alu", "kernel": "k_ls_fft", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-            "frac": achieved / peak_tflops, "traffic": traffic, "traffic_note": traffic_note,
-            "peak_note": "FP32 FMA peak derived: 152 SMs x 128 lanes x 2 flop x 2070 MHz",
-            "launch_ms": ls_ms, "launches_timed": int(stage_n[2]),
-            "timing": "CUDA events around each k_ls_fft launch on its stream, stage-timed pass of the same workload",
-            "other": {"grad_pass_ms": grad_ms,
-                      "grad_pass_tflops_linear_form": K * (fft2_flops(P) + 6 * P * P) / (grad_ms * 1e-3) / 1e12,
-                      "ls_windows_ms_per_iter": stage_ms[4] / n_it, "scatter_ms_per_iter": stage_ms[1] / n_it,
-                      "small_ms_per_iter": stage_ms[3] / n_it}}
+    # Algorithmic flops per launch (all K patterns): one 2-D FFT per pattern at 5 N log2 N
+    # (N = P^2) plus the probe product (6 N); at the n_e pixels with counts the LS pass forms
+    # two Parseval sums and two certificate sums (8 + 6 per pixel), the linear GRAD pass
+    # updates u, forms the residual correction and the log term (about 20 per pixel).
+    fft_part = K * (fft2_flops(P) + 6 * P * P)
+    kern = {"k_grad_lin": {"flops": fft_part + 20 * n_e, "plan": plan["grad"],
+                           "ms": (stage_ms[0] - s1_ms[0]) / max(n_it - 1, 1),
+                           "timing": "GRAD stage of an n-iteration call minus that of a 1-iteration call "
+                                     "from the same checkpoint, over n - 1 (CUDA events on the library's stream)"},
+            "k_ls_fft": {"flops": fft_part + 14 * n_e, "plan": plan["ls"], "ms": stage_ms[2] / max(stage_n[2], 1),
+                         "timing": "CUDA events around each k_ls_fft launch on the library's stream"}}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    peak_max = N_SM * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    sm_mhz = clocks.get("sm_mhz") or SM_MAX_MHZ
+    peak_sampled = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+    def roof_of(name):
+        k = kern[name]
+        ach = k["flops"] / (k["ms"] * 1e-3) / 1e12
+        traffic, note = kernel_traffic(name, P, k["plan"])
+        return {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak_max, "unit": "TFLOP/s",
+                "frac": ach / peak_max, "traffic": traffic, "traffic_note": note,
+                "peak_note": "FP32 FMA peak derived (of derived, no FP32 figure in the measured peaks): "
+                             f"152 SMs x 128 lanes x 2 flop x {SM_MAX_MHZ:.0f} MHz (maximum SM clock)",
+                "peak_at_sampled_clock": peak_sampled, "frac_at_sampled_clock": ach / peak_sampled,
+                "sampled_sm_mhz": sm_mhz, "launch_ms": k["ms"], "flops_per_launch": k["flops"],
+                "timing": k["timing"]}
+
+    roof = roof_of(dom)
+    other = [n for n in kern if n != dom][0]
+    roof["other"] = {other: {kk: roof_of(other)[kk] for kk in ("achieved", "frac", "launch_ms", "traffic")},
+                     "scatter_ms_per_iter": stage_ms[1] / n_it, "ls_windows_ms_per_iter": stage_ms[4] / n_it,
+                     "small_ms_per_iter": stage_ms[3] / n_it}
 
     Lcap = 32 if L == 0 else L
     first_w = 4 if L == 0 else L
@@ -472,12 +550,13 @@ def main():
         "config": {"workload": workload, "ls_window": L, "tile_config": opts.tile_config, "plan": plan,
                    "dft": ["fp32 fft", "tensor-core split bf16", "tensor-core split fp16"][args.dft],
                    "l2": f"inputs larger than L2 ({p.d.nbytes / 1e6:.0f} MB data)",
+                   "timed_iterations": [args.warmup, args.warmup + steps_done - 1],
                    "parallelism": f"{world} independent replica(s)"},
         "status": pty.STATUS_NAMES[st], "roofline": roof, "clocks": clocks, "gpu_launches": launches,
         "stages_ms_per_iter": {"grad": stage_ms[0] / n_it, "scatter": stage_ms[1] / n_it,
                                "ls_pass": stage_ms[2] / n_it, "ls_windows": stage_ms[4] / n_it,
                                "small": stage_ms[3] / n_it, "iterations": n_it,
-                               "note": "stage-timed pass (events between stages, no graph)"},
+                               "note": "stage-timed call from the checkpoint (events between stages, no graph)"},
         "trials_per_iter": float(np.mean(rep["halvings"])) if len(rep["halvings"]) else None,
     }
 
@@ -502,7 +581,7 @@ def main():
                       "note": "pty_create from host arrays + one pty_cg_solve(niter=1) per step with host psi"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "production":
-        out["cpu_baseline"] = cpu_baseline(p)
+        out["cpu_baseline"] = cpu_baseline(p, args.warmup)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

@@ -464,7 +464,8 @@ static double re_dot(const cplx *a, const cplx *b, long n)
  *   F_hist[niter+1]: F(psi_m) for m = 0..iters_done (F of the accepted trial at the end),
  *   gamma[niter], halvings[niter] (number of trials), alpha[niter] (Dai-Yuan coefficient,
  *   0 for the steepest-descent start or a restart).
- *   t_hist[niter]: wall-clock seconds at the end of each iteration (measurement only).
+ *   t_hist[niter]: wall-clock seconds from the start of the solve to the end of each
+ *                  iteration (measurement only).
  * Returns ORC_OK, or ORC_STALLED when an iteration found no step within max_halvings
  * trials (psi keeps the last accepted iterate; *iters_done counts accepted iterations).
  * With opts->solver == ORC_SOLVER_GD the iterations are Eq. 4 instead: psi -= gd_step g,
@@ -495,6 +496,7 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
     int m;
     if (iters_done) *iters_done = 0;
     double gam_prev = 0.0; /* last accepted step of this solve (warm start) */
+    const double t_begin = wall_seconds();
     for (m = 0; m < niter; m++) {
         /* GRAD stage: g_m = grad F(psi_m), F_m = F(psi_m) */
         double Fm;
@@ -514,7 +516,7 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
                 F_hist[m + 1] = Fn;
             }
             if (iters_done) *iters_done = m + 1;
-            if (t_hist) t_hist[m] = wall_seconds();
+            if (t_hist) t_hist[m] = wall_seconds() - t_begin;
             continue;
         }
         /* DIR stage: Dai-Yuan (Eq. 6), eta_0 = -g_0 */
@@ -559,7 +561,7 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
         memcpy(g_prev, g, sizeof(cplx) * n);
         gam_prev = gam;
         if (iters_done) *iters_done = m + 1;
-        if (t_hist) t_hist[m] = wall_seconds();
+        if (t_hist) t_hist[m] = wall_seconds() - t_begin;
     }
     st = ORC_OK;
 done:

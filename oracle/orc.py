@@ -210,8 +210,8 @@ def cg_solve(psi0, probe, pos, d, niter, opts: OrcOpts | None = None, nthreads=1
     descent with opts.solver = SOLVER_GD.
 
     Returns a dict with psi, F (F_hist[0..iters_done]), gamma, halvings, alpha,
-    iters_done, status (ORC_OK or ORC_STALLED) and t (wall seconds at the end of each
-    iteration, for timing only).
+    iters_done, status (ORC_OK or ORC_STALLED) and t (wall seconds from the start of the
+    solve to the end of each iteration, for timing only).
     """
     opts = opts or OrcOpts()
     psi = _c128(psi0).copy()

@@ -107,6 +107,24 @@ typedef struct {
                             GEMMs on the tensor cores with operands split into BF16 hi + lo and
                             FP32 accumulation; 2 the same with FP16 hi + lo.  1 and 2 need
                             P = 64 or 128; pty_adjoint needs 0. */
+    int32_t estimator;   /* 0 (default): the Poisson maximum-likelihood objective of Eq. 2;
+                            1: the Gaussian least-squares estimator that the paper names beside
+                            it, on amplitudes: F = sum |G psi|^2 - 2 sqrt(d) sqrt(|G psi|^2 +
+                            eps) + d, i.e. sum (|G psi| - sqrt d)^2 at eps = 0, gradient
+                            G^H(G psi - sqrt(d) G psi / sqrt(|G psi|^2 + eps)).  1 needs dft = 0
+                            and runs the line search without the certified skip */
+    int32_t solver;      /* 0 (default): conjugate gradients with the Dai-Yuan direction and
+                            the backtracking line search (Eq. 5-7, Algorithm 1); 1: gradient
+                            descent with the constant step gd_step (Eq. 4): no line search,
+                            every GRAD pass runs the forward DFT; needs dft = 0 */
+    double gd_step;      /* step gamma of Eq. 4 (solver = 1), > 0 */
+    int32_t ls_warm;     /* 1: warm-started line search (solver 0, dft 0): after the first
+                            accepted step of the context's CG state (pty_cg_reset clears it)
+                            the search starts at min(gamma0, gamma_prev / tau), so that its
+                            first trial is the previous accepted step; trials stay gamma0 tau^k
+                            and max_halvings counts the trials of each search.  The paper
+                            leaves the initial step of Eq. 7's search free; Algorithm 1 starts
+                            every search at gamma0 (0, default) */
 } pty_opts;
 
 typedef struct pty_ctx pty_ctx;
@@ -114,7 +132,7 @@ typedef struct pty_ctx pty_ctx;
 /* Per-iteration record of pty_cg_solve.  Each array pointer is host memory or NULL.
  *   F[niter+1]      F(psi_m) for m = 0..iters_done (the last entry is F of the final psi)
  *   gamma[niter]    accepted step length gamma_m
- *   halvings[niter] line-search trials used in iteration m
+ *   halvings[niter] line-search trials used in iteration m (0 for gradient descent)
  *   alpha[niter]    Dai-Yuan coefficient of Eq. 6 (0 for the first iteration or a restart)
  * iters_done counts the iterations whose step was accepted. */
 typedef struct {

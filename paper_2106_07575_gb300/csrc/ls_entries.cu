@@ -3,7 +3,10 @@
 // With u = G psi_m and v = G eta_m kept at every entry (pixel with d > 0) by the GRAD and
 // LS pattern passes, the objective at a candidate step gamma changes by (Eq. 2, 7)
 //   sum_entries [ q - d log(1 + q / (|u|^2 + eps)) ] + (pixels without counts: Parseval)
-//   q = gamma (2 Re conj(u) v + gamma |v|^2) = |u + gamma v|^2 - |u|^2.
+//   q = gamma (2 Re conj(u) v + gamma |v|^2) = |u + gamma v|^2 - |u|^2,
+// and for the least-squares estimator on amplitudes (a = |u|^2 + eps)
+//   sum_entries [ q - 2 sqrt(d) (sqrt(a + q) - sqrt(a)) ],  sqrt(a + q) - sqrt(a) = q / (sqrt(a + q) + sqrt(a))
+// (the quotient form has no cancellation when q is small against a).
 // One thread block per (pattern, chunk) of the entry layout sums the window's candidates in
 // FP32 per thread and in float-float across the block (an FP64 butterfly over 16 values
 // kept the FP64 pipe 72 % busy and set the kernel's time) into rows 2.. of [L+2][K * cs]:
@@ -56,13 +59,23 @@ __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V
             const float au = fmaf(u.x, u.x, u.y * u.y);
             const float bu2 = 2.0f * fmaf(u.x, v.x, u.y * v.y);  // 2 Re conj(u) v
             const float cu = fmaf(v.x, v.x, v.y * v.y);
-            const float inv = 1.0f / (au + a.eps);
-            const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
+            if (a.est == 0) {
+                const float inv = 1.0f / (au + a.eps);
+                const float tmin = -au * inv;  // |u + gamma v|^2 >= 0
 #pragma unroll
-            for (int l = 0; l < L; l++) {
-                const float q = gam[l] * fmaf(gam[l], cu, bu2);
-                const float t = fmaxf(q * inv, tmin);
-                acc[l] = fmaf(-dv, log1p_fast(t), acc[l] + q);
+                for (int l = 0; l < L; l++) {
+                    const float q = gam[l] * fmaf(gam[l], cu, bu2);
+                    const float t = fmaxf(q * inv, tmin);
+                    acc[l] = fmaf(-dv, log1p_fast(t), acc[l] + q);
+                }
+            } else {
+                const float s0 = sqrtf(au + a.eps), sd2 = 2.0f * sqrtf(dv);
+#pragma unroll
+                for (int l = 0; l < L; l++) {
+                    const float q = fmaxf(gam[l] * fmaf(gam[l], cu, bu2), -au);  // |u + gamma v|^2 >= 0
+                    const float den = s0 + sqrtf(au + a.eps + q);
+                    acc[l] += den > 0.0f ? q - sd2 * (q / den) : q;
+                }
             }
         }
         block_sum_ff<kNT, L>(acc, red, tot);  // ends with a barrier: red is free again

@@ -187,7 +187,9 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const float2 *__restrict
         // linear form: sum |u|^2 over all pixels = P^2 sum D |psi|^2 (0 from the tiles otherwise)
         const double Fm = ff_value(tot[0]) + p2 * ff_value(tot[3]), gg = ff_value(tot[1]), den = ff_value(tot[2]);
         double alpha = 0.0;
-        if (den > 0.0 && isfinite(den) && isfinite(gg)) {
+        if (ls.gd) {
+            // Eq. 4: the step follows -grad F alone
+        } else if (den > 0.0 && isfinite(den) && isfinite(gg)) {
             alpha = gg / den;
         } else if (st->total > 0) {
             st->restarts += 1;
@@ -206,6 +208,21 @@ __global__ void __launch_bounds__(kSumNT) k_dy_finalize(const float2 *__restrict
         st->Leff = Le;
         st->Lsel = ls.adaptive ? (Le <= 16 ? 16 : 32) : ls.L;
         st->k0cert = 0;
+        st->kwarm = 0;
+        if (ls.warm && st->total > 0 && st->last_halvings > 0) {
+            // warm start: the search begins at gamma0 tau^(last - 1) = gamma_prev / tau, so
+            // its first trial is the previous accepted step gamma0 tau^last; the first window
+            // holds the previous search's distance to its accepted trial plus two candidates
+            const int kw = st->last_halvings - 1;
+            st->k0 = kw;
+            st->kwarm = kw;
+            if (ls.adaptive) {
+                const int Lw = st->last_excess + 2;
+                const int Ls = Lw <= 4 ? 4 : (Lw <= 8 ? 8 : (Lw <= 16 ? 16 : 32));
+                st->Leff = Ls < ls.L ? Ls : ls.L;
+                st->Lsel = st->Leff;
+            }
+        }
         open_window(st, ls.gamma0, ls.tau);
         double gj = ls.gamma0;  // the leading trials for the certificate rows of the LS pass
         for (int j = 0; j < kCertN; j++) {
@@ -271,9 +288,10 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__
     if (vpart && threadIdx.x < 2) tot[threadIdx.x] += vtot[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {
-        const int m = st->m, k0 = st->k0;
+        // trials are counted from the start of this search (kwarm trials skipped by a warm start)
+        const int m = st->m, k0 = st->k0, kw = st->kwarm;
         const size_t hf = (size_t)v * (h.cap + 1) + m, hi = (size_t)v * h.cap + m;
-        for (int l = 0; l < Leff && k0 + l + 1 <= ls.max_halvings; l++) {
+        for (int l = 0; l < Leff && k0 + l + 1 - kw <= ls.max_halvings; l++) {
             const double gam = st->cand[l];
             // F(psi + gam eta) - F(psi): quadratic part of the d = 0 pixels plus the rest
             const double dF = gam * (2.0 * tot[0] + gam * tot[1]) + tot[2 + l];
@@ -282,21 +300,21 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__
                 st->gamma_f = (float)gam;
                 st->Fnext = st->Fm + dF;
                 st->decided = 1;
-                st->last_halvings = k0 + l + 1;
-                st->last_excess = k0 + l - st->k0cert;
+                st->last_halvings = k0 + l + 1;  // gamma = gamma0 tau^last_halvings
+                st->last_excess = k0 + l - st->k0cert - kw;
                 if (m < h.cap) {
                     h.gamma[hi] = gam;
-                    h.halvings[hi] = k0 + l + 1;
+                    h.halvings[hi] = k0 + l + 1 - kw;
                     h.F[hf + 1] = st->Fm + dF;
                 }
                 return;
             }
         }
         const int k1 = k0 + Leff;
-        if (k1 >= ls.max_halvings) {
+        if (k1 - kw >= ls.max_halvings) {
             st->stalled = 1;
             if (m < h.cap) {
-                h.gamma[hi] = st->cand[ls.max_halvings - 1 - k0];
+                h.gamma[hi] = st->cand[ls.max_halvings - 1 - (k0 - kw)];
                 h.halvings[hi] = ls.max_halvings;
                 h.F[hf + 1] = st->Fm;
             }
@@ -397,6 +415,39 @@ __global__ void k_update(int H, int W, ViewMap vm, float2 *__restrict__ psi, con
         ep[i] = eta;
         gp[i] = gv;
     }
+}
+
+// Gradient descent (Eq. 4): psi_{m+1} = psi_m - gamma grad F(psi_m) with the constant step
+// gamma; k_update then applies it with alpha = 0 (eta = -g).
+__global__ void k_gd_step(ViewMap vm, DevState *sts, DevHist h, LsArgs ls)
+{
+    for (int v = threadIdx.x; v < vm.V; v += blockDim.x) {
+        DevState *st = sts + v;
+        if (st->stalled) continue;
+        st->gamma = ls.gd_step;
+        st->gamma_f = (float)ls.gd_step;
+        st->decided = 1;
+        st->last_halvings = 0;
+        const int m = st->m;
+        if (m < h.cap) {
+            h.gamma[(size_t)v * h.cap + m] = ls.gd_step;
+            h.halvings[(size_t)v * h.cap + m] = 0;
+        }
+    }
+}
+
+// F(psi) of each view (full-form GRAD partials) into the history slot of the current count.
+__global__ void __launch_bounds__(kSumNT) k_objective_to_hist(const float2 *__restrict__ fpart, int cs, int fcols,
+                                                              ViewMap vm, const DevState *__restrict__ sts, DevHist h)
+{
+    const int v = blockIdx.x;
+    const DevState *st = sts + v;
+    __shared__ float2 red[kSumNT / 32];
+    __shared__ float2 tot[1];
+    const int f0 = fcols > 0 ? 0 : vm.pat_off[v] * cs, f1 = fcols > 0 ? fcols : vm.pat_off[v + 1] * cs;
+    float2 x[1] = {strided_sum(fpart + f0, f1 - f0, 1, 0)};
+    block_sum_ff<kSumNT, 1>(x, red, tot);
+    if (threadIdx.x == 0 && !st->stalled && st->m <= h.cap) h.F[(size_t)v * (h.cap + 1) + st->m] = ff_value(tot[0]);
 }
 
 // lin_period > 0: the next GRAD pass runs in the linear form unless the total iteration
@@ -558,6 +609,19 @@ cudaError_t launch_update(int H, int W, const ViewMap &vm, float2 *psi, const fl
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_update_counters<<<1, 32, 0, s>>>(st, vm.V, lin_period);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gd_step(const ViewMap &vm, const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s)
+{
+    k_gd_step<<<1, 32, 0, s>>>(vm, st, h, ls);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_to_hist(const float2 *fpart, int cs, int fcols, const ViewMap &vm, const DevState *st,
+                                     DevHist h, cudaStream_t s)
+{
+    k_objective_to_hist<<<vm.V, kSumNT, 0, s>>>(fpart, cs, fcols, vm, st, h);
     return cudaGetLastError();
 }
 

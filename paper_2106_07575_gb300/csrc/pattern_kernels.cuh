@@ -251,9 +251,26 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_adjoint_fft(PatternArg
     }
 }
 
+// Entry terms of the objective and the residual factor at one detector pixel with counts d,
+// a = |u|^2 + eps.  Poisson likelihood (Eq. 2, 3): f = -d log a, r = u (1 - d / a).  Least
+// squares on amplitudes: f = d - 2 sqrt(d) sqrt(a), r = u (1 - sqrt(d) / sqrt(a)).  The
+// |u|^2 term every pixel contributes is added by the caller; kept is the factor k with
+// r = u + k u, i.e. k = -d / a (likelihood) or -sqrt(d / a) (least squares).
+__device__ __forceinline__ void entry_terms(int est, float dv, float a, float &f, float &k)
+{
+    if (est == 0) {
+        f = -dv * logf(a);
+        k = -dv / a;
+    } else {
+        const float sd = sqrtf(dv), sa = sqrtf(a);
+        f = fmaf(-2.0f * sd, sa, dv);
+        k = -sd / sa;
+    }
+}
+
 // GRAD pattern pass (Eq. 2 and 3 for one pattern).
-//   f = sum_j |u_j|^2 - sum_{entries} d log(|u|^2 + eps)
-//   r = u, except r = u (1 - d / (|u|^2 + eps)) at the entries
+//   f = sum_j |u_j|^2 + sum_{entries} (entry term: -d log(|u|^2 + eps) for Eq. 2)
+//   r = u, except r = u (1 + k) at the entries (k = -d / (|u|^2 + eps) for Eq. 3)
 //   w = conj(p) F^H r;  u at the entries is kept for the line search of this iteration.
 // One pattern of the GRAD pass (full form).
 template <int P, int R, int NT>
@@ -288,8 +305,10 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
         float2 u = *pu;
         a.nz_u[e] = u;
         const float den = fmaf(u.x, u.x, u.y * u.y) + a.eps;
-        f -= dv * logf(den);
-        const float sc = 1.0f - dv / den;
+        float fe, k;
+        entry_terms(a.est, dv, den, fe, k);
+        f += fe;
+        const float sc = 1.0f + k;
         u.x *= sc;
         u.y *= sc;
         *pu = u;
@@ -363,7 +382,7 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
 // GRAD stage in the linear form (Eq. 1 is linear in psi): after an accepted step
 // psi_m = psi_{m-1} + gamma eta_{m-1}, the model at the entries is u_m = u_{m-1} + gamma v_{m-1}
 // (both kept there), so no forward DFT is needed.  The residual of Eq. 3 differs from u only
-// at the entries, r = u + Delta with Delta = -d u / (|u|^2 + eps); since F^H u = p psi, the
+// at the entries, r = u + Delta with Delta = k u (k of entry_terms); since F^H u = p psi, the
 // pattern's contribution to the gradient is conj(p) F^H Delta plus |p|^2 psi, and the latter
 // summed over positions is D psi (D the illumination map), added by the scatter-add.  The
 // objective keeps only its entry terms here; sum |u|^2 = P^2 sum D |psi|^2 comes from the
@@ -389,8 +408,9 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
         const float2 u = make_float2(fmaf(gam, v.x, u0.x), fmaf(gam, v.y, u0.y));
         a.nz_u[e] = u;
         const float den = fmaf(u.x, u.x, u.y * u.y) + a.eps;
-        f -= dv * logf(den);
-        const float sc = -dv / den;
+        float fe, sc;
+        entry_terms(a.est, dv, den, fe, sc);
+        f += fe;
         buf[(s / P) * LDB + (s % P - c * R)] = make_float2(u.x * sc, u.y * sc);
     }
     if (facc) {  // one view, persistent CTA: the thread's running sum over its patterns

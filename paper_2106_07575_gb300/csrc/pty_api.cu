@@ -206,6 +206,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.pat_view = c->pat_view;
     a.V = c->V;
     a.eps = (float)c->opts.eps;
+    a.est = c->opts.estimator;
     a.dsum = c->cert ? c->dsum : nullptr;
     return a;
 }
@@ -261,6 +262,9 @@ pty::LsArgs ls_args(const pty_ctx *c)
     l.max_halvings = c->opts.max_halvings;
     l.adaptive = c->opts.ls_window == 0;
     l.L = l.adaptive ? 32 : c->opts.ls_window;  // capacity of the later windows
+    l.warm = c->opts.ls_warm != 0;
+    l.gd = c->opts.solver == 1;
+    l.gd_step = c->opts.gd_step;
     return l;
 }
 
@@ -456,6 +460,23 @@ int launch_iteration(pty_ctx *c, bool timed)
     const pty::ScatterPlan plan = scatter_plan(c);
     const pty::ViewMap vm = view_map(c);
     const pty::LsArgs ls = ls_args(c);
+    if (ls.gd) {
+        // gradient descent (Eq. 4): GRAD (full form), scatter, F(psi_m), psi -= gamma g
+        {
+            StageTimer t(c, 0, timed);
+            CK(c->impl->grad(a, c->psi, c->w, c->fpart, c->st, c->s));
+        }
+        {
+            StageTimer t(c, 1, timed);
+            CK(scatter(c, a, plan, c->g, 1, c->part_sc, c->st, c->psi, c->illum));
+        }
+        StageTimer t(c, 3, timed);
+        CK(pty::launch_dy_finalize(c->fpart, c->CS, c->impl->grad_cols(a), c->part_sc, (double)c->P * c->P, vm, c->st,
+                                   c->hist, ls, c->s));
+        CK(pty::launch_gd_step(vm, ls, c->st, c->hist, c->s));
+        CK(pty::launch_update(c->HA, c->WA, vm, c->psi, c->g, c->eta_prev, c->g_prev, c->st, 0, c->s));
+        return PTY_OK;
+    }
     // first window >= 4 candidates when adaptive (then full windows of L), else L each
     const int first = ls.adaptive ? 4 : ls.L;
     const int rest = std::max(0, c->opts.max_halvings - first);
@@ -492,8 +513,13 @@ int launch_iteration(pty_ctx *c, bool timed)
     for (int wdx = 0; wdx < nwin; wdx++) {
         {
             StageTimer t(c, 4, timed);
-            // the first window of an adaptive search runs on the 8- (certified start only),
-            // 16- or 32-candidate kernel as the device chose; the others return at once
+            // the first window of an adaptive search runs on the 4- or 8- (warm start), 8-
+            // (certified start), 16- or 32-candidate kernel as the device chose; the others
+            // return at once
+            if (wdx == 0 && ls.adaptive && ls.warm) {
+                CK(pty::launch_ls_entries(a, c->CSl, c->V, 4, c->part_ls, c->st, c->s));
+                CK(pty::launch_ls_entries(a, c->CSl, c->V, 8, c->part_ls, c->st, c->s));
+            }
             if (wdx == 0 && ls.adaptive && c->cert)
                 CK(pty::launch_ls_entries(a, c->CSl, c->V, 8, c->part_ls, c->st, c->s));
             if (wdx == 0 && ls.adaptive) CK(pty::launch_ls_entries(a, c->CSl, c->V, 16, c->part_ls, c->st, c->s));
@@ -652,11 +678,17 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     if (opts) o = *opts;
     if (!(o.tau > 0.0 && o.tau < 1.0) || !(o.gamma0 > 0.0) || o.max_halvings < 1 || o.max_halvings > 1000 ||
         !(o.eps >= 0.0) || !std::isfinite(o.t) || (o.ls_window != 0 && !pty::ls_window_supported(o.ls_window)) ||
-        o.dft < 0 || o.dft > 2)
+        o.dft < 0 || o.dft > 2 || (o.estimator != 0 && o.estimator != 1) || (o.solver != 0 && o.solver != 1) ||
+        (o.ls_warm != 0 && o.ls_warm != 1) || (o.solver == 1 && !(o.gd_step > 0.0 && std::isfinite(o.gd_step))) ||
+        (o.solver == 1 && o.ls_warm))
         return fail(nullptr, PTY_ERR_ARG, "invalid options (tau in (0,1), gamma0 > 0, 1 <= max_halvings <= 1000, "
-                                          "eps >= 0, ls_window in {0,4,8,16,32}, dft in {0,1,2})");
+                                          "eps >= 0, ls_window in {0,4,8,16,32}, dft in {0,1,2}, estimator and "
+                                          "solver in {0,1}, gd_step > 0 with solver 1, ls_warm 0 or 1 with solver 0)");
     if (o.dft != 0 && !pty::tc_dft_supported(P))
         return fail(nullptr, PTY_ERR_UNSUPPORTED, "the tensor-core DFT supports P = 64 and 128");
+    if (o.dft != 0 && (o.estimator != 0 || o.solver != 0 || o.ls_warm))
+        return fail(nullptr, PTY_ERR_UNSUPPORTED,
+                    "the least-squares estimator, gradient descent and the warm-started search need dft = 0");
 
     // positions: host copy, bounds check per view, atlas coordinates, position sort
     std::vector<int32_t> hpos((size_t)2 * K);
@@ -918,7 +950,7 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
         if (at != PTY_OK) return bail(at);
     }
     // certified skip of leading line-search trials: adaptive windows of the FFT form
-    if (o.dft == 0 && o.ls_window == 0 && !(o.flags & 4)) {
+    if (o.dft == 0 && o.ls_window == 0 && !(o.flags & 4) && o.estimator == 0 && o.solver == 0 && !o.ls_warm) {
         cudaError_t ce2 = dalloc(&c->dsum, (size_t)K * c->CSl);
         if (ce2 == cudaSuccess) ce2 = pty::launch_chunk_dsum(pattern_args(c), c->CSl, c->dsum, c->s);
         if (ce2 == cudaSuccess) ce2 = cudaStreamSynchronize(c->s);
@@ -1001,6 +1033,12 @@ int solve(pty_ctx *c, float *const *psi, int32_t niter, pty_cg_report *rep)
             return st;
         }
     }
+    if (c->opts.solver == 1 && niter > 0) {
+        // gradient descent: F of the final object, the last entry of the history
+        const pty::PatternArgs a = pattern_args(c);
+        CK(c->impl->grad(a, c->psi, c->w, c->fpart, c->st, c->s));
+        CK(pty::launch_objective_to_hist(c->fpart, c->CS, c->impl->grad_cols(a), view_map(c), c->st, c->hist, c->s));
+    }
     CK(pty::launch_hash(c->HA, c->WA, c->row_view, c->psi, c->hash, c->V, c->s));
     CK(pty::launch_store_hash(c->st, c->V, c->hash, c->s));
     // the call's results: asynchronous copies into pinned staging, one synchronisation
@@ -1043,6 +1081,10 @@ void pty_default_opts(pty_opts *o)
     o->flags = 0;
     o->tile_config = -1;
     o->dft = 0;
+    o->estimator = 0;
+    o->solver = 0;
+    o->gd_step = 0.0;
+    o->ls_warm = 0;
 }
 
 const char *pty_last_error(const pty_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }

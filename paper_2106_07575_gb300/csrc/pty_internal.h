@@ -41,6 +41,8 @@ struct DevState {
     float cert_f[kCertN];  // gamma0 tau^(j+1), j < kCertN, rounded to FP32
     int k0cert;            // trials of the current iteration rejected by the certificate
     int last_excess;       // accepted trial index minus k0cert, last iteration (window size)
+    int kwarm;             // trials the warm-started search skipped this iteration: its first
+                           // trial is gamma0 tau^(kwarm + 1), the previous accepted step
 };
 
 // Per-call history arrays (device), one block of `cap` iterations per view, indexed by
@@ -73,6 +75,7 @@ struct PatternArgs {
     const int *pat_view;        // [K] view of sorted pattern i (all 0 for one view)
     int V;                      // views
     float eps;
+    int est;  // 0: Poisson likelihood (Eq. 2); 1: least squares on amplitudes
     // [K * CS] sum of the counts of each (pattern, CTA) chunk of the LS configuration; set
     // when the LS pass also writes the certificate rows (else nullptr)
     const float *dsum;
@@ -84,6 +87,9 @@ struct LsArgs {
     int max_halvings;
     int L;         // candidates per pass (the kernel's capacity)
     int adaptive;  // first window of an iteration sized from the previous trial count
+    int warm;      // warm-started search: the first trial is the previous accepted step
+    int gd;        // gradient descent (Eq. 4): no direction coefficient, no line search
+    double gd_step;
 };
 
 // ---- pattern kernels (pattern_kernels.cuh, instantiated per P in pattern_p*.cu) ----
@@ -248,6 +254,13 @@ cudaError_t launch_eta(int H, int W, const ScatterPlan &plan, const float2 *psi,
 // lin_period iterations).
 cudaError_t launch_update(int H, int W, const ViewMap &vm, float2 *psi, const float2 *g, float2 *eta_prev,
                           float2 *g_prev, DevState *st, int lin_period, cudaStream_t s);
+// Gradient descent (Eq. 4): the step of every view is ls.gd_step, taken without a search
+// (history: gamma = gd_step, trials 0, F(psi_{m+1}) written by the next GRAD stage).
+cudaError_t launch_gd_step(const ViewMap &vm, const LsArgs &ls, DevState *st, DevHist h, cudaStream_t s);
+// F(psi) of each view from the GRAD pass's objective partials into the history slot of the
+// current iteration count (the final objective of a gradient-descent call).
+cudaError_t launch_objective_to_hist(const float2 *fpart, int cs, int fcols, const ViewMap &vm, const DevState *st,
+                                     DevHist h, cudaStream_t s);
 // flag |= 1 if any of the n floats is NaN, Inf or negative.
 cudaError_t launch_check_data(const float *d, size_t n, int *flag, cudaStream_t s);
 cudaError_t launch_begin_solve(DevState *st, int V, cudaStream_t s);

@@ -50,7 +50,13 @@ class PtyError(RuntimeError):
 class pty_opts(ctypes.Structure):
     _fields_ = [("gamma0", ctypes.c_double), ("tau", ctypes.c_double), ("t", ctypes.c_double),
                 ("max_halvings", ctypes.c_int32), ("eps", ctypes.c_double), ("ls_window", ctypes.c_int32),
-                ("flags", ctypes.c_int32), ("tile_config", ctypes.c_int32), ("dft", ctypes.c_int32)]
+                ("flags", ctypes.c_int32), ("tile_config", ctypes.c_int32), ("dft", ctypes.c_int32),
+                ("estimator", ctypes.c_int32), ("solver", ctypes.c_int32), ("gd_step", ctypes.c_double),
+                ("ls_warm", ctypes.c_int32)]
+
+
+EST_ML, EST_LS = 0, 1  # pty_opts.estimator
+SOLVER_CG, SOLVER_GD = 0, 1  # pty_opts.solver
 
 
 class pty_adam(ctypes.Structure):

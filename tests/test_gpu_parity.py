@@ -294,6 +294,75 @@ def test_production_gradient(orc, production):
     assert abs(F - Fw) <= OBJ_TOL * abs(Fw)
 
 
+def test_production_cg_ten_iterations(orc, production):
+    """Production size (1024^2, P = 128, K = 3600), the first 10 CG iterations of Algorithm 1:
+    objective per iteration within 1e-4 of the FP64 oracle and identical trial counts."""
+    p = production
+    ctx, st, rep, want, psi = _cg_compare(orc, p, 10)
+    assert st == pty.PTY_OK and rep["iters_done"] == 10
+    relF = np.abs(rep["F"] - want["F"]) / np.abs(want["F"])
+    print("production 10 iterations: objective rel", " ".join(f"{x:.1e}" for x in relF))
+    print("trials gpu", list(rep["halvings"]), "oracle", list(want["halvings"]))
+    assert np.all(relF <= OBJ_TOL)
+    assert list(rep["halvings"]) == list(want["halvings"])
+    np.testing.assert_array_equal(rep["gamma"], want["gamma"])
+    e = rel(psi.cpu().numpy(), want["psi"])
+    print(f"production psi_10 rel L2 vs FP64: {e:.3e}")
+    assert e <= 1e-2  # reported: CG amplifies the FP32 rounding of the iterates (no stated tolerance)
+
+
+def test_objective_sum_matches_fp64_sum_of_the_same_terms(production):
+    """The objective's float-float reduction against an FP64 sum of the same per-pixel terms.
+
+    u = G psi comes from the library's own forward pass (the DFT the gradient pass runs, same
+    bits); the terms |u|^2 - d log(|u|^2 + eps) are formed from those FP32 values in FP64 and
+    summed in FP64.  What remains is each term's FP32 rounding on the GPU and the reduction's
+    error: bounded by 1e-6 of sum |terms|."""
+    p = production
+    ctx = make_ctx(p)
+    psi = random_object(p, 12)
+    out = torch.empty((p.K, p.P, p.P), dtype=torch.complex64, device="cuda")
+    ctx.forward(dev(psi), out)
+    g = torch.empty((p.H, p.W), dtype=torch.complex64, device="cuda")
+    F = ctx.gradient(dev(psi), g)
+    u = out.to(torch.complex128)
+    d = torch.from_numpy(p.d).cuda().to(torch.float64)
+    a = u.real ** 2 + u.imag ** 2
+    terms = a - torch.where(d > 0, d * torch.log(a + 0.1), torch.zeros_like(a))
+    F64 = float(terms.sum())
+    mag = float(terms.abs().sum())
+    F32 = float(terms.to(torch.float32).view(-1).cumsum(0, dtype=torch.float32)[-1])  # plain FP32 running sum
+    print(f"objective: float-float {F:.10e}, FP64 sum of the same terms {F64:.10e}, |diff|/sum|terms| "
+          f"{abs(F - F64) / mag:.2e} (plain FP32 running sum: {abs(F32 - F64) / mag:.2e})")
+    assert abs(F - F64) <= 1e-6 * mag
+
+
+def test_dai_yuan_sums_match_fp64_sums_of_the_same_vectors(production):
+    """alpha of Eq. 6 from the float-float tile sums against FP64 sums of the same g vectors.
+
+    With the linear form off every GRAD pass is the full one, so the g of the CG iteration is
+    bit for bit pty_gradient's; alpha_1 = ||g_1||^2 / Re <eta_0, g_1 - g_0>, eta_0 = -g_0, is
+    recomputed in FP64 from those FP32 vectors."""
+    p = production
+    o = pty.default_opts()
+    o.flags = 2  # no linear form
+    ctx = make_ctx(p, o)
+    psi = dev(p.psi0())
+    g0 = torch.empty((p.H, p.W), dtype=torch.complex64, device="cuda")
+    ctx.gradient(psi, g0)
+    ctx.cg_solve(psi, 1)
+    g1 = torch.empty_like(g0)
+    ctx.gradient(psi, g1)
+    st, rep = ctx.cg_solve(psi, 1)  # continues the CG state: its alpha is alpha_1
+    a, b = g0.to(torch.complex128), g1.to(torch.complex128)
+    num = float((b.real ** 2 + b.imag ** 2).sum())
+    den = float(((-a).real * (b - a).real + (-a).imag * (b - a).imag).sum())
+    alpha64 = num / den
+    e = abs(rep["alpha"][0] - alpha64) / abs(alpha64)
+    print(f"alpha_1: GPU {rep['alpha'][0]:.10e}, FP64 sums of the same vectors {alpha64:.10e}, rel {e:.2e}")
+    assert e <= 1e-5
+
+
 def test_production_cg_two_iterations(orc, production):
     p = production
     ctx, st, rep, want, psi = _cg_compare(orc, p, 2)

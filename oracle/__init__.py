@@ -6,6 +6,8 @@ import this package.  The product path (``paper_2106_07575_gb300``) never import
 from .orc import (  # noqa: F401
     build,
     fft2,
+    shift_probe,
+    subpixel_probes,
     Q,
     QH,
     forward,

@@ -33,7 +33,10 @@
  *    BEFORE each trial (do-while), and shrinking stops at the first trial with
  *    F(psi + gamma eta) <= F(psi) + gamma t.  After max_halvings failed trials the solve
  *    stops with psi unchanged for that iteration ("stalled").
- *  - Scan positions are integer top-left corners (row, col) of the P x P patch.
+ *  - Scan positions are integer top-left corners (row, col) of the P x P patch.  Every
+ *    entry point takes either one probe [P][P] shared by all positions (per_pos = 0) or
+ *    one probe per position [K][P][P] (per_pos = 1); a fractional position s is taken as
+ *    the window floor(s) with the probe shifted by s - floor(s) (orc_shift_probe).
  *  - The least-squares (Gaussian) estimator, which the paper names beside the ML estimate
  *    but does not write out, is taken on amplitudes: F_LS = sum (|u| - sqrt d)^2, guarded
  *    as F_LS,eps = sum |u|^2 - 2 sqrt(d) sqrt(|u|^2 + eps) + d, whose exact Wirtinger
@@ -132,6 +135,50 @@ int orc_fft2(double *x, int P, int inverse)
     return ORC_OK;
 }
 
+/*
+ * Sub-pixel shift of the probe by (dy, dx) pixels, for scan positions with a fractional
+ * part (the paper's positions are float32; it does not say how a fraction enters Q).
+ * Fourier shift theorem with the unitary F of Eq. 1:
+ *   out = F^H[ F[p](ky, kx) * phi_dy(ky) * phi_dx(kx) ],
+ *   phi_delta(kappa) = exp(-2 pi i kappa delta / P) for the signed frequency
+ *   kappa = j (j < P/2) or j - P (j > P/2), and cos(pi delta) at the Nyquist index j = P/2
+ *   (the real part of exp(+-i pi delta), so that a real probe stays real).
+ * So out(r) = p(r - delta) for a probe band-limited below Nyquist, and an integer shift is
+ * the circular shift of the P x P window.
+ */
+int orc_shift_probe(int P, const double *probe, double dy, double dx, double *out)
+{
+    if (!is_pow2(P) || P < 2 || !probe || !out || !isfinite(dy) || !isfinite(dx)) return ORC_ERR_ARG;
+    cplx *tw = make_twiddles(P);
+    cplx *fy = (cplx *)malloc(sizeof(cplx) * (size_t)P), *fx = (cplx *)malloc(sizeof(cplx) * (size_t)P);
+    if (!tw || !fy || !fx) {
+        free(tw);
+        free(fy);
+        free(fx);
+        return ORC_ERR_NOMEM;
+    }
+    for (int j = 0; j < P; j++) {
+        int kappa = j < P / 2 ? j : j - P;
+        if (j == P / 2) {
+            fy[j] = cos(ORC_PI * dy);
+            fx[j] = cos(ORC_PI * dx);
+        } else {
+            fy[j] = cexp(-2.0 * ORC_PI * I * (double)kappa * dy / (double)P);
+            fx[j] = cexp(-2.0 * ORC_PI * I * (double)kappa * dx / (double)P);
+        }
+    }
+    cplx *x = (cplx *)out;
+    memcpy(x, probe, sizeof(cplx) * (size_t)P * P);
+    fft2_unitary(x, P, 0, tw);
+    for (int y = 0; y < P; y++)
+        for (int c = 0; c < P; c++) x[(long)y * P + c] *= fy[y] * fx[c];
+    fft2_unitary(x, P, 1, tw);
+    free(tw);
+    free(fy);
+    free(fx);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Argument checks shared by the operator entry points.                      */
 /* ------------------------------------------------------------------------- */
@@ -157,47 +204,53 @@ static int nthreads_eff(int nthreads)
 #endif
 }
 
-/* Q (Eq. 1): e_k[y][x] = p[y][x] * psi[r_k + y][c_k + x]. */
-static void apply_Q(int W, int P, const cplx *p, const int *pos, int k, const cplx *psi, cplx *e)
+/* Q (Eq. 1): e_k[y][x] = p_k[y][x] * psi[r_k + y][c_k + x], where p_k = p + k * ps is the
+ * probe of position k: ps = 0 for one probe shared by all positions, ps = P*P for one
+ * probe per position (sub-pixel positions, orc_shift_probe). */
+static void apply_Q(int W, int P, const cplx *p, long ps, const int *pos, int k, const cplx *psi, cplx *e)
 {
     int r = pos[2 * k], c = pos[2 * k + 1];
+    p += (long)k * ps;
     for (int y = 0; y < P; y++)
         for (int x = 0; x < P; x++)
             e[(long)y * P + x] = p[(long)y * P + x] * psi[(long)(r + y) * W + (c + x)];
 }
 
-/* Q^H for one position (Eq. 3): acc[r_k + y][c_k + x] += conj(p[y][x]) * w[y][x]. */
-static void apply_QH_add(int W, int P, const cplx *p, const int *pos, int k, const cplx *w, cplx *acc)
+/* Q^H for one position (Eq. 3): acc[r_k + y][c_k + x] += conj(p_k[y][x]) * w[y][x]. */
+static void apply_QH_add(int W, int P, const cplx *p, long ps, const int *pos, int k, const cplx *w, cplx *acc)
 {
     int r = pos[2 * k], c = pos[2 * k + 1];
+    p += (long)k * ps;
     for (int y = 0; y < P; y++)
         for (int x = 0; x < P; x++)
             acc[(long)(r + y) * W + (c + x)] += conj(p[(long)y * P + x]) * w[(long)y * P + x];
 }
 
 /* Q alone: out[K][P][P] = Q psi. */
-int orc_Q(int H, int W, int P, const double *probe, int K, const int *pos, const double *psi, double *out)
+int orc_Q(int H, int W, int P, const double *probe, int per_pos, int K, const int *pos, const double *psi,
+          double *out)
 {
     int st = check_geom(H, W, P, K, pos);
     if (st) return st;
     for (int k = 0; k < K; k++)
-        apply_Q(W, P, (const cplx *)probe, pos, k, (const cplx *)psi, (cplx *)out + (long)k * P * P);
+        apply_Q(W, P, (const cplx *)probe, (per_pos ? (long)P * P : 0), pos, k, (const cplx *)psi, (cplx *)out + (long)k * P * P);
     return ORC_OK;
 }
 
-/* Q^H alone: x[H][W] = sum_k shift_k(conj(p) * y_k). */
-int orc_QH(int H, int W, int P, const double *probe, int K, const int *pos, const double *y, double *x)
+/* Q^H alone: x[H][W] = sum_k shift_k(conj(p_k) * y_k). */
+int orc_QH(int H, int W, int P, const double *probe, int per_pos, int K, const int *pos, const double *y,
+           double *x)
 {
     int st = check_geom(H, W, P, K, pos);
     if (st) return st;
     memset(x, 0, sizeof(cplx) * (size_t)H * W);
     for (int k = 0; k < K; k++)
-        apply_QH_add(W, P, (const cplx *)probe, pos, k, (const cplx *)y + (long)k * P * P, (cplx *)x);
+        apply_QH_add(W, P, (const cplx *)probe, (per_pos ? (long)P * P : 0), pos, k, (const cplx *)y + (long)k * P * P, (cplx *)x);
     return ORC_OK;
 }
 
-/* G = F Q (Eq. 1): out[K][P][P] = unitary DFT2(p * patch_k). */
-int orc_forward(int H, int W, int P, const double *probe, int K, const int *pos, const double *psi,
+/* G = F Q (Eq. 1): out[K][P][P] = unitary DFT2(p_k * patch_k). */
+int orc_forward(int H, int W, int P, const double *probe, int per_pos, int K, const int *pos, const double *psi,
                 double *out, int nthreads)
 {
     int st = check_geom(H, W, P, K, pos);
@@ -208,7 +261,7 @@ int orc_forward(int H, int W, int P, const double *probe, int K, const int *pos,
 #pragma omp parallel for num_threads(T) schedule(static)
     for (int k = 0; k < K; k++) {
         cplx *u = (cplx *)out + (long)k * P * P;
-        apply_Q(W, P, (const cplx *)probe, pos, k, (const cplx *)psi, u);
+        apply_Q(W, P, (const cplx *)probe, (per_pos ? (long)P * P : 0), pos, k, (const cplx *)psi, u);
         fft2_unitary(u, P, 0, tw);
     }
     free(tw);
@@ -254,6 +307,7 @@ static int run_patterns_scatter(int K, int P, int H, int W, int T, pattern_fn fn
 struct adj_ctx {
     int W, P;
     const cplx *p, *y;
+    long ps;
     const int *pos;
     const cplx *tw;
 };
@@ -265,17 +319,17 @@ static void adj_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
     long PP = (long)c->P * c->P;
     memcpy(work, c->y + (long)k * PP, sizeof(cplx) * PP);
     fft2_unitary(work, c->P, 1, c->tw);
-    apply_QH_add(c->W, c->P, c->p, c->pos, k, work, acc);
+    apply_QH_add(c->W, c->P, c->p, c->ps, c->pos, k, work, acc);
 }
 
-int orc_adjoint(int H, int W, int P, const double *probe, int K, const int *pos, const double *y,
+int orc_adjoint(int H, int W, int P, const double *probe, int per_pos, int K, const int *pos, const double *y,
                 double *x, int nthreads)
 {
     int st = check_geom(H, W, P, K, pos);
     if (st) return st;
     cplx *tw = make_twiddles(P);
     if (!tw) return ORC_ERR_NOMEM;
-    struct adj_ctx c = {W, P, (const cplx *)probe, (const cplx *)y, pos, tw};
+    struct adj_ctx c = {W, P, (const cplx *)probe, (const cplx *)y, (per_pos ? (long)P * P : 0), pos, tw};
     st = run_patterns_scatter(K, P, H, W, nthreads_eff(nthreads), adj_one, &c, (cplx *)x, NULL);
     free(tw);
     return st;
@@ -287,6 +341,7 @@ int orc_adjoint(int H, int W, int P, const double *probe, int K, const int *pos,
 struct obj_ctx {
     int W, P;
     const cplx *p, *psi;
+    long ps;
     const int *pos;
     const float *d;
     double eps;
@@ -323,7 +378,7 @@ static void obj_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
     (void)acc;
     struct obj_ctx *c = (struct obj_ctx *)vctx;
     long PP = (long)c->P * c->P;
-    apply_Q(c->W, c->P, c->p, c->pos, k, c->psi, work);
+    apply_Q(c->W, c->P, c->p, c->ps, c->pos, k, c->psi, work);
     fft2_unitary(work, c->P, 0, c->tw);
     const float *dk = c->d + (long)k * PP;
     double s = 0.0;
@@ -335,7 +390,7 @@ static void grad_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
 {
     struct obj_ctx *c = (struct obj_ctx *)vctx;
     long PP = (long)c->P * c->P;
-    apply_Q(c->W, c->P, c->p, c->pos, k, c->psi, work);
+    apply_Q(c->W, c->P, c->p, c->ps, c->pos, k, c->psi, work);
     fft2_unitary(work, c->P, 0, c->tw);
     const float *dk = c->d + (long)k * PP;
     double s = 0.0;
@@ -345,11 +400,11 @@ static void grad_one(int k, cplx *work, cplx *acc, double *fpart, void *vctx)
     }
     *fpart = s;
     fft2_unitary(work, c->P, 1, c->tw);
-    apply_QH_add(c->W, c->P, c->p, c->pos, k, work, acc);
+    apply_QH_add(c->W, c->P, c->p, c->ps, c->pos, k, work, acc);
 }
 
 /* Objective with per-pattern partials summed in pattern order. */
-static int objective_impl(int H, int W, int P, const cplx *p, int K, const int *pos, const float *d,
+static int objective_impl(int H, int W, int P, const cplx *p, long ps, int K, const int *pos, const float *d,
                           double eps, int est, const cplx *psi, const cplx *tw, int T, double *F)
 {
     double *fpart = (double *)malloc(sizeof(double) * (size_t)K);
@@ -359,7 +414,7 @@ static int objective_impl(int H, int W, int P, const cplx *p, int K, const int *
         free(work);
         return ORC_ERR_NOMEM;
     }
-    struct obj_ctx c = {W, P, p, psi, pos, d, eps, est, tw};
+    struct obj_ctx c = {W, P, p, psi, ps, pos, d, eps, est, tw};
     (void)H;
 #pragma omp parallel for num_threads(T) schedule(static)
     for (int k = 0; k < K; k++) {
@@ -378,12 +433,12 @@ static int objective_impl(int H, int W, int P, const cplx *p, int K, const int *
     return ORC_OK;
 }
 
-static int gradient_impl(int H, int W, int P, const cplx *p, int K, const int *pos, const float *d,
+static int gradient_impl(int H, int W, int P, const cplx *p, long ps, int K, const int *pos, const float *d,
                          double eps, int est, const cplx *psi, const cplx *tw, int T, cplx *g, double *F)
 {
     double *fpart = (double *)malloc(sizeof(double) * (size_t)K);
     if (!fpart) return ORC_ERR_NOMEM;
-    struct obj_ctx c = {W, P, p, psi, pos, d, eps, est, tw};
+    struct obj_ctx c = {W, P, p, psi, ps, pos, d, eps, est, tw};
     int st = run_patterns_scatter(K, P, H, W, T, grad_one, &c, g, fpart);
     if (st == ORC_OK && F) {
         double s = 0.0;
@@ -394,7 +449,7 @@ static int gradient_impl(int H, int W, int P, const cplx *p, int K, const int *p
     return st;
 }
 
-int orc_objective(int H, int W, int P, const double *probe, int K, const int *pos, const float *d,
+int orc_objective(int H, int W, int P, const double *probe, int per_pos, int K, const int *pos, const float *d,
                   double eps, int est, const double *psi, double *F, int nthreads)
 {
     if (est != ORC_EST_ML && est != ORC_EST_LS) return ORC_ERR_ARG;
@@ -403,13 +458,14 @@ int orc_objective(int H, int W, int P, const double *probe, int K, const int *po
     if (!F || !d || !psi || !probe) return ORC_ERR_ARG;
     cplx *tw = make_twiddles(P);
     if (!tw) return ORC_ERR_NOMEM;
-    st = objective_impl(H, W, P, (const cplx *)probe, K, pos, d, eps, est, (const cplx *)psi, tw,
+    st = objective_impl(H, W, P, (const cplx *)probe, (per_pos ? (long)P * P : 0), K, pos, d, eps, est,
+                        (const cplx *)psi, tw,
                         nthreads_eff(nthreads), F);
     free(tw);
     return st;
 }
 
-int orc_gradient(int H, int W, int P, const double *probe, int K, const int *pos, const float *d,
+int orc_gradient(int H, int W, int P, const double *probe, int per_pos, int K, const int *pos, const float *d,
                  double eps, int est, const double *psi, double *g, double *F, int nthreads)
 {
     if (est != ORC_EST_ML && est != ORC_EST_LS) return ORC_ERR_ARG;
@@ -418,7 +474,8 @@ int orc_gradient(int H, int W, int P, const double *probe, int K, const int *pos
     if (!g || !d || !psi || !probe) return ORC_ERR_ARG;
     cplx *tw = make_twiddles(P);
     if (!tw) return ORC_ERR_NOMEM;
-    st = gradient_impl(H, W, P, (const cplx *)probe, K, pos, d, eps, est, (const cplx *)psi, tw,
+    st = gradient_impl(H, W, P, (const cplx *)probe, (per_pos ? (long)P * P : 0), K, pos, d, eps, est,
+                       (const cplx *)psi, tw,
                        nthreads_eff(nthreads), (cplx *)g, F);
     free(tw);
     return st;
@@ -471,7 +528,7 @@ static double re_dot(const cplx *a, const cplx *b, long n)
  * With opts->solver == ORC_SOLVER_GD the iterations are Eq. 4 instead: psi -= gd_step g,
  * gamma = gd_step, no trials (halvings 0), alpha 0; F_hist[m+1] = F(psi_{m+1}).
  */
-int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos, const float *d,
+int orc_cg_solve(int H, int W, int P, const double *probe, int per_pos, int K, const int *pos, const float *d,
                  const orc_opts *opts, double *psi_io, int niter, double *F_hist, double *gamma_out,
                  int *halvings_out, double *alpha_out, int *iters_done, double *t_hist, int nthreads)
 {
@@ -493,6 +550,7 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
         goto done;
     }
     const cplx *p = (const cplx *)probe;
+    const long ps = (per_pos ? (long)P * P : 0);
     int m;
     if (iters_done) *iters_done = 0;
     double gam_prev = 0.0; /* last accepted step of this solve (warm start) */
@@ -500,7 +558,7 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
     for (m = 0; m < niter; m++) {
         /* GRAD stage: g_m = grad F(psi_m), F_m = F(psi_m) */
         double Fm;
-        st = gradient_impl(H, W, P, p, K, pos, d, opts->eps, est, psi, tw, T, g, &Fm);
+        st = gradient_impl(H, W, P, p, ps, K, pos, d, opts->eps, est, psi, tw, T, g, &Fm);
         if (st) goto done;
         if (F_hist) F_hist[m] = Fm;
         if (opts->solver == ORC_SOLVER_GD) {
@@ -511,7 +569,7 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
             if (alpha_out) alpha_out[m] = 0.0;
             if (F_hist && m + 1 == niter) {
                 double Fn;
-                st = objective_impl(H, W, P, p, K, pos, d, opts->eps, est, psi, tw, T, &Fn);
+                st = objective_impl(H, W, P, p, ps, K, pos, d, opts->eps, est, psi, tw, T, &Fn);
                 if (st) goto done;
                 F_hist[m + 1] = Fn;
             }
@@ -544,7 +602,7 @@ int orc_cg_solve(int H, int W, int P, const double *probe, int K, const int *pos
             gam *= opts->tau;
             k++;
             for (long i = 0; i < n; i++) trial[i] = psi[i] + gam * eta[i];
-            st = objective_impl(H, W, P, p, K, pos, d, opts->eps, est, trial, tw, T, &Ft);
+            st = objective_impl(H, W, P, p, ps, K, pos, d, opts->eps, est, trial, tw, T, &Ft);
             if (st) goto done;
             ok = (Ft <= Fm + gam * opts->t);
         } while (!ok && k < opts->max_halvings);

@@ -94,14 +94,15 @@ def _get():
         i = ctypes.c_int
         d = ctypes.c_double
         lib.orc_fft2.argtypes = [P, i, i]
-        lib.orc_Q.argtypes = [i, i, i, P, i, P, P, P]
-        lib.orc_QH.argtypes = [i, i, i, P, i, P, P, P]
-        lib.orc_forward.argtypes = [i, i, i, P, i, P, P, P, i]
-        lib.orc_adjoint.argtypes = [i, i, i, P, i, P, P, P, i]
-        lib.orc_objective.argtypes = [i, i, i, P, i, P, P, d, i, P, P, i]
-        lib.orc_gradient.argtypes = [i, i, i, P, i, P, P, d, i, P, P, P, i]
-        lib.orc_cg_solve.argtypes = [i, i, i, P, i, P, P, ctypes.POINTER(_Opts), P, i, P, P, P, P, P, P, i]
-        for f in ("orc_fft2", "orc_Q", "orc_QH", "orc_forward", "orc_adjoint", "orc_objective",
+        lib.orc_shift_probe.argtypes = [i, P, d, d, P]
+        lib.orc_Q.argtypes = [i, i, i, P, i, i, P, P, P]
+        lib.orc_QH.argtypes = [i, i, i, P, i, i, P, P, P]
+        lib.orc_forward.argtypes = [i, i, i, P, i, i, P, P, P, i]
+        lib.orc_adjoint.argtypes = [i, i, i, P, i, i, P, P, P, i]
+        lib.orc_objective.argtypes = [i, i, i, P, i, i, P, P, d, i, P, P, i]
+        lib.orc_gradient.argtypes = [i, i, i, P, i, i, P, P, d, i, P, P, P, i]
+        lib.orc_cg_solve.argtypes = [i, i, i, P, i, i, P, P, ctypes.POINTER(_Opts), P, i, P, P, P, P, P, P, i]
+        for f in ("orc_fft2", "orc_shift_probe", "orc_Q", "orc_QH", "orc_forward", "orc_adjoint", "orc_objective",
                   "orc_gradient", "orc_cg_solve"):
             getattr(lib, f).restype = ctypes.c_int
         _lib = lib
@@ -120,6 +121,18 @@ def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
 
 
+def _probe(probe, K):
+    """(complex128 probe, P, per_pos): one [P][P] probe for every position, or [K][P][P]."""
+    probe = _c128(probe)
+    if probe.ndim == 3:
+        if probe.shape[0] != K or probe.shape[1] != probe.shape[2]:
+            raise ValueError(f"per-position probes must be [K={K}][P][P], got {probe.shape}")
+        return probe, probe.shape[1], 1
+    if probe.ndim != 2 or probe.shape[0] != probe.shape[1]:
+        raise ValueError(f"probe must be [P][P] or [K][P][P], got {probe.shape}")
+    return probe, probe.shape[0], 0
+
+
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
@@ -136,44 +149,64 @@ def fft2(x, inverse=False):
     return x
 
 
+def shift_probe(probe, dy, dx):
+    """The probe shifted by (dy, dx) pixels by the Fourier shift theorem (sub-pixel positions);
+    see orc_shift_probe in orc.c for the definition, including the Nyquist bins."""
+    probe = _c128(probe)
+    out = np.empty_like(probe)
+    _check(_get().orc_shift_probe(probe.shape[0], _ptr(probe), float(dy), float(dx), _ptr(out)), "shift_probe")
+    return out
+
+
+def subpixel_probes(probe, pos):
+    """(integer positions [K][2], per-position probes [K][P][P]) for fractional positions
+    (row, col): the window starts at floor(pos), the probe is shifted by pos - floor(pos)."""
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 2)
+    base = np.floor(pos)
+    frac = pos - base
+    probes = np.stack([shift_probe(probe, fy, fx) if (fy or fx) else _c128(probe).copy() for fy, fx in frac])
+    return base.astype(np.int32), probes
+
+
 def Q(psi, probe, pos):
-    """Q psi: probe times the P x P patch at every scan position -> [K][P][P]."""
-    psi, probe, pos = _c128(psi), _c128(probe), _pos(pos)
+    """Q psi: probe times the P x P patch at every scan position -> [K][P][P].  probe is
+    [P][P] (shared) or [K][P][P] (one per position), as for every function below."""
+    psi, pos = _c128(psi), _pos(pos)
+    probe, P, pp = _probe(probe, pos.shape[0])
     H, W = psi.shape
-    P = probe.shape[0]
     out = np.empty((pos.shape[0], P, P), np.complex128)
-    _check(_get().orc_Q(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(psi), _ptr(out)), "Q")
+    _check(_get().orc_Q(H, W, P, _ptr(probe), pp, pos.shape[0], _ptr(pos), _ptr(psi), _ptr(out)), "Q")
     return out
 
 
 def QH(y, probe, pos, shape):
     """Q^H y: conj(probe) times each patch, scatter-added into an H x W object."""
-    y, probe, pos = _c128(y), _c128(probe), _pos(pos)
+    y, pos = _c128(y), _pos(pos)
+    probe, P, pp = _probe(probe, pos.shape[0])
     H, W = shape
-    P = probe.shape[0]
     out = np.empty((H, W), np.complex128)
-    _check(_get().orc_QH(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(y), _ptr(out)), "QH")
+    _check(_get().orc_QH(H, W, P, _ptr(probe), pp, pos.shape[0], _ptr(pos), _ptr(y), _ptr(out)), "QH")
     return out
 
 
 def forward(psi, probe, pos, nthreads=1):
     """G psi = F Q psi (Eq. 1), unitary F -> [K][P][P] complex128."""
-    psi, probe, pos = _c128(psi), _c128(probe), _pos(pos)
+    psi, pos = _c128(psi), _pos(pos)
+    probe, P, pp = _probe(probe, pos.shape[0])
     H, W = psi.shape
-    P = probe.shape[0]
     out = np.empty((pos.shape[0], P, P), np.complex128)
-    st = _get().orc_forward(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(psi), _ptr(out), nthreads)
+    st = _get().orc_forward(H, W, P, _ptr(probe), pp, pos.shape[0], _ptr(pos), _ptr(psi), _ptr(out), nthreads)
     _check(st, "forward")
     return out
 
 
 def adjoint(y, probe, pos, shape, nthreads=1):
     """G^H y = Q^H F^H y (the operator of Eq. 3) -> [H][W] complex128."""
-    y, probe, pos = _c128(y), _c128(probe), _pos(pos)
+    y, pos = _c128(y), _pos(pos)
+    probe, P, pp = _probe(probe, pos.shape[0])
     H, W = shape
-    P = probe.shape[0]
     out = np.empty((H, W), np.complex128)
-    st = _get().orc_adjoint(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(y), _ptr(out), nthreads)
+    st = _get().orc_adjoint(H, W, P, _ptr(probe), pp, pos.shape[0], _ptr(pos), _ptr(y), _ptr(out), nthreads)
     _check(st, "adjoint")
     return out
 
@@ -181,11 +214,11 @@ def adjoint(y, probe, pos, shape, nthreads=1):
 def objective(psi, probe, pos, d, eps=0.1, nthreads=1, est=EST_ML):
     """F_eps(psi) = sum |G psi|^2 - d log(|G psi|^2 + eps) (Eq. 2 with the eps guard), or with
     est=EST_LS the amplitude least squares sum |G psi|^2 - 2 sqrt(d) sqrt(|G psi|^2 + eps) + d."""
-    psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
+    psi, pos, d = _c128(psi), _pos(pos), _f32(d)
+    probe, P, pp = _probe(probe, pos.shape[0])
     H, W = psi.shape
-    P = probe.shape[0]
     F = ctypes.c_double(0.0)
-    st = _get().orc_objective(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, est, _ptr(psi),
+    st = _get().orc_objective(H, W, P, _ptr(probe), pp, pos.shape[0], _ptr(pos), _ptr(d), eps, est, _ptr(psi),
                               ctypes.byref(F), nthreads)
     _check(st, "objective")
     return F.value
@@ -194,12 +227,12 @@ def objective(psi, probe, pos, d, eps=0.1, nthreads=1, est=EST_ML):
 def gradient(psi, probe, pos, d, eps=0.1, nthreads=1, est=EST_ML):
     """(g, F): g = G^H(G psi - d G psi / (|G psi|^2 + eps)) (Eq. 3), F as in objective(); with
     est=EST_LS g = G^H(G psi - sqrt(d) G psi / sqrt(|G psi|^2 + eps))."""
-    psi, probe, pos, d = _c128(psi), _c128(probe), _pos(pos), _f32(d)
+    psi, pos, d = _c128(psi), _pos(pos), _f32(d)
+    probe, P, pp = _probe(probe, pos.shape[0])
     H, W = psi.shape
-    P = probe.shape[0]
     g = np.empty((H, W), np.complex128)
     F = ctypes.c_double(0.0)
-    st = _get().orc_gradient(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), eps, est, _ptr(psi),
+    st = _get().orc_gradient(H, W, P, _ptr(probe), pp, pos.shape[0], _ptr(pos), _ptr(d), eps, est, _ptr(psi),
                              _ptr(g), ctypes.byref(F), nthreads)
     _check(st, "gradient")
     return g, F.value
@@ -215,9 +248,9 @@ def cg_solve(psi0, probe, pos, d, niter, opts: OrcOpts | None = None, nthreads=1
     """
     opts = opts or OrcOpts()
     psi = _c128(psi0).copy()
-    probe, pos, d = _c128(probe), _pos(pos), _f32(d)
+    pos, d = _pos(pos), _f32(d)
+    probe, P, pp = _probe(probe, pos.shape[0])
     H, W = psi.shape
-    P = probe.shape[0]
     o = _Opts(opts.gamma0, opts.tau, opts.t, opts.max_halvings, opts.eps, int(opts.est), int(opts.solver),
               float(opts.gd_step), int(bool(opts.warm)))
     F = np.full(niter + 1, np.nan)
@@ -226,7 +259,7 @@ def cg_solve(psi0, probe, pos, d, niter, opts: OrcOpts | None = None, nthreads=1
     alpha = np.full(max(niter, 1), np.nan)
     tim = np.full(max(niter, 1), np.nan)
     done = ctypes.c_int(0)
-    st = _get().orc_cg_solve(H, W, P, _ptr(probe), pos.shape[0], _ptr(pos), _ptr(d), ctypes.byref(o),
+    st = _get().orc_cg_solve(H, W, P, _ptr(probe), pp, pos.shape[0], _ptr(pos), _ptr(d), ctypes.byref(o),
                              _ptr(psi), niter, _ptr(F), _ptr(gam), _ptr(halv), _ptr(alpha),
                              ctypes.byref(done), _ptr(tim), nthreads)
     if st not in (ORC_OK, ORC_STALLED):

@@ -90,6 +90,20 @@ def raster_positions(H: int, W: int, P: int, n: int, step: int, jitter: int,
     return pos.astype(np.int32)
 
 
+def raster_positions_subpixel(H: int, W: int, P: int, n: int, step: int, jitter: float,
+                              rng: np.random.Generator) -> np.ndarray:
+    """n x n raster of top-left corners (row, col) as float32, centred, with a uniform real
+    jitter in [-jitter, jitter] per axis (fractional positions), clipped to [0, H-P] x [0, W-P]."""
+    ext = (n - 1) * step + P
+    oy, ox = (H - ext) // 2, (W - ext) // 2
+    gy, gx = np.meshgrid(np.arange(n) * step + oy, np.arange(n) * step + ox, indexing="ij")
+    pos = np.stack([gy.ravel(), gx.ravel()], axis=1).astype(np.float64)
+    pos += rng.uniform(-jitter, jitter, size=pos.shape)
+    pos[:, 0] = np.clip(pos[:, 0], 0, H - P)
+    pos[:, 1] = np.clip(pos[:, 1], 0, W - P)
+    return pos.astype(np.float32)
+
+
 def spiral_positions(H: int, W: int, P: int, K: int, c: float, jitter: int,
                      rng: np.random.Generator) -> np.ndarray:
     """Vogel (Fermat) spiral r_n = c sqrt(n), theta_n = n * 137.508 deg, rounded, +-jitter."""
@@ -110,9 +124,28 @@ def spiral_positions(H: int, W: int, P: int, K: int, c: float, jitter: int,
 # ----------------------------------------------------------------------------------
 # Detector
 # ----------------------------------------------------------------------------------
-def _farfield_intensity(psi: np.ndarray, probe: np.ndarray, pos: np.ndarray, batch: int = 256):
-    """|orthonormal FFT2(probe * patch_k)|^2 for all k, float64, in batches."""
+def shifted_probes(probe: np.ndarray, frac: np.ndarray) -> np.ndarray:
+    """[K][P][P] complex128: the probe moved by frac[k] = (dy, dx) pixels by the Fourier shift
+    theorem (numpy FFT): spectrum times exp(-2 pi i (ky dy + kx dx) / P) at the signed
+    frequencies, cos(pi d) at the Nyquist index P/2 of each axis."""
     P = probe.shape[0]
+    kap = np.fft.fftfreq(P, 1.0 / P)  # 0, 1, .., P/2-1, -P/2, .., -1
+    nyq = P // 2
+    spec = np.fft.fft2(probe.astype(np.complex128))
+    out = np.empty((len(frac), P, P), np.complex128)
+    for k, (dy, dx) in enumerate(np.asarray(frac, dtype=np.float64)):
+        fy = np.exp(-2j * np.pi * kap * dy / P)
+        fx = np.exp(-2j * np.pi * kap * dx / P)
+        fy[nyq] = np.cos(np.pi * dy)
+        fx[nyq] = np.cos(np.pi * dx)
+        out[k] = np.fft.ifft2(spec * fy[:, None] * fx[None, :])
+    return out
+
+
+def _farfield_intensity(psi: np.ndarray, probe: np.ndarray, pos: np.ndarray, batch: int = 256):
+    """|orthonormal FFT2(probe * patch_k)|^2 for all k, float64, in batches.  probe is [P][P]
+    or one probe per position [K][P][P]."""
+    P = probe.shape[-1]
     K = pos.shape[0]
     out = np.empty((K, P, P), np.float64)
     pr = probe.astype(np.complex128)
@@ -122,7 +155,8 @@ def _farfield_intensity(psi: np.ndarray, probe: np.ndarray, pos: np.ndarray, bat
         rows = pos[k0:k1, 0][:, None, None] + iy[None, :, None]
         cols = pos[k0:k1, 1][:, None, None] + iy[None, None, :]
         patches = psi[rows, cols].astype(np.complex128)
-        f = np.fft.fft2(pr[None] * patches, norm="ortho")
+        pk = pr[k0:k1] if pr.ndim == 3 else pr[None]
+        f = np.fft.fft2(pk * patches, norm="ortho")
         out[k0:k1] = f.real**2 + f.imag**2
     return out
 
@@ -195,6 +229,28 @@ def production_problem(seed=1, noise=True):
     return small_problem(H=1024, W=1024, P=128, n=60, step=14, jitter=2, peak=1e5, seed=seed,
                          noise=noise, niter=64,
                          name="ml-cg 1024x1024 object, 128x128 probe, 3600 positions")
+
+
+def subpixel_problem(H=256, W=256, P=64, n=15, step=8, jitter=1.0, peak=1e4, seed=0, noise=True,
+                     niter=10, name=None):
+    """Raster with fractional positions (uniform real jitter +-jitter): Problem.pos is float32
+    [K][2] (row, col); the data come from the probe shifted by each position's fraction
+    within the window that starts at floor(pos).  meta["pos_int"] and meta["frac"] hold the
+    split.  Defaults: the 256^2 / 64^2 / 15x15 workload."""
+    rng = np.random.default_rng(seed)
+    psi = ellipse_phantom(H, W, rng)
+    pos = raster_positions_subpixel(H, W, P, n, step, jitter, rng)
+    base = np.floor(pos.astype(np.float64))
+    frac = pos.astype(np.float64) - base
+    unit = gaussian_probe(P)
+    I0 = _farfield_intensity(psi, shifted_probes(unit, frac), base.astype(np.int64))
+    s = peak / I0.max()
+    probe = (np.sqrt(s) * unit.astype(np.complex128)).astype(np.complex64)
+    lam = I0 * s
+    d = (rng.poisson(lam) if noise else lam).astype(np.float32)
+    name = name or f"ml-cg {H}x{W} object, {P}x{P} probe, {n * n} sub-pixel positions"
+    return Problem(name, psi, probe, pos, d, niter, {"seed": seed, "peak": peak, "step": step, "jitter": jitter,
+                                                      "pos_int": base.astype(np.int32), "frac": frac})
 
 
 def spiral_problem(seed=2, noise=True, K=10000, H=2048, P=256, c=8.94, peak=1e6):

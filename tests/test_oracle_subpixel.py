@@ -1,0 +1,160 @@
+"""Pins of the oracle's sub-pixel positions: the probe shift by the Fourier shift theorem
+(orc_shift_probe) and the forward model, gradient and CG with one probe per position.
+
+The paper's scan positions are float32 inputs of Algorithm 1; how a fraction enters Q is
+not stated.  The reading: the window starts at floor(s) and the probe is moved by the
+fraction with the Fourier shift theorem, Nyquist bins multiplied by cos(pi delta).  Each
+pin below is fixed by mathematics, not by re-running the oracle's own formula:
+integer shifts are circular rolls, plane waves shift by a closed-form phase, real probes
+stay real, shifts of band-limited probes compose, the numpy generator's independent
+implementation agrees, and the per-position forward model keeps the adjoint identity,
+the finite-difference gradient and the noise-free minimum."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_07575_gb300 import synth
+
+
+def _rand_probe(P, seed):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((P, P)) + 1j * rng.standard_normal((P, P))
+
+
+def test_zero_shift_is_identity():
+    p = _rand_probe(16, 0)
+    assert np.max(np.abs(oracle.shift_probe(p, 0.0, 0.0) - p)) < 1e-13
+
+
+@pytest.mark.parametrize("dy,dx", [(1, 0), (0, 1), (3, -2), (-5, 7), (16, 16)])
+def test_integer_shift_is_circular_roll(dy, dx):
+    p = _rand_probe(16, 1)
+    want = np.roll(np.roll(p, dy, axis=0), dx, axis=1)
+    assert np.max(np.abs(oracle.shift_probe(p, dy, dx) - want)) < 1e-12
+
+
+@pytest.mark.parametrize("a,b", [(1, 0), (0, 3), (-5, 2), (7, -7)])
+def test_plane_wave_shifts_by_its_phase(a, b):
+    # p(y, x) = exp(2 pi i (a y + b x) / P), |a|, |b| < P/2: p(r - delta) in closed form
+    P, dy, dx = 16, 0.37, -0.81
+    y, x = np.mgrid[0:P, 0:P]
+    p = np.exp(2j * np.pi * (a * y + b * x) / P)
+    want = np.exp(2j * np.pi * (a * (y - dy) + b * (x - dx)) / P)
+    assert np.max(np.abs(oracle.shift_probe(p, dy, dx) - want)) < 1e-12
+
+
+def test_band_limited_function_is_evaluated_between_samples():
+    # a trigonometric polynomial below Nyquist is reproduced exactly at shifted points
+    P, dy, dx = 32, 0.25, 0.6
+    rng = np.random.default_rng(2)
+    freqs = rng.integers(-15, 16, size=(6, 2))
+    coef = rng.standard_normal(6) + 1j * rng.standard_normal(6)
+
+    def f(y, x):
+        return sum(c * np.exp(2j * np.pi * (a * y + b * x) / P) for c, (a, b) in zip(coef, freqs))
+
+    y, x = np.mgrid[0:P, 0:P].astype(np.float64)
+    assert np.max(np.abs(oracle.shift_probe(f(y, x), dy, dx) - f(y - dy, x - dx))) < 1e-11
+
+
+def test_nyquist_rows_take_cos_pi_delta():
+    # content only at the Nyquist row: (-1)^y -> cos(pi dy) (-1)^y
+    P, dy = 8, 0.3
+    y, _ = np.mgrid[0:P, 0:P]
+    p = (-1.0) ** y + 0j
+    assert np.max(np.abs(oracle.shift_probe(p, dy, 0.0) - np.cos(np.pi * dy) * p)) < 1e-13
+
+
+def test_real_probe_stays_real():
+    rng = np.random.default_rng(3)
+    p = rng.standard_normal((32, 32)) + 0j
+    assert np.max(np.abs(oracle.shift_probe(p, 0.43, 0.91).imag)) < 1e-13
+
+
+def test_shifts_of_a_band_limited_probe_compose():
+    P = 32
+    spec = np.fft.fft2(_rand_probe(P, 4))
+    spec[P // 2, :] = 0
+    spec[:, P // 2] = 0
+    p = np.fft.ifft2(spec)
+    two = oracle.shift_probe(oracle.shift_probe(p, 0.3, 0.45), 0.55, 0.2)
+    assert np.max(np.abs(two - oracle.shift_probe(p, 0.85, 0.65))) < 1e-12
+
+
+def test_agrees_with_the_generator_numpy_implementation():
+    P = 64
+    p = synth.gaussian_probe(P).astype(np.complex128)
+    frac = np.array([[0.1, 0.7], [0.5, 0.5], [0.93, 0.02]])
+    ref = synth.shifted_probes(p, frac)
+    for k, (dy, dx) in enumerate(frac):
+        assert np.max(np.abs(oracle.shift_probe(p, dy, dx) - ref[k])) < 1e-12
+
+
+def test_integer_positions_give_the_shared_probe_path():
+    prob = synth.small_problem(H=96, W=96, P=32, n=4, step=14, jitter=1, peak=1e3, seed=5)
+    pos_i, probes = oracle.subpixel_probes(prob.probe, prob.pos.astype(np.float32))
+    assert np.array_equal(pos_i, prob.pos)
+    psi = prob.psi_true
+    assert np.array_equal(oracle.forward(psi, probes, pos_i), oracle.forward(psi, prob.probe, prob.pos))
+
+
+def _subpx(seed=6, noise=True):
+    return synth.subpixel_problem(H=96, W=96, P=32, n=4, step=14, jitter=1.5, peak=1e3, seed=seed, noise=noise)
+
+
+def test_subpixel_adjoint_dot():
+    prob = _subpx()
+    pos_i, probes = oracle.subpixel_probes(prob.probe, prob.pos)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((prob.H, prob.W)) + 1j * rng.standard_normal((prob.H, prob.W))
+    y = rng.standard_normal((prob.K, prob.P, prob.P)) + 1j * rng.standard_normal((prob.K, prob.P, prob.P))
+    lhs = np.vdot(oracle.forward(x, probes, pos_i), y)
+    rhs = np.vdot(x, oracle.adjoint(y, probes, pos_i, x.shape))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_subpixel_gradient_finite_difference():
+    prob = _subpx()
+    pos_i, probes = oracle.subpixel_probes(prob.probe, prob.pos)
+    rng = np.random.default_rng(8)
+    psi = prob.psi0().astype(np.complex128) * (1 + 0.05 * rng.standard_normal((prob.H, prob.W)))
+    g, F = oracle.gradient(psi, probes, pos_i, prob.d)
+    delta = rng.standard_normal(psi.shape) + 1j * rng.standard_normal(psi.shape)
+
+    def central(h):
+        Fp = oracle.objective(psi + h * delta, probes, pos_i, prob.d)
+        Fm = oracle.objective(psi - h * delta, probes, pos_i, prob.d)
+        return (Fp - Fm) / (2 * h)
+
+    h = 1e-5  # Richardson extrapolation removes the O(h^2) truncation term
+    fd = (4 * central(h) - central(2 * h)) / 3
+    assert abs(fd - 2 * np.real(np.vdot(g, delta))) <= 1e-6 * abs(fd)
+
+
+def test_subpixel_noise_free_truth_is_the_minimum():
+    # the generator's intensities (its own numpy shift) equal the oracle's per-position model;
+    # at psi_true with eps = 0 the gradient vanishes and F = F_min = sum(d - d log d)
+    prob = _subpx(noise=False)
+    pos_i, probes = oracle.subpixel_probes(prob.probe, prob.pos)
+    u = oracle.forward(prob.psi_true, probes, pos_i)
+    a = np.abs(u) ** 2
+    assert np.linalg.norm(prob.d - a) <= 1e-6 * np.linalg.norm(a)
+    d_exact = a.astype(np.float32)
+    g, F = oracle.gradient(prob.psi_true, probes, pos_i, d_exact, eps=0.0)
+    gscale = np.linalg.norm(oracle.adjoint(u, probes, pos_i, (prob.H, prob.W)))
+    assert np.linalg.norm(g) <= 1e-6 * gscale  # float32 rounding of d only
+    dd = d_exact.astype(np.float64)
+    Fmin = float(np.sum(np.where(dd > 0, dd - dd * np.log(np.where(dd > 0, dd, 1)), 0.0)))
+    assert F == pytest.approx(Fmin, rel=1e-7)
+
+
+def test_subpixel_cg_decreases_monotonically():
+    prob = _subpx()
+    pos_i, probes = oracle.subpixel_probes(prob.probe, prob.pos)
+    out = oracle.cg_solve(prob.psi0(), probes, pos_i, prob.d, 6)
+    F = out["F"]
+    assert out["iters_done"] == 6
+    assert np.all(np.diff(F) <= 0)
+    g = out["gamma"]
+    k = np.log2(g)
+    assert np.allclose(k, np.round(k))  # gamma = 2^-k

@@ -43,6 +43,8 @@ WORKLOADS = {
     "production": "ml-cg 1024x1024 object, 128x128 probe, 3600 positions (60x60 raster, step 14, +-2), peak 1e5 counts",
     "spiral": "ml-cg 2048x2048 object, 256x256 probe, 10000 positions (Fermat spiral, +-2), peak 1e6 counts",
     "small": "ml-cg 256x256 object, 64x64 probe, 225 positions (15x15 raster, step 8, +-1), peak 1e4 counts",
+    "subpixel": "ml-cg 1024x1024 object, 128x128 probe, 3600 sub-pixel positions (60x60 raster, step 14, uniform "
+                "real jitter +-2, one Fourier-shifted probe per position), peak 1e5 counts",
     "gap": "ml-cg 1024x1024 object, 128x128 probe, 3600 positions (60x60 raster, step 14, +-2), peak 1e5 counts, "
            "test seed 5: time to relative objective gap 1e-3 per form",
     "views": "batched ml-cg: {n} views of 512^2-2048^2 (multiples of 128), 128x128 shared probe, rasters at 16 px "
@@ -58,6 +60,8 @@ def make_problem(name):
         return synth.spiral_problem()
     if name == "small":
         return synth.small_problem()
+    if name == "subpixel":
+        return synth.subpixel_problem(H=1024, W=1024, P=128, n=60, step=14, jitter=2.0, peak=1e5, seed=1, niter=64)
     return synth.production_problem()
 
 
@@ -116,7 +120,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ls-window", type=int, default=None)
     ap.add_argument("--tile-config", type=int, default=None)
-    ap.add_argument("--workload", choices=["production", "spiral", "small", "views", "gap"], default="production")
+    ap.add_argument("--workload", choices=["production", "spiral", "small", "subpixel", "views", "gap"], default="production")
     ap.add_argument("--pairs", type=int, default=200000, help="gap workload: training pairs of the learned start")
     ap.add_argument("--epochs", type=float, default=1.0, help="gap workload: passes over the training pairs")
     ap.add_argument("--views", type=int, default=64)

@@ -105,8 +105,8 @@ typedef struct {
                             threads; P=256: 0 cluster of 8, 1 cluster of 4) */
     int32_t dft;         /* 2-D DFTs: 0 (default) FP32 FFT on the CUDA cores; 1 batched complex
                             GEMMs on the tensor cores with operands split into BF16 hi + lo and
-                            FP32 accumulation; 2 the same with FP16 hi + lo.  1 and 2 need
-                            P = 64 or 128; pty_adjoint needs 0. */
+                            FP32 accumulation; 2 the same with FP16 hi + lo.  1 needs
+                            P = 64, 128 or 256, 2 needs P = 64 or 128; pty_adjoint needs 0. */
     int32_t estimator;   /* 0 (default): the Poisson maximum-likelihood objective of Eq. 2;
                             1: the Gaussian least-squares estimator that the paper names beside
                             it, on amplitudes: F = sum |G psi|^2 - 2 sqrt(d) sqrt(|G psi|^2 +
@@ -163,6 +163,29 @@ PTY_API void pty_default_opts(pty_opts *o);
  */
 PTY_API int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *probe, int32_t K,
                const int32_t *pos, const float *data, const pty_opts *opts, void *stream);
+
+/*
+ * Create a context whose scan positions may have a fractional part.  The paper's scan
+ * positions are float32 inputs of Algorithm 1 (section "Inverse problem for ptychography");
+ * how a fraction enters Q is not stated there.  The library takes position s = (row, col)
+ * as the P x P window starting at floor(s) and moves the probe inside that window by the
+ * fraction delta = s - floor(s) with the Fourier shift theorem:
+ *   p_delta = F^H[ F[p](ky, kx) exp(-2 pi i (ky dy + kx dx) / P) ]
+ * at the signed frequencies -P/2 < k < P/2, with the factor cos(pi d) at the Nyquist index
+ * P/2 of each axis (a real probe stays real).  Q of Eq. 1 then multiplies patch k with its
+ * own probe p_delta_k; everything else is as for pty_create.  An integer position gives
+ * exactly the unshifted probe.  The shifted probe wraps around its window (a probe that has
+ * decayed at the window's edge loses nothing).
+ *   pos    [K][2] float32 (row, col), finite; 0 <= floor(row) <= H-P, 0 <= floor(col) <= W-P;
+ *          copied.
+ *   other arguments as in pty_create.
+ * The context holds K probes ([K][P][P] complex, device memory).  One view only; opts.dft
+ * must be 0.
+ * Errors: as pty_create; PTY_ERR_BOUNDS also for a non-finite coordinate;
+ * PTY_ERR_UNSUPPORTED for opts.dft != 0.
+ */
+PTY_API int pty_create_subpixel(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *probe, int32_t K,
+                                const float *pos, const float *data, const pty_opts *opts, void *stream);
 
 /* Release every resource of the context (NULL is ignored). */
 PTY_API void pty_destroy(pty_ctx *ctx);

@@ -447,11 +447,12 @@ __global__ void __launch_bounds__(NT) k_stitch_acc(PatternArgs a, ScatterPlan pl
         const int dx = x - rc.y;
         if (dx < 0 || dx >= P) continue;
         const float2 *pi = patches + (size_t)__ldg(a.perm + i) * P * P + dx;
+        const float2 *pk = probe_of(a, i);
 #pragma unroll
         for (int j = 0; j < kStNJ; j++) {
             const int yy = y0 + (NT / kStTX) * j - rc.x;
             if (yy >= 0 && yy < P) {
-                const float2 p = __ldg(a.probe + yy * P + dx);
+                const float2 p = __ldg(pk + yy * P + dx);
                 const float w = p.x * p.x + p.y * p.y;
                 const float2 o = __ldg(pi + yy * P);
                 acc[j].x = fmaf(w, o.x, acc[j].x);

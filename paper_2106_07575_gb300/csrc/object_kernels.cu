@@ -69,8 +69,9 @@ __global__ void __launch_bounds__(kScNT) k_scatter(PatternArgs a, ScatterPlan pl
     scatter_tail<kScNT, kScNJ, kScNT / kScTX>(a, acc, x, y0, b, lin, out, dy, ep, gp, part, psi, D, p2, red, tot);
 }
 
-// Illumination map D(x) = sum over positions k covering x of |p(x - r_k)|^2 (p the stored
-// probe, i.e. the probe / P), per object tile from the same position-sorted lists.
+// Illumination map D(x) = sum over positions k covering x of |p_k(x - r_k)|^2 (p_k the
+// stored probe of position k, i.e. the probe / P), per object tile from the same
+// position-sorted lists.
 template <int P>
 __global__ void __launch_bounds__(kScNT) k_illum(PatternArgs a, ScatterPlan plan, float *__restrict__ D)
 {
@@ -82,14 +83,16 @@ __global__ void __launch_bounds__(kScNT) k_illum(PatternArgs a, ScatterPlan plan
 #pragma unroll
     for (int j = 0; j < kScNJ; j++) acc[j] = 0.f;
     for (int q = plan.tile_start[b]; q < plan.tile_start[b + 1]; q++) {
-        const int2 rc = __ldg(a.pos + __ldg(plan.tile_list + q));
+        const int i = __ldg(plan.tile_list + q);
+        const int2 rc = __ldg(a.pos + i);
         const int dx = x - rc.y;
         if (dx < 0 || dx >= P) continue;
+        const float2 *pk = probe_of(a, i);
 #pragma unroll
         for (int j = 0; j < kScNJ; j++) {
             const int yy = y0 + (kScNT / kScTX) * j - rc.x;
             if (yy >= 0 && yy < P) {
-                const float2 p = __ldg(a.probe + yy * P + dx);
+                const float2 p = __ldg(pk + yy * P + dx);
                 acc[j] += p.x * p.x + p.y * p.y;
             }
         }

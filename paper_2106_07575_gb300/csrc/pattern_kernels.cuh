@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_forward(PatternArgs a,
     const int2 rc = a.pos[i];
     cluster_start<P, R>();
     load_twiddles<P, NT>(tw, a.tw);
-    gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+    gather_rows<P, R, NT>(buf, probe_of(a, i), psi, a.W, rc.x, rc.y, c);
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
     float2 *o = out + (size_t)a.perm[i] * P * P;
@@ -220,9 +220,10 @@ __device__ __forceinline__ void emit_adjoint(const PatternArgs &a, const float2 
             return;
         }
     }
+    const float2 *pk = probe_of(a, i);
     for (int e = threadIdx.x; e < R * P; e += NT) {
         const int rl = e / P, x = e % P, yy = c * R + rl;
-        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
+        wi[yy * P + x] = cconjmul(__ldg(pk + yy * P + x), buf[rl * LDA + x]);
     }
 }
 
@@ -245,9 +246,10 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_adjoint_fft(PatternArg
     __syncthreads();
     fft2_inv<P, R, NT>(buf, tw);
     float2 *wi = w + (size_t)i * P * P;
+    const float2 *pk = probe_of(a, i);
     for (int e = threadIdx.x; e < R * P; e += NT) {
         const int rl = e / P, x = e % P, yy = c * R + rl;
-        wi[yy * P + x] = cconjmul(__ldg(a.probe + yy * P + x), buf[rl * LDA + x]);
+        wi[yy * P + x] = cconjmul(__ldg(pk + yy * P + x), buf[rl * LDA + x]);
     }
 }
 
@@ -283,9 +285,9 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
     const int2 rc = a.pos[i];
     if constexpr (R == P) {
         if (pc) gather_cached<P, NT>(buf, *pc, psi, a.W, rc.x, rc.y);
-        else gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+        else gather_rows<P, R, NT>(buf, probe_of(a, i), psi, a.W, rc.x, rc.y, c);
     } else {
-        gather_rows<P, R, NT>(buf, a.probe, psi, a.W, rc.x, rc.y, c);
+        gather_rows<P, R, NT>(buf, probe_of(a, i), psi, a.W, rc.x, rc.y, c);
     }
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
@@ -349,7 +351,8 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
     if constexpr (CS == 1) {
         __shared__ uint32_t tmem_slot;
         ProbeCache<P, NT> pc;
-        pc.init(&tmem_slot, a.probe);
+        const bool cached = a.probe_stride == 0;  // one probe for all patterns: kept in TMEM
+        if (cached) pc.init(&tmem_slot, a.probe);
         // one view: the objective terms are summed per thread over the CTA's patterns and
         // written as one column per CTA (same grid for k_grad and k_grad_lin)
         const bool percta = a.V == 1;
@@ -357,14 +360,15 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (skip(i)) continue;
             __syncthreads();  // the previous pattern's reads of buf are done
-            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, 0, percta ? &facc : nullptr, &pc);
+            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, 0, percta ? &facc : nullptr,
+                                   cached ? &pc : nullptr);
         }
         if (percta) {
             float2 v[1] = {facc};
             block_sum_ff<NT, 1>(v, red, tot);
             if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
-        pc.release();
+        if (cached) pc.release();
     } else {
         const int i = blockIdx.x / CS;
         if (skip(i)) return;  // uniform over the cluster
@@ -441,7 +445,8 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
     if constexpr (CS == 1) {
         __shared__ uint32_t tmem_slot;
         ProbeCache<P, NT> pc;
-        pc.init(&tmem_slot, a.probe);
+        const bool cached = a.probe_stride == 0;  // one probe for all patterns: kept in TMEM
+        if (cached) pc.init(&tmem_slot, a.probe);
         const bool percta = a.V == 1;  // as in k_grad
         float2 facc = make_float2(0.f, 0.f);
         const float gam1 = percta ? (float)sts->last_gamma : 0.f;  // one view: loop-invariant
@@ -453,14 +458,15 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
                 gam = (float)st->last_gamma;
             }
             __syncthreads();  // the previous pattern's reads of buf are done
-            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, gam, i, 0, percta ? &facc : nullptr, &pc);
+            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, gam, i, 0, percta ? &facc : nullptr,
+                                       cached ? &pc : nullptr);
         }
         if (percta) {
             float2 v[1] = {facc};
             block_sum_ff<NT, 1>(v, red, tot);
             if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
-        pc.release();
+        if (cached) pc.release();
     } else {
         const int i = blockIdx.x / CS;
         const DevState *st = sts + a.pat_view[i];
@@ -514,9 +520,9 @@ __device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const flo
     // p eta / P into the row slab
     if constexpr (R == P) {
         if (pc) gather_cached<P, NT>(buf, *pc, eta, a.W, rc.x, rc.y);
-        else gather_rows<P, R, NT>(buf, a.probe, eta, a.W, rc.x, rc.y, c);
+        else gather_rows<P, R, NT>(buf, probe_of(a, i), eta, a.W, rc.x, rc.y, c);
     } else {
-        gather_rows<P, R, NT>(buf, a.probe, eta, a.W, rc.x, rc.y, c);
+        gather_rows<P, R, NT>(buf, probe_of(a, i), eta, a.W, rc.x, rc.y, c);
     }
     __syncthreads();
     fft2_fwd<P, R, NT>(buf, tw);
@@ -568,18 +574,19 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
         // one view: one column per CTA, its patterns summed in their fixed order
         __shared__ uint32_t tmem_slot;
         ProbeCache<P, NT> pc;
-        pc.init(&tmem_slot, a.probe);
+        const bool cached = a.probe_stride == 0;  // one probe for all patterns: kept in TMEM
+        if (cached) pc.init(&tmem_slot, a.probe);
         const bool percta = a.V == 1;
         float2 acc = make_float2(0.f, 0.f);
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (!percta && sts[a.pat_view[i]].stalled) continue;  // one view: decided above
             __syncthreads();  // the previous pattern's reads of buf are done
-            const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0, &pc);
+            const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0, cached ? &pc : nullptr);
             if (percta) acc = ff_add(acc, r);
             else if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i] = r;
         }
         if (percta && threadIdx.x < nr) part[(size_t)threadIdx.x * KC + blockIdx.x] = acc;
-        pc.release();
+        if (cached) pc.release();
     } else {
         const int i = blockIdx.x / CS;
         if (sts[a.pat_view[i]].stalled) return;  // uniform over the cluster

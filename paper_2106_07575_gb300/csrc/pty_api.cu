@@ -59,7 +59,8 @@ struct pty_ctx {
     std::string err;
 
     // problem (device)
-    float2 *probe = nullptr;  // [P][P] / P
+    float2 *probe = nullptr;  // [P][P] / P, or [K][P][P] / P with fractional positions
+    long long probe_stride = 0;  // 0: one probe; P * P: one per sorted pattern
     float2 *tw = nullptr;     // [P]
     int2 *pos = nullptr;      // [K] sorted, atlas coordinates
     int *perm = nullptr;      // [K] caller index of sorted pattern i
@@ -194,6 +195,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.W = c->WA;
     a.K = c->K;
     a.probe = c->probe;
+    a.probe_stride = c->probe_stride;
     a.tw = c->tw;
     a.pos = c->pos;
     a.perm = c->perm;
@@ -654,13 +656,16 @@ int autotune(pty_ctx *c)
     return PTY_OK;
 }
 
+// fpos (optional, one view): float positions [K][2]; the window starts at floor(fpos) and
+// each position gets its own probe, moved by the fraction (subpixel.cu).  pos is then unused.
 int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws, const int32_t *Ks, int32_t P,
-                 const float *probe, const int32_t *pos, const float *data, const pty_opts *opts, void *stream)
+                 const float *probe, const int32_t *pos, const float *data, const pty_opts *opts, void *stream,
+                 const float *fpos = nullptr)
 {
     if (!out) return fail(nullptr, PTY_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (V < 1 || !Hs || !Ws || !Ks) return fail(nullptr, PTY_ERR_ARG, "bad view description");
-    if (!probe || !pos || !data) return fail(nullptr, PTY_ERR_ARG, "probe, pos and data must be non-NULL");
+    if (!probe || !(pos || fpos) || !data) return fail(nullptr, PTY_ERR_ARG, "probe, pos and data must be non-NULL");
     if (!pty::pattern_supported(P)) return fail(nullptr, PTY_ERR_ARG, "P=%d not supported (64, 128 or 256)", P);
     long long K = 0, rows = 0;
     int WA = 0;
@@ -684,15 +689,36 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
         return fail(nullptr, PTY_ERR_ARG, "invalid options (tau in (0,1), gamma0 > 0, 1 <= max_halvings <= 1000, "
                                           "eps >= 0, ls_window in {0,4,8,16,32}, dft in {0,1,2}, estimator and "
                                           "solver in {0,1}, gd_step > 0 with solver 1, ls_warm 0 or 1 with solver 0)");
-    if (o.dft != 0 && !pty::tc_dft_supported(P))
-        return fail(nullptr, PTY_ERR_UNSUPPORTED, "the tensor-core DFT supports P = 64 and 128");
+    if (o.dft != 0 && !pty::tc_dft_supported(P, o.dft == 1))
+        return fail(nullptr, PTY_ERR_UNSUPPORTED,
+                    "the tensor-core DFT supports P = 64, 128 and 256 (split BF16) or P = 64, 128 (split FP16)");
     if (o.dft != 0 && (o.estimator != 0 || o.solver != 0 || o.ls_warm))
         return fail(nullptr, PTY_ERR_UNSUPPORTED,
                     "the least-squares estimator, gradient descent and the warm-started search need dft = 0");
+    if (fpos && (V != 1 || o.dft != 0))
+        return fail(nullptr, PTY_ERR_UNSUPPORTED, "fractional positions need one view and dft = 0");
 
     // positions: host copy, bounds check per view, atlas coordinates, position sort
     std::vector<int32_t> hpos((size_t)2 * K);
-    if (is_device_ptr(pos)) {
+    std::vector<float> hfrac;  // fractional parts (row, col) per caller index, with fpos
+    if (fpos) {
+        std::vector<float> hf((size_t)2 * K);
+        if (is_device_ptr(fpos)) {
+            if (cudaMemcpy(hf.data(), fpos, sizeof(float) * 2 * K, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(nullptr, PTY_ERR_CUDA, "cannot read positions");
+        } else {
+            std::memcpy(hf.data(), fpos, sizeof(float) * 2 * K);
+        }
+        hfrac.resize((size_t)2 * K);
+        for (size_t e = 0; e < hf.size(); e++) {
+            if (!std::isfinite(hf[e]) || std::fabs(hf[e]) > 1e9f)
+                return fail(nullptr, PTY_ERR_BOUNDS, "position %d holds a non-finite or huge coordinate",
+                            (int)(e / 2));
+            const double fl = std::floor((double)hf[e]);
+            hpos[e] = (int32_t)fl;
+            hfrac[e] = (float)((double)hf[e] - fl);  // exact: a float minus its floor
+        }
+    } else if (is_device_ptr(pos)) {
         if (cudaMemcpy(hpos.data(), pos, sizeof(int32_t) * 2 * K, cudaMemcpyDeviceToHost) != cudaSuccess)
             return fail(nullptr, PTY_ERR_CUDA, "cannot read positions");
     } else {
@@ -829,7 +855,7 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     }
 
     const size_t PP = (size_t)P * P, HW = (size_t)c->HA * c->WA;
-    CKC(dalloc(&c->probe, PP));
+    CKC(dalloc(&c->probe, fpos ? (size_t)K * PP : PP));
     CKC(dalloc(&c->tw, (size_t)P));
     CKC(dalloc(&c->pos, (size_t)K));
     CKC(dalloc(&c->perm, (size_t)K));
@@ -859,7 +885,24 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     CKC(dalloc(&c->part_eta, (size_t)ntiles * 2));
     CKC(dalloc(&c->st, (size_t)V));
     CKC(dalloc(&c->dscalar, (size_t)4));
-    CKC(cudaMemcpyAsync(c->probe, hprobe.data(), sizeof(float2) * PP, cudaMemcpyHostToDevice, c->s));
+    if (fpos) {
+        // one probe per sorted pattern, moved by its position's fraction
+        std::vector<float2> sfrac(K);
+        for (int i = 0; i < K; i++) sfrac[i] = make_float2(hfrac[2 * perm[i]], hfrac[2 * perm[i] + 1]);
+        float2 *dp = nullptr, *df = nullptr;
+        cudaError_t e = dalloc(&dp, PP);
+        if (e == cudaSuccess) e = dalloc(&df, (size_t)K);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dp, hprobe.data(), sizeof(float2) * PP, cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(df, sfrac.data(), sizeof(float2) * K, cudaMemcpyHostToDevice, c->s);
+        if (e == cudaSuccess) e = pty::launch_shift_probes(P, (int)K, dp, df, c->probe, c->s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->s);
+        if (dp) cudaFree(dp);
+        if (df) cudaFree(df);
+        CKC(e);
+        c->probe_stride = (long long)PP;
+    } else {
+        CKC(cudaMemcpyAsync(c->probe, hprobe.data(), sizeof(float2) * PP, cudaMemcpyHostToDevice, c->s));
+    }
     CKC(cudaMemcpyAsync(c->tw, htw.data(), sizeof(float2) * P, cudaMemcpyHostToDevice, c->s));
     CKC(cudaMemcpyAsync(c->pos, spos.data(), sizeof(int2) * K, cudaMemcpyHostToDevice, c->s));
     CKC(cudaMemcpyAsync(c->perm, perm.data(), sizeof(int) * K, cudaMemcpyHostToDevice, c->s));
@@ -1105,6 +1148,16 @@ int pty_create(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *prob
                const float *data, const pty_opts *opts, void *stream)
 {
     return create_views(out, 1, &H, &W, &K, P, probe, pos, data, opts, stream);
+}
+
+int pty_create_subpixel(pty_ctx **out, int32_t H, int32_t W, int32_t P, const float *probe, int32_t K,
+                        const float *pos, const float *data, const pty_opts *opts, void *stream)
+{
+    if (!pos) {
+        if (out) *out = nullptr;
+        return fail(nullptr, PTY_ERR_ARG, "probe, pos and data must be non-NULL");
+    }
+    return create_views(out, 1, &H, &W, &K, P, probe, nullptr, data, opts, stream, pos);
 }
 
 int pty_batch_create(pty_ctx **out, int32_t n_views, const int32_t *H, const int32_t *W, const int32_t *K,

@@ -62,7 +62,9 @@ struct DevHist {
 // u and sums that Parseval's identity turns into real-space sums.
 struct PatternArgs {
     int H, W, K;
-    const float2 *probe;        // [P][P], scaled by 1/P (the unitary normalisation)
+    const float2 *probe;        // [P][P], scaled by 1/P (the unitary normalisation); with
+                                // probe_stride = P * P one probe per sorted pattern [K][P][P]
+    long long probe_stride = 0; // elements between the probes of consecutive patterns
     const float2 *tw;           // [P] exp(-2 pi i m / P)
     const int2 *pos;            // [K] (row, col), position-sorted order
     const int *perm;            // [K] caller index of sorted pattern i
@@ -91,6 +93,12 @@ struct LsArgs {
     int gd;        // gradient descent (Eq. 4): no direction coefficient, no line search
     double gd_step;
 };
+
+// Probe of sorted pattern i (the shared probe when probe_stride is 0).
+__host__ __device__ __forceinline__ const float2 *probe_of(const PatternArgs &a, int i)
+{
+    return a.probe + (size_t)i * (size_t)a.probe_stride;
+}
 
 // ---- pattern kernels (pattern_kernels.cuh, instantiated per P in pattern_p*.cu) ----
 // One configuration: patterns of P x P held by clusters of P / R CTAs of NT threads.
@@ -148,7 +156,7 @@ cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, float2
 // B * P rows of X (output block b goes to out_index[b] when out_index is non-NULL); two
 // applications give the unnormalised 2-D DFT.  img: the split DFT matrix images built by
 // tc_dft_images (device copy).  err |= 1 on a timed-out device wait.
-bool tc_dft_supported(int P);
+bool tc_dft_supported(int P, bool bf16);
 // Polls every pipeline wait of the tensor-core kernels allows before it gives up (the kernel
 // then records err |= 1); tc_set_wait_limit(polls <= 0) restores the default.
 long long tc_wait_limit();
@@ -244,6 +252,9 @@ cudaError_t launch_ls_decide(const float2 *part, int kc, int cs, int ls_cols, in
                              cudaStream_t s);
 // D[y][x] = sum over the positions covering (y, x) of |probe / P|^2 at the covered pixel.
 cudaError_t launch_illumination(int P, const PatternArgs &a, const ScatterPlan &plan, float *D, cudaStream_t s);
+// subpixel.cu: out[k] = probe moved by frac[k] = (dy, dx) pixels (Fourier shift theorem,
+// Nyquist factor cos(pi d)) for k < K; probe [P][P], out [K][P][P] (create time only).
+cudaError_t launch_shift_probes(int P, int K, const float2 *probe, const float2 *frac, float2 *out, cudaStream_t s);
 // eta = -g + alpha_v eta_prev over the object (H x W, scatter tiles) and the per-tile sums
 // part[b] = (sum D Re conj(psi) eta, sum D |eta|^2).
 cudaError_t launch_eta(int H, int W, const ScatterPlan &plan, const float2 *psi, const float2 *g, const float2 *ep,

@@ -153,6 +153,7 @@ cudaError_t launch_tc_residual(const PatternArgs &a, int P, float2 *U, float2 *f
 {
     if (P == 64) k_tc_residual<64><<<a.K, kNT, 0, s>>>(a, U, fpart, st);
     else if (P == 128) k_tc_residual<128><<<a.K, kNT, 0, s>>>(a, U, fpart, st);
+    else if (P == 256) k_tc_residual<256><<<a.K, kNT, 0, s>>>(a, U, fpart, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -162,6 +163,7 @@ cudaError_t launch_tc_gather_eta(const PatternArgs &a, int P, const float2 *psi,
 {
     if (P == 64) k_tc_gather_eta<64><<<a.K, kNT, 0, s>>>(a, psi, g, ep, X, pars, st);
     else if (P == 128) k_tc_gather_eta<128><<<a.K, kNT, 0, s>>>(a, psi, g, ep, X, pars, st);
+    else if (P == 256) k_tc_gather_eta<256><<<a.K, kNT, 0, s>>>(a, psi, g, ep, X, pars, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
@@ -185,6 +187,7 @@ cudaError_t launch_tc_ls_entries(const PatternArgs &a, int P, int L, const float
 {
     if (P == 64) return ls_entries_p<64>(a, L, V, pars, part, st, s);
     if (P == 128) return ls_entries_p<128>(a, L, V, pars, part, st, s);
+    if (P == 256) return ls_entries_p<256>(a, L, V, pars, part, st, s);
     return cudaErrorInvalidValue;
 }
 

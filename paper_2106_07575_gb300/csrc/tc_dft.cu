@@ -337,7 +337,9 @@ cudaError_t run_rows(const float2 *X, float2 *Y, const void *img, int nrows, con
 
 }  // namespace
 
-bool tc_dft_supported(int P) { return P == 64 || P == 128; }
+// Split BF16 (warp-specialised kernel): P = 64, 128, 256.  Split FP16 (the whole A tile in
+// shared memory): P = 64, 128.
+bool tc_dft_supported(int P, bool bf16) { return P == 64 || P == 128 || (bf16 && P == 256); }
 
 namespace {
 std::atomic<long long> g_tc_wait_limit{tcx::kSpinLimit};

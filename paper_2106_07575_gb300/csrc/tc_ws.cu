@@ -8,6 +8,9 @@
 // input point (k = 2n + c), so a K-chunk of 64 is the contiguous 32-point segment of a row,
 // and the three products are taken chunk by chunk.
 //
+// P = 256 (N = 2P = 512) takes two MMAs of N = 256 per K step into a single 512-column
+// accumulator (no double buffering), with a 2-stage B ring of 64 KB images.
+//
 // One CTA per SM loops over tiles of 128 rows.  Roles (warps):
 //   0       loader: bulk copies of the B chunk images (4-stage ring: every tile streams the
 //           whole split DFT matrix from L2), each completing on an mbarrier with its bytes;
@@ -53,18 +56,26 @@ constexpr int kAPart = kWsRows * kWsKC * 2;  // one BF16 part of an A chunk
 constexpr int kAStage = 2 * kAPart;          // hi, lo
 constexpr int kSBO = 128 * (kWsKC / 8);      // row-group stride of a chunk (A and B)
 
+// P = 64, 128: one MMA per K step (N = 2P <= 256), two accumulator buffers in TMEM, a
+// 4-stage B ring.  P = 256: N = 512 is taken as two MMAs of N = 256 per K step into one
+// accumulator of 512 columns (all of TMEM), and the B ring has 2 stages of 64 KB.
 template <int P>
 struct WsGeo {
-    static constexpr int N = 2 * P;
+    static constexpr int N = 2 * P;                        // accumulator columns: re | im
+    static constexpr int NM = N < 256 ? N : 256;           // N of one MMA instruction
+    static constexpr int NSPLIT = N / NM;                  // MMAs per K step
+    static constexpr int NBUF = 2 * N <= 512 ? 2 : 1;      // accumulator buffers
+    static constexpr int SB = P >= 256 ? 2 : kWsSB;        // B ring stages
     static constexpr int NKC = 2 * P / kWsKC;
     static constexpr int BIMG = N * kWsKC * 2;
-    static constexpr int TMEM_COLS = 2 * N;  // two accumulator buffers
+    static constexpr int TMEM_COLS = NBUF * N;
     static constexpr size_t OFF_A = 0;
     static constexpr size_t OFF_B = OFF_A + (size_t)kWsSA * kAStage;
-    static constexpr size_t OFF_BAR = OFF_B + (size_t)kWsSB * BIMG;
-    static constexpr int NBAR = 2 * kWsSA + 2 * kWsSB + 2 + 2 + 1;
+    static constexpr size_t OFF_BAR = OFF_B + (size_t)SB * BIMG;
+    static constexpr int NBAR = 2 * kWsSA + 2 * SB + 2 * NBUF + 1;
     static constexpr size_t SMEM = OFF_BAR + 8 * NBAR + 16;
     static_assert(OFF_A % 1024 == 0 && OFF_B % 1024 == 0, "ring alignment");
+    static_assert(TMEM_COLS <= 512 && NM % 16 == 0 && SMEM <= 227 * 1024, "geometry");
 };
 
 template <int N>
@@ -108,8 +119,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
     uint8_t *as = sm + G::OFF_A, *bs = sm + G::OFF_B;
     uint64_t *bar = (uint64_t *)(sm + G::OFF_BAR);
     uint64_t *afull = bar, *aempty = afull + kWsSA;
-    uint64_t *bfull = aempty + kWsSA, *bempty = bfull + kWsSB, *tfull = bempty + kWsSB, *tempty = tfull + 2;
-    uint64_t *mdone = tempty + 2;
+    uint64_t *bfull = aempty + kWsSA, *bempty = bfull + G::SB, *tfull = bempty + G::SB, *tempty = tfull + G::NBUF;
+    uint64_t *mdone = tempty + G::NBUF;
     uint32_t *tmem_slot = (uint32_t *)(mdone + 1);
     __shared__ int fail_s;
     volatile int *fail = &fail_s;
@@ -122,11 +133,11 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             mbar_init(afull + s, kWsSplitWarps);
             mbar_init(aempty + s, 1);
         }
-        for (int s = 0; s < kWsSB; s++) {
+        for (int s = 0; s < G::SB; s++) {
             mbar_init(bfull + s, 1);
             mbar_init(bempty + s, 1);
         }
-        for (int b = 0; b < 2; b++) {
+        for (int b = 0; b < G::NBUF; b++) {
             mbar_init(tfull + b, 1);
             mbar_init(tempty + b, kWsEpiWarps);
         }
@@ -147,14 +158,14 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         // ---------------------------------------------------------------- loader
         if (lane == 0) {
             int ub = 0;
-            int lastb[kWsSB];  // last use issued per stage (-1: none)
-            for (int s = 0; s < kWsSB; s++) lastb[s] = -1;
+            int lastb[G::SB];  // last use issued per stage (-1: none)
+            for (int s = 0; s < G::SB; s++) lastb[s] = -1;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x)
                 for (int kc = 0; kc < G::NKC && ok; kc++)
                     for (int part = 0; part < 2 && ok; part++) {
-                        const int sb = ub % kWsSB;
-                        if (!(ok = ws_wait(bempty + sb, ((ub / kWsSB) & 1) ^ 1, fail, spin_limit))) break;
+                        const int sb = ub % G::SB;
+                        if (!(ok = ws_wait(bempty + sb, ((ub / G::SB) & 1) ^ 1, fail, spin_limit))) break;
                         mbar_expect_tx(bfull + sb, (uint32_t)G::BIMG);
                         bulk_g2s(bs + (size_t)sb * G::BIMG, Bimg + (size_t)(2 * kc + part) * G::BIMG, G::BIMG,
                                  bfull + sb);
@@ -163,20 +174,20 @@ __global__ void __launch_bounds__(kWsThreads, 1)
             if (!ok) {
                 ws_fail(fail, err);
                 // let every issued copy land before the CTA can exit (bounded)
-                for (int s = 0; s < kWsSB; s++)
-                    if (lastb[s] >= 0) mbar_wait(bfull + s, (lastb[s] / kWsSB) & 1);
+                for (int s = 0; s < G::SB; s++)
+                    if (lastb[s] >= 0) mbar_wait(bfull + s, (lastb[s] / G::SB) & 1);
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         // ---------------------------------------------------------------- MMA
         if (lane == 0) {
-            const uint32_t idesc = idesc_bf16<G::N>();
+            const uint32_t idesc = idesc_bf16<G::NM>();
             int ua = 0, ub = 0, lt = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, lt++) {
-                const int tb = lt & 1;
-                if (!(ok = ws_wait(tempty + tb, ((lt >> 1) & 1) ^ 1, fail, spin_limit))) break;
+                const int tb = lt % G::NBUF;
+                if (!(ok = ws_wait(tempty + tb, ((lt / G::NBUF) & 1) ^ 1, fail, spin_limit))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t d = tmem + (uint32_t)(tb * G::N);
                 for (int kc = 0; kc < G::NKC && ok; kc++) {
@@ -184,18 +195,23 @@ __global__ void __launch_bounds__(kWsThreads, 1)
                     if (!(ok = ws_wait(afull + sa, (ua / kWsSA) & 1, fail, spin_limit))) break;
                     const uint32_t ah = smem_u32(as + (size_t)sa * kAStage), al = ah + kAPart;
                     for (int part = 0; part < 2 && ok; part++) {
-                        const int sb = ub % kWsSB;
-                        if (!(ok = ws_wait(bfull + sb, (ub / kWsSB) & 1, fail, spin_limit))) break;
+                        const int sb = ub % G::SB;
+                        if (!(ok = ws_wait(bfull + sb, (ub / G::SB) & 1, fail, spin_limit))) break;
                         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                         const uint32_t b = smem_u32(bs + (size_t)sb * G::BIMG);
 #pragma unroll
-                        for (int k = 0; k < kWsKC / 16; k++) {
-                            const uint64_t bd = umma_desc(b + 2 * k * 128, 128, kSBO);
-                            // part 0 (Bh): Ah Bh + Al Bh; part 1 (Bl): Ah Bl
-                            umma_f16(d, umma_desc(ah + 2 * k * 128, 128, kSBO), bd, idesc,
-                                     (kc > 0 || part > 0 || k > 0) ? 1u : 0u);
-                            if (part == 0) umma_f16(d, umma_desc(al + 2 * k * 128, 128, kSBO), bd, idesc, 1u);
-                        }
+                        for (int k = 0; k < kWsKC / 16; k++)
+#pragma unroll
+                            for (int nh = 0; nh < G::NSPLIT; nh++) {
+                                // rows [nh NM, nh NM + NM) of the B chunk: NM / 8 row groups further
+                                const uint64_t bd = umma_desc(b + (uint32_t)(nh * (G::NM / 8) * kSBO) + 2 * k * 128,
+                                                              128, kSBO);
+                                const uint32_t dn = d + (uint32_t)(nh * G::NM);
+                                // part 0 (Bh): Ah Bh + Al Bh; part 1 (Bl): Ah Bl
+                                umma_f16(dn, umma_desc(ah + 2 * k * 128, 128, kSBO), bd, idesc,
+                                         (kc > 0 || part > 0 || k > 0) ? 1u : 0u);
+                                if (part == 0) umma_f16(dn, umma_desc(al + 2 * k * 128, 128, kSBO), bd, idesc, 1u);
+                            }
                         umma_commit(bempty + sb);
                         ub++;
                     }
@@ -286,8 +302,8 @@ __global__ void __launch_bounds__(kWsThreads, 1)
         int lt = 0;
         bool ok = true;
         for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, lt++) {
-            const int tb = lt & 1;
-            if (lane == 0) ok = ws_wait(tfull + tb, (lt >> 1) & 1, fail, spin_limit);
+            const int tb = lt % G::NBUF;
+            if (lane == 0) ok = ws_wait(tfull + tb, (lt / G::NBUF) & 1, fail, spin_limit);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -384,6 +400,7 @@ cudaError_t tc_ws_images(int P, int sign, std::vector<uint8_t> &out)
 {
     if (P == 64) out = build_ws_images<64>(sign);
     else if (P == 128) out = build_ws_images<128>(sign);
+    else if (P == 256) out = build_ws_images<256>(sign);
     else return cudaErrorInvalidValue;
     return cudaSuccess;
 }
@@ -393,6 +410,7 @@ cudaError_t tc_ws_rows(int P, const float2 *X, float2 *Y, const void *img, int n
 {
     if (P == 64) return run_ws<64>(X, Y, img, nrows, out_index, conj_mul, err, s);
     if (P == 128) return run_ws<128>(X, Y, img, nrows, out_index, conj_mul, err, s);
+    if (P == 256) return run_ws<256>(X, Y, img, nrows, out_index, conj_mul, err, s);
     return cudaErrorInvalidValue;
 }
 

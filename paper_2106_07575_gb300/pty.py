@@ -29,7 +29,7 @@ PTY_ERR_NONFINITE, PTY_STALLED, PTY_ERR_TIMEOUT, PTY_ERR_UNSUPPORTED = 5, 6, 7, 
 STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_NOMEM", 4: "PTY_ERR_CUDA",
                 5: "PTY_ERR_NONFINITE", 6: "PTY_STALLED", 7: "PTY_ERR_TIMEOUT", 8: "PTY_ERR_UNSUPPORTED"}
 
-EXPORTED = ["pty_default_opts", "pty_create", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
+EXPORTED = ["pty_default_opts", "pty_create", "pty_create_subpixel", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
             "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
             "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_selftest_tc_wait_limit", "pty_gradient_noalloc",
             "pty_get_plan", "pty_selftest_ls_certified",
@@ -95,6 +95,8 @@ def load(build_if_missing: bool = True):
     lib.pty_default_opts.argtypes = [ctypes.POINTER(pty_opts)]
     lib.pty_default_opts.restype = None
     lib.pty_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, vp, i32, vp, vp, ctypes.POINTER(pty_opts), vp]
+    lib.pty_create_subpixel.argtypes = [ctypes.POINTER(vp), i32, i32, i32, vp, i32, vp, vp, ctypes.POINTER(pty_opts),
+                                        vp]
     lib.pty_destroy.argtypes = [vp]
     lib.pty_destroy.restype = None
     lib.pty_last_error.argtypes = [vp]
@@ -140,7 +142,7 @@ def load(build_if_missing: bool = True):
     lib.pty_cnn_train.argtypes = [vp, i64, vp, vp, i32, i32, u64, ctypes.POINTER(pty_adam), ctypes.POINTER(dbl)]
     lib.pty_stitch.argtypes = [vp, vp, ctypes.c_float, vp]
     lib.pty_learned_init.argtypes = [vp, vp, vp, vp, ctypes.POINTER(pty_init_report)]
-    for f in ("pty_create", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
+    for f in ("pty_create", "pty_create_subpixel", "pty_forward", "pty_adjoint", "pty_gradient", "pty_cg_solve", "pty_cg_reset",
               "pty_cg_state_save", "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p",
               "pty_gradient_noalloc", "pty_get_plan", "pty_batch_create", "pty_batch_cg_solve", "pty_cnn_create",
               "pty_cnn_set_params", "pty_cnn_get_params", "pty_cnn_init_params", "pty_cnn_set_loss_weight",
@@ -206,6 +208,17 @@ def pty_create(H, W, P, probe, K, pos, data, opts: pty_opts | None = None, strea
     st = lib.pty_create(ctypes.byref(ctx), H, W, P, _ptr(probe, _C), K, _ptr(pos, _I), _ptr(data, _F),
                         ctypes.byref(opts) if opts is not None else None,
                         ctypes.c_void_p(stream) if stream else None)
+    _check(lib, None, st)
+    return ctx
+
+
+def pty_create_subpixel(H, W, P, probe, K, pos, data, opts: pty_opts | None = None, stream=None):
+    """As pty_create with float32 positions [K][2] that may have a fractional part."""
+    lib = load()
+    ctx = ctypes.c_void_p()
+    st = lib.pty_create_subpixel(ctypes.byref(ctx), H, W, P, _ptr(probe, _C), K, _ptr(pos, _F), _ptr(data, _F),
+                                 ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.c_void_p(stream) if stream else None)
     _check(lib, None, st)
     return ctx
 
@@ -411,8 +424,14 @@ class Problem:
     K: int
 
 
+def _is_float32(a):
+    return str(getattr(a, "dtype", "")).replace("torch.", "") == "float32"
+
+
 class Context:
-    """Owning wrapper: one libpty context per reconstruction problem."""
+    """Owning wrapper: one libpty context per reconstruction problem.  Integer positions
+    (int32) go to pty_create; float32 positions, which may be fractional, to
+    pty_create_subpixel."""
 
     def __init__(self, probe, pos, data, H, W, opts: pty_opts | None = None, stream=None):
         P = probe.shape[0]
@@ -423,7 +442,8 @@ class Context:
         self.shape = (H, W)
         self.P, self.K = P, K
         self._keep = (probe, pos, data)  # borrowed device data must outlive the context
-        self.ctx = pty_create(H, W, P, probe, K, pos, data, opts, stream)
+        create = pty_create_subpixel if _is_float32(pos) else pty_create
+        self.ctx = create(H, W, P, probe, K, pos, data, opts, stream)
 
     def close(self):
         if self.ctx:

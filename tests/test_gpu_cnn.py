@@ -198,7 +198,8 @@ def test_learned_init_fallback_keeps_ones():
 def test_learned_init_trained_gain():
     """Train on forward-model pairs (ellipse and Voronoi phantoms), then compare the learned
     start with the ones start on a held-out scan: objective at the start, and CG iterations
-    to a relative objective gap of 1e-3 (gap normalised by the ones start, F* = F(psi_true))."""
+    to a relative objective gap of 1e-3 (gap normalised by the ones start, F* = F(psi_true)).
+    Fails unless the trained start is kept and saves at least a fifth of the iterations."""
     from paper_2106_07575_gb300 import learned
 
     prob, ctx = _small_test_problem()
@@ -229,4 +230,10 @@ def test_learned_init_trained_gain():
     print(f"learned start: used={rep['used_learned']} scale={rep['scale']:.4f} gap at start {gap0:.3f}; "
           f"iterations to gap 1e-3: ones {res['ones']}, learned {res['learned']}")
     assert res["ones"] is not None and res["learned"] is not None
+    # the gain itself: the trained network's start is kept (its objective is below the ones
+    # start's), begins closer to the optimum, and reaches the gap in clearly fewer iterations
+    # (measured 18 against 32); an untrained or useless network fails here
+    assert rep["used_learned"] and rep["F_learned"] < rep["F_ones"]
+    assert gap0 < 1.0  # measured 0.92: a small head start that CG turns into far fewer iterations
+    assert res["learned"] <= 0.8 * res["ones"]
     ctx.close()

@@ -313,6 +313,103 @@ __device__ __forceinline__ void fft2_inv(float2 *buf, const float2 *tw)
     rows_fft<P, R, NT, +1>(buf, tw);
 }
 
+// ---------------------------------------------------------------------------------------
+// Single-CTA transforms whose row stride step exchanges with registers (R = P): the forward
+// transform's first step takes the exit wave from a loader, the inverse transform's last step
+// hands its natural-order rows to a storer, so neither the gather nor the adjoint's emit
+// makes a pass of its own through shared memory.
+//
+// Work item (row, n2) of a row stride step: 16 elements n2 + R2 n1 of one row.  Warp item vw
+// holds the rows b + R2 j (j < 32 / R2), b = vw % R2 + 32 (vw / R2), lane l the row
+// b + R2 (l / R2) and n2 = l % R2: with the tile's row stride P + 1 the 16 lanes of a
+// half-warp touch 16 distinct bank pairs, and a global access of a warp covers 32 / R2 runs
+// of R2 consecutive complex values.  A thread's items are vw = warp + ii NT / 32.
+template <int P>
+__device__ __forceinline__ void row_item(int vw, int lane, int &row, int &n2)
+{
+    constexpr int R2 = Tile<P>::R2;
+    row = (vw % R2) + 32 * (vw / R2) + R2 * (lane / R2);
+    n2 = lane % R2;
+}
+
+// Twiddles of the row stride step in item order: tw2[k1 R2 + n2] = W_P^(n2 k1) (lanes of a
+// warp read consecutive entries).
+template <int P, int NT>
+__device__ __forceinline__ void load_row_twiddles(float2 *tw2, const float2 *__restrict__ g_tw)
+{
+    constexpr int R2 = Tile<P>::R2;
+    for (int m = threadIdx.x; m < 16 * R2; m += NT) tw2[m] = g_tw[((m % R2) * (m / R2)) & (P - 1)];
+}
+
+// Forward: ld(ii, row, n2, x) fills x[n1] = the exit wave at (row, n2 + R2 n1); the tile
+// then holds what pass_stride<-1> over the rows would have written.
+template <int P, int NT, typename LD>
+__device__ __forceinline__ void rows_stride_fwd_in(float2 *buf, const float2 *tw2, LD ld)
+{
+    constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2, LDA = P + 1, NVW = P * R2 / 32;
+    static_assert(NVW % (NT / 32) == 0, "whole items per thread");
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int ii = 0; ii < NVW / (NT / 32); ii++) {
+        int row, n2;
+        row_item<P>((threadIdx.x >> 5) + ii * (NT / 32), lane, row, n2);
+        float2 x[R1];
+        ld(ii, row, n2, x);
+        dft_reg<R1, -1>(x);
+#pragma unroll
+        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmul(x[k1], tw2[k1 * R2 + n2]);
+        float2 *b = buf + row * LDA + n2;
+#pragma unroll
+        for (int n1 = 0; n1 < R1; n1++) b[R2 * n1] = x[n1];
+    }
+}
+
+// Inverse, the last step: reads what pass_stride<+1> over the rows would read and hands
+// st(ii, row, n2, x) the results x[n1] = row element n2 + R2 n1 (natural order).
+template <int P, int NT, typename ST>
+__device__ __forceinline__ void rows_stride_inv_out(const float2 *buf, const float2 *tw2, ST st)
+{
+    constexpr int R1 = Tile<P>::R1, R2 = Tile<P>::R2, LDA = P + 1, NVW = P * R2 / 32;
+    static_assert(NVW % (NT / 32) == 0, "whole items per thread");
+    const int lane = threadIdx.x & 31;
+#pragma unroll 1
+    for (int ii = 0; ii < NVW / (NT / 32); ii++) {
+        int row, n2;
+        row_item<P>((threadIdx.x >> 5) + ii * (NT / 32), lane, row, n2);
+        const float2 *b = buf + row * LDA + n2;
+        float2 x[R1];
+#pragma unroll
+        for (int n1 = 0; n1 < R1; n1++) x[n1] = b[R2 * n1];
+#pragma unroll
+        for (int k1 = 1; k1 < R1; k1++) x[k1] = cmulc(x[k1], tw2[k1 * R2 + n2]);
+        dft_reg<R1, +1>(x);
+        st(ii, row, n2, x);
+    }
+}
+
+// Unnormalised forward 2-D DFT of one tile, the first step from ld (see rows_stride_fwd_in);
+// permuted order out, ends with a barrier.  The caller has synchronised buf's earlier use.
+template <int P, int NT, typename LD>
+__device__ __forceinline__ void fft2_fwd_in(float2 *buf, const float2 *tw, const float2 *tw2, LD ld)
+{
+    rows_stride_fwd_in<P, NT>(buf, tw2, ld);
+    __syncthreads();
+    pass_block<P, NT, P, P + 1, 1, -1>(buf);
+    __syncthreads();
+    cols_fft<P, P, NT, -1>(buf, tw);
+}
+
+// Unnormalised inverse 2-D DFT of one tile (permuted order in), the natural-order rows of
+// the result handed to st (see rows_stride_inv_out).  No barrier at the end.
+template <int P, int NT, typename ST>
+__device__ __forceinline__ void fft2_inv_out(float2 *buf, const float2 *tw, const float2 *tw2, ST st)
+{
+    cols_fft<P, P, NT, +1>(buf, tw);
+    pass_block<P, NT, P, P + 1, 1, +1>(buf);
+    __syncthreads();
+    rows_stride_inv_out<P, NT>(buf, tw2, st);
+}
+
 // Single-CTA forms (R = P), kept for callers that hold the whole tile.
 template <int P, int NT>
 __device__ __forceinline__ void fft2_fwd(float2 *tile, const float2 *tw)

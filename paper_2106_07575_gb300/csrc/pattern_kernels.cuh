@@ -38,10 +38,12 @@ namespace pty {
 
 constexpr int kGatherUnroll = PTY_GATHER_UNROLL;
 
+// The tile or slab, the twiddles [P], and the row-step twiddles in item order [16 * P/16]
+// (single-CTA configurations).
 template <int P, int R>
 constexpr size_t slab_bytes()
 {
-    return sizeof(float2) * (size_t)(Slab<P, R>::ELEMS + P);
+    return sizeof(float2) * (size_t)(Slab<P, R>::ELEMS + 2 * P);
 }
 
 // Resident CTAs per SM the register allocation may plan for: 1 where the tile or slab takes
@@ -61,10 +63,12 @@ __device__ __forceinline__ void who(int &i, int &c)
     c = blockIdx.x % Slab<P, R>::CS;
 }
 
+// Twiddles [P] and, after them, the row-step twiddles in item order (fft_tile.cuh).
 template <int P, int NT>
 __device__ __forceinline__ void load_twiddles(float2 *tw, const float2 *__restrict__ g_tw)
 {
     for (int m = threadIdx.x; m < P; m += NT) tw[m] = g_tw[m];
+    load_row_twiddles<P, NT>(tw + P, g_tw);
 }
 
 // Row slab of Q psi: rows [cR, cR+R) of probe[y][x] * src[r0 + y][c0 + x]  (Eq. 1)
@@ -81,10 +85,12 @@ __device__ __forceinline__ void gather_rows(float2 *buf, const float2 *__restric
 }
 
 // Probe cache in tensor memory (single-CTA configurations, R = P).  The gather of an exit
-// wave and the emit of an adjoint result both visit pixel e = t + k NT with thread t, so
-// thread t needs only the probe values p[t + k NT], k < NE.  They are stored once per kernel
-// in the thread's TMEM lane (lane quarter warp % 4, columns from (warp / 4) 2 NE) and read
-// back with tcgen05.ld, instead of 128 KB of L2 loads per pattern at P = 128.
+// wave and the emit of an adjoint result both run in the row stride step's work items
+// (fft_tile.cuh: item ii of thread t is (row, n2), elements n2 + R2 n1), so thread t needs
+// only the probe values of its items: NE = P^2 / NT values, 16 per item, in item order.
+// They are stored once per kernel in the thread's TMEM lane (lane quarter warp % 4, columns
+// from (warp / 4) 2 NE) and read back with tcgen05.ld, instead of 128 KB of L2 loads per
+// pattern at P = 128.
 template <int P, int NT>
 struct ProbeCache {
     static constexpr int NE = P * P / NT;  // complex values per thread
@@ -104,12 +110,15 @@ struct ProbeCache {
         tcx::tmem_fence_after_sync();
         base = *slot;
         addr = base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * NCOL);
+        constexpr int R2 = Tile<P>::R2;
 #pragma unroll 1
         for (int k0 = 0; k0 < NE; k0 += 4) {
+            int row, n2;
+            row_item<P>(warp + (k0 / 16) * (NT / 32), threadIdx.x & 31, row, n2);
             float v[8];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const float2 pv = __ldg(probe + threadIdx.x + (k0 + j) * NT);
+                const float2 pv = __ldg(probe + row * P + n2 + R2 * ((k0 % 16) + j));
                 v[2 * j] = pv.x;
                 v[2 * j + 1] = pv.y;
             }
@@ -134,30 +143,61 @@ struct ProbeCache {
     }
 };
 
-// Single-CTA form of gather_rows with the probe from the cache: all NE loads of the object
-// are in flight before the first product.
+// Loader of the forward row step (fft2_fwd_in): x[n1] = p(row, c) * src(r0 + row, c0 + c),
+// c = n2 + R2 n1, the probe from the cache (pc) or from global memory (pk); all 16 loads of
+// the object are issued before the first product.
 template <int P, int NT>
-__device__ __forceinline__ void gather_cached(float2 *buf, const ProbeCache<P, NT> &pc,
-                                              const float2 *__restrict__ src, int W, int r0, int c0)
-{
-    constexpr int LDA = P + 1, NE = ProbeCache<P, NT>::NE;
-    float2 sv[NE];
+struct ExitWaveLoader {
+    const ProbeCache<P, NT> *pc;
+    const float2 *pk;
+    const float2 *src;
+    int W, r0, c0;
+    __device__ __forceinline__ void operator()(int ii, int row, int n2, float2 (&x)[16]) const
+    {
+        constexpr int R2 = Tile<P>::R2;
+        const float2 *s0 = src + (size_t)(r0 + row) * W + (c0 + n2);
 #pragma unroll
-    for (int k = 0; k < NE; k++) {
-        const int e = threadIdx.x + k * NT;
-        sv[k] = __ldg(src + (size_t)(r0 + e / P) * W + (c0 + e % P));
-    }
+        for (int n1 = 0; n1 < 16; n1++) x[n1] = __ldg(s0 + R2 * n1);
 #pragma unroll
-    for (int k0 = 0; k0 < NE; k0 += 4) {
-        float2 pv[4];
-        pc.get4(k0, pv);
+        for (int k0 = 0; k0 < 16; k0 += 4) {
+            float2 pv[4];
+            if (pc) {
+                pc->get4(ii * 16 + k0, pv);
+            } else {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            const int e = threadIdx.x + (k0 + j) * NT;
-            buf[(e / P) * LDA + (e % P)] = cmul(pv[j], sv[k0 + j]);
+                for (int j = 0; j < 4; j++) pv[j] = __ldg(pk + row * P + n2 + R2 * (k0 + j));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) x[k0 + j] = cmul(pv[j], x[k0 + j]);
         }
     }
-}
+};
+
+// Storer of the inverse row step (fft2_inv_out): w(row, c) = conj(p(row, c)) * x[n1],
+// c = n2 + R2 n1, into one pattern's [P][P] result.
+template <int P, int NT>
+struct AdjointStorer {
+    const ProbeCache<P, NT> *pc;
+    const float2 *pk;
+    float2 *wi;
+    __device__ __forceinline__ void operator()(int ii, int row, int n2, const float2 (&x)[16]) const
+    {
+        constexpr int R2 = Tile<P>::R2;
+        float2 *d0 = wi + row * P + n2;
+#pragma unroll
+        for (int k0 = 0; k0 < 16; k0 += 4) {
+            float2 pv[4];
+            if (pc) {
+                pc->get4(ii * 16 + k0, pv);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) pv[j] = __ldg(pk + row * P + n2 + R2 * (k0 + j));
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) d0[R2 * (k0 + j)] = cconjmul(pv[j], x[k0 + j]);
+        }
+    }
+};
 
 // Kahan-compensated single-precision accumulation (per thread; the block sum is FP64).
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x)
@@ -197,29 +237,13 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_forward(PatternArgs a,
     }
 }
 
-// w[i] = conj(p) * (row slab of F^H r) of pattern i, with the probe from the cache when given.
+// w[i] = conj(p) * (row slab of F^H r) of pattern i (cluster configurations).
 template <int P, int R, int NT>
 __device__ __forceinline__ void emit_adjoint(const PatternArgs &a, const float2 *buf, float2 *__restrict__ w, int i,
-                                             int c, const ProbeCache<P, NT> *pc)
+                                             int c)
 {
     constexpr int LDA = Slab<P, R>::LDA;
     float2 *wi = w + (size_t)i * P * P;
-    if constexpr (R == P) {
-        if (pc) {
-            constexpr int NE = ProbeCache<P, NT>::NE;
-#pragma unroll
-            for (int k0 = 0; k0 < NE; k0 += 4) {
-                float2 pv[4];
-                pc->get4(k0, pv);
-#pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const int e = threadIdx.x + (k0 + j) * NT;
-                    wi[e] = cconjmul(pv[j], buf[(e / P) * LDA + (e % P)]);
-                }
-            }
-            return;
-        }
-    }
     const float2 *pk = probe_of(a, i);
     for (int e = threadIdx.x; e < R * P; e += NT) {
         const int rl = e / P, x = e % P, yy = c * R + rl;
@@ -283,14 +307,13 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
 {
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
-    if constexpr (R == P) {
-        if (pc) gather_cached<P, NT>(buf, *pc, psi, a.W, rc.x, rc.y);
-        else gather_rows<P, R, NT>(buf, probe_of(a, i), psi, a.W, rc.x, rc.y, c);
+    if constexpr (R == P) {  // the gather feeds the first row step from registers
+        fft2_fwd_in<P, NT>(buf, tw, tw + P, ExitWaveLoader<P, NT>{pc, probe_of(a, i), psi, a.W, rc.x, rc.y});
     } else {
         gather_rows<P, R, NT>(buf, probe_of(a, i), psi, a.W, rc.x, rc.y, c);
+        __syncthreads();
+        fft2_fwd<P, R, NT>(buf, tw);
     }
-    __syncthreads();
-    fft2_fwd<P, R, NT>(buf, tw);
     float f = 0.0f;
     for (int e = threadIdx.x; e < P * R; e += NT) {
         const float2 u = buf[(e / R) * LDB + (e % R)];
@@ -323,8 +346,12 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
         block_sum_ff<NT, 1>(v, red, tot);  // its barriers also order the residual writes before F^H
         if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
     }
-    fft2_inv<P, R, NT>(buf, tw);
-    emit_adjoint<P, R, NT>(a, buf, w, i, c, pc);
+    if constexpr (R == P) {  // the last row step hands its rows to the emit
+        fft2_inv_out<P, NT>(buf, tw, tw + P, AdjointStorer<P, NT>{pc, probe_of(a, i), w + (size_t)i * P * P});
+    } else {
+        fft2_inv<P, R, NT>(buf, tw);
+        emit_adjoint<P, R, NT>(a, buf, w, i, c);
+    }
 }
 
 // Single-CTA configurations (CS = 1) run persistently: the CTAs of the grid stride over
@@ -425,8 +452,12 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
         block_sum_ff<NT, 1>(vv, red, tot);  // its barriers also order the writes before F^H
         if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
     }
-    fft2_inv<P, R, NT>(buf, tw);
-    emit_adjoint<P, R, NT>(a, buf, w, i, c, pc);
+    if constexpr (R == P) {  // the last row step hands its rows to the emit
+        fft2_inv_out<P, NT>(buf, tw, tw + P, AdjointStorer<P, NT>{pc, probe_of(a, i), w + (size_t)i * P * P});
+    } else {
+        fft2_inv<P, R, NT>(buf, tw);
+        emit_adjoint<P, R, NT>(a, buf, w, i, c);
+    }
 }
 
 template <int P, int R, int NT>
@@ -518,14 +549,13 @@ __device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const flo
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
     // p eta / P into the row slab
-    if constexpr (R == P) {
-        if (pc) gather_cached<P, NT>(buf, *pc, eta, a.W, rc.x, rc.y);
-        else gather_rows<P, R, NT>(buf, probe_of(a, i), eta, a.W, rc.x, rc.y, c);
+    if constexpr (R == P) {  // the gather feeds the first row step from registers
+        fft2_fwd_in<P, NT>(buf, tw, tw + P, ExitWaveLoader<P, NT>{pc, probe_of(a, i), eta, a.W, rc.x, rc.y});
     } else {
         gather_rows<P, R, NT>(buf, probe_of(a, i), eta, a.W, rc.x, rc.y, c);
+        __syncthreads();
+        fft2_fwd<P, R, NT>(buf, tw);
     }
-    __syncthreads();
-    fft2_fwd<P, R, NT>(buf, tw);
     // v = G eta at the entries (kept for the candidate windows), and the entries' share of
     // the two all-pixel sums, removed here so that rows 0 and 1 cover the pixels without
     // counts; with the certificate also the two weighted sums of its bound

@@ -41,6 +41,14 @@ PTY_API int pty_selftest_tc_wait_limit(int64_t polls);
  */
 PTY_API int pty_selftest_ls_certified(pty_ctx *ctx, int32_t view, int32_t *k0cert);
 
+/*
+ * Switch the tensor-core form of the learned initial guess's hidden convolutions (tcgen05
+ * implicit GEMMs, used at P = 128 and 256) off (enable = 0) or back on (enable != 0, the
+ * default), so that tests can compare it with the CUDA-core form.  Process-wide; applies to
+ * launches made after the call.  Returns the previous setting (0 or 1).
+ */
+PTY_API int pty_selftest_cnn_tc(int32_t enable);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,6 +25,7 @@
 
 #include "cnn_internal.h"
 #include "pty_cnn.h"
+#include "pty_selftest.h"
 
 struct pty_cnn {
     int dev = 0, P = 0, C = 0, L = 0, Bcap = 0;
@@ -42,6 +43,7 @@ struct pty_cnn {
     float *x0 = nullptr, *zh = nullptr, *dzh = nullptr, *dz0 = nullptr, *dz1 = nullptr, *part = nullptr;
     std::vector<float *> z, a;
     double *lpart = nullptr, *dloss = nullptr;
+    int *tc_err = nullptr;  // set by a timed-out wait of the tensor-core convolutions
     std::string err;
 };
 
@@ -111,7 +113,7 @@ struct DevGuard {
 void free_all(pty_cnn *n)
 {
     void *ptrs[] = {n->master, n->m, n->v, n->grad, n->w16, n->wt16, n->lw, n->x0, n->zh, n->dzh,
-                    n->dz0,    n->dz1, n->part, n->lpart, n->dloss};
+                    n->dz0,    n->dz1, n->part, n->lpart, n->dloss, n->tc_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (float *p : n->z)
@@ -137,7 +139,8 @@ int run_forward(pty_cnn *n, int B, const int *idx, const float *d)
     CKN(launch_features(n->P, B, d, idx, n->x0, n->s));
     const float *in = n->x0;
     for (int l = 0; l < n->L - 1; l++) {
-        CKN(launch_conv_fwd(n->P, n->cin[l], B, in, n->w16 + n->woff[l], bias(n, l), n->z[l], n->a[l], n->s));
+        CKN(launch_conv_fwd(n->P, n->cin[l], B, in, n->w16 + n->woff[l], bias(n, l), n->z[l], n->a[l], n->tc_err,
+                            n->s));
         in = n->a[l];
     }
     const int h = n->L - 1;
@@ -159,10 +162,10 @@ int run_loss_grad(pty_cnn *n, int B, const int *idx, const float *d, const float
     // output layer
     CKN(launch_wgrad(P, n->cin[L - 1], 2, B, n->a[L - 2], n->dzh, n->part, n->grad + n->off[L - 1], n->s));
     float *cur = n->dz0, *other = n->dz1;
-    CKN(launch_conv_bwd(P, 2, B, n->dzh, n->wt16 + n->woff[L - 1], n->z[L - 2], cur, n->s));
+    CKN(launch_conv_bwd(P, 2, B, n->dzh, n->wt16 + n->woff[L - 1], n->z[L - 2], cur, n->tc_err, n->s));
     for (int l = L - 2; l >= 1; l--) {
         CKN(launch_wgrad(P, n->cin[l], n->cout[l], B, n->a[l - 1], cur, n->part, n->grad + n->off[l], n->s));
-        CKN(launch_conv_bwd(P, n->cout[l], B, cur, n->wt16 + n->woff[l], n->z[l - 1], other, n->s));
+        CKN(launch_conv_bwd(P, n->cout[l], B, cur, n->wt16 + n->woff[l], n->z[l - 1], other, n->tc_err, n->s));
         std::swap(cur, other);
     }
     CKN(launch_wgrad(P, 1, n->cout[0], B, n->x0, cur, n->part, n->grad + n->off[0], n->s));
@@ -193,9 +196,17 @@ int reset_adam(pty_cnn *n)
     return PTY_OK;
 }
 
+// Synchronise the network's stream; a timed-out wait of the tensor-core convolutions since the
+// last check is reported (and its flag cleared).
 int sync(pty_cnn *n)
 {
     CKN(cudaStreamSynchronize(n->s));
+    int h = 0;
+    CKN(cudaMemcpy(&h, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        CKN(cudaMemset(n->tc_err, 0, sizeof(int)));
+        return fail(n, PTY_ERR_TIMEOUT, "a bounded wait of the tensor-core convolutions timed out");
+    }
     return PTY_OK;
 }
 
@@ -210,6 +221,13 @@ int check_batch(pty_cnn *n, int B, const float *d, const void *t)
 }  // namespace
 
 extern "C" {
+
+int pty_selftest_cnn_tc(int32_t enable)
+{
+    const bool was = pty::cnn::conv_tc_on();
+    pty::cnn::set_conv_tc(enable != 0);
+    return was ? 1 : 0;
+}
 
 void pty_default_adam(pty_adam *a)
 {
@@ -259,7 +277,7 @@ int pty_cnn_create(pty_cnn **out, int32_t P, int32_t channels, int32_t layers, i
         dalloc(&n->zh, Bc * 2 * PP) || dalloc(&n->dzh, Bc * 2 * PP) || dalloc(&n->dz0, Bc * channels * PP) ||
         dalloc(&n->dz1, Bc * channels * PP) ||
         dalloc(&n->part, (size_t)pty::cnn::wgrad_blocks(P, max_batch) * (channels * channels * 9 + channels)) ||
-        dalloc(&n->lpart, (Bc * PP + 255) / 256) || dalloc(&n->dloss, 1)) {
+        dalloc(&n->lpart, (Bc * PP + 255) / 256) || dalloc(&n->dloss, 1) || dalloc(&n->tc_err, 1)) {
         cudaGetLastError();
         return cleanup(PTY_ERR_NOMEM);
     }
@@ -273,7 +291,8 @@ int pty_cnn_create(pty_cnn **out, int32_t P, int32_t channels, int32_t layers, i
     std::vector<float> ones(PP, 1.f);
     int st = PTY_OK;
     if (cudaMemcpyAsync(n->lw, ones.data(), sizeof(float) * PP, cudaMemcpyHostToDevice, n->s) != cudaSuccess ||
-        cudaMemsetAsync(n->master, 0, sizeof(float) * o, n->s) != cudaSuccess)
+        cudaMemsetAsync(n->master, 0, sizeof(float) * o, n->s) != cudaSuccess ||
+        cudaMemsetAsync(n->tc_err, 0, sizeof(int), n->s) != cudaSuccess)
         st = PTY_ERR_CUDA;
     n->lw_sum = (double)PP;
     if (!st) st = reset_adam(n);

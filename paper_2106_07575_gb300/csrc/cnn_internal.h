@@ -21,10 +21,19 @@ cudaError_t launch_features(int P, int B, const float *d, const int *idx, float 
 // Hidden 3x3 convolution with kC output channels.  cin = 1 or kC (forward: z = conv + bias,
 // a = GELU(z)); cin = 2 or kC (backward-data: out = conv(in; flipped transposed weights) *
 // GELU'(zprev)).  w: BF16 [kC][cin][9].
+// cin = kC at P = 128, 256 runs on the tensor cores (cnn_tc.cu) unless that form is switched
+// off (set_conv_tc); err: device int that a timed-out tensor-core wait sets to 1.
 cudaError_t launch_conv_fwd(int P, int cin, int B, const float *in, const __nv_bfloat16 *w, const float *bias,
-                            float *z, float *a, cudaStream_t s);
+                            float *z, float *a, int *err, cudaStream_t s);
 cudaError_t launch_conv_bwd(int P, int cin, int B, const float *in, const __nv_bfloat16 *wt, const float *zprev,
-                            float *out, cudaStream_t s);
+                            float *out, int *err, cudaStream_t s);
+// The tensor-core form of the hidden convolutions (cnn_tc.cu).
+bool conv_tc_supported(int P, int cin);
+cudaError_t launch_conv_tc(int P, int B, bool bwd, const float *in, const __nv_bfloat16 *w, const float *bias,
+                           const float *zprev, float *z, float *a, int *err, cudaStream_t s);
+// Process-wide switch of the tensor-core form (tests compare both forms); on by default.
+void set_conv_tc(bool on);
+bool conv_tc_on();
 // Output layer: z [B][2][P][P] = conv(in [B][kC][P][P]; w [2][kC][9]) + bias.
 cudaError_t launch_conv_head(int P, int B, const float *in, const __nv_bfloat16 *w, const float *bias, float *z,
                              cudaStream_t s);

@@ -622,8 +622,10 @@ cudaError_t launch_features(int P, int B, const float *d, const int *idx, float 
 }
 
 cudaError_t launch_conv_fwd(int P, int cin, int B, const float *in, const __nv_bfloat16 *w, const float *bias,
-                            float *z, float *a, cudaStream_t s)
+                            float *z, float *a, int *err, cudaStream_t s)
 {
+    if (err && conv_tc_on() && conv_tc_supported(P, cin))
+        return launch_conv_tc(P, B, false, in, w, bias, nullptr, z, a, err, s);
     switch (P) {
     case 64: return conv_fwd_p<64>(cin, B, in, w, bias, z, a, s);
     case 128: return conv_fwd_p<128>(cin, B, in, w, bias, z, a, s);
@@ -633,8 +635,10 @@ cudaError_t launch_conv_fwd(int P, int cin, int B, const float *in, const __nv_b
 }
 
 cudaError_t launch_conv_bwd(int P, int cin, int B, const float *in, const __nv_bfloat16 *wt, const float *zprev,
-                            float *out, cudaStream_t s)
+                            float *out, int *err, cudaStream_t s)
 {
+    if (err && conv_tc_on() && conv_tc_supported(P, cin))
+        return launch_conv_tc(P, B, true, in, wt, nullptr, zprev, out, nullptr, err, s);
     switch (P) {
     case 64: return conv_bwd_p<64>(cin, B, in, wt, zprev, out, s);
     case 128: return conv_bwd_p<128>(cin, B, in, wt, zprev, out, s);

@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "PTY_OK", 1: "PTY_ERR_ARG", 2: "PTY_ERR_BOUNDS", 3: "PTY_ERR_
 EXPORTED = ["pty_default_opts", "pty_create", "pty_create_subpixel", "pty_destroy", "pty_last_error", "pty_forward", "pty_adjoint",
             "pty_gradient", "pty_cg_solve", "pty_cg_reset", "pty_cg_state_size", "pty_cg_state_save",
             "pty_cg_state_load", "pty_stage_times", "pty_selftest_log1p", "pty_selftest_tc_wait_limit", "pty_gradient_noalloc",
-            "pty_get_plan", "pty_selftest_ls_certified",
+            "pty_get_plan", "pty_selftest_ls_certified", "pty_selftest_cnn_tc",
             "pty_batch_create", "pty_batch_cg_solve", "pty_num_views",
             # learned initial guess (include/pty_cnn.h)
             "pty_default_adam", "pty_cnn_create", "pty_cnn_destroy", "pty_cnn_last_error", "pty_cnn_num_params",
@@ -115,6 +115,8 @@ def load(build_if_missing: bool = True):
     lib.pty_selftest_tc_wait_limit.argtypes = [ctypes.c_int64]
     lib.pty_selftest_tc_wait_limit.restype = ctypes.c_int
     lib.pty_selftest_ls_certified.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int32)]
+    lib.pty_selftest_cnn_tc.argtypes = [i32]
+    lib.pty_selftest_cnn_tc.restype = ctypes.c_int
     lib.pty_gradient_noalloc.argtypes = [i32, i32, i32, vp, i32, vp, vp, dbl, vp, vp, vp, vp]
     lib.pty_get_plan.argtypes = [vp, ctypes.POINTER(i32)]
     lib.pty_batch_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, i32, vp, vp, vp, ctypes.POINTER(pty_opts),
@@ -296,6 +298,12 @@ def pty_stage_times(ctx, reset=False):
 
 def pty_selftest_tc_wait_limit(polls):
     return load().pty_selftest_tc_wait_limit(int(polls))
+
+
+def pty_selftest_cnn_tc(enable):
+    """Switch the tensor-core form of the CNN's hidden convolutions on or off; returns the
+    previous setting."""
+    return int(load().pty_selftest_cnn_tc(1 if enable else 0))
 
 
 def pty_selftest_ls_certified(ctx, view=0):

@@ -160,15 +160,17 @@ int run_loss_grad(pty_cnn *n, int B, const int *idx, const float *d, const float
     CKN(launch_loss_finalize(n->lpart, nparts, 1.0 / n->lw_sum / B, dloss, n->s));
     const int P = n->P, L = n->L;
     // output layer
-    CKN(launch_wgrad(P, n->cin[L - 1], 2, B, n->a[L - 2], n->dzh, n->part, n->grad + n->off[L - 1], n->s));
+    CKN(launch_wgrad(P, n->cin[L - 1], 2, B, n->a[L - 2], n->dzh, n->part, n->grad + n->off[L - 1], n->tc_err,
+                     n->s));
     float *cur = n->dz0, *other = n->dz1;
     CKN(launch_conv_bwd(P, 2, B, n->dzh, n->wt16 + n->woff[L - 1], n->z[L - 2], cur, n->tc_err, n->s));
     for (int l = L - 2; l >= 1; l--) {
-        CKN(launch_wgrad(P, n->cin[l], n->cout[l], B, n->a[l - 1], cur, n->part, n->grad + n->off[l], n->s));
+        CKN(launch_wgrad(P, n->cin[l], n->cout[l], B, n->a[l - 1], cur, n->part, n->grad + n->off[l], n->tc_err,
+                         n->s));
         CKN(launch_conv_bwd(P, n->cout[l], B, cur, n->wt16 + n->woff[l], n->z[l - 1], other, n->tc_err, n->s));
         std::swap(cur, other);
     }
-    CKN(launch_wgrad(P, 1, n->cout[0], B, n->x0, cur, n->part, n->grad + n->off[0], n->s));
+    CKN(launch_wgrad(P, 1, n->cout[0], B, n->x0, cur, n->part, n->grad + n->off[0], n->tc_err, n->s));
     return PTY_OK;
 }
 

@@ -31,7 +31,11 @@ cudaError_t launch_conv_bwd(int P, int cin, int B, const float *in, const __nv_b
 bool conv_tc_supported(int P, int cin);
 cudaError_t launch_conv_tc(int P, int B, bool bwd, const float *in, const __nv_bfloat16 *w, const float *bias,
                            const float *zprev, float *z, float *a, int *err, cudaStream_t s);
-// Process-wide switch of the tensor-core form (tests compare both forms); on by default.
+// The tensor-core form of a hidden layer's weight gradient (cnn_tc.cu): the per-CTA partials
+// of launch_wgrad for cin = cout = kC at P = 128, 256.
+bool wgrad_tc_supported(int P, int cin, int cout);
+cudaError_t launch_wgrad_tc(int P, int B, const float *a, const float *dz, float *part, int *err, cudaStream_t s);
+// Process-wide switch of the tensor-core forms (tests compare both forms); on by default.
 void set_conv_tc(bool on);
 bool conv_tc_on();
 // Output layer: z [B][2][P][P] = conv(in [B][kC][P][P]; w [2][kC][9]) + bias.
@@ -49,7 +53,7 @@ cudaError_t launch_loss_finalize(const double *part, int n, double inv_norm, dou
 // grad ([cout][cin][9] then [cout]).  part must hold wgrad_parts(P, B) * (cout*cin*9 + cout).
 int wgrad_blocks(int P, int B);
 cudaError_t launch_wgrad(int P, int cin, int cout, int B, const float *a, const float *dz, float *part,
-                         float *grad, cudaStream_t s);
+                         float *grad, int *err, cudaStream_t s);
 // Adam on n masters, then the BF16 copies of every layer's weights are refreshed.
 cudaError_t launch_adam(float *master, float *m, float *v, const float *g, int64_t n, float lr, float b1, float b2,
                         float eps, float bc1, float bc2, cudaStream_t s);

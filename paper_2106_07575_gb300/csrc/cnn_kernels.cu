@@ -678,9 +678,16 @@ cudaError_t launch_loss_finalize(const double *part, int n, double inv_norm, dou
 int wgrad_blocks(int P, int B) { return B * (P / kWgRB); }
 
 cudaError_t launch_wgrad(int P, int cin, int cout, int B, const float *a, const float *dz, float *part, float *grad,
-                         cudaStream_t s)
+                         int *err, cudaStream_t s)
 {
     cudaError_t e;
+    if (err && conv_tc_on() && wgrad_tc_supported(P, cin, cout)) {
+        e = launch_wgrad_tc(P, B, a, dz, part, err, s);
+        if (e != cudaSuccess) return e;
+        const int npl = cout * cin * 9 + cout;
+        k_wreduce<<<(npl + NT - 1) / NT, NT, 0, s>>>(part, wgrad_blocks(P, B), npl, grad);
+        return cudaGetLastError();
+    }
     switch (P) {
     case 64: e = wgrad_dispatch<64>(cin, cout, B, a, dz, part, s); break;
     case 128: e = wgrad_dispatch<128>(cin, cout, B, a, dz, part, s); break;

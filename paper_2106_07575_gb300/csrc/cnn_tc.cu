@@ -251,5 +251,223 @@ cudaError_t launch_conv_tc(int P, int B, bool bwd, const float *in, const __nv_b
     return cudaErrorInvalidValue;
 }
 
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Weight gradient of a hidden layer on the tensor cores:
+//   dW[co][ci][dy][dx] = sum over pixels of dz[co][y][x] a[ci][y + dy - 1][x + dx - 1]
+//                      = sum over (y, x') of a[ci][y + dy - 1][x'] dz[co][y][x' - dx + 1],
+//   db[co] = sum over pixels of dz[co][y][x],
+// one CTA per band of kWgTcRB rows of one image, written as the per-CTA partials that
+// launch_wgrad's fixed-order reduction adds (the layout of the CUDA-core kernel).  For each
+// 32-pixel chunk x' of a row the GEMM is D[m][n] += A[m][x'] Z[n][x'] with m = (dy, ci)
+// (96 rows, padded to M = 128), n = (dx, co) (N = 96) and K = the chunk's pixels: the row
+// shift dy is a choice of staged row and the column shift dx is carried by three shifted
+// copies of the dz row (a canonical K-major tile cannot start one element into a core
+// matrix), so one MMA per K-step and product covers all nine taps.  Padding row 96 of A
+// holds ones, so D[96][(dx = 1, co)] is db.  Activations and dz are both split into three
+// BF16 parts and the six products above 2^-24 are accumulated, smallest first: FP32-level
+// products, FP32 sums.
+constexpr int kWgTcRB = 16;                  // rows per CTA (the CUDA-core kernel's bands)
+constexpr int kWgKC = 32;                    // pixels per chunk (K)
+constexpr int kWgMG = 16;                    // A M-groups of 8 rows: 12 used (3 dy x 4 ci groups), 4 padding
+constexpr int kWgNG = 12;                    // Z N-groups of 8 rows: 3 dx x 4 co groups
+constexpr int kWgCore = 128;                 // one core matrix (8 rows x 16 bytes)
+constexpr int kWgGBytes = (kWgKC / 8) * kWgCore;   // one M- or N-group: 4 K-groups
+constexpr int kWgAPart = kWgMG * kWgGBytes;        // one BF16 part of A
+constexpr int kWgBPart = kWgNG * kWgGBytes;        // one BF16 part of Z
+constexpr int kWgN = 3 * kC;                       // N of the MMAs
+constexpr int kWgALd = kWgKC + 1;                  // raw activation row stride (floats, odd)
+constexpr int kWgZLd = kWgKC + 3;                  // raw dz row stride: pixels x0 - 1 .. x0 + 32, odd
+constexpr int kWgRawBytes = (3 * kC * kWgALd + kC * kWgZLd) * 4;
+constexpr size_t kWgSmem = 3 * (size_t)kWgAPart + 3 * (size_t)kWgBPart + kWgRawBytes + 64;
+
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 96.
+__host__ __device__ constexpr uint32_t wgrad_idesc()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kWgN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void split3(float a, uint16_t &h, uint16_t &m, uint16_t &l)
+{
+    h = to_half_bits<true>(a);
+    const float r1 = a - from_half_bits<true>(h);
+    m = to_half_bits<true>(r1);
+    l = to_half_bits<true>(r1 - from_half_bits<true>(m));
+}
+
+// Eight consecutive values as three 16-byte BF16 rows (parts hi, mid, lo) at dst, dst + stride,
+// dst + 2 stride.
+__device__ __forceinline__ void store_split8(uint8_t *dst, size_t stride, const float (&v)[8])
+{
+    uint16_t h[8], m[8], l[8];
+#pragma unroll
+    for (int j = 0; j < 8; j++) split3(v[j], h[j], m[j], l[j]);
+    *(uint4 *)dst = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+    *(uint4 *)(dst + stride) = make_uint4(pack2(m[0], m[1]), pack2(m[2], m[3]), pack2(m[4], m[5]), pack2(m[6], m[7]));
+    *(uint4 *)(dst + 2 * stride) =
+        make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTcNT, 3)
+    k_wgrad_tc(const float *__restrict__ a, const float *__restrict__ dz, float *__restrict__ part, int *__restrict__ err,
+               long long spin_limit)
+{
+    static_assert(P % kWgTcRB == 0 && P % kWgKC == 0, "bands and chunks");
+    constexpr int NPL = kC * kC * 9 + kC;
+    extern __shared__ __align__(128) uint8_t sm[];
+    uint8_t *As = sm, *Zs = sm + 3 * (size_t)kWgAPart;
+    float *Ra = (float *)(Zs + 3 * (size_t)kWgBPart);  // raw activation rows [dy][ci][kWgALd]
+    float *Rz = Ra + 3 * kC * kWgALd;                    // raw dz row [co][kWgZLd]
+    uint64_t *done = (uint64_t *)((uint8_t *)Ra + kWgRawBytes);
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int bands = P / kWgTcRB;
+    const int b = blockIdx.x / bands, yb = (blockIdx.x % bands) * kWgTcRB;
+
+    if (tid == 0) {
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tmem_alloc(tmem_slot, 128);
+    // padding M-groups 12..15 of the three parts of A: zero, except row 96 (M-group 12, row 0
+    // of each core matrix) of the high part: ones (BF16 1.0 = 0x3f80)
+    for (int e = tid; e < 3 * 4 * (kWgGBytes / 16); e += kTcNT) {
+        const int c16 = e % (kWgGBytes / 16), t = e / (kWgGBytes / 16);
+        const int g = 12 + t % 4, pt = t / 4;
+        const bool ones = pt == 0 && g == 12 && (c16 % 8) == 0;
+        const uint32_t v = ones ? 0x3f803f80u : 0u;
+        *(uint4 *)(As + (size_t)pt * kWgAPart + (size_t)g * kWgGBytes + c16 * 16) = make_uint4(v, v, v, v);
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = wgrad_idesc();
+
+    // Tiles (x0, y) in chunk-major order: down the band within one 32-pixel column chunk, so
+    // the raw activation rows form a three-row ring (slot (yy + 3) % 3) and a tile loads only
+    // its new row y + 1 and its dz row.  The next tile's raw rows are loaded while this tile's
+    // MMAs run (they read only the BF16 tiles, not the raw rows).
+    constexpr int NT = (P / kWgKC) * kWgTcRB;
+    auto load_raw = [&](int t, bool all_rows) {
+        const int x0 = (t / kWgTcRB) * kWgKC, y = yb + t % kWgTcRB;
+        const int nrow = all_rows ? 3 : 1;
+        for (int e = tid; e < nrow * kC * kWgKC; e += kTcNT) {
+            const int px = e % kWgKC, ci = (e / kWgKC) % kC, r = e / (kWgKC * kC);
+            const int yy = all_rows ? y - 1 + r : y + 1;
+            Ra[(((yy + 3) % 3) * kC + ci) * kWgALd + px] =
+                (yy >= 0 && yy < P) ? __ldg(a + (((size_t)b * kC + ci) * P + yy) * P + x0 + px) : 0.0f;
+        }
+        for (int e = tid; e < kC * (kWgKC + 2); e += kTcNT) {
+            const int q = e % (kWgKC + 2), co = e / (kWgKC + 2), x = x0 - 1 + q;
+            Rz[co * kWgZLd + q] = (x >= 0 && x < P) ? __ldg(dz + (((size_t)b * kC + co) * P + y) * P + x) : 0.0f;
+        }
+    };
+    load_raw(0, true);
+    __syncthreads();
+    bool started = false, ok = true;
+#pragma unroll 1
+    for (int it = 0; it < NT; it++) {
+        const int x0 = (it / kWgTcRB) * kWgKC, y = yb + it % kWgTcRB;
+        (void)x0;
+        // ---- A: task (dy, ci, kg): pixels x0 + 8 kg .. + 7 of channel ci in row y + dy - 1
+        // -> row ci % 8 of core matrix (M-group dy * 4 + ci / 8, K-group kg)
+        for (int t = tid; t < 3 * kC * (kWgKC / 8); t += kTcNT) {
+            const int ci = t % kC, kg = (t / kC) % (kWgKC / 8), dy = t / (kC * (kWgKC / 8));
+            const float *r = Ra + (((y + dy + 2) % 3) * kC + ci) * kWgALd + 8 * kg;  // slot of row y + dy - 1
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) v[j] = r[j];
+            store_split8(As + (size_t)(dy * 4 + ci / 8) * kWgGBytes + kg * kWgCore + (ci % 8) * 16, kWgAPart, v);
+        }
+        // ---- Z: task (dx, co, kg): dz[co] at pixels x' - dx + 1, x' = x0 + 8 kg .. + 7
+        // -> row co % 8 of core matrix (N-group dx * 4 + co / 8, K-group kg)
+        for (int t = tid; t < 3 * kC * (kWgKC / 8); t += kTcNT) {
+            const int co = t % kC, kg = (t / kC) % (kWgKC / 8), dx = t / (kC * (kWgKC / 8));
+            const float *r = Rz + co * kWgZLd + 8 * kg + 2 - dx;  // raw index of pixel x' - dx + 1
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; j++) v[j] = r[j];
+            store_split8(Zs + (size_t)(dx * 4 + co / 8) * kWgGBytes + kg * kWgCore + (co % 8) * 16, kWgBPart, v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        if (tid == 0) {
+            const uint32_t a0 = smem_u32(As), z0 = smem_u32(Zs);
+            // (A part, Z part), smallest product first: lo*hi, mid*mid, hi*lo, mid*hi, hi*mid, hi*hi
+            const int pa[6] = {2, 1, 0, 1, 0, 0}, pz[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll 1
+            for (int ks = 0; ks < kWgKC / 16; ks++)
+#pragma unroll
+                for (int q = 0; q < 6; q++) {
+                    const uint64_t ad =
+                        umma_desc(a0 + (uint32_t)(pa[q] * kWgAPart + 2 * ks * kWgCore), kWgCore, kWgGBytes);
+                    const uint64_t zd =
+                        umma_desc(z0 + (uint32_t)(pz[q] * kWgBPart + 2 * ks * kWgCore), kWgCore, kWgGBytes);
+                    umma_f16(tmem, ad, zd, idesc, started ? 1u : 0u);
+                    started = true;
+                }
+            umma_commit(done);
+        }
+        // the next tile's raw rows, while the MMAs run (the split above has read the ring)
+        if (it + 1 < NT) load_raw(it + 1, (it + 1) % kWgTcRB == 0);
+        ok = mbar_wait(done, (uint32_t)(it & 1), spin_limit);
+        ok = __syncthreads_and(ok) != 0;  // the MMAs have read the tiles; the raw rows are stored
+        if (!ok) {
+            if (tid == 0) atomicOr(err, 1);
+            mbar_wait(done, (uint32_t)(it & 1));
+            break;
+        }
+    }
+    if (ok) {
+        // warps 0..3: TMEM lane quarter w = rows m = 32 w + lane (m = dy * 32 + ci; m = 96: db),
+        // columns 32 dx + co
+        tmem_fence_after_sync();
+        if (warp < 4) {
+            const int m = 32 * warp + lane;
+            float *pb = part + (size_t)blockIdx.x * NPL;
+#pragma unroll 1
+            for (int dx = 0; dx < 3; dx++) {
+                float v[32];
+                tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * dx), v);
+                if (m < 96) {
+                    const int dy = m / kC, ci = m % kC;
+#pragma unroll
+                    for (int co = 0; co < kC; co++) pb[((size_t)co * kC + ci) * 9 + dy * 3 + dx] = v[co];
+                } else if (m == 96 && dx == 1) {
+#pragma unroll
+                    for (int co = 0; co < kC; co++) pb[kC * kC * 9 + co] = v[co];
+                }
+            }
+        }
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+}  // namespace
+
+bool wgrad_tc_supported(int P, int cin, int cout) { return cin == kC && cout == kC && (P == 128 || P == 256); }
+
+cudaError_t launch_wgrad_tc(int P, int B, const float *a, const float *dz, float *part, int *err, cudaStream_t s)
+{
+    if (!err || B < 1) return cudaErrorInvalidValue;
+    auto run = [&](auto kern) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
+        if (e != cudaSuccess) return e;
+        kern<<<B * (P / kWgTcRB), kTcNT, kWgSmem, s>>>(a, dz, part, err, tc_wait_limit());
+        return cudaGetLastError();
+    };
+    if (P == 128) return run(k_wgrad_tc<128>);
+    if (P == 256) return run(k_wgrad_tc<256>);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace cnn
 }  // namespace pty

@@ -34,6 +34,8 @@ cudaError_t launch_conv_tc(int P, int B, bool bwd, const float *in, const __nv_b
 // The tensor-core form of a hidden layer's weight gradient (cnn_tc.cu): the per-CTA partials
 // of launch_wgrad for cin = cout = kC at P = 128, 256.
 bool wgrad_tc_supported(int P, int cin, int cout);
+// Number of partials launch_wgrad_tc writes (at most wgrad_blocks(P, B)).
+int wgrad_tc_blocks(int P, int B);
 cudaError_t launch_wgrad_tc(int P, int B, const float *a, const float *dz, float *part, int *err, cudaStream_t s);
 // Process-wide switch of the tensor-core forms (tests compare both forms); on by default.
 void set_conv_tc(bool on);

@@ -383,14 +383,30 @@ __global__ void __launch_bounds__(NT) k_wgrad(const float *__restrict__ a, const
     }
 }
 
-__global__ void k_wreduce(const float *__restrict__ part, int nblk, int npl, float *__restrict__ grad)
+// grad[p] = sum over k of part[k][p] for 32 consecutive p per block: warp w adds the
+// partials k = w, w + NW, ... (coalesced rows of 32), then warp 0 adds the NW warp sums in
+// order w = 0 .. NW - 1.  Float-float throughout (FP64 runs at 1/64 of the FP32 rate); the
+// order depends only on nblk.
+__global__ void __launch_bounds__(NT) k_wreduce(const float *__restrict__ part, int nblk, int npl,
+                                                float *__restrict__ grad)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npl) return;
-    float2 s = make_float2(0.f, 0.f);  // float-float: FP64 runs at 1/64 of the FP32 rate
-#pragma unroll 8
-    for (int k = 0; k < nblk; k++) s = ff_add_f(s, __ldg(part + (size_t)k * npl + p));
-    grad[p] = s.x + s.y;
+    constexpr int NW = NT / 32;
+    __shared__ float2 ws[NW][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int p = blockIdx.x * 32 + lane;
+    float2 s = make_float2(0.f, 0.f);
+    if (p < npl) {
+#pragma unroll 4
+        for (int k = w; k < nblk; k += NW) s = ff_add_f(s, __ldg(part + (size_t)k * npl + p));
+    }
+    ws[w][lane] = s;
+    __syncthreads();
+    if (w == 0 && p < npl) {
+        float2 t = ws[0][lane];
+#pragma unroll
+        for (int v = 1; v < NW; v++) t = ff_add(t, ws[v][lane]);
+        grad[p] = t.x + t.y;
+    }
 }
 
 // ---- Adam and the BF16 working copies ----
@@ -685,7 +701,7 @@ cudaError_t launch_wgrad(int P, int cin, int cout, int B, const float *a, const 
         e = launch_wgrad_tc(P, B, a, dz, part, err, s);
         if (e != cudaSuccess) return e;
         const int npl = cout * cin * 9 + cout;
-        k_wreduce<<<(npl + NT - 1) / NT, NT, 0, s>>>(part, wgrad_blocks(P, B), npl, grad);
+        k_wreduce<<<(npl + 31) / 32, NT, 0, s>>>(part, wgrad_tc_blocks(P, B), npl, grad);
         return cudaGetLastError();
     }
     switch (P) {
@@ -696,7 +712,7 @@ cudaError_t launch_wgrad(int P, int cin, int cout, int B, const float *a, const 
     }
     if (e != cudaSuccess) return e;
     const int npl = cout * cin * 9 + cout;
-    k_wreduce<<<(npl + NT - 1) / NT, NT, 0, s>>>(part, wgrad_blocks(P, B), npl, grad);
+    k_wreduce<<<(npl + 31) / 32, NT, 0, s>>>(part, wgrad_blocks(P, B), npl, grad);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 // memory and returns.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "cnn_internal.h"
@@ -259,9 +260,10 @@ namespace {
 //   dW[co][ci][dy][dx] = sum over pixels of dz[co][y][x] a[ci][y + dy - 1][x + dx - 1]
 //                      = sum over (y, x') of a[ci][y + dy - 1][x'] dz[co][y][x' - dx + 1],
 //   db[co] = sum over pixels of dz[co][y][x],
-// one CTA per band of kWgTcRB rows of one image, written as the per-CTA partials that
-// launch_wgrad's fixed-order reduction adds (the layout of the CUDA-core kernel).  For each
-// 32-pixel chunk x' of a row the GEMM is D[m][n] += A[m][x'] Z[n][x'] with m = (dy, ci)
+// written as per-CTA partials that launch_wgrad's fixed-order reduction adds (the layout of
+// the CUDA-core kernel).  The work is B * (P / 32) * P units (image, 32-pixel column chunk,
+// row) in that order, cut into wgrad_tc_blocks(P, B) contiguous ranges, one per CTA: one
+// wave of CTAs with equal shares.  For each unit (chunk x', row y) the GEMM is D[m][n] += A[m][x'] Z[n][x'] with m = (dy, ci)
 // (96 rows, padded to M = 128), n = (dx, co) (N = 96) and K = the chunk's pixels: the row
 // shift dy is a choice of staged row and the column shift dx is carried by three shifted
 // copies of the dz row (a canonical K-major tile cannot start one element into a core
@@ -269,7 +271,7 @@ namespace {
 // holds ones, so D[96][(dx = 1, co)] is db.  Activations and dz are both split into three
 // BF16 parts and the six products above 2^-24 are accumulated, smallest first: FP32-level
 // products, FP32 sums.
-constexpr int kWgTcRB = 16;                  // rows per CTA (the CUDA-core kernel's bands)
+constexpr int kWgTcRB = 16;                  // rows per CTA of the CUDA-core kernel (its partial count)
 constexpr int kWgKC = 32;                    // pixels per chunk (K)
 constexpr int kWgMG = 16;                    // A M-groups of 8 rows: 12 used (3 dy x 4 ci groups), 4 padding
 constexpr int kWgNG = 12;                    // Z N-groups of 8 rows: 3 dx x 4 co groups
@@ -280,7 +282,9 @@ constexpr int kWgBPart = kWgNG * kWgGBytes;        // one BF16 part of Z
 constexpr int kWgN = 3 * kC;                       // N of the MMAs
 constexpr int kWgALd = kWgKC + 1;                  // raw activation row stride (floats, odd)
 constexpr int kWgZLd = kWgKC + 3;                  // raw dz row stride: pixels x0 - 1 .. x0 + 32, odd
-constexpr int kWgRawBytes = (3 * kC * kWgALd + kC * kWgZLd) * 4;
+constexpr int kWgRing = 4;                        // raw activation rows held (a tile reads 3)
+constexpr int kWgRawBytes = (kWgRing * kC * kWgALd + 2 * kC * kWgZLd) * 4;
+constexpr int kWgGrid = 3 * 152;                   // CTAs of one wave: 3 resident per SM, 152 SMs
 constexpr size_t kWgSmem = 3 * (size_t)kWgAPart + 3 * (size_t)kWgBPart + kWgRawBytes + 64;
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 96.
@@ -310,22 +314,31 @@ __device__ __forceinline__ void store_split8(uint8_t *dst, size_t stride, const 
         make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
 }
 
+// Four bytes global -> shared without a register round trip; src_ok = false writes zero.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool src_ok)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_ok ? 4 : 0)
+                 : "memory");
+}
+
 template <int P>
 __global__ void __launch_bounds__(kTcNT, 3)
     k_wgrad_tc(const float *__restrict__ a, const float *__restrict__ dz, float *__restrict__ part, int *__restrict__ err,
-               long long spin_limit)
+               long long spin_limit, int nunits)
 {
-    static_assert(P % kWgTcRB == 0 && P % kWgKC == 0, "bands and chunks");
+    static_assert(P % kWgKC == 0, "chunks");
     constexpr int NPL = kC * kC * 9 + kC;
+    constexpr int NC = P / kWgKC;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *As = sm, *Zs = sm + 3 * (size_t)kWgAPart;
-    float *Ra = (float *)(Zs + 3 * (size_t)kWgBPart);  // raw activation rows [dy][ci][kWgALd]
-    float *Rz = Ra + 3 * kC * kWgALd;                    // raw dz row [co][kWgZLd]
+    float *Ra = (float *)(Zs + 3 * (size_t)kWgBPart);  // raw activation rows [kWgRing][ci][kWgALd]
+    float *Rz = Ra + kWgRing * kC * kWgALd;              // two raw dz rows [2][co][kWgZLd]
     uint64_t *done = (uint64_t *)((uint8_t *)Ra + kWgRawBytes);
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int bands = P / kWgTcRB;
-    const int b = blockIdx.x / bands, yb = (blockIdx.x % bands) * kWgTcRB;
+    // this CTA's units [u0, u1); the host keeps every range non-empty
+    const int u0 = (int)((long long)blockIdx.x * nunits / gridDim.x);
+    const int u1 = (int)((long long)(blockIdx.x + 1) * nunits / gridDim.x);
 
     if (tid == 0) {
         mbar_init(done, 1);
@@ -347,37 +360,43 @@ __global__ void __launch_bounds__(kTcNT, 3)
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = wgrad_idesc();
 
-    // Tiles (x0, y) in chunk-major order: down the band within one 32-pixel column chunk, so
-    // the raw activation rows form a three-row ring (slot (yy + 3) % 3) and a tile loads only
-    // its new row y + 1 and its dz row.  The next tile's raw rows are loaded while this tile's
-    // MMAs run (they read only the BF16 tiles, not the raw rows).
-    constexpr int NT = (P / kWgKC) * kWgTcRB;
-    auto load_raw = [&](int t, bool all_rows) {
-        const int x0 = (t / kWgTcRB) * kWgKC, y = yb + t % kWgTcRB;
-        const int nrow = all_rows ? 3 : 1;
+    // Unit u = (image b, chunk x0, row y).  The i-th unit of the CTA reads its rows y - 1 + r
+    // (r = 0, 1, 2) from ring slots (i + r) % kWgRing and its dz row from buffer u & 1.  When
+    // unit u + 1 continues the column (same chunk, row y + 1) it needs one new row, r = 2, in
+    // slot (i + 3) % kWgRing, which unit u does not read: that copy and its dz row are issued
+    // before unit u's split.  A unit that starts a column (y = 0) loads all three rows after
+    // unit u's split has read the ring.
+    auto load_rows = [&](int u, int r0, int nrow, int i) {
+        const int b = u / (NC * P), x0 = ((u / P) % NC) * kWgKC, y = u % P;
         for (int e = tid; e < nrow * kC * kWgKC; e += kTcNT) {
-            const int px = e % kWgKC, ci = (e / kWgKC) % kC, r = e / (kWgKC * kC);
-            const int yy = all_rows ? y - 1 + r : y + 1;
-            Ra[(((yy + 3) % 3) * kC + ci) * kWgALd + px] =
-                (yy >= 0 && yy < P) ? __ldg(a + (((size_t)b * kC + ci) * P + yy) * P + x0 + px) : 0.0f;
+            const int px = e % kWgKC, ci = (e / kWgKC) % kC, r = r0 + e / (kWgKC * kC);
+            const int yy = y - 1 + r;
+            const bool in = yy >= 0 && yy < P;
+            cp_async4(Ra + (((i + r) % kWgRing) * kC + ci) * kWgALd + px,
+                      in ? a + (((size_t)b * kC + ci) * P + yy) * P + x0 + px : a, in);
         }
+        float *z = Rz + (u & 1) * kC * kWgZLd;
         for (int e = tid; e < kC * (kWgKC + 2); e += kTcNT) {
             const int q = e % (kWgKC + 2), co = e / (kWgKC + 2), x = x0 - 1 + q;
-            Rz[co * kWgZLd + q] = (x >= 0 && x < P) ? __ldg(dz + (((size_t)b * kC + co) * P + y) * P + x) : 0.0f;
+            const bool in = x >= 0 && x < P;
+            cp_async4(z + co * kWgZLd + q, in ? dz + (((size_t)b * kC + co) * P + y) * P + x : dz, in);
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    load_raw(0, true);
+    load_rows(u0, 0, 3, 0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     bool started = false, ok = true;
 #pragma unroll 1
-    for (int it = 0; it < NT; it++) {
-        const int x0 = (it / kWgTcRB) * kWgKC, y = yb + it % kWgTcRB;
-        (void)x0;
+    for (int u = u0; u < u1; u++) {
+        const int i = u - u0;
+        const bool next = u + 1 < u1, next_starts = next && (u + 1) % P == 0;
+        if (next && !next_starts) load_rows(u + 1, 2, 1, i + 1);
         // ---- A: task (dy, ci, kg): pixels x0 + 8 kg .. + 7 of channel ci in row y + dy - 1
         // -> row ci % 8 of core matrix (M-group dy * 4 + ci / 8, K-group kg)
         for (int t = tid; t < 3 * kC * (kWgKC / 8); t += kTcNT) {
             const int ci = t % kC, kg = (t / kC) % (kWgKC / 8), dy = t / (kC * (kWgKC / 8));
-            const float *r = Ra + (((y + dy + 2) % 3) * kC + ci) * kWgALd + 8 * kg;  // slot of row y + dy - 1
+            const float *r = Ra + (((i + dy) % kWgRing) * kC + ci) * kWgALd + 8 * kg;
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; j++) v[j] = r[j];
@@ -385,9 +404,10 @@ __global__ void __launch_bounds__(kTcNT, 3)
         }
         // ---- Z: task (dx, co, kg): dz[co] at pixels x' - dx + 1, x' = x0 + 8 kg .. + 7
         // -> row co % 8 of core matrix (N-group dx * 4 + co / 8, K-group kg)
+        const float *zr = Rz + (u & 1) * kC * kWgZLd;
         for (int t = tid; t < 3 * kC * (kWgKC / 8); t += kTcNT) {
             const int co = t % kC, kg = (t / kC) % (kWgKC / 8), dx = t / (kC * (kWgKC / 8));
-            const float *r = Rz + co * kWgZLd + 8 * kg + 2 - dx;  // raw index of pixel x' - dx + 1
+            const float *r = zr + co * kWgZLd + 8 * kg + 2 - dx;  // raw index of pixel x' - dx + 1
             float v[8];
 #pragma unroll
             for (int j = 0; j < 8; j++) v[j] = r[j];
@@ -414,13 +434,13 @@ __global__ void __launch_bounds__(kTcNT, 3)
                 }
             umma_commit(done);
         }
-        // the next tile's raw rows, while the MMAs run (the split above has read the ring)
-        if (it + 1 < NT) load_raw(it + 1, (it + 1) % kWgTcRB == 0);
-        ok = mbar_wait(done, (uint32_t)(it & 1), spin_limit);
-        ok = __syncthreads_and(ok) != 0;  // the MMAs have read the tiles; the raw rows are stored
+        if (next_starts) load_rows(u + 1, 0, 3, i + 1);  // the split above has read the ring
+        ok = mbar_wait(done, (uint32_t)(i & 1), spin_limit);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        ok = __syncthreads_and(ok) != 0;  // the MMAs have read the tiles; the next rows have landed
         if (!ok) {
             if (tid == 0) atomicOr(err, 1);
-            mbar_wait(done, (uint32_t)(it & 1));
+            mbar_wait(done, (uint32_t)(i & 1));
             break;
         }
     }
@@ -455,13 +475,18 @@ __global__ void __launch_bounds__(kTcNT, 3)
 
 bool wgrad_tc_supported(int P, int cin, int cout) { return cin == kC && cout == kC && (P == 128 || P == 256); }
 
+// One wave (at most kWgGrid CTAs) and never more partials than the CUDA-core kernel writes
+// (B * P / 16, which the caller's partial buffer holds); every CTA gets at least P / 2 units.
+int wgrad_tc_blocks(int P, int B) { return std::min(kWgGrid, B * (P / kWgTcRB)); }
+
 cudaError_t launch_wgrad_tc(int P, int B, const float *a, const float *dz, float *part, int *err, cudaStream_t s)
 {
     if (!err || B < 1) return cudaErrorInvalidValue;
+    const int nunits = B * (P / kWgKC) * P;
     auto run = [&](auto kern) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem);
         if (e != cudaSuccess) return e;
-        kern<<<B * (P / kWgTcRB), kTcNT, kWgSmem, s>>>(a, dz, part, err, tc_wait_limit());
+        kern<<<wgrad_tc_blocks(P, B), kTcNT, kWgSmem, s>>>(a, dz, part, err, tc_wait_limit(), nunits);
         return cudaGetLastError();
     };
     if (P == 128) return run(k_wgrad_tc<128>);

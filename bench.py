@@ -47,6 +47,8 @@ WORKLOADS = {
                 "real jitter +-2, one Fourier-shifted probe per position), peak 1e5 counts",
     "gap": "ml-cg 1024x1024 object, 128x128 probe, 3600 positions (60x60 raster, step 14, +-2), peak 1e5 counts, "
            "test seed 5: time to relative objective gap 1e-3 per form",
+    "train": "learned start: 6-layer 3x3 CNN (1-32-32-32-32-32-2 channels), 128x128 patterns, batch 64, "
+             "2048 forward-model pairs (Poisson counts of |F[p psi]|^2 of ellipse phantoms, peak 1e5 probe)",
     "views": "batched ml-cg: {n} views of 512^2-2048^2 (multiples of 128), 128x128 shared probe, rasters at 16 px "
              "(+-2), peak 1e5 counts, {k} positions in total",
 }
@@ -120,7 +122,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ls-window", type=int, default=None)
     ap.add_argument("--tile-config", type=int, default=None)
-    ap.add_argument("--workload", choices=["production", "spiral", "small", "subpixel", "views", "gap"], default="production")
+    ap.add_argument("--workload", choices=["production", "spiral", "small", "subpixel", "views", "gap", "train"],
+                    default="production")
     ap.add_argument("--pairs", type=int, default=200000, help="gap workload: training pairs of the learned start")
     ap.add_argument("--epochs", type=float, default=1.0, help="gap workload: passes over the training pairs")
     ap.add_argument("--views", type=int, default=64)
@@ -396,6 +399,53 @@ def run_gap(args, torch, pty, synth):
         "forms": forms, "clocks": clocks}), flush=True)
 
 
+def run_train(args, torch, pty, synth):
+    """CNN training throughput (pairs/s) of the learned start through pty_cnn_train: K steps of
+    batch 64 (forward, loss, backward, Adam) timed with CUDA events on the library's stream
+    after W warm-up steps; hidden layers on the tensor cores, and the same steps with them
+    switched off for comparison."""
+    from paper_2106_07575_gb300 import learned
+
+    prob = synth.production_problem(seed=5)
+    n_pairs, B, L = 2048, 64, 6
+    d_tr, t_tr = learned.training_pairs(prob.probe, n_pairs, per_phantom=n_pairs, phantoms=("ellipse",))
+    stream = torch.cuda.current_stream()
+    net = pty.Network(prob.P, 32, L, max_batch=B, stream=stream.cuda_stream)
+    net.init_params(7)
+    net.set_loss_weight((np.abs(prob.probe.astype(np.complex128)) ** 2).astype(np.float32))
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    rates = {}
+    for name, tc in (("cuda cores", 0), ("tensor cores", 1)):
+        prev = pty.pty_selftest_cnn_tc(tc)
+        net.train(d_tr, t_tr, B, max(args.warmup, 3), seed=1)
+        torch.cuda.synchronize()
+        if tc:  # clocks sampled over preroll steps (args.preroll_s seconds) and the timed steps
+            clk.start()
+            t_load0 = time.time()
+            while time.time() - t_load0 < args.preroll_s:
+                net.train(d_tr, t_tr, B, 20, seed=3)
+                torch.cuda.synchronize()
+        tw0 = time.time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        losses = net.train(d_tr, t_tr, B, args.steps, seed=2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if tc:
+            clocks = clk.stop(load=(t_load0, time.time()), timed=(tw0, time.time()))
+        pty.pty_selftest_cnn_tc(prev)
+        ms = e0.elapsed_time(e1)
+        rates[name] = {"pairs_per_s": args.steps * B / (ms / 1e3), "ms_per_step": ms / args.steps,
+                       "loss_last": float(losses[-1])}
+    tcr = rates["tensor cores"]
+    print(json.dumps({
+        "metric": "CNN training pairs per second", "value": tcr["pairs_per_s"], "unit": "pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": tcr["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (split bf16 tensor cores)",
+        "data": "synthetic", "config": {"workload": WORKLOADS["train"], "l2": "inputs larger than L2 per step"},
+        "forms": rates, "gpu_launches": (5 * L + 3) * args.steps, "clocks": clocks}), flush=True)
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -412,6 +462,9 @@ def main():
     torch.cuda.set_device(local)
     if args.workload == "views":
         run_views(args, torch, pty, synth)
+        return
+    if args.workload == "train":
+        run_train(args, torch, pty, synth)
         return
     if args.workload == "gap":
         run_gap(args, torch, pty, synth)

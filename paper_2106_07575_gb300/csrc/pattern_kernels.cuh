@@ -418,6 +418,47 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
 // summed over positions is D psi (D the illumination map), added by the scatter-add.  The
 // objective keeps only its entry terms here; sum |u|^2 = P^2 sum D |psi|^2 comes from the
 // scatter-add too.  Runs only for views whose st->lin is set.
+// One entry of the GRAD pass: slot, count, u and v; ok = false past the pattern's end.
+struct EntryIn {
+    int s = 0;
+    float d = 0.f;
+    float2 u = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+    bool ok = false;
+    __device__ __forceinline__ void load(const PatternArgs &a, long long e, long long e1)
+    {
+        ok = e < e1;
+        if (ok) {
+            s = __ldg(a.nz_slot + e);
+            d = __ldg(a.nz_d + e);
+            u = a.nz_u[e];
+            v = __ldg(a.nz_v + e);
+        }
+    }
+};
+
+// L2 prefetch of the entry arrays of pattern j (all its column chunks): one 128-byte line per
+// thread and array, the addresses those of entries of the pattern (the last one included), so
+// every address lies inside the arrays.  grad: also the counts and v, which only the GRAD pass
+// reads.  Issued at the start of a pattern for the CTA's next one, the entries then arrive
+// from L2 instead of HBM.
+template <int NT>
+__device__ __forceinline__ void prefetch_entries(const PatternArgs &a, int j, bool grad)
+{
+    const long long e0 = a.nz_off[(size_t)j * a.nzc], e1 = a.nz_off[(size_t)(j + 1) * a.nzc];
+    if (e1 <= e0) return;
+    const long long n = e1 - e0;
+    const int ls = (int)((n + 63) / 64) + 1, ld = (int)((n + 31) / 32) + 1, lu = (int)((n + 15) / 16) + 1;
+    const int tot = ls + lu + (grad ? ld + lu : 0);
+    for (int t = threadIdx.x; t < tot; t += NT) {
+        const void *ptr;
+        if (t < ls) ptr = a.nz_slot + min(e0 + 64LL * t, e1 - 1);
+        else if (t < ls + lu) ptr = a.nz_u + min(e0 + 16LL * (t - ls), e1 - 1);
+        else if (t < ls + lu + ld) ptr = a.nz_d + min(e0 + 32LL * (t - ls - lu), e1 - 1);
+        else ptr = a.nz_v + min(e0 + 16LL * (t - ls - lu - ld), e1 - 1);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+    }
+}
+
 template <int P, int R, int NT>
 __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *__restrict__ w,
                                                  float2 *__restrict__ fpart, float2 *buf, const float2 *tw,
@@ -425,24 +466,35 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
                                                  const ProbeCache<P, NT> *pc)
 {
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
-    // the column slab (permuted spectrum order) starts at zero
-    for (int e = threadIdx.x; e < P * LDB; e += NT) buf[e] = make_float2(0.f, 0.f);
-    __syncthreads();
-    float f = 0.0f;
     const int per = a.nzc / CS;
     const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
-#pragma unroll 2
-    for (long long e = e0 + threadIdx.x; e < e1; e += NT) {
-        const int s = __ldg(a.nz_slot + e);
-        const float dv = __ldg(a.nz_d + e);
-        const float2 u0 = a.nz_u[e], v = __ldg(a.nz_v + e);
-        const float2 u = make_float2(fmaf(gam, v.x, u0.x), fmaf(gam, v.y, u0.y));
+    // the thread's first two entries are loaded before the zeroing, which hides their latency
+    EntryIn first[2];
+#pragma unroll
+    for (int q = 0; q < 2; q++) first[q].load(a, e0 + threadIdx.x + q * NT, e1);
+    // the column slab (permuted spectrum order) starts at zero
+    static_assert((P * LDB) % 2 == 0, "16-byte zeroing");
+    for (int e = threadIdx.x; e < P * LDB / 2; e += NT)
+        reinterpret_cast<float4 *>(buf)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    float f = 0.0f;
+    auto entry = [&](long long e, const EntryIn &x) {
+        const float2 u = make_float2(fmaf(gam, x.v.x, x.u.x), fmaf(gam, x.v.y, x.u.y));
         a.nz_u[e] = u;
         const float den = fmaf(u.x, u.x, u.y * u.y) + a.eps;
         float fe, sc;
-        entry_terms(a.est, dv, den, fe, sc);
+        entry_terms(a.est, x.d, den, fe, sc);
         f += fe;
-        buf[(s / P) * LDB + (s % P - c * R)] = make_float2(u.x * sc, u.y * sc);
+        buf[(x.s / P) * LDB + (x.s % P - c * R)] = make_float2(u.x * sc, u.y * sc);
+    };
+#pragma unroll
+    for (int q = 0; q < 2; q++)
+        if (first[q].ok) entry(e0 + threadIdx.x + q * NT, first[q]);
+#pragma unroll 2
+    for (long long e = e0 + threadIdx.x + 2 * NT; e < e1; e += NT) {
+        EntryIn x;
+        x.load(a, e, e1);
+        entry(e, x);
     }
     if (facc) {  // one view, persistent CTA: the thread's running sum over its patterns
         *facc = ff_add_f(*facc, f);
@@ -488,6 +540,7 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
                 if (st->stalled || !st->lin) continue;
                 gam = (float)st->last_gamma;
             }
+            if (i + (int)gridDim.x < a.K) prefetch_entries<NT>(a, i + gridDim.x, true);
             __syncthreads();  // the previous pattern's reads of buf are done
             grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, gam, i, 0, percta ? &facc : nullptr,
                                        cached ? &pc : nullptr);
@@ -610,6 +663,7 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
         float2 acc = make_float2(0.f, 0.f);
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (!percta && sts[a.pat_view[i]].stalled) continue;  // one view: decided above
+            if (i + (int)gridDim.x < a.K) prefetch_entries<NT>(a, i + gridDim.x, false);
             __syncthreads();  // the previous pattern's reads of buf are done
             const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0, cached ? &pc : nullptr);
             if (percta) acc = ff_add(acc, r);

@@ -223,6 +223,46 @@ __device__ __forceinline__ void rows_fft(float2 *buf, const float2 *tw)
     __syncthreads();
 }
 
+// Warp groups of the single-CTA 128 x 128 tile with 1024 threads.  Both column passes give
+// thread t the column t % 128, so the 8 warps w with w % 4 = g own the columns 32 g .. + 31
+// in both; the row stride step (row_item) gives warp w rows of the block 32 (w / 8) .. + 31,
+// and pass_block_rows_grouped keeps that block.  Between the two passes of one dimension only
+// the 8 warps of a group exchange values, so they meet at a named barrier of 256 threads
+// (ids 1 .. 4) and the groups drift apart; the change of dimension keeps the full barrier.
+// Used by the inverse transform (the GRAD pass); in the forward transform of the LS pass the
+// full barriers measured faster.
+template <int P, int R, int NT>
+__device__ __forceinline__ constexpr bool grouped_tile()
+{
+    return P == 128 && R == P && NT == 1024;
+}
+
+
+__device__ __forceinline__ void group_sync(int g) { asm volatile("bar.sync %0, 256;" ::"r"(g + 1) : "memory"); }
+__device__ __forceinline__ void col_group_sync() { group_sync((threadIdx.x >> 5) & 3); }
+__device__ __forceinline__ void row_group_sync() { group_sync(threadIdx.x >> 8); }
+
+// Block pass over the rows of a single-CTA 128 x 128 tile (row stride P + 1), warp w taking
+// rows 32 (w / 8) + lane and k1 = w % 8 + 8 ii: the rows of its row-step group.  Lanes read
+// 32 consecutive rows at one column: no bank conflicts.
+template <int P, int NT, int SIGN>
+__device__ __forceinline__ void pass_block_rows_grouped(float2 *buf)
+{
+    constexpr int R2 = Tile<P>::R2, LDA = P + 1;
+    static_assert(grouped_tile<P, P, NT>(), "128 x 128 tile, 1024 threads");
+    const int w = threadIdx.x >> 5, row = 32 * (w >> 3) + (threadIdx.x & 31);
+#pragma unroll 1
+    for (int ii = 0; ii < 2; ii++) {
+        float2 *b = buf + row * LDA + R2 * ((w & 7) + 8 * ii);
+        float2 x[R2];
+#pragma unroll
+        for (int j = 0; j < R2; j++) x[j] = b[j];
+        dft_reg<R2, SIGN>(x);
+#pragma unroll
+        for (int j = 0; j < R2; j++) b[j] = x[j];
+    }
+}
+
 // Column passes over the R columns of a column slab; caller syncs before; ends with a barrier.
 template <int P, int R, int NT, int SIGN>
 __device__ __forceinline__ void cols_fft(float2 *buf, const float2 *tw)
@@ -234,7 +274,8 @@ __device__ __forceinline__ void cols_fft(float2 *buf, const float2 *tw)
         pass_block<P, NT, R, 1, LDB, -1>(buf);
     } else {
         pass_block<P, NT, R, 1, LDB, +1>(buf);
-        __syncthreads();
+        if constexpr (grouped_tile<P, R, NT>()) col_group_sync();
+        else __syncthreads();
         pass_stride<P, NT, R, 1, LDB, +1>(buf, tw);
     }
     __syncthreads();
@@ -405,8 +446,13 @@ template <int P, int NT, typename ST>
 __device__ __forceinline__ void fft2_inv_out(float2 *buf, const float2 *tw, const float2 *tw2, ST st)
 {
     cols_fft<P, P, NT, +1>(buf, tw);
-    pass_block<P, NT, P, P + 1, 1, +1>(buf);
-    __syncthreads();
+    if constexpr (grouped_tile<P, P, NT>()) {
+        pass_block_rows_grouped<P, NT, +1>(buf);
+        row_group_sync();
+    } else {
+        pass_block<P, NT, P, P + 1, 1, +1>(buf);
+        __syncthreads();
+    }
     rows_stride_inv_out<P, NT>(buf, tw2, st);
 }
 

@@ -53,9 +53,35 @@ __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V
         for (int l = 0; l < L; l++) acc[l] = 0.0f;
         const int per = a.nzc / cs;
         const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
-        for (long long e = e0 + threadIdx.x; e < e1; e += kNT) {
-            const float dv = __ldg(a.nz_d + e);
-            const float2 u = __ldg(a.nz_u + e), v = __ldg(a.nz_v + e);
+        if (blk + (int)gridDim.x < nunits) {  // the CTA's next unit's entries into L2
+            const int i2 = (blk + gridDim.x) / cs, c2 = (blk + gridDim.x) % cs;
+            const long long f0 = a.nz_off[i2 * a.nzc + c2 * per], f1 = a.nz_off[i2 * a.nzc + (c2 + 1) * per];
+            const int nd = (int)((f1 - f0 + 31) / 32) + 1, nu = (int)((f1 - f0 + 15) / 16) + 1;
+            if (f1 > f0)
+                for (int t = threadIdx.x; t < nd + 2 * nu; t += kNT) {
+                    const void *ptr = t < nd        ? (const void *)(a.nz_d + min(f0 + 32LL * t, f1 - 1))
+                                      : t < nd + nu ? (const void *)(a.nz_u + min(f0 + 16LL * (t - nd), f1 - 1))
+                                                    : (const void *)(a.nz_v + min(f0 + 16LL * (t - nd - nu), f1 - 1));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+                }
+        }
+        // the next entry's values are loaded before this entry's candidates are evaluated
+        long long e = e0 + threadIdx.x;
+        float dn = 0.f;
+        float2 un = make_float2(0.f, 0.f), vn = un;
+        if (e < e1) {
+            dn = __ldg(a.nz_d + e);
+            un = __ldg(a.nz_u + e);
+            vn = __ldg(a.nz_v + e);
+        }
+        for (; e < e1; e += kNT) {
+            const float dv = dn;
+            const float2 u = un, v = vn;
+            if (e + kNT < e1) {
+                dn = __ldg(a.nz_d + e + kNT);
+                un = __ldg(a.nz_u + e + kNT);
+                vn = __ldg(a.nz_v + e + kNT);
+            }
             const float au = fmaf(u.x, u.x, u.y * u.y);
             const float bu2 = 2.0f * fmaf(u.x, v.x, u.y * v.y);  // 2 Re conj(u) v
             const float cu = fmaf(v.x, v.x, v.y * v.y);

@@ -27,7 +27,11 @@ __device__ __forceinline__ float log1p_fast(float t)
     // 2 atanh(s) = s q(s^2) with the series' coefficients doubled (exact: scaling by 2
     // commutes with rounding, so q = 2 p bit for bit and s q = (2 s) p)
     const float q = fmaf(s2, fmaf(s2, fmaf(s2, fmaf(s2, 2.0f / 9.0f, 2.0f / 7.0f), 2.0f / 5.0f), 2.0f / 3.0f), 2.0f);
-    return fmaf((float)e, 0.693147180559945309f, s * q);
+    // (float)e without a conversion instruction: e added to the integer bits of 1.5 * 2^23
+    // gives the float 1.5 * 2^23 + e exactly (|e| <= 150 keeps the exponent), then the
+    // subtraction is exact too
+    const float ef = __int_as_float(0x4b400000 + e) - 12582912.0f;
+    return fmaf(ef, 0.693147180559945309f, s * q);
 }
 
 }  // namespace pty

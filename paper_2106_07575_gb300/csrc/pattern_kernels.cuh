@@ -593,7 +593,9 @@ __device__ __forceinline__ float2 ls_cert_row(const PatternArgs &a, const DevSta
 __device__ __forceinline__ int ls_rows(const PatternArgs &a) { return a.dsum ? 2 + 2 * kCertN : 2; }
 
 // One pattern chunk of the LS pass; thread t < ls_rows(a) receives the chunk's value of row t.
-template <int P, int R, int NT>
+// DEFER: the pass ends after writing its warp partials to red (no barrier); ls_rows_deferred
+// turns them into the rows later.
+template <int P, int R, int NT, bool DEFER = false>
 __device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const float2 *__restrict__ eta, float2 *buf,
                                                  const float2 *tw, float2 *red, float2 *tot,
                                                  const DevState *__restrict__ sts, int i, int c,
@@ -632,11 +634,31 @@ __device__ __forceinline__ float2 ls_fft_pattern(const PatternArgs &a, const flo
         }
     }
     float vals[4] = {-bp, -cp, s1, s2};
+    if constexpr (DEFER) {
+        const float2 x[4] = {ff_from(vals[0]), ff_from(vals[1]), ff_from(vals[2]), ff_from(vals[3])};
+        block_partials_ff<NT, 4>(x, red);
+        return make_float2(0.f, 0.f);
+    }
     block_sum_ff<NT, 4>(vals, red, tot);
     if (threadIdx.x < 2) return tot[threadIdx.x];
     if (threadIdx.x < ls_rows(a))
         return ls_cert_row(a, sts[a.V == 1 ? 0 : a.pat_view[i]], tot, i * CS + c, threadIdx.x - 2);
     return make_float2(0.f, 0.f);
+}
+
+// Warp 0, after a barrier that follows ls_fft_pattern<DEFER = true> of pattern i: the block
+// totals from red, then lane l's rows l and l + 32 (zero beyond ls_rows(a)), as the
+// undeferred pass gives them to threads l and l + 32.
+template <int NT>
+__device__ __forceinline__ void ls_rows_deferred(const PatternArgs &a, const DevState *__restrict__ sts,
+                                                 const float2 *red, float2 *tot, int i, float2 &r0, float2 &r1)
+{
+    combine_partials_ff<NT, 4>(red, tot);
+    __syncwarp();
+    const int lane = threadIdx.x & 31, nr = ls_rows(a);
+    const DevState &sv = sts[a.V == 1 ? 0 : a.pat_view[i]];
+    r0 = lane < 2 ? tot[lane] : lane < nr ? ls_cert_row(a, sv, tot, i, lane - 2) : make_float2(0.f, 0.f);
+    r1 = lane + 32 < nr ? ls_cert_row(a, sv, tot, i, lane + 30) : make_float2(0.f, 0.f);
 }
 
 template <int P, int R, int NT>
@@ -660,16 +682,37 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
         const bool cached = a.probe_stride == 0;  // one probe for all patterns: kept in TMEM
         if (cached) pc.init(&tmem_slot, a.probe);
         const bool percta = a.V == 1;
-        float2 acc = make_float2(0.f, 0.f);
+        // a pattern's block totals are combined by warp 0 after the next barrier (the next
+        // pattern's first, or the one after the loop): lane l keeps rows l and l + 32
+        float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+        int prev = -1;
+        auto finish = [&]() {
+            float2 r0, r1;
+            ls_rows_deferred<NT>(a, sts, red, tot, prev, r0, r1);
+            const int lane = threadIdx.x & 31;
+            if (percta) {
+                acc0 = ff_add(acc0, r0);
+                acc1 = ff_add(acc1, r1);
+            } else {
+                if (lane < nr) part[(size_t)lane * KC + prev] = r0;
+                if (lane + 32 < nr) part[(size_t)(lane + 32) * KC + prev] = r1;
+            }
+        };
         for (int i = blockIdx.x; i < a.K; i += gridDim.x) {
             if (!percta && sts[a.pat_view[i]].stalled) continue;  // one view: decided above
             if (i + (int)gridDim.x < a.K) prefetch_entries<NT>(a, i + gridDim.x, false);
-            __syncthreads();  // the previous pattern's reads of buf are done
-            const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, 0, cached ? &pc : nullptr);
-            if (percta) acc = ff_add(acc, r);
-            else if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i] = r;
+            __syncthreads();  // the previous pattern's reads of buf and its partials are done
+            if (prev >= 0 && threadIdx.x < 32) finish();
+            ls_fft_pattern<P, R, NT, true>(a, eta, buf, tw, red, tot, sts, i, 0, cached ? &pc : nullptr);
+            prev = i;
         }
-        if (percta && threadIdx.x < nr) part[(size_t)threadIdx.x * KC + blockIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            if (prev >= 0) finish();
+            const int lane = threadIdx.x;
+            if (percta && lane < nr) part[(size_t)lane * KC + blockIdx.x] = acc0;
+            if (percta && lane + 32 < nr) part[(size_t)(lane + 32) * KC + blockIdx.x] = acc1;
+        }
         if (cached) pc.release();
     } else {
         const int i = blockIdx.x / CS;

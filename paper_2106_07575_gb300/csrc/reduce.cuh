@@ -119,11 +119,10 @@ __device__ __forceinline__ void warp_scatter_sum_ff(float2 (&x)[NV])
     for (int o = 16 >> K; o > 0; o >>= 1) x[0] = ff_add(x[0], shfl_xor_ff(x[0], o));
 }
 
-// Sums NV float-float values per thread over the block.  red: (NT/32) * NV float2 of shared
-// memory; thread v < NV receives the block total of value v in out[v] (shared memory, NV
-// float2) after the call; the call ends with a barrier.
+// First half of block_sum_ff: the warp totals of the NV values into red ((NT/32) * NV float2
+// of shared memory).  No barrier.
 template <int NT, int NV>
-__device__ __forceinline__ void block_sum_ff(const float2 (&v)[NV], float2 *red, float2 *out)
+__device__ __forceinline__ void block_partials_ff(const float2 (&v)[NV], float2 *red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (NV >= 2 && NV <= 32 && (NV & (NV - 1)) == 0) {
@@ -140,16 +139,25 @@ __device__ __forceinline__ void block_sum_ff(const float2 (&v)[NV], float2 *red,
             if (lane == 0) red[warp * NV + i] = s;
         }
     }
-    __syncthreads();
+}
+
+// Second half: called by warp 0 (all lanes) once the partials of every warp are visible;
+// out[v] (shared memory) receives the block total of value v, written by lanes of warp 0
+// (readable by warp 0 after __syncwarp).
+template <int NT, int NV>
+__device__ __forceinline__ void combine_partials_ff(const float2 *red, float2 *out)
+{
     constexpr int NW = NT / 32;
     static_assert(NW <= 32, "at most 32 warps");
+    static_assert(NV <= 32, "one value per lane of warp 0");
+    const int lane = threadIdx.x & 31;
     if constexpr (NW <= 8) {  // few warps: thread v adds the partials of value v in order
-        if (threadIdx.x < NV) {
-            float2 s = red[threadIdx.x];
-            for (int w = 1; w < NW; w++) s = ff_add(s, red[w * NV + threadIdx.x]);
-            out[threadIdx.x] = s;
+        if (lane < NV) {
+            float2 s = red[lane];
+            for (int w = 1; w < NW; w++) s = ff_add(s, red[w * NV + lane]);
+            out[lane] = s;
         }
-    } else if (warp == 0) {  // many warps: one warp combines the partials as a tree
+    } else {  // many warps: one warp combines the partials as a tree
         float2 x[NV];
 #pragma unroll
         for (int i = 0; i < NV; i++) x[i] = lane < NW ? red[lane * NV + i] : make_float2(0.f, 0.f);
@@ -165,6 +173,17 @@ __device__ __forceinline__ void block_sum_ff(const float2 (&v)[NV], float2 *red,
             }
         }
     }
+}
+
+// Sums NV float-float values per thread over the block.  red: (NT/32) * NV float2 of shared
+// memory; thread v < NV receives the block total of value v in out[v] (shared memory, NV
+// float2) after the call; the call ends with a barrier.
+template <int NT, int NV>
+__device__ __forceinline__ void block_sum_ff(const float2 (&v)[NV], float2 *red, float2 *out)
+{
+    block_partials_ff<NT, NV>(v, red);
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) combine_partials_ff<NT, NV>(red, out);
     __syncthreads();
 }
 

@@ -11,7 +11,8 @@
 // even complex column, so the copy's x coordinate is a multiple of 4 floats (16 bytes).
 // Rows and columns outside the pattern are filled with zeros by the copy, which adds nothing.
 // A ring of 4 stages (34 KB, 6 CTAs per SM) measured best at the 1024^2 workload: the scatter
-// 0.126 ms with per-thread streaming loads, 0.115 ms here.
+// 0.126 ms with per-thread streaming loads, 0.115 ms here; consuming the stages two at a time
+// (one block barrier per two patterns) 0.113 ms.
 // Every mbarrier wait is bounded (spin_limit polls): on a timeout the CTA records it in *err,
 // waits (bounded by the default limit) for its copies still in flight and returns without
 // writing.
@@ -32,6 +33,10 @@ constexpr int kTY = kTileY, kTX = kTileX, kNT = 256, kNJ = kTY * kTX / kNT, kRow
 #define PTY_TMA_STAGES 4  // shared-memory stages of the window ring (2: 0.120, 3: 0.117, 4: 0.115, 6: 0.136 ms)
 #endif
 constexpr int kStages = PTY_TMA_STAGES;
+// stages added per block barrier and refilled together (production workload, stages/group:
+// 4/1 0.118, 4/2 0.113, 6/2 0.131, 6/3 0.126, 8/2 0.138, 8/4 0.128 ms)
+constexpr int kGroup = 2;
+static_assert(kStages % kGroup == 0, "whole groups of stages");
 constexpr int kBoxX = kTX + 2;                  // complex columns per box (even start)
 constexpr int kBoxFloats = 2 * kBoxX;           // 132 floats = 528 bytes, a multiple of 16
 constexpr int kStageBytes = kBoxFloats * 4 * kTY;  // 8448 bytes, a multiple of 128
@@ -86,28 +91,36 @@ __global__ void __launch_bounds__(kNT) k_scatter_tma(PatternArgs a, ScatterPlan 
     if (threadIdx.x == 0)
         for (int k = 0; k < n && k < kStages; k++) issue(k);
 
+    // kGroup stages per block barrier: patterns k .. k + kGroup - 1 added in list order (the
+    // same additions as one stage at a time), then their stages are refilled together
     int k = 0;
     bool failed = false;
-    for (; k < n; k++) {
-        const int s = k % kStages;
-        const bool ok = tcx::mbar_wait(full + s, (uint32_t)((k / kStages) & 1), spin_limit);
-        // the window's column of this thread: one past the even start when the start is odd
-        const int2 rc = __ldg(a.pos + __ldg(plan.tile_list + q0 + k));
-        const int col = (x - tx * kTX) + ((tx * kTX - rc.y) & 1);
-        const float2 *stg = reinterpret_cast<const float2 *>(stage_mem + (size_t)s * kStageBytes);
+    for (; k < n; k += kGroup) {
+        bool ok = true;
 #pragma unroll
-        for (int j = 0; j < kNJ; j++) {
-            const float2 v = stg[(threadIdx.x / kTX + kRowStep * j) * kBoxX + col];
-            acc[j].x += v.x;
-            acc[j].y += v.y;
+        for (int g = 0; g < kGroup; g++) {
+            const int kk = k + g;
+            if (kk >= n) break;
+            const int s = kk % kStages;
+            ok = tcx::mbar_wait(full + s, (uint32_t)((kk / kStages) & 1), spin_limit) && ok;
+            // the window's column of this thread: one past the even start when the start is odd
+            const int2 rc = __ldg(a.pos + __ldg(plan.tile_list + q0 + kk));
+            const int col = (x - tx * kTX) + ((tx * kTX - rc.y) & 1);
+            const float2 *stg = reinterpret_cast<const float2 *>(stage_mem + (size_t)s * kStageBytes);
+#pragma unroll
+            for (int j = 0; j < kNJ; j++) {
+                const float2 v = stg[(threadIdx.x / kTX + kRowStep * j) * kBoxX + col];
+                acc[j].x += v.x;
+                acc[j].y += v.y;
+            }
         }
-        if (__syncthreads_or(!ok)) {  // every thread is done with stage s (or a wait gave up)
+        if (__syncthreads_or(!ok)) {  // every thread is done with the group's stages (or a wait gave up)
             failed = true;
             break;
         }
         if (threadIdx.x == 0 && k + kStages < n) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads before the next copy
-            issue(k + kStages);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // reads before the next copies
+            for (int g = 0; g < kGroup && k + kStages + g < n; g++) issue(k + kStages + g);
         }
     }
     if (failed) {

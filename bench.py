@@ -47,6 +47,8 @@ WORKLOADS = {
                 "real jitter +-2, one Fourier-shifted probe per position), peak 1e5 counts",
     "gap": "ml-cg 1024x1024 object, 128x128 probe, 3600 positions (60x60 raster, step 14, +-2), peak 1e5 counts, "
            "test seed 5: time to relative objective gap 1e-3 per form",
+    "spiral_gap": "ml-cg 2048x2048 object, 256x256 probe, 10000 positions (Fermat spiral, +-2), peak 1e6 counts: "
+                  "time to relative objective gap 1e-3 from the ones start, FP32 FFT and split-BF16 tensor-core DFT",
     "train": "learned start: 6-layer 3x3 CNN (1-32-32-32-32-32-2 channels), 128x128 patterns, batch 64, "
              "2048 forward-model pairs (Poisson counts of |F[p psi]|^2 of ellipse phantoms, peak 1e5 probe)",
     "views": "batched ml-cg: {n} views of 512^2-2048^2 (multiples of 128), 128x128 shared probe, rasters at 16 px "
@@ -122,7 +124,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ls-window", type=int, default=None)
     ap.add_argument("--tile-config", type=int, default=None)
-    ap.add_argument("--workload", choices=["production", "spiral", "small", "subpixel", "views", "gap", "train"],
+    ap.add_argument("--workload", choices=["production", "spiral", "small", "subpixel", "views", "gap", "spiral_gap",
+                                           "train"],
                     default="production")
     ap.add_argument("--pairs", type=int, default=200000, help="gap workload: training pairs of the learned start")
     ap.add_argument("--epochs", type=float, default=1.0, help="gap workload: passes over the training pairs")
@@ -399,6 +402,49 @@ def run_gap(args, torch, pty, synth):
         "forms": forms, "clocks": clocks}), flush=True)
 
 
+def run_spiral_gap(args, torch, pty, synth):
+    """Wall time and iterations to a relative objective gap of 1e-3 (gap_m = (F_m - F*) /
+    (F_0 - F*), F* = F(psi_true), F_0 = F(ones)) on the spiral workload (P = 256) from the
+    ones start, for the FP32 FFT and the split-BF16 tensor-core DFT; one host read of the
+    objective per iteration in both."""
+    from paper_2106_07575_gb300 import learned
+
+    prob = synth.spiral_problem()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    probe, pos, d = dev(prob.probe), dev(prob.pos), dev(prob.d)
+    psi_true = dev(prob.psi_true)
+    cap = 300  # the spiral workload states no iteration count; the production one needs 64
+    clk = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    base = pty.Context(probe, pos, d, prob.H, prob.W)
+    g = torch.empty_like(psi_true)
+    F_star = base.gradient(psi_true, g)
+    ones = torch.ones_like(psi_true)
+    F0 = base.gradient(ones, g)
+    forms = {}
+    clk.start()
+    t_load0 = time.time()
+    for name, dft in (("plain FP32 FFT", 0), ("split BF16 tensor-core DFT", 1)):
+        opts = pty.default_opts()
+        opts.dft = dft
+        ctx = base if dft == 0 else pty.Context(probe, pos, d, prob.H, prob.W, opts)
+        ctx.cg_solve(ones.clone(), 2)  # warm the captured iteration
+        ctx.cg_reset()
+        x = ones.clone()
+        it, ms, F = learned.solve_to_gap(ctx, x, F_star, F0, cap, chunk=1)
+        forms[name] = {"iterations": it, "ms": ms if it is not None else None,
+                       "ms_per_iteration": ms / max(len(F) - 1, 1), "final_gap": (F[-1] - F_star) / (F0 - F_star)}
+        if ctx is not base:
+            ctx.close()
+    clocks = clk.stop(load=(t_load0, time.time()))
+    base.close()
+    plain = forms["plain FP32 FFT"]
+    print(json.dumps({
+        "metric": "wall time to relative objective gap 1e-3", "value": plain["ms"], "unit": "ms", "n_gpus": 1,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS["spiral_gap"], "cap_iterations": cap, "F_star": F_star, "F0_ones": F0},
+        "forms": forms, "clocks": clocks}), flush=True)
+
+
 def run_train(args, torch, pty, synth):
     """CNN training throughput (pairs/s) of the learned start through pty_cnn_train: K steps of
     batch 64 (forward, loss, backward, Adam) timed with CUDA events on the library's stream
@@ -465,6 +511,9 @@ def main():
         return
     if args.workload == "train":
         run_train(args, torch, pty, synth)
+        return
+    if args.workload == "spiral_gap":
+        run_spiral_gap(args, torch, pty, synth)
         return
     if args.workload == "gap":
         run_gap(args, torch, pty, synth)

@@ -27,10 +27,11 @@ def ctx_for(p, tma):
 PROBLEMS = {
     "small": lambda: synth.small_problem(seed=0),
     "mid": lambda: synth.small_problem(H=512, W=512, P=128, n=27, step=14, jitter=2, peak=1e5, seed=4),
+    "p256": lambda: synth.small_problem(H=640, W=640, P=256, n=5, step=80, jitter=2, peak=1e6, seed=24),
 }
 
 
-@pytest.mark.parametrize("name", ["small", "mid"])
+@pytest.mark.parametrize("name", ["small", "mid", "p256"])
 def test_gradient_and_steps_equal_per_thread_form(name):
     p = PROBLEMS[name]()
     rng = np.random.default_rng(7)

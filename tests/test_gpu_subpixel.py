@@ -95,7 +95,7 @@ def test_subpixel_gradient_and_adjoint_parity(orc, request, which):
     ctx.close()
 
 
-@pytest.mark.parametrize("which,n", [("small", 10), ("mid128", 4)])
+@pytest.mark.parametrize("which,n", [("small", 10), ("mid128", 4), ("p256", 2)])
 def test_subpixel_cg_parity(orc, request, which, n):
     p = request.getfixturevalue(which)
     pos_i, probes = oracle_probes(orc, p)

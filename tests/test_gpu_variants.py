@@ -48,6 +48,13 @@ def mid128():
                                name="mid")
 
 
+@pytest.fixture(scope="module")
+def p256():
+    """P = 256 (the cluster form of the pattern passes): 640^2 object, 5 x 5 raster, peak 1e6."""
+    return synth.small_problem(H=640, W=640, P=256, n=5, step=80, jitter=2, peak=1e6, seed=23, niter=2,
+                               name="p256")
+
+
 def random_object(p, seed):
     rng = np.random.default_rng(seed)
     return (p.psi_true * (1 + 0.05 * (rng.standard_normal((p.H, p.W)) + 1j * rng.standard_normal((p.H, p.W))))
@@ -55,7 +62,7 @@ def random_object(p, seed):
 
 
 # ------------------------------------------------------------------------------- LS estimator
-@pytest.mark.parametrize("which", ["small", "mid128"])
+@pytest.mark.parametrize("which", ["small", "mid128", "p256"])
 def test_ls_estimator_gradient_parity(orc, request, which):
     p = request.getfixturevalue(which)
     ctx = make_ctx(p, opts(estimator=pty.EST_LS))
@@ -71,10 +78,10 @@ def test_ls_estimator_gradient_parity(orc, request, which):
         assert abs(F - Fw) <= OBJ_TOL * abs(Fw)
 
 
-@pytest.mark.parametrize("which", ["small", "mid128"])
+@pytest.mark.parametrize("which", ["small", "mid128", "p256"])
 def test_ls_estimator_cg_parity(orc, request, which):
     p = request.getfixturevalue(which)
-    n = 10 if which == "small" else 4
+    n = {"small": 10, "mid128": 4, "p256": 3}[which]
     ctx = make_ctx(p, opts(estimator=pty.EST_LS))
     psi = dev(p.psi0())
     st, rep = ctx.cg_solve(psi, n)
@@ -144,10 +151,10 @@ def test_gd_continues_across_calls(small):
 
 
 # ------------------------------------------------------------------------------- warm start
-@pytest.mark.parametrize("which", ["small", "mid128"])
+@pytest.mark.parametrize("which", ["small", "mid128", "p256"])
 def test_warm_start_parity(orc, request, which):
     p = request.getfixturevalue(which)
-    n = 10 if which == "small" else 5
+    n = {"small": 10, "mid128": 5, "p256": 3}[which]
     ctx = make_ctx(p, opts(ls_warm=1))
     psi = dev(p.psi0())
     st, rep = ctx.cg_solve(psi, n)
@@ -159,7 +166,19 @@ def test_warm_start_parity(orc, request, which):
     assert list(rep["halvings"]) == list(want["halvings"])
     np.testing.assert_array_equal(rep["gamma"], want["gamma"])
     assert np.all(relF <= OBJ_TOL)
-    assert rel(psi.cpu().numpy(), want["psi"]) <= 1e-3
+    # the iterate has no stated tolerance: its error is reported plain and weighted by the
+    # illumination map D = sum_k |p|^2 (where the data fix psi).  At P = 256, peak 1e6 the FP32
+    # iterate departs from FP64 by about 6x per iteration with or without the warm start
+    # (2.6e-6, 1.7e-4, 1.1e-3 after 1, 2, 3 iterations, same steps and trials): the start's
+    # gradient differs by 1.3e-5 and the CG directions amplify it.  The bounds only catch a
+    # broken update.
+    D = np.real(orc.QH(np.ascontiguousarray(np.broadcast_to(p.probe, (p.K, p.P, p.P))), p.probe, p.pos, (p.H, p.W)))
+    x = psi.cpu().numpy()
+    e_plain = rel(x, want["psi"])
+    e_w = rel(np.sqrt(D) * x, np.sqrt(D) * want["psi"])
+    print(f"warm start ({which}): iterate rel L2 {e_plain:.2e}, illumination-weighted {e_w:.2e}")
+    bound = 1e-2 if which == "p256" else 1e-3
+    assert e_w <= bound and e_plain <= bound
 
 
 @pytest.mark.parametrize("L", [0, 8])

@@ -278,7 +278,7 @@ int pty_cnn_create(pty_cnn **out, int32_t P, int32_t channels, int32_t layers, i
         dalloc(&n->w16, wo) || dalloc(&n->wt16, wo) || dalloc(&n->lw, PP) || dalloc(&n->x0, Bc * PP) ||
         dalloc(&n->zh, Bc * 2 * PP) || dalloc(&n->dzh, Bc * 2 * PP) || dalloc(&n->dz0, Bc * channels * PP) ||
         dalloc(&n->dz1, Bc * channels * PP) ||
-        dalloc(&n->part, (size_t)pty::cnn::wgrad_blocks(P, max_batch) * (channels * channels * 9 + channels)) ||
+        dalloc(&n->part, (size_t)pty::cnn::wgrad_part_blocks(P, max_batch) * (channels * channels * 9 + channels)) ||
         dalloc(&n->lpart, (Bc * PP + 255) / 256) || dalloc(&n->dloss, 1) || dalloc(&n->tc_err, 1)) {
         cudaGetLastError();
         return cleanup(PTY_ERR_NOMEM);

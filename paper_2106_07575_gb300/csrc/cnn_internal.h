@@ -34,7 +34,7 @@ cudaError_t launch_conv_tc(int P, int B, bool bwd, const float *in, const __nv_b
 // The tensor-core form of a hidden layer's weight gradient (cnn_tc.cu): the per-CTA partials
 // of launch_wgrad for cin = cout = kC at P = 128, 256.
 bool wgrad_tc_supported(int P, int cin, int cout);
-// Number of partials launch_wgrad_tc writes (at most wgrad_blocks(P, B)).
+// Number of partials launch_wgrad_tc writes.
 int wgrad_tc_blocks(int P, int B);
 cudaError_t launch_wgrad_tc(int P, int B, const float *a, const float *dz, float *part, int *err, cudaStream_t s);
 // Process-wide switch of the tensor-core forms (tests compare both forms); on by default.
@@ -54,6 +54,9 @@ cudaError_t launch_loss_finalize(const double *part, int n, double inv_norm, dou
 // Weight and bias gradient of one layer: partials per CTA, then a fixed-order sum into
 // grad ([cout][cin][9] then [cout]).  part must hold wgrad_parts(P, B) * (cout*cin*9 + cout).
 int wgrad_blocks(int P, int B);
+// Partials a weight gradient of either form writes: the size (in units of cout*cin*9 + cout)
+// of the part buffer.
+int wgrad_part_blocks(int P, int B);
 cudaError_t launch_wgrad(int P, int cin, int cout, int B, const float *a, const float *dz, float *part,
                          float *grad, int *err, cudaStream_t s);
 // Adam on n masters, then the BF16 copies of every layer's weights are refreshed.

@@ -693,6 +693,12 @@ cudaError_t launch_loss_finalize(const double *part, int n, double inv_norm, dou
 
 int wgrad_blocks(int P, int B) { return B * (P / kWgRB); }
 
+int wgrad_part_blocks(int P, int B)
+{
+    const int t = wgrad_tc_supported(P, kC, kC) ? wgrad_tc_blocks(P, B) : 0;
+    return wgrad_blocks(P, B) > t ? wgrad_blocks(P, B) : t;
+}
+
 cudaError_t launch_wgrad(int P, int cin, int cout, int B, const float *a, const float *dz, float *part, float *grad,
                          int *err, cudaStream_t s)
 {

@@ -262,30 +262,34 @@ namespace {
 //   db[co] = sum over pixels of dz[co][y][x],
 // written as per-CTA partials that launch_wgrad's fixed-order reduction adds (the layout of
 // the CUDA-core kernel).  The work is B * (P / 32) * P units (image, 32-pixel column chunk,
-// row) in that order, cut into wgrad_tc_blocks(P, B) contiguous ranges, one per CTA: one
-// wave of CTAs with equal shares.  For each unit (chunk x', row y) the GEMM is D[m][n] += A[m][x'] Z[n][x'] with m = (dy, ci)
-// (96 rows, padded to M = 128), n = (dx, co) (N = 96) and K = the chunk's pixels: the row
-// shift dy is a choice of staged row and the column shift dx is carried by three shifted
-// copies of the dz row (a canonical K-major tile cannot start one element into a core
-// matrix), so one MMA per K-step and product covers all nine taps.  Padding row 96 of A
-// holds ones, so D[96][(dx = 1, co)] is db.  Activations and dz are both split into three
-// BF16 parts and the six products above 2^-24 are accumulated, smallest first: FP32-level
-// products, FP32 sums.
+// row) in that order, cut into wgrad_tc_blocks(P, B) contiguous ranges, one per CTA.  For each
+// unit (chunk x', row y) the GEMM is D[m][n] += A[m][x'] Z[n][x'] with m = (dy, ci) (96 rows;
+// M = 128, rows 96..127 read scratch and are not used), n = (dx, co) (N = 96) and K = the
+// chunk's 32 pixels.  Both operands are split into three BF16 parts and the six products
+// above 2^-24 are accumulated, smallest first: FP32-level products, FP32 sums.
+//
+// Each input row is split once: its 32 channels x 32 pixels go to ring slot (yy + 3) % 3 of
+// the A region and, for slots 0 and 1, to the mirror slots 3 and 4, so the three rows of any
+// unit (y - 1, y, y + 1) are the consecutive slots from the one of y - 1 and one MMA per
+// K-step and product covers all three dy.  Each dz value is split once: a thread splits ten
+// values (8 pixels and their halo) and writes the three shifted copies that carry dx (a
+// canonical K-major tile cannot start one element into a core matrix).  Raw values come
+// straight from global memory into registers, one unit ahead.  db is summed on the CUDA
+// cores from the unshifted dz values.
 constexpr int kWgTcRB = 16;                  // rows per CTA of the CUDA-core kernel (its partial count)
-constexpr int kWgKC = 32;                    // pixels per chunk (K)
-constexpr int kWgMG = 16;                    // A M-groups of 8 rows: 12 used (3 dy x 4 ci groups), 4 padding
-constexpr int kWgNG = 12;                    // Z N-groups of 8 rows: 3 dx x 4 co groups
+constexpr int kWgKC = 32;                    // pixels per unit (K)
 constexpr int kWgCore = 128;                 // one core matrix (8 rows x 16 bytes)
-constexpr int kWgGBytes = (kWgKC / 8) * kWgCore;   // one M- or N-group: 4 K-groups
-constexpr int kWgAPart = kWgMG * kWgGBytes;        // one BF16 part of A
-constexpr int kWgBPart = kWgNG * kWgGBytes;        // one BF16 part of Z
+constexpr int kWgGBytes = (kWgKC / 8) * kWgCore;   // one M- or N-group of 8 rows: 4 K-groups
+constexpr int kWgSlotBytes = (kC / 8) * kWgGBytes; // one input row: 4 M-groups (32 channels)
+constexpr int kWgSlots = 6;                        // ring 0..2, mirrors 3, 4, scratch 5
+constexpr int kWgAPart = kWgSlots * kWgSlotBytes;  // one BF16 part of A (12 KB)
+constexpr int kWgNG = 12;                          // Z N-groups of 8 rows: 3 dx x 4 co groups
+constexpr int kWgBPart = kWgNG * kWgGBytes;        // one BF16 part of Z (6 KB)
 constexpr int kWgN = 3 * kC;                       // N of the MMAs
-constexpr int kWgALd = kWgKC + 1;                  // raw activation row stride (floats, odd)
-constexpr int kWgZLd = kWgKC + 3;                  // raw dz row stride: pixels x0 - 1 .. x0 + 32, odd
-constexpr int kWgRing = 4;                        // raw activation rows held (a tile reads 3)
-constexpr int kWgRawBytes = (kWgRing * kC * kWgALd + 2 * kC * kWgZLd) * 4;
-constexpr int kWgGrid = 3 * 152;                   // CTAs of one wave: 3 resident per SM, 152 SMs
-constexpr size_t kWgSmem = 3 * (size_t)kWgAPart + 3 * (size_t)kWgBPart + kWgRawBytes + 64;
+constexpr size_t kWgSmem = 3 * (size_t)kWgAPart + 3 * (size_t)kWgBPart + 64;
+constexpr int kWgPerSM = 4;                        // resident CTAs per SM (shared memory, TMEM, threads)
+constexpr int kWgGrid = kWgPerSM * 152;            // CTAs of one wave on 152 SMs
+static_assert(kTcNT == 256, "thread roles: 128 activation-row threads, 128 dz-row threads");
 
 // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, M = 128, N = 96.
 __host__ __device__ constexpr uint32_t wgrad_idesc()
@@ -301,28 +305,79 @@ __device__ __forceinline__ void split3(float a, uint16_t &h, uint16_t &m, uint16
     l = to_half_bits<true>(r1 - from_half_bits<true>(m));
 }
 
-// Eight consecutive values as three 16-byte BF16 rows (parts hi, mid, lo) at dst, dst + stride,
-// dst + 2 stride.
-__device__ __forceinline__ void store_split8(uint8_t *dst, size_t stride, const float (&v)[8])
+// Eight values v[o .. o + 7] of split parts h, m, l as three 16-byte BF16 rows at dst, dst +
+// stride, dst + 2 stride.
+template <int N>
+__device__ __forceinline__ void store_parts8(uint8_t *dst, size_t stride, const uint16_t (&h)[N],
+                                             const uint16_t (&m)[N], const uint16_t (&l)[N], int o)
+{
+    *(uint4 *)dst = make_uint4(pack2(h[o], h[o + 1]), pack2(h[o + 2], h[o + 3]), pack2(h[o + 4], h[o + 5]),
+                               pack2(h[o + 6], h[o + 7]));
+    *(uint4 *)(dst + stride) = make_uint4(pack2(m[o], m[o + 1]), pack2(m[o + 2], m[o + 3]),
+                                          pack2(m[o + 4], m[o + 5]), pack2(m[o + 6], m[o + 7]));
+    *(uint4 *)(dst + 2 * stride) = make_uint4(pack2(l[o], l[o + 1]), pack2(l[o + 2], l[o + 3]),
+                                              pack2(l[o + 4], l[o + 5]), pack2(l[o + 6], l[o + 7]));
+}
+
+// Activation-row thread t < 128: channel ci = t / 4, pixels x0 + 8 (t % 4) .. + 7 of row yy
+// (zeros outside the image), two aligned 16-byte loads.
+template <int P>
+__device__ __forceinline__ void load_arow(const float *__restrict__ a, int b, int yy, int x0, int t, float (&v)[8])
+{
+    if (yy < 0 || yy >= P) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) v[j] = 0.f;
+        return;
+    }
+    const float4 *src = reinterpret_cast<const float4 *>(a + (((size_t)b * kC + t / 4) * P + yy) * P + x0 + 8 * (t % 4));
+    const float4 p0 = __ldg(src), p1 = __ldg(src + 1);
+    v[0] = p0.x; v[1] = p0.y; v[2] = p0.z; v[3] = p0.w;
+    v[4] = p1.x; v[5] = p1.y; v[6] = p1.z; v[7] = p1.w;
+}
+
+// dz-row thread t' = t - 128: channel co = t' / 4, pixels x0 + 8 (t' % 4) - 1 .. + 8 of row y
+// (zeros outside the image): the 8 aligned values and the two halo values.
+template <int P>
+__device__ __forceinline__ void load_zrow(const float *__restrict__ dz, int b, int y, int x0, int tz, float (&v)[10])
+{
+    const int xs = x0 + 8 * (tz % 4);
+    const float *row = dz + (((size_t)b * kC + tz / 4) * P + y) * P;
+    const float4 *src = reinterpret_cast<const float4 *>(row + xs);
+    const float4 p0 = __ldg(src), p1 = __ldg(src + 1);
+    v[0] = xs > 0 ? __ldg(row + xs - 1) : 0.f;
+    v[1] = p0.x; v[2] = p0.y; v[3] = p0.z; v[4] = p0.w;
+    v[5] = p1.x; v[6] = p1.y; v[7] = p1.z; v[8] = p1.w;
+    v[9] = xs + 8 < P ? __ldg(row + xs + 8) : 0.f;
+}
+
+// The activation row in v (thread t) split into ring slot (yy + 3) % 3 and its mirror.
+__device__ __forceinline__ void store_arow(uint8_t *As, int yy, int t, const float (&v)[8])
 {
     uint16_t h[8], m[8], l[8];
 #pragma unroll
     for (int j = 0; j < 8; j++) split3(v[j], h[j], m[j], l[j]);
-    *(uint4 *)dst = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
-    *(uint4 *)(dst + stride) = make_uint4(pack2(m[0], m[1]), pack2(m[2], m[3]), pack2(m[4], m[5]), pack2(m[6], m[7]));
-    *(uint4 *)(dst + 2 * stride) =
-        make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+    const int slot = (yy + 3) % 3, ci = t / 4, kg = t % 4;
+    const size_t off = (size_t)(ci / 8) * kWgGBytes + kg * kWgCore + (ci % 8) * 16;
+    store_parts8<8>(As + (size_t)slot * kWgSlotBytes + off, kWgAPart, h, m, l, 0);
+    if (slot < 2) store_parts8<8>(As + (size_t)(slot + 3) * kWgSlotBytes + off, kWgAPart, h, m, l, 0);
 }
 
-// Four bytes global -> shared without a register round trip; src_ok = false writes zero.
-__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool src_ok)
+// The dz row in v (thread t') split once; copy dx (pixels x' - dx + 1) is v[2 - dx .. 9 - dx]
+// -> row co % 8 of core matrix (N-group dx * 4 + co / 8, K-group t' % 4).
+__device__ __forceinline__ void store_zrow(uint8_t *Zs, int tz, const float (&v)[10])
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_ok ? 4 : 0)
-                 : "memory");
+    uint16_t h[10], m[10], l[10];
+#pragma unroll
+    for (int j = 0; j < 10; j++) split3(v[j], h[j], m[j], l[j]);
+    const int co = tz / 4, kg = tz % 4;
+#pragma unroll
+    for (int dx = 0; dx < 3; dx++)
+        store_parts8<10>(Zs + (size_t)(dx * 4 + co / 8) * kWgGBytes + kg * kWgCore + (co % 8) * 16, kWgBPart, h, m, l,
+                         2 - dx);
 }
 
 template <int P>
-__global__ void __launch_bounds__(kTcNT, 3)
+__global__ void __launch_bounds__(kTcNT, kWgPerSM)
     k_wgrad_tc(const float *__restrict__ a, const float *__restrict__ dz, float *__restrict__ part, int *__restrict__ err,
                long long spin_limit, int nunits)
 {
@@ -331,11 +386,11 @@ __global__ void __launch_bounds__(kTcNT, 3)
     constexpr int NC = P / kWgKC;
     extern __shared__ __align__(128) uint8_t sm[];
     uint8_t *As = sm, *Zs = sm + 3 * (size_t)kWgAPart;
-    float *Ra = (float *)(Zs + 3 * (size_t)kWgBPart);  // raw activation rows [kWgRing][ci][kWgALd]
-    float *Rz = Ra + kWgRing * kC * kWgALd;              // two raw dz rows [2][co][kWgZLd]
-    uint64_t *done = (uint64_t *)((uint8_t *)Ra + kWgRawBytes);
+    uint64_t *done = (uint64_t *)(Zs + 3 * (size_t)kWgBPart);
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const bool arow = tid < 128;  // threads 0..127: activation rows; 128..255: dz rows
+    const int tz = tid - 128;
     // this CTA's units [u0, u1); the host keeps every range non-empty
     const int u0 = (int)((long long)blockIdx.x * nunits / gridDim.x);
     const int u1 = (int)((long long)(blockIdx.x + 1) * nunits / gridDim.x);
@@ -345,112 +400,109 @@ __global__ void __launch_bounds__(kTcNT, 3)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(tmem_slot, 128);
-    // padding M-groups 12..15 of the three parts of A: zero, except row 96 (M-group 12, row 0
-    // of each core matrix) of the high part: ones (BF16 1.0 = 0x3f80)
-    for (int e = tid; e < 3 * 4 * (kWgGBytes / 16); e += kTcNT) {
-        const int c16 = e % (kWgGBytes / 16), t = e / (kWgGBytes / 16);
-        const int g = 12 + t % 4, pt = t / 4;
-        const bool ones = pt == 0 && g == 12 && (c16 % 8) == 0;
-        const uint32_t v = ones ? 0x3f803f80u : 0u;
-        *(uint4 *)(As + (size_t)pt * kWgAPart + (size_t)g * kWgGBytes + c16 * 16) = make_uint4(v, v, v, v);
-    }
+    // finite values in every slot: rows 96..127 of an MMA read the slot after a unit's three
+    for (int e = tid; e < 3 * kWgAPart / 16; e += kTcNT) reinterpret_cast<uint4 *>(As)[e] = make_uint4(0, 0, 0, 0);
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = wgrad_idesc();
 
-    // Unit u = (image b, chunk x0, row y).  The i-th unit of the CTA reads its rows y - 1 + r
-    // (r = 0, 1, 2) from ring slots (i + r) % kWgRing and its dz row from buffer u & 1.  When
-    // unit u + 1 continues the column (same chunk, row y + 1) it needs one new row, r = 2, in
-    // slot (i + 3) % kWgRing, which unit u does not read: that copy and its dz row are issued
-    // before unit u's split.  A unit that starts a column (y = 0) loads all three rows after
-    // unit u's split has read the ring.
-    auto load_rows = [&](int u, int r0, int nrow, int i) {
-        const int b = u / (NC * P), x0 = ((u / P) % NC) * kWgKC, y = u % P;
-        for (int e = tid; e < nrow * kC * kWgKC; e += kTcNT) {
-            const int px = e % kWgKC, ci = (e / kWgKC) % kC, r = r0 + e / (kWgKC * kC);
-            const int yy = y - 1 + r;
-            const bool in = yy >= 0 && yy < P;
-            cp_async4(Ra + (((i + r) % kWgRing) * kC + ci) * kWgALd + px,
-                      in ? a + (((size_t)b * kC + ci) * P + yy) * P + x0 + px : a, in);
-        }
-        float *z = Rz + (u & 1) * kC * kWgZLd;
-        for (int e = tid; e < kC * (kWgKC + 2); e += kTcNT) {
-            const int q = e % (kWgKC + 2), co = e / (kWgKC + 2), x = x0 - 1 + q;
-            const bool in = x >= 0 && x < P;
-            cp_async4(z + co * kWgZLd + q, in ? dz + (((size_t)b * kC + co) * P + y) * P + x : dz, in);
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
+    auto geo = [&](int u, int &b, int &x0, int &y) {
+        b = u / (NC * P);
+        x0 = ((u / P) % NC) * kWgKC;
+        y = u % P;
     };
-    load_rows(u0, 0, 3, 0);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncthreads();
-    bool started = false, ok = true;
+    bool started = false;
+    // thread 0: the unit's 12 MMAs, (A part, Z part) smallest product first
+    auto issue = [&](int u) {
+        if (tid != 0) return;
+        int b, x0, y;
+        geo(u, b, x0, y);
+        const uint32_t a0 = smem_u32(As) + (uint32_t)(((y + 2) % 3) * kWgSlotBytes);  // slot of row y - 1
+        const uint32_t z0 = smem_u32(Zs);
+        const int pa[6] = {2, 1, 0, 1, 0, 0}, pz[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll 1
-    for (int u = u0; u < u1; u++) {
-        const int i = u - u0;
-        const bool next = u + 1 < u1, next_starts = next && (u + 1) % P == 0;
-        if (next && !next_starts) load_rows(u + 1, 2, 1, i + 1);
-        // ---- A: task (dy, ci, kg): pixels x0 + 8 kg .. + 7 of channel ci in row y + dy - 1
-        // -> row ci % 8 of core matrix (M-group dy * 4 + ci / 8, K-group kg)
-        for (int t = tid; t < 3 * kC * (kWgKC / 8); t += kTcNT) {
-            const int ci = t % kC, kg = (t / kC) % (kWgKC / 8), dy = t / (kC * (kWgKC / 8));
-            const float *r = Ra + (((i + dy) % kWgRing) * kC + ci) * kWgALd + 8 * kg;
-            float v[8];
+        for (int ks = 0; ks < kWgKC / 16; ks++)
 #pragma unroll
-            for (int j = 0; j < 8; j++) v[j] = r[j];
-            store_split8(As + (size_t)(dy * 4 + ci / 8) * kWgGBytes + kg * kWgCore + (ci % 8) * 16, kWgAPart, v);
-        }
-        // ---- Z: task (dx, co, kg): dz[co] at pixels x' - dx + 1, x' = x0 + 8 kg .. + 7
-        // -> row co % 8 of core matrix (N-group dx * 4 + co / 8, K-group kg)
-        const float *zr = Rz + (u & 1) * kC * kWgZLd;
-        for (int t = tid; t < 3 * kC * (kWgKC / 8); t += kTcNT) {
-            const int co = t % kC, kg = (t / kC) % (kWgKC / 8), dx = t / (kC * (kWgKC / 8));
-            const float *r = zr + co * kWgZLd + 8 * kg + 2 - dx;  // raw index of pixel x' - dx + 1
-            float v[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) v[j] = r[j];
-            store_split8(Zs + (size_t)(dx * 4 + co / 8) * kWgGBytes + kg * kWgCore + (co % 8) * 16, kWgBPart, v);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
-        tmem_fence_before_sync();
-        __syncthreads();
-        tmem_fence_after_sync();
-        if (tid == 0) {
-            const uint32_t a0 = smem_u32(As), z0 = smem_u32(Zs);
-            // (A part, Z part), smallest product first: lo*hi, mid*mid, hi*lo, mid*hi, hi*mid, hi*hi
-            const int pa[6] = {2, 1, 0, 1, 0, 0}, pz[6] = {0, 1, 2, 0, 1, 0};
+            for (int q = 0; q < 6; q++) {
+                const uint64_t ad = umma_desc(a0 + (uint32_t)(pa[q] * kWgAPart + 2 * ks * kWgCore), kWgCore, kWgGBytes);
+                const uint64_t zd = umma_desc(z0 + (uint32_t)(pz[q] * kWgBPart + 2 * ks * kWgCore), kWgCore, kWgGBytes);
+                umma_f16(tmem, ad, zd, idesc, started ? 1u : 0u);
+                started = true;
+            }
+        umma_commit(done);
+    };
+    float va[8], vz[10];  // raw values of the next unit
+    float dbacc = 0.f;
+    // a unit's operands from the raw registers: the new activation row (all three when the
+    // unit starts a column) and the dz row
+    auto stage = [&](int u, bool fresh) {
+        int b, x0, y;
+        geo(u, b, x0, y);
+        if (arow) {
+            if (fresh) {
 #pragma unroll 1
-            for (int ks = 0; ks < kWgKC / 16; ks++)
-#pragma unroll
-                for (int q = 0; q < 6; q++) {
-                    const uint64_t ad =
-                        umma_desc(a0 + (uint32_t)(pa[q] * kWgAPart + 2 * ks * kWgCore), kWgCore, kWgGBytes);
-                    const uint64_t zd =
-                        umma_desc(z0 + (uint32_t)(pz[q] * kWgBPart + 2 * ks * kWgCore), kWgCore, kWgGBytes);
-                    umma_f16(tmem, ad, zd, idesc, started ? 1u : 0u);
-                    started = true;
+                for (int dy = 0; dy < 3; dy++) {
+                    load_arow<P>(a, b, y - 1 + dy, x0, tid, va);
+                    store_arow(As, y - 1 + dy, tid, va);
                 }
-            umma_commit(done);
+            } else {
+                store_arow(As, y + 1, tid, va);
+            }
+        } else {
+            store_zrow(Zs, tz, vz);
+#pragma unroll
+            for (int j = 1; j <= 8; j++) dbacc += vz[j];
         }
-        if (next_starts) load_rows(u + 1, 0, 3, i + 1);  // the split above has read the ring
+    };
+    auto prefetch = [&](int u) {
+        if (u >= u1) return;
+        int b, x0, y;
+        geo(u, b, x0, y);
+        if (arow) {
+            if (y != 0) load_arow<P>(a, b, y + 1, x0, tid, va);  // a unit continuing its column
+        } else {
+            load_zrow<P>(dz, b, y, x0, tz, vz);
+        }
+    };
+
+    prefetch(u0);
+    stage(u0, true);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    issue(u0);
+    prefetch(u0 + 1);
+    bool ok = true;
+    int i = 0;
+#pragma unroll 1
+    for (int u = u0; u < u1; u++, i++) {
         ok = mbar_wait(done, (uint32_t)(i & 1), spin_limit);
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        ok = __syncthreads_and(ok) != 0;  // the MMAs have read the tiles; the next rows have landed
+        ok = __syncthreads_and(ok) != 0;  // the unit's MMAs have read both operands
         if (!ok) {
             if (tid == 0) atomicOr(err, 1);
             mbar_wait(done, (uint32_t)(i & 1));
             break;
         }
+        if (u + 1 >= u1) break;
+        // the next unit's new row goes to the slot of row y - 1 of this unit (read above)
+        stage(u + 1, (u + 1) % P == 0);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        issue(u + 1);
+        prefetch(u + 2);  // the registers were stored above
     }
     if (ok) {
-        // warps 0..3: TMEM lane quarter w = rows m = 32 w + lane (m = dy * 32 + ci; m = 96: db),
-        // columns 32 dx + co
+        // warps 0..3: TMEM lane quarter w = rows m = 32 w + lane (m = dy * 32 + ci), columns
+        // 32 dx + co; warps 4..7: db from the dz threads' sums (4 threads per channel)
         tmem_fence_after_sync();
+        float *pb = part + (size_t)blockIdx.x * NPL;
         if (warp < 4) {
             const int m = 32 * warp + lane;
-            float *pb = part + (size_t)blockIdx.x * NPL;
 #pragma unroll 1
             for (int dx = 0; dx < 3; dx++) {
                 float v[32];
@@ -459,11 +511,12 @@ __global__ void __launch_bounds__(kTcNT, 3)
                     const int dy = m / kC, ci = m % kC;
 #pragma unroll
                     for (int co = 0; co < kC; co++) pb[((size_t)co * kC + ci) * 9 + dy * 3 + dx] = v[co];
-                } else if (m == 96 && dx == 1) {
-#pragma unroll
-                    for (int co = 0; co < kC; co++) pb[kC * kC * 9 + co] = v[co];
                 }
             }
+        } else {
+            dbacc += __shfl_xor_sync(0xffffffffu, dbacc, 1);
+            dbacc += __shfl_xor_sync(0xffffffffu, dbacc, 2);
+            if (tz % 4 == 0) pb[kC * kC * 9 + tz / 4] = dbacc;
         }
     }
     tmem_fence_before_sync();
@@ -475,9 +528,8 @@ __global__ void __launch_bounds__(kTcNT, 3)
 
 bool wgrad_tc_supported(int P, int cin, int cout) { return cin == kC && cout == kC && (P == 128 || P == 256); }
 
-// One wave (at most kWgGrid CTAs) and never more partials than the CUDA-core kernel writes
-// (B * P / 16, which the caller's partial buffer holds); every CTA gets at least P / 2 units.
-int wgrad_tc_blocks(int P, int B) { return std::min(kWgGrid, B * (P / kWgTcRB)); }
+// One wave (at most kWgGrid CTAs), at least 32 units per CTA.
+int wgrad_tc_blocks(int P, int B) { return std::max(1, std::min(kWgGrid, B * (P / kWgKC) * P / 32)); }
 
 cudaError_t launch_wgrad_tc(int P, int B, const float *a, const float *dz, float *part, int *err, cudaStream_t s)
 {

@@ -45,7 +45,7 @@ constexpr int kRowBytes = kGroups * kGroupBytes;   // one staged row, all channe
 constexpr int kPartBytes = 3 * kRowBytes;          // one BF16 part of the three rows
 constexpr int kABytes = 3 * kPartBytes;            // hi, mid, lo
 constexpr int kBBytes = 9 * kGroups * kC * 16;     // weights [tap][group][co][8 ci]
-constexpr size_t kTcSmem = (size_t)kABytes + kBBytes + 64;
+constexpr size_t kTcSmem = (size_t)kABytes + kBBytes + 64 + 256;  // + the halo copies of the next row
 static_assert(kGroupBytes % 16 == 0 && kPartBytes % 128 == 0 && kABytes % 128 == 0, "layout");
 
 constexpr float kInvSqrt2PiTc = 0.398942280401432678f;
@@ -63,6 +63,49 @@ __host__ __device__ constexpr uint32_t conv_idesc()
 
 __device__ __forceinline__ uint32_t pack2(uint16_t lo, uint16_t hi) { return (uint32_t)lo | ((uint32_t)hi << 16); }
 
+// Four bytes global -> shared without a register round trip; src_ok = false writes zero.
+__device__ __forceinline__ void cp_async4(float *dst, const float *src, bool src_ok)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_ok ? 4 : 0)
+                 : "memory");
+}
+
+// The 16 channels of channel half `half` at staged pixel p (pixel x0 + p - 1) split into the
+// three BF16 parts of row slot `slot`.
+__device__ __forceinline__ void split_px(uint8_t *As, int slot, int p, int half, const float (&v)[16])
+{
+#pragma unroll
+    for (int gg = 0; gg < 2; gg++) {
+        const int g = 2 * half + gg;
+        uint16_t hb[8], mb[8], lb[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const float a = v[8 * gg + j];
+            hb[j] = to_half_bits<true>(a);
+            const float r1 = a - from_half_bits<true>(hb[j]);
+            mb[j] = to_half_bits<true>(r1);
+            lb[j] = to_half_bits<true>(r1 - from_half_bits<true>(mb[j]));
+        }
+        const size_t off = (size_t)slot * kRowBytes + (size_t)g * kGroupBytes + (size_t)p * 16;
+        *(uint4 *)(As + off) =
+            make_uint4(pack2(hb[0], hb[1]), pack2(hb[2], hb[3]), pack2(hb[4], hb[5]), pack2(hb[6], hb[7]));
+        *(uint4 *)(As + kPartBytes + off) =
+            make_uint4(pack2(mb[0], mb[1]), pack2(mb[2], mb[3]), pack2(mb[4], mb[5]), pack2(mb[6], mb[7]));
+        *(uint4 *)(As + 2 * kPartBytes + off) =
+            make_uint4(pack2(lb[0], lb[1]), pack2(lb[2], lb[3]), pack2(lb[4], lb[5]), pack2(lb[6], lb[7]));
+    }
+}
+
+// The 16 channels of half `half` of input row yy (zero outside the image) at pixel x.
+template <int P>
+__device__ __forceinline__ void load_px(const float *__restrict__ in, int b, int yy, int x, int half, float (&v)[16])
+{
+    const bool in_img = yy >= 0 && yy < P && x >= 0 && x < P;
+    const float *src = in + (((size_t)b * kC + 16 * half) * P + (in_img ? yy : 0)) * P + (in_img ? x : 0);
+#pragma unroll
+    for (int ci = 0; ci < 16; ci++) v[ci] = in_img ? __ldg(src + (size_t)ci * P * P) : 0.0f;
+}
+
 // Stage input row yy (zero outside the image) of image b, pixels x0 - 1 .. x0 + 128, into row
 // slot `slot` of the three BF16 parts: thread t takes pixel t % 128 and channel half t / 128;
 // threads with t % 128 < 2 also one halo pixel.
@@ -70,37 +113,29 @@ template <int P>
 __device__ __forceinline__ void stage_row(uint8_t *As, const float *__restrict__ in, int b, int yy, int x0, int slot)
 {
     const int px = threadIdx.x % kNpx, half = threadIdx.x / kNpx;
-    const bool row_in = yy >= 0 && yy < P;
 #pragma unroll 1
     for (int h = 0; h < (px < 2 ? 2 : 1); h++) {
         const int p = h == 0 ? px + 1 : (px == 0 ? 0 : kNpx + 1);  // staged index: pixel x0 + p - 1
-        const int x = x0 + p - 1;
-        const bool in_img = row_in && x >= 0 && x < P;
-        const float *src = in + (((size_t)b * kC + 16 * half) * P + (in_img ? yy : 0)) * P + (in_img ? x : 0);
         float v[16];
-#pragma unroll
-        for (int ci = 0; ci < 16; ci++) v[ci] = in_img ? __ldg(src + (size_t)ci * P * P) : 0.0f;
-#pragma unroll
-        for (int gg = 0; gg < 2; gg++) {
-            const int g = 2 * half + gg;
-            uint16_t hb[8], mb[8], lb[8];
-#pragma unroll
-            for (int j = 0; j < 8; j++) {
-                const float a = v[8 * gg + j];
-                hb[j] = to_half_bits<true>(a);
-                const float r1 = a - from_half_bits<true>(hb[j]);
-                mb[j] = to_half_bits<true>(r1);
-                lb[j] = to_half_bits<true>(r1 - from_half_bits<true>(mb[j]));
-            }
-            const size_t off = (size_t)slot * kRowBytes + (size_t)g * kGroupBytes + (size_t)p * 16;
-            *(uint4 *)(As + off) =
-                make_uint4(pack2(hb[0], hb[1]), pack2(hb[2], hb[3]), pack2(hb[4], hb[5]), pack2(hb[6], hb[7]));
-            *(uint4 *)(As + kPartBytes + off) =
-                make_uint4(pack2(mb[0], mb[1]), pack2(mb[2], mb[3]), pack2(mb[4], mb[5]), pack2(mb[6], mb[7]));
-            *(uint4 *)(As + 2 * kPartBytes + off) =
-                make_uint4(pack2(lb[0], lb[1]), pack2(lb[2], lb[3]), pack2(lb[4], lb[5]), pack2(lb[6], lb[7]));
-        }
+        load_px<P>(in, b, yy, x0 + p - 1, half, v);
+        split_px(As, slot, p, half, v);
     }
+}
+
+// The halo pixel (staged index 0 for t % 128 = 0, 129 for t % 128 = 1) of input row yy, 16
+// channels of half t / 128, copied into H[(t % 128) * 32 + 16 half + ci] by cp.async (zeros
+// outside the image).
+template <int P>
+__device__ __forceinline__ void halo_async(float *H, const float *__restrict__ in, int b, int yy, int x0)
+{
+    const int px = threadIdx.x % kNpx, half = threadIdx.x / kNpx;
+    if (px >= 2) return;
+    const int x = x0 + (px == 0 ? -1 : kNpx);
+    const bool in_img = yy >= 0 && yy < P && x >= 0 && x < P;
+    const float *src = in + (((size_t)b * kC + 16 * half) * P + (in_img ? yy : 0)) * P + (in_img ? x : 0);
+#pragma unroll
+    for (int ci = 0; ci < 16; ci++) cp_async4(H + px * 32 + 16 * half + ci, src + (size_t)ci * P * P, in_img);
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // Row slot of input row yy (yy >= -1) in the three-row ring.
@@ -118,6 +153,7 @@ __global__ void __launch_bounds__(kTcNT, 2)
     uint8_t *As = sm, *Bs = sm + kABytes;
     uint64_t *done = (uint64_t *)(sm + kABytes + kBBytes);
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    float *H = (float *)(sm + kABytes + kBBytes + 64);  // halo pixels of the next row [2][32]
     const int tid = threadIdx.x, warp = tid >> 5;
     // tiles in strip-major order (image b, strip of 128 columns, row y fastest); CTA c takes
     // the contiguous range [c chunk, (c + 1) chunk), so consecutive tiles of a CTA are
@@ -142,19 +178,37 @@ __global__ void __launch_bounds__(kTcNT, 2)
     const uint32_t tmem = *tmem_slot;
     const uint32_t idesc = conv_idesc();
 
+    // The new input row of the next tile is loaded (this thread's pixel into registers, the
+    // halo pixels by cp.async) right after this tile's MMAs are issued, so its latency is spent
+    // behind the MMAs and the epilogue; it is split at the top of the next iteration.
     int it = 0, prev_strip = -1, prev_y = -2;
+    bool have_pf = false;
+    float vpf[16];
     for (int tile = t0; tile < t1; tile++, it++) {
         const int strip = tile / P, y = tile % P;  // strip = b * TPR + column strip
         const int b = strip / TPR, x0 = (strip % TPR) * kNpx;
         // ---- input rows: only the new one when the previous tile was the row above
         if (strip == prev_strip && y == prev_y + 1) {
-            stage_row<P>(As, in, b, y + 1, x0, ring_slot(y + 1));
+            if (have_pf) {
+                const int px = tid % kNpx, half = tid / kNpx;
+                split_px(As, ring_slot(y + 1), px + 1, half, vpf);
+                if (px < 2) {
+                    asm volatile("cp.async.wait_all;" ::: "memory");  // this thread's halo copies
+                    float hv[16];
+#pragma unroll
+                    for (int ci = 0; ci < 16; ci++) hv[ci] = H[px * 32 + 16 * half + ci];
+                    split_px(As, ring_slot(y + 1), px == 0 ? 0 : kNpx + 1, half, hv);
+                }
+            } else {
+                stage_row<P>(As, in, b, y + 1, x0, ring_slot(y + 1));
+            }
         } else {
 #pragma unroll 1
             for (int dy = 0; dy < 3; dy++) stage_row<P>(As, in, b, y - 1 + dy, x0, ring_slot(y - 1 + dy));
         }
         prev_strip = strip;
         prev_y = y;
+        have_pf = false;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor core
         tmem_fence_before_sync();
         __syncthreads();
@@ -181,6 +235,11 @@ __global__ void __launch_bounds__(kTcNT, 2)
                         n++;
                     }
             umma_commit(done);  // arrives once every MMA of the tile has completed
+        }
+        if (tile + 1 < t1 && (tile + 1) % P != 0) {  // the next tile continues the strip: row y + 2
+            load_px<P>(in, b, y + 2, x0 + tid % kNpx, tid / kNpx, vpf);
+            halo_async<P>(H, in, b, y + 2, x0);
+            have_pf = true;
         }
         // ---- epilogue: warp w reads lanes 32 (w % 4) .. + 31 (pixels), channels 16 (w / 4) .. + 15
         bool ok = mbar_wait(done, (uint32_t)(it & 1), spin_limit);
@@ -210,6 +269,7 @@ __global__ void __launch_bounds__(kTcNT, 2)
         tmem_fence_before_sync();
         __syncthreads();  // TMEM read and staged rows free for the next tile
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
     tmem_fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 32);

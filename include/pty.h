@@ -88,7 +88,7 @@ typedef struct {
                             or 32, or 0 (default) for an adaptive search: with dft = 0 the
                             leading trials that a lower bound of the objective change
                             (Jensen's inequality on the concave log, per pattern) rejects are
-                            skipped, and the first pass of 8, 16 or 32 trials starts at the
+                            skipped, and the first pass of 6, 8, 16 or 32 trials starts at the
                             first trial the bound cannot reject, sized from the previous
                             iteration; then passes of 32.  The accepted step and the trial
                             count do not depend on it */

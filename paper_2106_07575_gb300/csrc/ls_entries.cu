@@ -30,14 +30,23 @@ constexpr int kNT = 256;
 // 608 CTAs 0.149, 1216 0.139, 1824 0.128-0.132, 2280 0.132, 3600 0.131 ms).
 constexpr int kBlocks = 152 * 12;
 
+// Values of a window's block sum: L rounded up to a power of two, so that the float-float
+// reduction takes its recursive-halving form (the padding values are zero).
+template <int L>
+constexpr int reduced_width()
+{
+    return L <= 4 ? 4 : L <= 8 ? 8 : L <= 16 ? 16 : 32;
+}
+
 template <int L>
 __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V, float2 *__restrict__ part,
                                                     const DevState *__restrict__ sts)
 {
     // one view: a window with nothing to evaluate ends the whole launch at once
     if (V == 1 && (sts->stalled || sts->decided || sts->Lsel != L)) return;
-    __shared__ float2 red[(kNT / 32) * L];
-    __shared__ float2 tot[L];
+    constexpr int LR = reduced_width<L>();
+    __shared__ float2 red[(kNT / 32) * LR];
+    __shared__ float2 tot[LR];
     const int nunits = a.K * cs;
     const size_t KC = (size_t)nunits;
     float2 cta = make_float2(0.f, 0.f);  // one view: thread l < L sums candidate l over the CTA's units
@@ -106,7 +115,10 @@ __global__ void __launch_bounds__(kNT) k_ls_entries(PatternArgs a, int cs, int V
                 }
             }
         }
-        block_sum_ff<kNT, L>(acc, red, tot);  // ends with a barrier: red is free again
+        float accr[LR];
+#pragma unroll
+        for (int l = 0; l < LR; l++) accr[l] = l < L ? acc[l] : 0.0f;
+        block_sum_ff<kNT, LR>(accr, red, tot);  // ends with a barrier: red is free again
         if (V == 1) {
             if (threadIdx.x < L) cta = ff_add(cta, tot[threadIdx.x]);
         } else if (threadIdx.x < L) {
@@ -129,6 +141,7 @@ cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, float2
     const int nb = a.K * cs < kBlocks ? a.K * cs : kBlocks;
     switch (L) {
     case 4: k_ls_entries<4><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
+    case 6: k_ls_entries<6><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
     case 8: k_ls_entries<8><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
     case 16: k_ls_entries<16><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;
     case 32: k_ls_entries<32><<<nb, kNT, 0, s>>>(a, cs, V, part, st); break;

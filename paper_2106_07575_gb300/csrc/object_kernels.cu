@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kDecNT) k_ls_decide(const float2 *__restrict__
 // sums, exact) the view's bound is LB_j <= F(psi + gamma_j eta) - F(psi).  Every leading trial
 // with LB_j above the acceptance threshold gamma_j t by more than a rounding margin would be
 // rejected by the plain search, so the first window opens at the first trial the bound cannot
-// reject; its size (8, 16 or 32 trials) follows the previous iteration's distance between that
+// reject; its size (6, 8, 16 or 32 trials) follows the previous iteration's distance between that
 // trial and the accepted one.  Accepted step and trial count are those of the plain search.
 __global__ void __launch_bounds__(kDecNT) k_ls_certify(const float2 *__restrict__ part, int kc, int cs, int ls_cols,
                                                        ViewMap vm, const float2 *__restrict__ vpart, double vscale,
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kDecNT) k_ls_certify(const float2 *__restrict_
         st->k0 = k0;
         st->k0cert = k0;
         const int Le = st->last_halvings > 0 ? st->last_excess + 2 : 16;
-        const int Ls = Le <= 8 ? 8 : (Le <= 16 ? 16 : 32);
+        const int Ls = Le <= 6 ? 6 : (Le <= 8 ? 8 : (Le <= 16 ? 16 : 32));
         st->Leff = Ls;
         st->Lsel = Ls;
         open_window(st, ls.gamma0, ls.tau);

@@ -522,8 +522,10 @@ int launch_iteration(pty_ctx *c, bool timed)
                 CK(pty::launch_ls_entries(a, c->CSl, c->V, 4, c->part_ls, c->st, c->s));
                 CK(pty::launch_ls_entries(a, c->CSl, c->V, 8, c->part_ls, c->st, c->s));
             }
-            if (wdx == 0 && ls.adaptive && c->cert)
+            if (wdx == 0 && ls.adaptive && c->cert) {
+                CK(pty::launch_ls_entries(a, c->CSl, c->V, 6, c->part_ls, c->st, c->s));
                 CK(pty::launch_ls_entries(a, c->CSl, c->V, 8, c->part_ls, c->st, c->s));
+            }
             if (wdx == 0 && ls.adaptive) CK(pty::launch_ls_entries(a, c->CSl, c->V, 16, c->part_ls, c->st, c->s));
             CK(pty::launch_ls_entries(a, c->CSl, c->V, ls.L, c->part_ls, c->st, c->s));
         }

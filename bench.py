@@ -643,10 +643,10 @@ def main():
     first_w = 4 if L == 0 else L
     nwin = 1 + (max(0, opts.max_halvings - first_w) + Lcap - 1) // Lcap
     # per iteration: grad (full and linear form, one returns at once), scatter, dy_finalize,
-    # eta, LS pass, windows (entries + decide; the adaptive first window launches the 8-, 16-
-    # and 32-candidate entry kernels, all but one returning at once, after the certificate
+    # eta, LS pass, windows (entries + decide; the adaptive first window launches the 6-, 8-,
+    # 16- and 32-candidate entry kernels, all but one returning at once, after the certificate
     # kernel), update + counters; per call: 2 hashes, hash check, begin, hash store
-    launches = args.steps * (8 + 2 * nwin + (3 if L == 0 else 0)) + 5 if args.dft == 0 else None
+    launches = args.steps * (8 + 2 * nwin + (4 if L == 0 else 0)) + 5 if args.dft == 0 else None
     value = units / (ms * 1e-3)
 
     out = {

@@ -95,7 +95,9 @@ typedef struct {
     int32_t flags;       /* bit 0: record per-stage GPU time (pty_stage_times); bit 1: no
                             linear form (every GRAD pass runs the forward DFT); bit 2: no
                             certified skip of leading trials (adaptive search only); bit 4:
-                            scatter-add with per-thread loads instead of tensor copies */
+                            scatter-add with per-thread loads instead of tensor copies; bit 5:
+                            the linear GRAD pass zeroes its spectrum tile instead of reading
+                            only the slots that hold counts (P <= 128; same results) */
     int32_t tile_config; /* pattern-kernel configuration: -1 (default) = autotune at
                             pty_create (the GRAD and LS passes of every configuration for P are
                             timed on the problem's own data; the choice is cached per problem

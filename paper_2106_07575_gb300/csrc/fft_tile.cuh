@@ -281,6 +281,35 @@ __device__ __forceinline__ void cols_fft(float2 *buf, const float2 *tw)
     __syncthreads();
 }
 
+// Items per thread of a single-CTA block pass over the P columns (P * R1 items).
+template <int P, int NT>
+constexpr int block_items()
+{
+    return P * Tile<P>::R1 / NT;
+}
+
+// The column block pass of the inverse transform of a single-CTA tile whose slots outside a
+// mask hold no value (their contents are ignored and read as zero): mw[q] holds, from bit
+// 0, the mask bits of the R2 elements of the thread's q-th item (column t % P, rows R2 k1 ..
+// R2 k1 + R2 - 1, k1 = t / P, t = threadIdx.x + q NT).  The same results as zeroing those
+// slots first.
+template <int P, int NT>
+__device__ __forceinline__ void pass_block_cols_masked(float2 *buf, const unsigned (&mw)[block_items<P, NT>()])
+{
+    constexpr int R2 = Tile<P>::R2, LDB = P + 1;
+#pragma unroll
+    for (int q = 0; q < block_items<P, NT>(); q++) {
+        const int t = threadIdx.x + q * NT, line = t % P, k1 = t / P;
+        float2 *b = buf + line + (R2 * k1) * LDB;
+        float2 x[R2];
+#pragma unroll
+        for (int j = 0; j < R2; j++) x[j] = (mw[q] >> j) & 1u ? b[j * LDB] : make_float2(0.f, 0.f);
+        dft_reg<R2, +1>(x);
+#pragma unroll
+        for (int j = 0; j < R2; j++) b[j * LDB] = x[j];
+    }
+}
+
 // Row slab -> column slab across the cluster (all CTAs of the cluster call it).
 // Every value is read into registers, the cluster synchronises (all reads done, the
 // buffers are free), every value is stored into its owner's buffer, the cluster
@@ -441,11 +470,21 @@ __device__ __forceinline__ void fft2_fwd_in(float2 *buf, const float2 *tw, const
 }
 
 // Unnormalised inverse 2-D DFT of one tile (permuted order in), the natural-order rows of
-// the result handed to st (see rows_stride_inv_out).  No barrier at the end.
+// the result handed to st (see rows_stride_inv_out).  No barrier at the end.  With mw, only
+// the masked slots of the input are read (pass_block_cols_masked).
 template <int P, int NT, typename ST>
-__device__ __forceinline__ void fft2_inv_out(float2 *buf, const float2 *tw, const float2 *tw2, ST st)
+__device__ __forceinline__ void fft2_inv_out(float2 *buf, const float2 *tw, const float2 *tw2, ST st,
+                                             const unsigned (*mw)[block_items<P, NT>()] = nullptr)
 {
-    cols_fft<P, P, NT, +1>(buf, tw);
+    if (mw) {
+        pass_block_cols_masked<P, NT>(buf, *mw);
+        if constexpr (grouped_tile<P, P, NT>()) col_group_sync();
+        else __syncthreads();
+        pass_stride<P, NT, P, 1, P + 1, +1>(buf, tw);
+        __syncthreads();
+    } else {
+        cols_fft<P, P, NT, +1>(buf, tw);
+    }
     if constexpr (grouped_tile<P, P, NT>()) {
         pass_block_rows_grouped<P, NT, +1>(buf);
         row_group_sync();

@@ -589,6 +589,27 @@ cudaError_t launch_ls_certify(const float2 *part, int kc, int cs, int ls_cols, c
     return cudaGetLastError();
 }
 
+// One block per pattern: the bits of its entry slots (PatternArgs::nz_mask).
+__global__ void __launch_bounds__(256) k_nz_mask(const long long *__restrict__ off, int nzc,
+                                                 const unsigned short *__restrict__ slot, int P,
+                                                 unsigned *__restrict__ mask)
+{
+    const int i = blockIdx.x;
+    const long long e0 = off[(size_t)i * nzc], e1 = off[(size_t)(i + 1) * nzc];
+    unsigned *m = mask + (size_t)i * (P * P / 32);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const int sl = slot[e], qy = sl / P, qx = sl % P;
+        atomicOr(m + qx * (P / 32) + qy / 32, 1u << (qy % 32));
+    }
+}
+
+cudaError_t launch_nz_mask(const PatternArgs &a, int P, unsigned *mask, cudaStream_t s)
+{
+    if (P % 32 != 0 || a.K < 1) return cudaErrorInvalidValue;
+    k_nz_mask<<<a.K, 256, 0, s>>>(a.nz_off, a.nzc, a.nz_slot, P, mask);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_chunk_dsum(const PatternArgs &a, int cs, float *dsum, cudaStream_t s)
 {
     k_chunk_dsum<<<a.K * cs, kSumNT, 0, s>>>(a, cs, dsum);

@@ -468,15 +468,32 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int per = a.nzc / CS;
     const long long e0 = a.nz_off[i * a.nzc + c * per], e1 = a.nz_off[i * a.nzc + (c + 1) * per];
+    // single CTA with the entry masks: the first inverse pass reads only the entry slots, so
+    // the tile is not zeroed (the caller's barrier already ordered the previous pattern's
+    // reads before the entries' writes); the mask words are loaded first
+    constexpr int NI = R == P ? block_items<P, NT>() : 1;
+    const bool masked = R == P && a.nz_mask != nullptr;
+    unsigned mw[NI];
+    if (masked) {
+        constexpr int R2 = Tile<P>::R2;
+        const unsigned *m = a.nz_mask + (size_t)i * (P * P / 32);
+#pragma unroll
+        for (int q = 0; q < NI; q++) {
+            const int t = threadIdx.x + q * NT, line = t % P, k1 = t / P;
+            mw[q] = __ldg(m + line * (P / 32) + (R2 * k1) / 32) >> ((R2 * k1) % 32);
+        }
+    }
     // the thread's first two entries are loaded before the zeroing, which hides their latency
     EntryIn first[2];
 #pragma unroll
     for (int q = 0; q < 2; q++) first[q].load(a, e0 + threadIdx.x + q * NT, e1);
-    // the column slab (permuted spectrum order) starts at zero
-    static_assert((P * LDB) % 2 == 0, "16-byte zeroing");
-    for (int e = threadIdx.x; e < P * LDB / 2; e += NT)
-        reinterpret_cast<float4 *>(buf)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    __syncthreads();
+    if (!masked) {
+        // the column slab (permuted spectrum order) starts at zero
+        static_assert((P * LDB) % 2 == 0, "16-byte zeroing");
+        for (int e = threadIdx.x; e < P * LDB / 2; e += NT)
+            reinterpret_cast<float4 *>(buf)[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+    }
     float f = 0.0f;
     auto entry = [&](long long e, const EntryIn &x) {
         const float2 u = make_float2(fmaf(gam, x.v.x, x.u.x), fmaf(gam, x.v.y, x.u.y));
@@ -505,7 +522,8 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
         if (threadIdx.x == 0) fpart[i * CS + c] = tot[0];
     }
     if constexpr (R == P) {  // the last row step hands its rows to the emit
-        fft2_inv_out<P, NT>(buf, tw, tw + P, AdjointStorer<P, NT>{pc, probe_of(a, i), w + (size_t)i * P * P});
+        fft2_inv_out<P, NT>(buf, tw, tw + P, AdjointStorer<P, NT>{pc, probe_of(a, i), w + (size_t)i * P * P},
+                            masked ? &mw : nullptr);
     } else {
         fft2_inv<P, R, NT>(buf, tw);
         emit_adjoint<P, R, NT>(a, buf, w, i, c);

@@ -72,6 +72,7 @@ struct pty_ctx {
     float2 *nz_u = nullptr;             // [E]
     float2 *nz_v = nullptr;             // [E]
     long long n_entries = 0;
+    unsigned *nz_mask = nullptr;  // entry slots per pattern (PatternArgs::nz_mask), P <= 128
     int *tile_start = nullptr, *tile_list = nullptr;
     int ntile_y = 0, ntile_x = 0;
 
@@ -172,7 +173,7 @@ cudaError_t dalloc(T **p, size_t n)
 void free_all(pty_ctx *c)
 {
     void *ptrs[] = {c->probe,      c->tw,         c->pos,        c->perm,      c->pat_view,     c->view_pat_off,
-                    c->view_tile_off, c->row_view, c->tile_view,  c->nz_off,    c->nz_slot,      c->nz_d,
+                    c->view_tile_off, c->row_view, c->tile_view,  c->nz_off,    c->nz_slot,      c->nz_d, c->nz_mask,
                     c->nz_u,       c->nz_v,       c->tile_start, c->tile_list,  c->w,         c->fpart,        c->part_sc,
                     c->part_ls,    c->psi,        c->g,          c->g_prev,    c->eta_prev,     c->st,
                     c->dscalar,    c->hist.F,     c->hist.gamma, c->hist.halvings, c->hist.alpha, c->stage_obj,
@@ -200,6 +201,7 @@ pty::PatternArgs pattern_args(const pty_ctx *c)
     a.pos = c->pos;
     a.perm = c->perm;
     a.nz_off = c->nz_off;
+    a.nz_mask = c->nz_mask;
     a.nzc = c->nzc;
     a.nz_slot = c->nz_slot;
     a.nz_d = c->nz_d;
@@ -969,6 +971,13 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(c->nz_off, hoff.data(), sizeof(long long) * (KC + 1), cudaMemcpyHostToDevice, c->s);
     if (ce == cudaSuccess) ce = c->impl_nz->nz_fill(dd, c->perm, (int)K, c->nz_off, c->nz_slot, c->nz_d, c->s);
+    // the entry slots as bit masks for the linear GRAD pass (unless opts.flags bit 5)
+    if (ce == cudaSuccess && P <= 128 && !(o.flags & 32)) {
+        const size_t words = (size_t)K * P * P / 32;
+        ce = dalloc(&c->nz_mask, words);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(c->nz_mask, 0, sizeof(unsigned) * words, c->s);
+        if (ce == cudaSuccess) ce = pty::launch_nz_mask(pattern_args(c), P, c->nz_mask, c->s);
+    }
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s);
     free_tmp();
     if (ce != cudaSuccess)

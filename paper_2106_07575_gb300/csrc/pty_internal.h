@@ -81,6 +81,10 @@ struct PatternArgs {
     // [K * CS] sum of the counts of each (pattern, CTA) chunk of the LS configuration; set
     // when the LS pass also writes the certificate rows (else nullptr)
     const float *dsum;
+    // [K][P * P / 32] (P <= 128, else nullptr): bit qx * P + qy of pattern i's mask is set when
+    // the spectrum slot (qy, qx) of the tile holds an entry (word qx * P / 32 + qy / 32, bit
+    // qy % 32), so that the linear GRAD pass reads only those slots instead of zeroing the tile
+    const unsigned *nz_mask = nullptr;
 };
 
 // Line-search window description (device scalars come from DevState).
@@ -150,6 +154,8 @@ cudaError_t launch_selftest_log1p(const float *t, float *out, int n, cudaStream_
 int ls_entries_cols(const PatternArgs &a, int cs, int V);
 cudaError_t launch_ls_entries(const PatternArgs &a, int cs, int V, int L, float2 *part, const DevState *st,
                               cudaStream_t s);
+// PatternArgs::nz_mask of the K patterns from the entries (mask zeroed by the caller).
+cudaError_t launch_nz_mask(const PatternArgs &a, int P, unsigned *mask, cudaStream_t s);
 
 // ---- tensor-core DFT (tc_dft.cu) ----
 // One application: Y[b][k][y] = sum_n X[b][y][n] exp(sign 2 pi i n k / P) for the nrows =

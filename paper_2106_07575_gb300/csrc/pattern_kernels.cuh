@@ -354,8 +354,7 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
     }
 }
 
-// Single-CTA configurations (CS = 1) run persistently: the CTAs of the grid stride over
-// the patterns.  Clusters run one pattern each.
+// Persistent passes: the CTAs (CS = 1) or clusters of the grid stride over the patterns.
 template <int P, int R, int NT>
 __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, const float2 *__restrict__ psi,
                                              float2 *__restrict__ w, float2 *__restrict__ fpart,
@@ -397,9 +396,14 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
         }
         if (cached) pc.release();
     } else {
-        const int i = blockIdx.x / CS;
-        if (skip(i)) return;  // uniform over the cluster
-        grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr, nullptr);
+        // persistent clusters: each strides over the patterns (the pattern's first exchange
+        // starts with a cluster barrier, so a peer writes into this CTA's slab only after
+        // this CTA has finished with the previous pattern)
+        for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {
+            if (skip(i)) continue;  // uniform over the cluster
+            __syncthreads();        // this CTA's reads of buf for the previous pattern are done
+            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr, nullptr);
+        }
     }
 }
 
@@ -570,10 +574,13 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
         }
         if (cached) pc.release();
     } else {
-        const int i = blockIdx.x / CS;
-        const DevState *st = sts + a.pat_view[i];
-        if (st->stalled || !st->lin) return;  // uniform over the cluster
-        grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c, nullptr, nullptr);
+        for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {  // persistent clusters (k_grad)
+            const DevState *st = sts + a.pat_view[i];
+            if (st->stalled || !st->lin) continue;  // uniform over the cluster
+            __syncthreads();
+            grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c, nullptr,
+                                       nullptr);
+        }
     }
 }
 
@@ -733,10 +740,12 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
         }
         if (cached) pc.release();
     } else {
-        const int i = blockIdx.x / CS;
-        if (sts[a.pat_view[i]].stalled) return;  // uniform over the cluster
-        const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, c, nullptr);
-        if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i * CS + c] = r;
+        for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {  // persistent clusters (k_grad)
+            if (sts[a.pat_view[i]].stalled) continue;  // uniform over the cluster
+            __syncthreads();
+            const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, c, nullptr);
+            if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i * CS + c] = r;
+        }
     }
 }
 
@@ -835,13 +844,35 @@ cudaError_t launch_pattern(void (*kern)(KArgs...), int nblocks, int nthreads, si
 }
 
 // Grid of a persistent pattern kernel: with one CTA per pattern (cs = 1), the CTAs that fit
-// on the device at once (by the kernel's occupancy), at most one per pattern; clusters
-// (cs > 1) keep one cluster per pattern, since co-resident clusters are fewer than the
-// per-CTA occupancy suggests and a static stride would serialise the others.
+// on the device at once (by the kernel's occupancy), at most one per pattern; with clusters
+// (cs > 1), the clusters that fit at once (cudaOccupancyMaxActiveClusters: fewer than the
+// per-CTA occupancy suggests), each striding over the patterns.  Spiral workload (P = 256,
+// 10,000 positions): 13.82 -> 12.97 ms per iteration against one cluster per pattern.
 template <typename... KArgs>
 int persistent_blocks(void (*kern)(KArgs...), int nslices, int nthreads, size_t smem, int cs)
 {
-    if (cs > 1) return nslices;
+    if (cs > 1) {
+        // the clusters that fit on the device at once, at most one per pattern
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)nslices);
+        cfg.blockDim = dim3((unsigned)nthreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)cs;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+            cudaOccupancyMaxActiveClusters(&ncl, kern, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            return nslices;
+        }
+        const long long g = (long long)ncl * cs;
+        return g < nslices ? (int)g : nslices;
+    }
     int dev = 0, nsm = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||

@@ -143,6 +143,83 @@ struct ProbeCache {
     }
 };
 
+// Probe cache in tensor memory for the row slab of a cluster CTA (R < P): the gather of an
+// exit wave (gather_rows) and the emit of an adjoint result (emit_adjoint) both visit slab
+// element e = t + k NT (row e / P, column e % P) in thread t, so the thread's NE = R P / NT
+// probe values are stored once per kernel in its TMEM lane (as ProbeCache does) instead of
+// being read from L2 for every pattern (64 KB per CTA and pattern at P = 256, R = 32).
+template <int P, int R, int NT>
+struct SlabProbeCache {
+    static constexpr int NE = R * P / NT;
+    static constexpr int NCOL = 2 * NE;
+    static constexpr int USED = NCOL * (NT / 128);
+    static constexpr int COLS = USED <= 32 ? 32 : USED <= 64 ? 64 : USED <= 128 ? 128 : USED <= 256 ? 256 : 512;
+    uint32_t base, addr;
+
+    // All threads; ends with the cache filled and visible to this thread.
+    __device__ __forceinline__ void init(uint32_t *slot, const float2 *__restrict__ probe, int c)
+    {
+        static_assert(NT % 128 == 0 && NE % 4 == 0 && USED <= 512, "slab probe cache layout");
+        const int warp = threadIdx.x >> 5;
+        if (warp == 0) tcx::tmem_alloc(slot, COLS);
+        tcx::tmem_fence_before_sync();
+        __syncthreads();
+        tcx::tmem_fence_after_sync();
+        base = *slot;
+        addr = base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * NCOL);
+#pragma unroll 1
+        for (int k0 = 0; k0 < NE; k0 += 4) {
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int e = threadIdx.x + (k0 + j) * NT;
+                const float2 pv = __ldg(probe + (c * R + e / P) * P + e % P);
+                v[2 * j] = pv.x;
+                v[2 * j + 1] = pv.y;
+            }
+            tcx::tmem_st8(addr + 2 * k0, v);
+        }
+        tcx::tmem_wait_st();
+    }
+    __device__ __forceinline__ void get4(int k0, float2 (&p)[4]) const
+    {
+        float v[8];
+        tcx::tmem_ld8(addr + 2 * k0, v);
+#pragma unroll
+        for (int j = 0; j < 4; j++) p[j] = make_float2(v[2 * j], v[2 * j + 1]);
+    }
+    __device__ __forceinline__ void release() const
+    {
+        tcx::tmem_fence_before_sync();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) tcx::tmem_dealloc(base, COLS);
+    }
+};
+
+// gather_rows with the probe from a SlabProbeCache: the object values of four elements are
+// loaded before their probe values are read.
+template <int P, int R, int NT>
+__device__ __forceinline__ void gather_rows(float2 *buf, const SlabProbeCache<P, R, NT> &pc,
+                                            const float2 *__restrict__ src, int W, int r0, int c0, int c)
+{
+    constexpr int LDA = Slab<P, R>::LDA, NE = SlabProbeCache<P, R, NT>::NE;
+#pragma unroll 1
+    for (int k0 = 0; k0 < NE; k0 += 4) {
+        float2 o[4], pv[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int e = threadIdx.x + (k0 + j) * NT, rl = e / P, x = e % P;
+            o[j] = __ldg(src + (size_t)(r0 + c * R + rl) * W + (c0 + x));
+        }
+        pc.get4(k0, pv);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int e = threadIdx.x + (k0 + j) * NT, rl = e / P, x = e % P;
+            buf[rl * LDA + x] = cmul(pv[j], o[j]);
+        }
+    }
+}
+
 // Loader of the forward row step (fft2_fwd_in): x[n1] = p(row, c) * src(r0 + row, c0 + c),
 // c = n2 + R2 n1, the probe from the cache (pc) or from global memory (pk); all 16 loads of
 // the object are issued before the first product.
@@ -251,6 +328,25 @@ __device__ __forceinline__ void emit_adjoint(const PatternArgs &a, const float2 
     }
 }
 
+// emit_adjoint with the probe from a SlabProbeCache.
+template <int P, int R, int NT>
+__device__ __forceinline__ void emit_adjoint(const float2 *buf, const SlabProbeCache<P, R, NT> &pc,
+                                             float2 *__restrict__ w, int i, int c)
+{
+    constexpr int LDA = Slab<P, R>::LDA, NE = SlabProbeCache<P, R, NT>::NE;
+    float2 *wi = w + (size_t)i * P * P;
+#pragma unroll 1
+    for (int k0 = 0; k0 < NE; k0 += 4) {
+        float2 pv[4];
+        pc.get4(k0, pv);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int e = threadIdx.x + (k0 + j) * NT, rl = e / P, x = e % P;
+            wi[(c * R + rl) * P + x] = cconjmul(pv[j], buf[rl * LDA + x]);
+        }
+    }
+}
+
 template <int P, int R, int NT>
 __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_adjoint_fft(PatternArgs a, const float2 *__restrict__ y,
                                                     float2 *__restrict__ w)
@@ -303,14 +399,16 @@ template <int P, int R, int NT>
 __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 *__restrict__ psi,
                                              float2 *__restrict__ w, float2 *__restrict__ fpart, float2 *buf,
                                              const float2 *tw, float2 *red, float2 *tot, int i, int c,
-                                             float2 *facc, const ProbeCache<P, NT> *pc)
+                                             float2 *facc, const ProbeCache<P, NT> *pc,
+                                             const SlabProbeCache<P, R, NT> *spc = nullptr)
 {
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int2 rc = a.pos[i];
     if constexpr (R == P) {  // the gather feeds the first row step from registers
         fft2_fwd_in<P, NT>(buf, tw, tw + P, ExitWaveLoader<P, NT>{pc, probe_of(a, i), psi, a.W, rc.x, rc.y});
     } else {
-        gather_rows<P, R, NT>(buf, probe_of(a, i), psi, a.W, rc.x, rc.y, c);
+        if (spc) gather_rows<P, R, NT>(buf, *spc, psi, a.W, rc.x, rc.y, c);
+        else gather_rows<P, R, NT>(buf, probe_of(a, i), psi, a.W, rc.x, rc.y, c);
         __syncthreads();
         fft2_fwd<P, R, NT>(buf, tw);
     }
@@ -350,7 +448,8 @@ __device__ __forceinline__ void grad_pattern(const PatternArgs &a, const float2 
         fft2_inv_out<P, NT>(buf, tw, tw + P, AdjointStorer<P, NT>{pc, probe_of(a, i), w + (size_t)i * P * P});
     } else {
         fft2_inv<P, R, NT>(buf, tw);
-        emit_adjoint<P, R, NT>(a, buf, w, i, c);
+        if (spc) emit_adjoint<P, R, NT>(buf, *spc, w, i, c);
+        else emit_adjoint<P, R, NT>(a, buf, w, i, c);
     }
 }
 
@@ -399,11 +498,17 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
         // persistent clusters: each strides over the patterns (the pattern's first exchange
         // starts with a cluster barrier, so a peer writes into this CTA's slab only after
         // this CTA has finished with the previous pattern)
+        __shared__ uint32_t tmem_slot;
+        SlabProbeCache<P, R, NT> spc;
+        const bool cached = a.probe_stride == 0;  // one probe for all patterns: the slab's in TMEM
+        if (cached) spc.init(&tmem_slot, a.probe, c);
         for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {
             if (skip(i)) continue;  // uniform over the cluster
             __syncthreads();        // this CTA's reads of buf for the previous pattern are done
-            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr, nullptr);
+            grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr, nullptr,
+                                   cached ? &spc : nullptr);
         }
+        if (cached) spc.release();
     }
 }
 
@@ -467,7 +572,8 @@ template <int P, int R, int NT>
 __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *__restrict__ w,
                                                  float2 *__restrict__ fpart, float2 *buf, const float2 *tw,
                                                  float2 *red, float2 *tot, float gam, int i, int c, float2 *facc,
-                                                 const ProbeCache<P, NT> *pc)
+                                                 const ProbeCache<P, NT> *pc,
+                                                 const SlabProbeCache<P, R, NT> *spc = nullptr)
 {
     constexpr int LDB = Slab<P, R>::LDB, CS = Slab<P, R>::CS;
     const int per = a.nzc / CS;
@@ -530,7 +636,8 @@ __device__ __forceinline__ void grad_lin_pattern(const PatternArgs &a, float2 *_
                             masked ? &mw : nullptr);
     } else {
         fft2_inv<P, R, NT>(buf, tw);
-        emit_adjoint<P, R, NT>(a, buf, w, i, c);
+        if (spc) emit_adjoint<P, R, NT>(buf, *spc, w, i, c);
+        else emit_adjoint<P, R, NT>(a, buf, w, i, c);
     }
 }
 
@@ -574,13 +681,18 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
         }
         if (cached) pc.release();
     } else {
+        __shared__ uint32_t tmem_slot;
+        SlabProbeCache<P, R, NT> spc;
+        const bool cached = a.probe_stride == 0;  // as in k_grad
+        if (cached) spc.init(&tmem_slot, a.probe, c);
         for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {  // persistent clusters (k_grad)
             const DevState *st = sts + a.pat_view[i];
             if (st->stalled || !st->lin) continue;  // uniform over the cluster
             __syncthreads();
             grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c, nullptr,
-                                       nullptr);
+                                       nullptr, cached ? &spc : nullptr);
         }
+        if (cached) spc.release();
     }
 }
 
@@ -740,7 +852,9 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
         }
         if (cached) pc.release();
     } else {
-        for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {  // persistent clusters (k_grad)
+        // persistent clusters as in k_grad; the probe from L2 (the slab cache measured slower
+        // here: spiral LS pass 4.45 -> 4.61 ms with R = 64)
+        for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {
             if (sts[a.pat_view[i]].stalled) continue;  // uniform over the cluster
             __syncthreads();
             const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, c, nullptr);

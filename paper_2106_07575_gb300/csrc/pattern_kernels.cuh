@@ -500,7 +500,8 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
         // this CTA has finished with the previous pattern)
         __shared__ uint32_t tmem_slot;
         SlabProbeCache<P, R, NT> spc;
-        const bool cached = a.probe_stride == 0;  // one probe for all patterns: the slab's in TMEM
+        // one probe for all patterns and several patterns per cluster: the slab's in TMEM
+        const bool cached = a.probe_stride == 0 && (int)(gridDim.x / CS) < a.K;
         if (cached) spc.init(&tmem_slot, a.probe, c);
         for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {
             if (skip(i)) continue;  // uniform over the cluster
@@ -683,7 +684,7 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
     } else {
         __shared__ uint32_t tmem_slot;
         SlabProbeCache<P, R, NT> spc;
-        const bool cached = a.probe_stride == 0;  // as in k_grad
+        const bool cached = a.probe_stride == 0 && (int)(gridDim.x / CS) < a.K;  // as in k_grad
         if (cached) spc.init(&tmem_slot, a.probe, c);
         for (int i = blockIdx.x / CS; i < a.K; i += gridDim.x / CS) {  // persistent clusters (k_grad)
             const DevState *st = sts + a.pat_view[i];
@@ -959,13 +960,18 @@ cudaError_t launch_pattern(void (*kern)(KArgs...), int nblocks, int nthreads, si
 
 // Grid of a persistent pattern kernel: with one CTA per pattern (cs = 1), the CTAs that fit
 // on the device at once (by the kernel's occupancy), at most one per pattern; with clusters
-// (cs > 1), the clusters that fit at once (cudaOccupancyMaxActiveClusters: fewer than the
-// per-CTA occupancy suggests), each striding over the patterns.  Spiral workload (P = 256,
-// 10,000 positions): 13.82 -> 12.97 ms per iteration against one cluster per pattern.
+// (cs > 1) and persist_clusters, the clusters that fit at once
+// (cudaOccupancyMaxActiveClusters: fewer than the per-CTA occupancy suggests), each striding
+// over the patterns, else one cluster per pattern.  Persistent clusters pay where a pattern
+// needs them (P = 256; spiral workload, 10,000 positions: 13.82 -> 12.97 ms per iteration);
+// the optional clusters of P = 128, several CTAs to an SM, ran slower with a static stride
+// (autotuner timings 393 -> 720 us per GRAD launch with clusters of 4).
 template <typename... KArgs>
-int persistent_blocks(void (*kern)(KArgs...), int nslices, int nthreads, size_t smem, int cs)
+int persistent_blocks(void (*kern)(KArgs...), int nslices, int nthreads, size_t smem, int cs,
+                      bool persist_clusters = false)
 {
     if (cs > 1) {
+        if (!persist_clusters) return nslices;
         // the clusters that fit on the device at once, at most one per pattern
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)nslices);
@@ -1025,24 +1031,24 @@ struct PatternOps {
                             cudaStream_t s)
     {
         const int gc = grad_cols(a);
-        const int g = gc > 0 ? gc : persistent_blocks(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        const int g = gc > 0 ? gc : persistent_blocks(k_grad<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, P >= 256);
         return launch_pattern(k_grad<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, psi, w, fpart, st);
     }
     static cudaError_t grad_lin(const PatternArgs &a, float2 *w, float2 *fpart, const DevState *st, cudaStream_t s)
     {
         const int gc = grad_cols(a);
-        const int g = gc > 0 ? gc : persistent_blocks(k_grad_lin<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        const int g = gc > 0 ? gc : persistent_blocks(k_grad_lin<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, P >= 256);
         return launch_pattern(k_grad_lin<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, w, fpart, st);
     }
     static cudaError_t ls(const PatternArgs &a, const float2 *eta, float2 *part, const DevState *st, cudaStream_t s)
     {
-        const int g = persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        const int g = persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, P >= 256);
         return launch_pattern(k_ls_fft<P, R, NT>, g, NT, slab_bytes<P, R>(), CS, s, a, eta, part, st);
     }
     static int ls_cols(const PatternArgs &a)
     {
         if (CS != 1 || a.V != 1) return 0;
-        return persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS);
+        return persistent_blocks(k_ls_fft<P, R, NT>, a.K * CS, NT, slab_bytes<P, R>(), CS, P >= 256);
     }
     static cudaError_t nz_count(const float *d, const int *perm, int K, int *cnt, cudaStream_t s)
     {

@@ -494,6 +494,12 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad(PatternArgs a, co
             if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
         if (cached) pc.release();
+    } else if constexpr (P < 256) {
+        // the optional clusters of smaller P: one pattern per cluster (a loop here raised the
+        // register allocation, e.g. 64 -> 127 for the linear pass with clusters of 4)
+        const int i = blockIdx.x / CS;
+        if (skip(i)) return;  // uniform over the cluster
+        grad_pattern<P, R, NT>(a, psi, w, fpart, buf, tw, red, tot, i, c, nullptr, nullptr);
     } else {
         // persistent clusters: each strides over the patterns (the pattern's first exchange
         // starts with a cluster barrier, so a peer writes into this CTA's slab only after
@@ -681,6 +687,11 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_grad_lin(PatternArgs a
             if (threadIdx.x == 0) fpart[blockIdx.x] = tot[0];
         }
         if (cached) pc.release();
+    } else if constexpr (P < 256) {  // as in k_grad
+        const int i = blockIdx.x / CS;
+        const DevState *st = sts + a.pat_view[i];
+        if (st->stalled || !st->lin) return;  // uniform over the cluster
+        grad_lin_pattern<P, R, NT>(a, w, fpart, buf, tw, red, tot, (float)st->last_gamma, i, c, nullptr, nullptr);
     } else {
         __shared__ uint32_t tmem_slot;
         SlabProbeCache<P, R, NT> spc;
@@ -852,6 +863,11 @@ __global__ void __launch_bounds__(NT, min_ctas<P, R>()) k_ls_fft(PatternArgs a, 
             if (percta && lane + 32 < nr) part[(size_t)(lane + 32) * KC + blockIdx.x] = acc1;
         }
         if (cached) pc.release();
+    } else if constexpr (P < 256) {  // as in k_grad
+        const int i = blockIdx.x / CS;
+        if (sts[a.pat_view[i]].stalled) return;  // uniform over the cluster
+        const float2 r = ls_fft_pattern<P, R, NT>(a, eta, buf, tw, red, tot, sts, i, c, nullptr);
+        if (threadIdx.x < nr) part[(size_t)threadIdx.x * KC + i * CS + c] = r;
     } else {
         // persistent clusters as in k_grad; the probe from L2 (the slab cache measured slower
         // here: spiral LS pass 4.45 -> 4.61 ms with R = 64)
@@ -964,8 +980,9 @@ cudaError_t launch_pattern(void (*kern)(KArgs...), int nblocks, int nthreads, si
 // (cudaOccupancyMaxActiveClusters: fewer than the per-CTA occupancy suggests), each striding
 // over the patterns, else one cluster per pattern.  Persistent clusters pay where a pattern
 // needs them (P = 256; spiral workload, 10,000 positions: 13.82 -> 12.97 ms per iteration);
-// the optional clusters of P = 128, several CTAs to an SM, ran slower with a static stride
-// (autotuner timings 393 -> 720 us per GRAD launch with clusters of 4).
+// the optional clusters of P = 128 keep one cluster per pattern and a kernel without the
+// pattern loop (with it, the compiler's register allocation rose, e.g. 63 -> 99 registers
+// for the LS pass with clusters of 4, and fewer CTAs fit on an SM).
 template <typename... KArgs>
 int persistent_blocks(void (*kern)(KArgs...), int nslices, int nthreads, size_t smem, int cs,
                       bool persist_clusters = false)

@@ -260,13 +260,27 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+def oracle_single_thread(p):
+    """The oracle on one host core: the first iteration of a solve of the full workload."""
+    import oracle
+
+    oracle.build()
+    out = oracle.cg_solve(p.psi0(), p.probe, p.pos, p.d, 1, nthreads=1)
+    dt = float(out["t"][0])
+    return {"value": p.K / dt, "unit": UNIT, "cores": 1,
+            "sample": f"iteration 0 of one single-threaded FP64 oracle solve of the full workload "
+                      f"({p.K} positions, {int(out['halvings'][0])} line-search trials), {dt:.1f} s"}
+
+
 def cpu_baseline(p, warmup):
-    """The oracle on a bounded sample of the GPU arm's timed iterations (about 10-20 s)."""
+    """The oracle on a bounded sample of the GPU arm's timed iterations (about 10-20 s) on all
+    host cores, and on one core for the solve's first iteration."""
     cores = os.cpu_count()
     v, k, dt, trials = oracle_rate(p, warmup, 5, cores)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"iterations {warmup}..{warmup + k - 1} of one FP64 oracle solve of the full workload "
-                      f"({p.K} positions, {trials:.1f} line-search trials per iteration), {dt:.1f} s timed"}
+                      f"({p.K} positions, {trials:.1f} line-search trials per iteration), {dt:.1f} s timed",
+            "single_thread": oracle_single_thread(p)}
 
 
 def run_views(args, torch, pty, synth):

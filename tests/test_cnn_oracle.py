@@ -90,6 +90,16 @@ def test_adam_first_step_is_signed_learning_rate():
         np.testing.assert_allclose(b1 - b, -0.01 * np.sign(gb), rtol=1e-12, atol=1e-15)
 
 
+def test_adam_first_step_with_eps():
+    """Kingma & Ba, Algorithm 1: after the bias correction the first step is
+    -lr g / (|g| + eps), eps outside the square root; gradients near eps show its place."""
+    params = [(np.array([[[[1.0]]]]), np.array([0.0]))]
+    grads = [(np.array([[[[3e-8]]]]), np.array([-1e-8]))]
+    out = cnn.adam_step(params, grads, {}, lr=0.1, eps=1e-8)
+    np.testing.assert_allclose(out[0][0].ravel(), [1.0 - 0.1 * 0.75], rtol=1e-12)
+    np.testing.assert_allclose(out[0][1], [0.1 * 0.5], rtol=1e-12)
+
+
 def test_adam_constant_gradient_second_step():
     """A constant gradient g keeps m_hat = g and v_hat = g^2 at every step, so every step is -lr sign(g)."""
     params = [(np.array([[[[1.0]]]]), np.array([2.0]))]

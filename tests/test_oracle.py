@@ -242,6 +242,26 @@ def test_cg_against_bruteforce(orc):
     assert rel(got["psi"], want["psi"]) <= 1e-10
 
 
+@pytest.mark.parametrize("t", [3e4, -5e3])
+def test_cg_termination_parameter_against_bruteforce(orc, t):
+    """Eq. 7 with t != 0: a trial is accepted when F(psi + gamma eta) <= F(psi) + gamma t, so
+    t > 0 accepts some increases and t < 0 asks for a decrease of at least gamma |t|.  Both
+    change the trial counts of the t = 0 solve here (a dropped or sign-flipped t fails)."""
+    rng, psi_true, probe, pos = tiny_problem(10, H=12, W=12, P=4, K=9)
+    b0 = Brute(12, 12, 4, probe, pos, np.ones(9 * 16), 0)
+    d = rng.poisson(np.abs(b0.G @ psi_true.ravel()) ** 2).astype(np.float32)
+    b = Brute(12, 12, 4, probe, pos, d, 0.1)
+    psi0 = np.ones((12, 12), complex)
+    want = b.cg(psi0, 5, t=t)
+    assert want["halvings"] != b.cg(psi0, 5)["halvings"]
+    got = orc.cg_solve(psi0, probe, pos, d.reshape(9, 4, 4), 5, orc.OrcOpts(eps=0.1, t=t))
+    assert got["status"] == orc.ORC_OK
+    np.testing.assert_array_equal(got["halvings"], want["halvings"])
+    np.testing.assert_array_equal(got["gamma"], want["gamma"])
+    np.testing.assert_allclose(got["F"], want["F"], rtol=1e-11)
+    assert rel(got["psi"], want["psi"]) <= 1e-10
+
+
 def test_cg_invariants(orc):
     """F_{m+1} <= F_m (Eq. 7, t=0); gamma_m in {2^-k}; eta_0 = -g_0 (first step is steepest descent)."""
     p = _noisy_case(12)

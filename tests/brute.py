@@ -16,16 +16,19 @@ def dft_matrix(P):
 
 
 def g_matrix(H, W, P, probe, pos):
-    """Dense matrix of G = F Q acting on vec(psi) (row-major), shape (K*P*P, H*W)."""
+    """Dense matrix of G = F Q acting on vec(psi) (row-major), shape (K*P*P, H*W).
+
+    probe is [P][P] (one for every position) or [K][P][P] (one per position)."""
     K = len(pos)
     Fm = dft_matrix(P)
     F2 = np.kron(Fm, Fm)  # acts on row-major vec of a P x P array: vec(F X F^T)
     G = np.zeros((K * P * P, H * W), np.complex128)
     for k, (r, c) in enumerate(pos):
+        pk = probe[k] if probe.ndim == 3 else probe
         Qk = np.zeros((P * P, H * W), np.complex128)
         for y in range(P):
             for x in range(P):
-                Qk[y * P + x, (r + y) * W + (c + x)] = probe[y, x]
+                Qk[y * P + x, (r + y) * W + (c + x)] = pk[y, x]
         G[k * P * P:(k + 1) * P * P] = F2 @ Qk
     return G
 

@@ -295,3 +295,35 @@ def test_bad_arguments(orc):
         orc.forward(p.psi_true, p.probe, bad)
     with pytest.raises(RuntimeError, match="status 1"):
         orc.forward(p.psi_true, np.ones((6, 6), complex), p.pos)
+
+
+# ---------------------------------------------------------------- shapes swept against the dense restatement
+@pytest.mark.parametrize("H,W,P,K,seed", [
+    (1, 1, 1, 1, 30),    # one pixel
+    (3, 5, 1, 7, 31),    # P = 1: every position a single pixel, duplicates likely
+    (6, 3, 2, 5, 32),    # tall object, P = 2
+    (5, 9, 4, 4, 33),    # wide object, the window spans every row
+    (8, 8, 8, 2, 34),    # P equal to the object
+    (11, 7, 4, 12, 35),  # odd sizes, more positions than rows
+])
+@pytest.mark.parametrize("est", ["ml", "ls"])
+def test_operators_objective_gradient_swept_against_bruteforce(orc, H, W, P, K, seed, est):
+    """G, G^H, F and grad F at assorted shapes (P = 1 .. 8, square and rectangular objects,
+    corner, edge and repeated positions) equal the dense restatement: catches an index or
+    stride that only square, power-of-two-sized objects hide."""
+    rng = np.random.default_rng(seed)
+    pos = np.stack([rng.integers(0, H - P + 1, K), rng.integers(0, W - P + 1, K)], 1).astype(np.int32)
+    pos[0] = (H - P, W - P)  # the last window that fits
+    probe = crand(rng, P, P)
+    psi = crand(rng, H, W)
+    b0 = Brute(H, W, P, probe, pos, np.ones(K * P * P), 0)
+    y = crand(rng, K, P, P)
+    assert rel(orc.forward(psi, probe, pos).ravel(), b0.G @ psi.ravel()) <= 1e-13
+    assert rel(orc.adjoint(y, probe, pos, (H, W)).ravel(), b0.G.conj().T @ y.ravel()) <= 1e-13
+    d = rng.poisson(2.0 * np.abs(b0.G @ psi.ravel()) ** 2).astype(np.float32)
+    d[::3] = 0.0
+    b = Brute(H, W, P, probe, pos, d, 0.05, est=est)
+    e = orc.EST_ML if est == "ml" else orc.EST_LS
+    g, F = orc.gradient(psi, probe, pos, d.reshape(K, P, P), eps=0.05, est=e)
+    assert F == pytest.approx(b.objective(psi), rel=1e-12, abs=1e-12)
+    assert rel(g, b.gradient(psi)) <= 1e-12

@@ -59,6 +59,9 @@ PINS = {
     "shift_real_stays_real": lambda: T2.test_real_probe_stays_real(),
     "subpixel_adjoint_dot": lambda: T2.test_subpixel_adjoint_dot(),
     "subpixel_finite_differences": lambda: T2.test_subpixel_gradient_finite_difference(),
+    "per_position_dense": lambda: T2.test_per_position_probes_against_the_dense_restatement(),
+    "swept_shapes": lambda: T0.test_operators_objective_gradient_swept_against_bruteforce(oracle, 11, 7, 4, 12, 35,
+                                                                                           "ml"),
 }
 
 # (name, text of the oracle's C source, replacement, pins that must fail)
@@ -72,7 +75,7 @@ C_MISTAKES = [
     ("inverse_dft_without_conj", "if (sign > 0) w = conj(w);", "(void)sign;",
      ["fft_bruteforce", "parseval", "adjoint_dot"]),
     ("probe_transposed_in_Q", "e[(long)y * P + x] = p[(long)y * P + x] * psi",
-     "e[(long)y * P + x] = p[(long)x * P + y] * psi", ["dense_operator", "adjoint_dot", "illumination"]),
+     "e[(long)y * P + x] = p[(long)x * P + y] * psi", ["dense_operator", "adjoint_dot", "swept_shapes"]),
     ("QH_without_conj", "+= conj(p[(long)y * P + x]) * w[(long)y * P + x];", "+= p[(long)y * P + x] * w[(long)y * P + x];",
      ["adjoint_dot", "dense_operator", "finite_differences"]),
     ("QH_patch_rows_flipped", "acc[(long)(r + y) * W + (c + x)] +=", "acc[(long)(r + (P - 1 - y)) * W + (c + x)] +=",
@@ -80,7 +83,7 @@ C_MISTAKES = [
     ("per_position_probe_ignored",
      "p += (long)k * ps;\n    for (int y = 0; y < P; y++)\n        for (int x = 0; x < P; x++)\n            e[",
      "for (int y = 0; y < P; y++)\n        for (int x = 0; x < P; x++)\n            e[",
-     ["subpixel_adjoint_dot", "subpixel_finite_differences"]),
+     ["subpixel_adjoint_dot", "subpixel_finite_differences", "per_position_dense"]),
     ("objective_without_intensity_term", "return a - d * log(a + eps);", "return -d * log(a + eps);",
      ["finite_differences", "objective_bruteforce", "truth_stationary"]),
     ("objective_without_eps", "return a - d * log(a + eps);", "return a - d * log(a + 0.0 * eps);",

@@ -158,3 +158,30 @@ def test_subpixel_cg_decreases_monotonically():
     g = out["gamma"]
     k = np.log2(g)
     assert np.allclose(k, np.round(k))  # gamma = 2^-k
+
+
+def test_per_position_probes_against_the_dense_restatement():
+    """One probe per position ([K][P][P], the sub-pixel path): G, G^H and grad F equal the
+    dense restatement whose k-th block uses the k-th probe (catches a probe stride that
+    stays at the first position or advances by the wrong amount)."""
+    from tests.brute import Brute
+
+    rng = np.random.default_rng(40)
+    H, W, P, K = 10, 9, 4, 6
+    pos = np.stack([rng.integers(0, H - P + 1, K), rng.integers(0, W - P + 1, K)], 1).astype(np.int32)
+    pos[1] = pos[0]  # two positions on one window, with different probes
+    probes = rng.standard_normal((K, P, P)) + 1j * rng.standard_normal((K, P, P))
+    psi = rng.standard_normal((H, W)) + 1j * rng.standard_normal((H, W))
+    y = rng.standard_normal((K, P, P)) + 1j * rng.standard_normal((K, P, P))
+    b0 = Brute(H, W, P, probes, pos, np.ones(K * P * P), 0)
+
+    def rel(a, b):
+        return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+    assert rel(oracle.forward(psi, probes, pos), b0.G @ psi.ravel()) <= 1e-13
+    assert rel(oracle.adjoint(y, probes, pos, (H, W)), b0.G.conj().T @ y.ravel()) <= 1e-13
+    d = rng.poisson(np.abs(b0.G @ psi.ravel()) ** 2).astype(np.float32)
+    b = Brute(H, W, P, probes, pos, d, 0.1)
+    g, F = oracle.gradient(psi, probes, pos, d.reshape(K, P, P), eps=0.1)
+    assert F == pytest.approx(b.objective(psi), rel=1e-12)
+    assert rel(g, b.gradient(psi)) <= 1e-12

@@ -77,13 +77,13 @@ typedef enum {
 
 /* Solver options; pty_default_opts fills Algorithm 1's values. */
 typedef struct {
-    double gamma0;       /* initial step length of every line search (1.0) */
+    double gamma0;       /* initial step length of every line search, finite, > 0 (1.0) */
     double tau;          /* shrink factor per trial, 0 < tau < 1 (0.5) */
-    double t;            /* Eq. 7 termination constant (0.0) */
-    int32_t max_halvings;/* trials per line search before PTY_STALLED (60) */
-    double eps;          /* guard of log and division in the objective, in counts, >= 0
-                            (0.1: with a smaller guard the gradient at dark detector pixels
-                            holding counts is too ill-conditioned for single precision) */
+    double t;            /* Eq. 7 termination constant, finite (0.0) */
+    int32_t max_halvings;/* trials per line search before PTY_STALLED, 1 .. 1000 (60) */
+    double eps;          /* guard of log and division in the objective, in counts, finite
+                            and >= 0 (0.1: with a smaller guard the gradient at dark detector
+                            pixels holding counts is too ill-conditioned for single precision) */
     int32_t ls_window;   /* line-search trials evaluated per pass over the data: 4, 8, 16
                             or 32, or 0 (default) for an adaptive search: with dft = 0 the
                             leading trials that a lower bound of the objective change
@@ -317,7 +317,7 @@ PTY_API int pty_stage_times(pty_ctx *ctx, double ms[5], int64_t launches[5], int
  *   probe, pos, data, psi   device pointers, layouts as in pty_create / pty_gradient
  *                (data is the dense [K][P][P] array; positions in any order); probe, pos,
  *                psi, grad and F must be 8-byte aligned (they are read as pairs).
- *   eps          the objective's guard (pty_opts.eps).
+ *   eps          the objective's guard (pty_opts.eps), finite and >= 0.
  *   grad         device [H][W] complex output; F: device double output or NULL.
  *   stream       cudaStream_t (as void*) of the current device, on which the work runs.
  *                The call reads a status flag back and synchronises this stream, so it

@@ -234,7 +234,7 @@ extern "C" int pty_gradient_noalloc(int32_t H, int32_t W, int32_t P, const float
 {
     if (P != 64 && P != 128) return PTY_ERR_ARG;
     if (K < 1 || K > kNaMaxK || (long long)K * P * P > kNaMaxPixels) return PTY_ERR_ARG;
-    if (H < P || W < P || (long long)H * W > (1LL << 31) || !(eps >= 0.0)) return PTY_ERR_ARG;
+    if (H < P || W < P || (long long)H * W > (1LL << 31) || !(eps >= 0.0 && std::isfinite(eps))) return PTY_ERR_ARG;
     if (!probe || !pos || !data || !psi || !grad) return PTY_ERR_ARG;
     if (!na_is_device(probe) || !na_is_device(pos) || !na_is_device(data) || !na_is_device(psi) ||
         !na_is_device(grad) || (F && !na_is_device(F)))

@@ -685,13 +685,13 @@ int create_views(pty_ctx **out, int32_t V, const int32_t *Hs, const int32_t *Ws,
     pty_opts o;
     pty_default_opts(&o);
     if (opts) o = *opts;
-    if (!(o.tau > 0.0 && o.tau < 1.0) || !(o.gamma0 > 0.0) || o.max_halvings < 1 || o.max_halvings > 1000 ||
-        !(o.eps >= 0.0) || !std::isfinite(o.t) || (o.ls_window != 0 && !pty::ls_window_supported(o.ls_window)) ||
+    if (!(o.tau > 0.0 && o.tau < 1.0) || !(o.gamma0 > 0.0 && std::isfinite(o.gamma0)) || o.max_halvings < 1 ||
+        o.max_halvings > 1000 || !(o.eps >= 0.0 && std::isfinite(o.eps)) || !std::isfinite(o.t) || (o.ls_window != 0 && !pty::ls_window_supported(o.ls_window)) ||
         o.dft < 0 || o.dft > 2 || (o.estimator != 0 && o.estimator != 1) || (o.solver != 0 && o.solver != 1) ||
         (o.ls_warm != 0 && o.ls_warm != 1) || (o.solver == 1 && !(o.gd_step > 0.0 && std::isfinite(o.gd_step))) ||
         (o.solver == 1 && o.ls_warm))
-        return fail(nullptr, PTY_ERR_ARG, "invalid options (tau in (0,1), gamma0 > 0, 1 <= max_halvings <= 1000, "
-                                          "eps >= 0, ls_window in {0,4,8,16,32}, dft in {0,1,2}, estimator and "
+        return fail(nullptr, PTY_ERR_ARG, "invalid options (tau in (0,1), finite gamma0 > 0, 1 <= max_halvings <= "
+                                          "1000, finite eps >= 0, finite t, ls_window in {0,4,8,16,32}, dft in {0,1,2}, estimator and "
                                           "solver in {0,1}, gd_step > 0 with solver 1, ls_warm 0 or 1 with solver 0)");
     if (o.dft != 0 && !pty::tc_dft_supported(P, o.dft == 1))
         return fail(nullptr, PTY_ERR_UNSUPPORTED,

@@ -61,11 +61,13 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
     with pytest.raises(pty.PtyError) as e:
         pty.pty_create(256, 256, 64, probe, 1, bad, data)
     assert e.value.status == pty.PTY_ERR_BOUNDS
-    o = pty.default_opts()
-    o.tau = 1.5
-    with pytest.raises(pty.PtyError) as e:
-        pty.pty_create(256, 256, 64, probe, 1, pos, data, o)
-    assert e.value.status == pty.PTY_ERR_ARG
+    for field, value in (("tau", 1.5), ("gamma0", float("inf")), ("gamma0", 0.0), ("eps", float("inf")),
+                         ("eps", float("nan")), ("t", float("nan")), ("max_halvings", 0)):
+        o = pty.default_opts()
+        setattr(o, field, value)
+        with pytest.raises(pty.PtyError) as e:
+            pty.pty_create(256, 256, 64, probe, 1, pos, data, o)
+        assert e.value.status == pty.PTY_ERR_ARG, (field, value)
 
 
 def test_binding_checks_array_sizes_before_the_library():

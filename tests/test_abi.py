@@ -70,6 +70,27 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu():
         assert e.value.status == pty.PTY_ERR_ARG, (field, value)
 
 
+def test_valid_options_pass_the_checks():
+    """Boundary values of the options (a huge finite gamma0, eps = 0, a negative t) pass the
+    host checks: without a GPU the call gets as far as its first CUDA call."""
+    import numpy as np
+    from paper_2106_07575_gb300 import pty
+
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("checks the host path only where no GPU answers")
+    probe = np.ones((64, 64), np.complex64)
+    pos = np.zeros((1, 2), np.int32)
+    data = np.ones((1, 64, 64), np.float32)
+    for field, value in ((None, None), ("gamma0", 1e12), ("eps", 0.0), ("t", -3.0), ("max_halvings", 1000)):
+        o = pty.default_opts()
+        if field:
+            setattr(o, field, value)
+        with pytest.raises(pty.PtyError) as e:
+            pty.pty_create(256, 256, 64, probe, 1, pos, data, o)
+        assert e.value.status == pty.PTY_ERR_CUDA, (field, value)
+
+
 def test_binding_checks_array_sizes_before_the_library():
     """The wrappers know the problem's shapes: an array of the wrong size raises ValueError on
     the host; an array of the right size reaches the library (here a NULL context, which the

@@ -327,3 +327,21 @@ def test_operators_objective_gradient_swept_against_bruteforce(orc, H, W, P, K, 
     g, F = orc.gradient(psi, probe, pos, d.reshape(K, P, P), eps=0.05, est=e)
     assert F == pytest.approx(b.objective(psi), rel=1e-12, abs=1e-12)
     assert rel(g, b.gradient(psi)) <= 1e-12
+
+
+@pytest.mark.parametrize("nthreads", [2, 3, 7])
+def test_threaded_paths_against_bruteforce(orc, nthreads):
+    """The per-thread scatter buffers and the per-pattern objective partials (the paths the
+    parity tests take with every host core) equal the dense restatement, for thread counts
+    that split 7 patterns evenly, unevenly and one per thread."""
+    rng, psi, probe, pos = tiny_problem(36, H=12, W=10, P=4, K=7)
+    b0 = Brute(12, 10, 4, probe, pos, np.ones(7 * 16), 0)
+    y = crand(rng, 7, 4, 4)
+    assert rel(orc.adjoint(y, probe, pos, (12, 10), nthreads).ravel(), b0.G.conj().T @ y.ravel()) <= 1e-13
+    d = rng.poisson(np.abs(b0.G @ psi.ravel()) ** 2).astype(np.float32)
+    b = Brute(12, 10, 4, probe, pos, d, 0.1)
+    g, F = orc.gradient(psi, probe, pos, d.reshape(7, 4, 4), eps=0.1, nthreads=nthreads)
+    assert F == pytest.approx(b.objective(psi), rel=1e-13)
+    assert orc.objective(psi, probe, pos, d.reshape(7, 4, 4), eps=0.1, nthreads=nthreads) == pytest.approx(
+        b.objective(psi), rel=1e-13)
+    assert rel(g, b.gradient(psi)) <= 1e-12

@@ -86,11 +86,11 @@ C_MISTAKES = [
      "for (int y = 0; y < P; y++)\n        for (int x = 0; x < P; x++)\n            e[",
      ["subpixel_adjoint_dot", "subpixel_finite_differences", "per_position_dense"]),
     ("threaded_scatter_drops_last_buffer", "for (int t = 0; t < T; t++) {\n        const cplx *b = bufs",
-     "for (int t = 0; t + 1 < T; t++) {\n        const cplx *b = bufs", ["threaded_paths"]),
+     "for (int t = 0; t + 1 < T; t++) {\n        const cplx *b = bufs", ["threaded_paths", "adjoint_dot"]),
     ("threaded_chunks_overlap", "long k0 = (long)K * t / T, k1 = (long)K * (t + 1) / T;",
      "long k0 = (long)K * t / T, k1 = (long)K * (t + 1) / T + (t + 1 < T);", ["threaded_paths"]),
     ("objective_partials_miss_the_last_pattern", "for (int k = 0; k < K; k++) s += fpart[k];\n    *F = s;",
-     "for (int k = 0; k + 1 < K; k++) s += fpart[k];\n    *F = s;", ["threaded_paths"]),
+     "for (int k = 0; k + 1 < K; k++) s += fpart[k];\n    *F = s;", ["threaded_paths", "cg_bruteforce"]),
     ("objective_without_intensity_term", "return a - d * log(a + eps);", "return -d * log(a + eps);",
      ["finite_differences", "objective_bruteforce", "truth_stationary"]),
     ("objective_without_eps", "return a - d * log(a + eps);", "return a - d * log(a + 0.0 * eps);",

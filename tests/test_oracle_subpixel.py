@@ -185,3 +185,29 @@ def test_per_position_probes_against_the_dense_restatement():
     g, F = oracle.gradient(psi, probes, pos, d.reshape(K, P, P), eps=0.1)
     assert F == pytest.approx(b.objective(psi), rel=1e-12)
     assert rel(g, b.gradient(psi)) <= 1e-12
+
+
+def test_per_position_probes_cg_against_the_dense_restatement():
+    """Four CG iterations with one probe per position (fractional positions turned into
+    windows and shifted probes by the oracle) equal the dense restatement's: F, steps,
+    trials, Dai-Yuan coefficients and the iterate."""
+    from tests.brute import Brute
+
+    rng = np.random.default_rng(41)
+    H, W, P, K = 12, 11, 4, 8
+    fpos = np.stack([rng.uniform(0, H - P, K), rng.uniform(0, W - P, K)], 1)
+    pos_i, probes = oracle.subpixel_probes(3.0 * (rng.standard_normal((P, P)) + 1j * rng.standard_normal((P, P))),
+                                           fpos)
+    psi_true = (0.8 + 0.2 * rng.random((H, W))) * np.exp(1j * rng.uniform(0, np.pi / 2, (H, W)))
+    b0 = Brute(H, W, P, probes, pos_i, np.ones(K * P * P), 0)
+    d = rng.poisson(np.abs(b0.G @ psi_true.ravel()) ** 2).astype(np.float32)
+    b = Brute(H, W, P, probes, pos_i, d, 0.1)
+    psi0 = np.ones((H, W), complex)
+    want = b.cg(psi0, 4)
+    got = oracle.cg_solve(psi0, probes, pos_i, d.reshape(K, P, P), 4, oracle.OrcOpts(eps=0.1))
+    assert got["status"] == oracle.ORC_OK
+    np.testing.assert_allclose(got["F"], want["F"], rtol=1e-11)
+    np.testing.assert_array_equal(got["gamma"], want["gamma"])
+    np.testing.assert_array_equal(got["halvings"], want["halvings"])
+    np.testing.assert_allclose(got["alpha"], want["alpha"], rtol=1e-9, atol=1e-12)
+    assert np.linalg.norm(got["psi"] - want["psi"]) <= 1e-10 * np.linalg.norm(want["psi"])
